@@ -1,0 +1,220 @@
+"""FP64 CPU oracle for the AMYTISS abstraction + Bellman backup (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by __graft_entry__.smoke() and by
+the CPU-baseline leg of bench.py.  The product path (paper_2005_06191_gb300)
+never imports it, and it never imports the product path.
+
+The arithmetic lives in amy_oracle.c (plain C, FP64, OpenMP over states); this
+module only marshals arguments.  build_oracle() compiles it with gcc.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "amy_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+_SYS = {"affine": 0, "unicycle": 1}
+_SPEC = {"safety": 0, "reach": 1, "reach_avoid": 2}
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile liboracle.so next to its source (gcc, FP64, no FMA contraction)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
+                                               os.path.getmtime(os.path.join(_HERE, "amy_oracle.h")))):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd, cwd=_HERE)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("n", C.c_int32), ("m", C.c_int32),
+        ("x_lb", C.POINTER(C.c_double)), ("x_eta", C.POINTER(C.c_double)),
+        ("x_count", C.POINTER(C.c_int32)), ("x_periodic", C.POINTER(C.c_uint8)),
+        ("u_lb", C.POINTER(C.c_double)), ("u_eta", C.POINTER(C.c_double)),
+        ("u_count", C.POINTER(C.c_int32)),
+        ("sys_kind", C.c_int32), ("params", C.POINTER(C.c_double)), ("n_params", C.c_int64),
+        ("sigma", C.POINTER(C.c_double)),
+        ("gamma", C.c_double), ("window", C.POINTER(C.c_int32)),
+    ]
+
+
+class _Spec(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int32),
+        ("safe_lb", C.POINTER(C.c_double)), ("safe_ub", C.POINTER(C.c_double)),
+        ("n_target", C.c_int32),
+        ("target_lb", C.POINTER(C.c_double)), ("target_ub", C.POINTER(C.c_double)),
+        ("n_avoid", C.c_int32),
+        ("avoid_lb", C.POINTER(C.c_double)), ("avoid_ub", C.POINTER(C.c_double)),
+    ]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build_oracle()
+        lib = C.CDLL(_LIB)
+        P, S = C.POINTER(_Problem), C.POINTER(_Spec)
+        lib.orc_grid_count.restype = C.c_int64
+        lib.orc_grid_count.argtypes = [C.c_double, C.c_double, C.c_double]
+        lib.orc_window_shape.argtypes = [P, C.c_void_p, C.c_void_p]
+        lib.orc_mean.argtypes = [P, C.c_int64, C.c_int64, C.c_void_p]
+        lib.orc_row.argtypes = [P, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]
+        lib.orc_spec_mask.argtypes = [P, S, C.c_void_p]
+        lib.orc_backup_states.argtypes = [P, S, C.c_void_p, C.c_void_p, C.c_int64,
+                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        lib.orc_synthesize.argtypes = [P, S, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_int]
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class _Keep:
+    """Owns the numpy buffers behind one ctypes struct."""
+
+    def __init__(self):
+        self.bufs = []
+
+    def f64(self, v):
+        a = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+        self.bufs.append(a)
+        return a.ctypes.data_as(C.POINTER(C.c_double))
+
+    def i32(self, v):
+        a = np.ascontiguousarray(np.asarray(v, dtype=np.int32))
+        self.bufs.append(a)
+        return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+    def u8(self, v):
+        a = np.ascontiguousarray(np.asarray(v, dtype=np.uint8))
+        self.bufs.append(a)
+        return a.ctypes.data_as(C.POINTER(C.c_uint8))
+
+
+def _problem(p, keep: _Keep) -> _Problem:
+    s = _Problem()
+    s.n, s.m = p.n, p.m
+    s.x_lb, s.x_eta = keep.f64(p.x_lb), keep.f64(p.x_eta)
+    s.x_count, s.x_periodic = keep.i32(p.x_count), keep.u8(p.x_periodic)
+    s.u_lb, s.u_eta, s.u_count = keep.f64(p.u_lb), keep.f64(p.u_eta), keep.i32(p.u_count)
+    s.sys_kind = _SYS[p.sys_kind]
+    s.params = keep.f64(p.params)
+    s.n_params = int(np.asarray(p.params).size)
+    s.sigma = keep.f64(p.sigma)
+    s.gamma = float(p.gamma)
+    s.window = keep.i32(p.window) if p.window is not None else C.POINTER(C.c_int32)()
+    return s
+
+
+def _spec(p, sp, keep: _Keep) -> _Spec:
+    n = p.n
+    s = _Spec()
+    s.kind = _SPEC[sp.kind]
+    if sp.safe is not None:
+        s.safe_lb, s.safe_ub = keep.f64(sp.safe[0]), keep.f64(sp.safe[1])
+    else:
+        s.safe_lb, s.safe_ub = keep.f64(np.full(n, -np.inf)), keep.f64(np.full(n, np.inf))
+    s.n_target = len(sp.targets)
+    s.target_lb = keep.f64(np.array([b[0] for b in sp.targets]).reshape(-1) if sp.targets else np.zeros(1))
+    s.target_ub = keep.f64(np.array([b[1] for b in sp.targets]).reshape(-1) if sp.targets else np.zeros(1))
+    s.n_avoid = len(sp.avoids)
+    s.avoid_lb = keep.f64(np.array([b[0] for b in sp.avoids]).reshape(-1) if sp.avoids else np.zeros(1))
+    s.avoid_ub = keep.f64(np.array([b[1] for b in sp.avoids]).reshape(-1) if sp.avoids else np.zeros(1))
+    return s
+
+
+def grid_count(lb: float, ub: float, eta: float) -> int:
+    return int(_load().orc_grid_count(lb, ub, eta))
+
+
+def window_shape(p):
+    lib, keep = _load(), _Keep()
+    W = np.zeros(p.n, np.int32)
+    xs = np.zeros(p.n, np.float64)
+    if lib.orc_window_shape(C.byref(_problem(p, keep)), W.ctypes.data, xs.ctypes.data) != 0:
+        raise ValueError("invalid cutting window")
+    return W, xs
+
+
+def mean(p, x: int, u: int) -> np.ndarray:
+    lib, keep = _load(), _Keep()
+    mu = np.zeros(p.n, np.float64)
+    if lib.orc_mean(C.byref(_problem(p, keep)), x, u, mu.ctypes.data) != 0:
+        raise ValueError("bad system")
+    return mu
+
+
+def row(p, x: int, u: int):
+    """(origin[n], probs[prod W]) of the transition row of (x, u), window C order."""
+    lib, keep = _load(), _Keep()
+    W, _ = window_shape(p)
+    origin = np.zeros(p.n, np.int32)
+    probs = np.zeros(int(np.prod(W, dtype=np.int64)), np.float64)
+    if lib.orc_row(C.byref(_problem(p, keep)), x, u, origin.ctypes.data, probs.ctypes.data) != 0:
+        raise ValueError("orc_row failed")
+    return origin, probs
+
+
+def spec_mask(p, sp) -> np.ndarray:
+    lib, keep = _load(), _Keep()
+    mask = np.zeros(p.n_states, np.uint8)
+    if lib.orc_spec_mask(C.byref(_problem(p, keep)), C.byref(_spec(p, sp, keep)), mask.ctypes.data) != 0:
+        raise ValueError("invalid specification")
+    return mask
+
+
+def backup_states(p, sp, V_next, states: Sequence[int], nthreads: int = 0):
+    """One Bellman backup at the listed states: (V, pi, gap)."""
+    lib, keep = _load(), _Keep()
+    Vn = np.ascontiguousarray(np.asarray(V_next, dtype=np.float64))
+    assert Vn.size == p.n_states
+    st = np.ascontiguousarray(np.asarray(states, dtype=np.int64))
+    V = np.zeros(st.size, np.float64)
+    pi = np.zeros(st.size, np.uint16)
+    gap = np.zeros(st.size, np.float64)
+    rc = lib.orc_backup_states(C.byref(_problem(p, keep)), C.byref(_spec(p, sp, keep)),
+                               Vn.ctypes.data, st.ctypes.data, st.size,
+                               V.ctypes.data, pi.ctypes.data, gap.ctypes.data, int(nthreads))
+    if rc != 0:
+        raise ValueError("orc_backup_states failed")
+    return V, pi, gap
+
+
+def synthesize(p, sp, horizon: int, want_all: bool = False, nthreads: int = 0) -> dict:
+    """Full synthesis: V0, pi[horizon][n_x], gap[horizon][n_x] (+ V_all when asked)."""
+    lib, keep = _load(), _Keep()
+    nx = p.n_states
+    V = np.zeros(nx, np.float64)
+    pi = np.zeros((horizon, nx), np.uint16)
+    gap = np.zeros((horizon, nx), np.float64)
+    V_all = np.zeros((horizon + 1, nx), np.float64) if want_all else None
+    rc = lib.orc_synthesize(C.byref(_problem(p, keep)), C.byref(_spec(p, sp, keep)), int(horizon),
+                            V.ctypes.data, pi.ctypes.data if horizon else None,
+                            gap.ctypes.data if horizon else None,
+                            V_all.ctypes.data if want_all else None, int(nthreads))
+    if rc != 0:
+        raise ValueError("orc_synthesize failed")
+    out = {"V": V, "pi": pi, "gap": gap}
+    if want_all:
+        out["V_all"] = V_all
+    return out

@@ -1,0 +1,455 @@
+/*
+ * amy_oracle.c -- plain, slow, FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
+ *
+ * Only tests, the smoke check and the benchmark's CPU-baseline leg load this.
+ * It shares no code with the CUDA library.  Every step follows the paper
+ * (arxiv 2005.06191, "AMYTISS") in its own order and notation:
+ *
+ *   Sec. 3 (finite MDP, Eq. trans_prob):  T^(x'|x,u) = T(Xi(x')|x,u), the
+ *       probability that f(x,u) + noise lands in the cell of x'.
+ *   Algorithm 1:  T entry = integral of the Gaussian density over the cell;
+ *       for a diagonal covariance this is a product of 1-D masses.
+ *   Sec. 4.2 + Remark on constructing the cutting region:  per dimension the
+ *       1-D density equals gamma at +-xs, and the kept post states are the
+ *       grid centres inside [mu - xs, mu + xs]; the row has a fixed width.
+ *   Algorithm 3 / Algorithm 4:  backward recursion over the horizon, V_in as
+ *       the window sum of T * V_{k+1}, then max (and lowest argmax) over u.
+ *   Sec. 5.1 (OFA):  rows are recomputed where needed; the oracle does so for
+ *       every state and step, which is the same arithmetic as storing them.
+ *
+ * Readings of points the paper leaves open (kept identical in the CUDA path,
+ * which implements them independently):
+ *   - points per dim N = floor((ub-lb)/eta + 1e-9) + 1, centre_j = lb + j*eta;
+ *   - cells tile [lb - eta/2, ub + eta/2]; mass leaving the grid is lost;
+ *   - gamma mode: xs = sigma*sqrt(2*log(1/(gamma*sigma*sqrt(2*pi)))),
+ *     W = floor(2*xs/eta) + 1, origin o = ceil(((mu - xs) - lb)/eta), slot
+ *     o+k kept iff its centre lb + (o+k)*eta <= mu + xs and it is on the grid
+ *     (or the dim is periodic, where the index wraps and the mass is that of
+ *     the unwrapped cell);
+ *   - explicit odd window W: o = floor((mu - lb)/eta + 0.5) - (W-1)/2;
+ *   - gamma == 0: dense, W = N, o = 0;
+ *   - reach-avoid via V masking (V = 1 on the target, 0 on the avoid set),
+ *     safety as V_k = 1_S * max_u sum;
+ *   - argmax ties: lowest input index; masked states carry policy 0xFFFF.
+ * The target-jump vector of Algorithm 3 is not formed: with V fixed to 1 on
+ * the target and 0 on the avoid set, sum_x' T V equals T0 + T_zeroed V exactly.
+ */
+#include "amy_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+static int64_t prod_i32(const int32_t *a, int n) {
+    int64_t p = 1;
+    for (int i = 0; i < n; ++i) p *= a[i];
+    return p;
+}
+
+/* C-order decode: last dimension fastest. */
+static void decode(int64_t lin, const int32_t *count, int n, int32_t *idx) {
+    for (int d = n - 1; d >= 0; --d) {
+        idx[d] = (int32_t)(lin % count[d]);
+        lin /= count[d];
+    }
+}
+
+static int is_periodic(const orc_problem *p, int d) {
+    return p->x_periodic != NULL && p->x_periodic[d] != 0;
+}
+
+/* Grid quantiser, Sec. 3 (map Pi_x and Eq. Pi_delta): points per dimension. */
+int64_t orc_grid_count(double lb, double ub, double eta) {
+    return (int64_t)floor((ub - lb) / eta + 1e-9) + 1;
+}
+
+/* Cutting region size, Sec. 4.2 and its Remark: solve the 1-D density = gamma
+ * per dimension, then the fixed number of slots per dimension. */
+int orc_window_shape(const orc_problem *p, int32_t *W, double *xstar) {
+    for (int d = 0; d < p->n; ++d) {
+        if (p->window != NULL) {
+            W[d] = p->window[d];
+            if (W[d] < 1 || (W[d] % 2) == 0) return -1;
+            if (is_periodic(p, d) && W[d] > p->x_count[d]) return -1;
+            xstar[d] = INFINITY;
+        } else if (p->gamma == 0.0) {
+            if (is_periodic(p, d)) return -1;
+            W[d] = p->x_count[d];
+            xstar[d] = INFINITY;
+        } else {
+            double s = p->sigma[d];
+            double arg = 1.0 / (p->gamma * s * sqrt(2.0 * M_PI));
+            if (!(arg > 1.0)) return -1; /* gamma at or above the peak density */
+            double xs = s * sqrt(2.0 * log(arg));
+            double w = floor(2.0 * xs / p->x_eta[d]) + 1.0;
+            if (!(w >= 1.0) || w > 1.0e6) return -1;
+            W[d] = (int32_t)w;
+            if (is_periodic(p, d) && W[d] > p->x_count[d]) return -1;
+            xstar[d] = xs;
+        }
+    }
+    return 0;
+}
+
+/* Mean of the post state, Algorithm 2 "Set mu = f(x, nu, w)" (no disturbance):
+ * the system is evaluated at the representative points of the state and input
+ * cells. */
+int orc_mean(const orc_problem *p, int64_t x, int64_t u, double *mu) {
+    const int n = p->n, m = p->m;
+    int32_t xi[ORC_MAXD], ui[ORC_MAXD];
+    double xc[ORC_MAXD], uc[ORC_MAXD];
+    decode(x, p->x_count, n, xi);
+    decode(u, p->u_count, m, ui);
+    for (int d = 0; d < n; ++d) xc[d] = p->x_lb[d] + (double)xi[d] * p->x_eta[d];
+    for (int d = 0; d < m; ++d) uc[d] = p->u_lb[d] + (double)ui[d] * p->u_eta[d];
+    if (p->sys_kind == ORC_SYS_AFFINE_PER_INPUT) {
+        const double *A = p->params + u * (int64_t)(n * n + n);
+        const double *c = A + n * n;
+        for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < n; ++j) acc = acc + A[i * n + j] * xc[j];
+            mu[i] = acc + c[i];
+        }
+        return 0;
+    }
+    if (p->sys_kind == ORC_SYS_UNICYCLE) {
+        double tau = p->params[0];
+        double v = uc[0], w = uc[1];
+        mu[0] = xc[0] + tau * v * cos(xc[2]);
+        mu[1] = xc[1] + tau * v * sin(xc[2]);
+        mu[2] = xc[2] + tau * w;
+        return 0;
+    }
+    return -1;
+}
+
+/* Gaussian mass of [elo, ehi) around mu, Algorithm 1's cell integral in one
+ * dimension.  Each tail is taken from the side where it is small, so no
+ * probability close to 1 is subtracted from another one. */
+static double cell_mass(double elo, double ehi, double mu, double sigma) {
+    const double k = sigma * sqrt(2.0);
+    if (elo >= mu) return 0.5 * erfc((elo - mu) / k) - 0.5 * erfc((ehi - mu) / k);
+    if (ehi <= mu) return 0.5 * erfc((mu - ehi) / k) - 0.5 * erfc((mu - elo) / k);
+    return 1.0 - 0.5 * erfc((mu - elo) / k) - 0.5 * erfc((ehi - mu) / k);
+}
+
+/* Cutting window of one dimension, Remark on constructing the cutting region:
+ * origin, per-slot mass and cell index (-1 for a dropped slot). */
+static int32_t dim_window(const orc_problem *p, int d, int32_t W, double xs, double mu,
+                          double *fac, int64_t *cell) {
+    const int32_t N = p->x_count[d];
+    const double lb = p->x_lb[d], eta = p->x_eta[d];
+    const int per = is_periodic(p, d);
+    double od;
+    if (p->window != NULL)
+        od = floor((mu - lb) / eta + 0.5) - (double)((W - 1) / 2);
+    else if (p->gamma == 0.0)
+        od = 0.0;
+    else
+        od = ceil(((mu - xs) - lb) / eta);
+    /* Clamp far-away origins: outside [-(W+1), N+1] every slot is off the grid
+     * anyway (non-periodic); periodic origins are kept within +-2^30. */
+    if (!per) {
+        if (!(od >= -(double)(W + 1))) od = -(double)(W + 1);
+        if (!(od <= (double)(N + 1))) od = (double)(N + 1);
+    } else {
+        if (!(od >= -1073741824.0)) od = -1073741824.0;
+        if (!(od <= 1073741824.0)) od = 1073741824.0;
+    }
+    const int32_t o = (int32_t)od;
+    const int gmode = (p->window == NULL && p->gamma != 0.0);
+    for (int32_t k = 0; k < W; ++k) {
+        int64_t s = (int64_t)o + k;
+        double c = lb + (double)s * eta;
+        int keep = per || (s >= 0 && s < N);
+        if (gmode && !(c <= mu + xs)) keep = 0;
+        if (!keep) {
+            fac[k] = 0.0;
+            cell[k] = -1;
+            continue;
+        }
+        fac[k] = cell_mass(c - 0.5 * eta, c + 0.5 * eta, mu, p->sigma[d]);
+        cell[k] = per ? (((s % N) + N) % N) : s;
+    }
+    return o;
+}
+
+typedef struct {
+    int32_t W[ORC_MAXD];
+    double xs[ORC_MAXD];
+    int64_t wtot;
+    int32_t wsum;
+    int64_t stride[ORC_MAXD];
+    int64_t nx, nu;
+} orc_shape;
+
+static int shape_of(const orc_problem *p, orc_shape *sh) {
+    if (p->n < 1 || p->n > ORC_MAXD || p->m < 1 || p->m > ORC_MAXD) return -1;
+    if (orc_window_shape(p, sh->W, sh->xs) != 0) return -1;
+    sh->wtot = prod_i32(sh->W, p->n);
+    sh->wsum = 0;
+    for (int d = 0; d < p->n; ++d) sh->wsum += sh->W[d];
+    sh->nx = prod_i32(p->x_count, p->n);
+    sh->nu = prod_i32(p->u_count, p->m);
+    int64_t st = 1;
+    for (int d = p->n - 1; d >= 0; --d) {
+        sh->stride[d] = st;
+        st *= p->x_count[d];
+    }
+    if (p->sys_kind == ORC_SYS_AFFINE_PER_INPUT &&
+        p->n_params != sh->nu * (int64_t)(p->n * p->n + p->n))
+        return -1;
+    if (p->sys_kind == ORC_SYS_UNICYCLE && (p->n != 3 || p->m != 2 || p->n_params < 1)) return -1;
+    return 0;
+}
+
+/* Per-dimension factors for one (x,u) pair; fac/cell hold sum_d W[d] entries. */
+static int pair_factors(const orc_problem *p, const orc_shape *sh, int64_t x, int64_t u,
+                        int32_t *origin, double *fac, int64_t *cell) {
+    double mu[ORC_MAXD];
+    if (orc_mean(p, x, u, mu) != 0) return -1;
+    int off = 0;
+    for (int d = 0; d < p->n; ++d) {
+        int32_t o = dim_window(p, d, sh->W[d], sh->xs[d], mu[d], fac + off, cell + off);
+        if (origin) origin[d] = o;
+        off += sh->W[d];
+    }
+    return 0;
+}
+
+int orc_row(const orc_problem *p, int64_t x, int64_t u, int32_t *origin, double *probs) {
+    orc_shape sh;
+    if (shape_of(p, &sh) != 0) return -1;
+    if (x < 0 || x >= sh.nx || u < 0 || u >= sh.nu) return -1;
+    double *fac = (double *)malloc(sizeof(double) * sh.wsum);
+    int64_t *cell = (int64_t *)malloc(sizeof(int64_t) * sh.wsum);
+    if (!fac || !cell || pair_factors(p, &sh, x, u, origin, fac, cell) != 0) {
+        free(fac);
+        free(cell);
+        return -1;
+    }
+    int32_t k[ORC_MAXD] = {0};
+    for (int64_t t = 0; t < sh.wtot; ++t) {
+        double v = 1.0;
+        int off = 0;
+        for (int d = 0; d < p->n; ++d) {
+            v = v * fac[off + k[d]];
+            off += sh.W[d];
+        }
+        probs[t] = v;
+        for (int d = p->n - 1; d >= 0; --d) {
+            if (++k[d] < sh.W[d]) break;
+            k[d] = 0;
+        }
+    }
+    free(fac);
+    free(cell);
+    return 0;
+}
+
+static int in_box(const double *c, const double *lb, const double *ub, int n) {
+    for (int d = 0; d < n; ++d)
+        if (!(lb[d] <= c[d] && c[d] <= ub[d])) return 0;
+    return 1;
+}
+
+/* Spec sets of Algorithm 3 evaluated on representative points (closed boxes). */
+int orc_spec_mask(const orc_problem *p, const orc_spec *s, uint8_t *mask) {
+    orc_shape sh;
+    if (shape_of(p, &sh) != 0) return -1;
+    const int n = p->n;
+    for (int64_t x = 0; x < sh.nx; ++x) {
+        int32_t xi[ORC_MAXD];
+        double c[ORC_MAXD];
+        decode(x, p->x_count, n, xi);
+        for (int d = 0; d < n; ++d) c[d] = p->x_lb[d] + (double)xi[d] * p->x_eta[d];
+        uint8_t f = 0;
+        for (int b = 0; b < s->n_target; ++b)
+            if (in_box(c, s->target_lb + b * n, s->target_ub + b * n, n)) f |= 1;
+        for (int b = 0; b < s->n_avoid; ++b)
+            if (in_box(c, s->avoid_lb + b * n, s->avoid_ub + b * n, n)) f |= 2;
+        if (s->kind == ORC_SAFETY) {
+            if (in_box(c, s->safe_lb, s->safe_ub, n)) f |= 4;
+        } else {
+            f |= 4;
+        }
+        if ((f & 3) == 3) return -1; /* target and avoid share a state */
+        mask[x] = f;
+    }
+    return 0;
+}
+
+/* The collect step of Algorithm 4 for one state: V_in by the window sum for
+ * every u, then max over u with the lowest maximising index. */
+static void backup_one(const orc_problem *p, const orc_shape *sh, const orc_spec *s,
+                       uint8_t f, const double *Vn, int64_t x, double *fac, int64_t *cell,
+                       double *V, uint16_t *pi, double *gap) {
+    const int n = p->n;
+    int masked;
+    double mval;
+    if (s->kind == ORC_SAFETY) {
+        masked = !(f & 4);
+        mval = 0.0;
+    } else {
+        masked = (f & 3) != 0;
+        mval = (f & 1) ? 1.0 : 0.0;
+    }
+    if (masked) {
+        *V = mval;
+        *pi = 0xFFFF;
+        *gap = INFINITY;
+        return;
+    }
+    double best = -INFINITY, best2 = -INFINITY;
+    int64_t arg = 0;
+    for (int64_t u = 0; u < sh->nu; ++u) {
+        pair_factors(p, sh, x, u, NULL, fac, cell);
+        int32_t k[ORC_MAXD] = {0};
+        double acc = 0.0;
+        for (int64_t t = 0; t < sh->wtot; ++t) {
+            double w = 1.0;
+            int64_t lin = 0;
+            int off = 0, drop = 0;
+            for (int d = 0; d < n; ++d) {
+                int64_t cidx = cell[off + k[d]];
+                if (cidx < 0) {
+                    drop = 1;
+                    break;
+                }
+                w = w * fac[off + k[d]];
+                lin += cidx * sh->stride[d];
+                off += sh->W[d];
+            }
+            if (!drop) acc += w * Vn[lin];
+            for (int d = n - 1; d >= 0; --d) {
+                if (++k[d] < sh->W[d]) break;
+                k[d] = 0;
+            }
+        }
+        if (acc > best) {
+            best2 = best;
+            best = acc;
+            arg = u;
+        } else if (acc > best2) {
+            best2 = acc;
+        }
+    }
+    *V = best;
+    *pi = (uint16_t)arg;
+    *gap = (sh->nu > 1) ? best - best2 : INFINITY;
+}
+
+int orc_backup_states(const orc_problem *p, const orc_spec *s, const double *V_next,
+                      const int64_t *states, int64_t n_states, double *V_out,
+                      uint16_t *pi_out, double *gap_out, int nthreads) {
+    orc_shape sh;
+    if (shape_of(p, &sh) != 0 || sh.nu > 65535) return -1;
+    uint8_t *mask = (uint8_t *)malloc((size_t)sh.nx);
+    if (!mask) return -1;
+    if (orc_spec_mask(p, s, mask) != 0) {
+        free(mask);
+        return -1;
+    }
+    int err = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+        double *fac = (double *)malloc(sizeof(double) * sh.wsum);
+        int64_t *cell = (int64_t *)malloc(sizeof(int64_t) * sh.wsum);
+        if (!fac || !cell) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            err = 1;
+        }
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+        for (int64_t i = 0; i < n_states; ++i) {
+            if (!fac || !cell) continue;
+            int64_t x = states[i];
+            if (x < 0 || x >= sh.nx) continue;
+            double V, gap;
+            uint16_t pi;
+            backup_one(p, &sh, s, mask[x], V_next, x, fac, cell, &V, &pi, &gap);
+            if (V_out) V_out[i] = V;
+            if (pi_out) pi_out[i] = pi;
+            if (gap_out) gap_out[i] = gap;
+        }
+        free(fac);
+        free(cell);
+    }
+    free(mask);
+    return err ? -1 : 0;
+}
+
+int orc_synthesize(const orc_problem *p, const orc_spec *s, int32_t horizon, double *V_out,
+                   uint16_t *pi_out, double *gap_out, double *V_all, int nthreads) {
+    orc_shape sh;
+    if (horizon < 0 || shape_of(p, &sh) != 0 || sh.nu > 65535) return -1;
+    const int64_t nx = sh.nx;
+    uint8_t *mask = (uint8_t *)malloc((size_t)nx);
+    double *Va = (double *)malloc(sizeof(double) * nx);
+    double *Vb = (double *)malloc(sizeof(double) * nx);
+    if (!mask || !Va || !Vb || orc_spec_mask(p, s, mask) != 0) {
+        free(mask);
+        free(Va);
+        free(Vb);
+        return -1;
+    }
+    /* V_N: indicator of the safe set (safety) or of the target (reach). */
+    for (int64_t x = 0; x < nx; ++x)
+        Va[x] = (s->kind == ORC_SAFETY) ? ((mask[x] & 4) ? 1.0 : 0.0) : ((mask[x] & 1) ? 1.0 : 0.0);
+    if (V_all) memcpy(V_all + (int64_t)horizon * nx, Va, sizeof(double) * nx);
+    int err = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#endif
+    for (int32_t k = horizon - 1; k >= 0; --k) {
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads)
+#endif
+        {
+            double *fac = (double *)malloc(sizeof(double) * sh.wsum);
+            int64_t *cell = (int64_t *)malloc(sizeof(int64_t) * sh.wsum);
+            if (!fac || !cell) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+                err = 1;
+            }
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+            for (int64_t x = 0; x < nx; ++x) {
+                if (!fac || !cell) continue;
+                double V, gap;
+                uint16_t pi;
+                backup_one(p, &sh, s, mask[x], Va, x, fac, cell, &V, &pi, &gap);
+                Vb[x] = V;
+                if (pi_out) pi_out[(int64_t)k * nx + x] = pi;
+                if (gap_out) gap_out[(int64_t)k * nx + x] = gap;
+            }
+            free(fac);
+            free(cell);
+        }
+        double *t = Va;
+        Va = Vb;
+        Vb = t;
+        if (V_all) memcpy(V_all + (int64_t)k * nx, Va, sizeof(double) * nx);
+    }
+    memcpy(V_out, Va, sizeof(double) * nx);
+    free(mask);
+    free(Va);
+    free(Vb);
+    return err ? -1 : 0;
+}

@@ -1,0 +1,106 @@
+/*
+ * amy_oracle.h -- plain FP64 CPU oracle for the finite-MDP abstraction and the
+ * finite-horizon Bellman backup of the AMYTISS method (arxiv 2005.06191).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or helper with the CUDA library; both are written from the
+ * paper independently.
+ *
+ * What it computes (paper sections cited per function in amy_oracle.c):
+ *   - grid quantiser (Sec. 3, Eq. (Pi_delta)): centres lb + j*eta, j < N,
+ *     N = floor((ub-lb)/eta + 1e-9) + 1;
+ *   - cutting region (Sec. 4.2, Remark "constructing the cutting region"):
+ *     per-dimension 1-D density cut, window widths and origins;
+ *   - transition probabilities (Algorithm 1 / Algorithm 2): Gaussian mass of
+ *     each post-state cell, a product of per-dimension masses for diagonal
+ *     covariance;
+ *   - Bellman synthesis (Algorithm 3 / Algorithm 4, OFA semantics of Sec. 5.1):
+ *     safety, reachability and reach-avoid value functions with the
+ *     lowest-index argmax policy.
+ *
+ * Everything is IEEE FP64; compile with -ffp-contract=off so that no multiply
+ * and add are fused (the exact operation order is part of the definition of
+ * the window origin, see amy_oracle.c).
+ */
+#ifndef AMY_ORACLE_H
+#define AMY_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_MAXD 8
+
+enum { ORC_SYS_AFFINE_PER_INPUT = 0, ORC_SYS_UNICYCLE = 1 };
+enum { ORC_SAFETY = 0, ORC_REACH = 1, ORC_REACH_AVOID = 2 };
+
+typedef struct {
+    int32_t n;                 /* state dimension, 1..8 */
+    int32_t m;                 /* input dimension, 1..8 */
+    const double *x_lb;        /* [n] first state centre per dim */
+    const double *x_eta;       /* [n] state quantisation step */
+    const int32_t *x_count;    /* [n] points per dim */
+    const uint8_t *x_periodic; /* [n] 1 = index wraps modulo count (may be NULL) */
+    const double *u_lb;        /* [m] */
+    const double *u_eta;       /* [m] */
+    const int32_t *u_count;    /* [m] */
+    int32_t sys_kind;          /* ORC_SYS_* */
+    const double *params;      /* affine: per input u (C-order) A_u[n*n] row-major then c_u[n];
+                                  unicycle: {tau} */
+    int64_t n_params;
+    const double *sigma;       /* [n] per-dim noise standard deviation */
+    double gamma;              /* cutting threshold; 0 = dense */
+    const int32_t *window;     /* [n] explicit odd window widths, or NULL */
+} orc_problem;
+
+typedef struct {
+    int32_t kind;              /* ORC_SAFETY / ORC_REACH / ORC_REACH_AVOID */
+    const double *safe_lb;     /* [n] (safety only) */
+    const double *safe_ub;
+    int32_t n_target;
+    const double *target_lb;   /* [n_target*n] */
+    const double *target_ub;
+    int32_t n_avoid;
+    const double *avoid_lb;    /* [n_avoid*n] */
+    const double *avoid_ub;
+} orc_spec;
+
+/* N = floor((ub - lb)/eta + 1e-9) + 1 */
+int64_t orc_grid_count(double lb, double ub, double eta);
+
+/* Window widths W[n] and cut half-widths xstar[n] (INFINITY when not in gamma
+ * mode).  Returns 0, or -1 when the cut is empty / invalid. */
+int orc_window_shape(const orc_problem *p, int32_t *W, double *xstar);
+
+/* Mean mu[n] = f(centre(x), centre(u)) for linear state index x, input index u. */
+int orc_mean(const orc_problem *p, int64_t x, int64_t u, double *mu);
+
+/* One transition row: origin[n] (first slot index per dim, unwrapped) and the
+ * |W| window probabilities in C order over the window box (0 for dropped
+ * slots).  Returns 0 or -1. */
+int orc_row(const orc_problem *p, int64_t x, int64_t u, int32_t *origin, double *probs);
+
+/* Per-state flags: bit0 target, bit1 avoid, bit2 safe. */
+int orc_spec_mask(const orc_problem *p, const orc_spec *s, uint8_t *mask);
+
+/* One Bellman backup for a list of states given V_next[n_x].
+ * V_out[i], pi_out[i] (0xFFFF on masked states) and gap_out[i] (top-1 minus
+ * top-2 action value, +INF when n_u == 1 or masked) for states[i].
+ * Any output pointer may be NULL.  nthreads <= 0: OpenMP default. */
+int orc_backup_states(const orc_problem *p, const orc_spec *s, const double *V_next,
+                      const int64_t *states, int64_t n_states,
+                      double *V_out, uint16_t *pi_out, double *gap_out, int nthreads);
+
+/* Full synthesis over `horizon` backups.  V_out[n_x] = V_0.
+ * pi_out: [horizon][n_x] (pi_k for k = 0..horizon-1) or NULL.
+ * gap_out: [horizon][n_x] or NULL.  V_all: [(horizon+1)][n_x] (V_k, k=0..horizon) or NULL. */
+int orc_synthesize(const orc_problem *p, const orc_spec *s, int32_t horizon,
+                   double *V_out, uint16_t *pi_out, double *gap_out, double *V_all,
+                   int nthreads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
