@@ -1,0 +1,263 @@
+/*
+ * amy.h -- C ABI of the GB300 engine for the data-parallel hot path of the
+ * AMYTISS method (arxiv 2005.06191): finite-MDP transition probabilities on a
+ * uniform grid fused with the finite-horizon Bellman backup for safety,
+ * reachability and reach-avoid specifications.
+ *
+ * Conventions (every entry point):
+ *   - returns amy_status; no C++ exception crosses this boundary;
+ *   - outputs are written only when AMY_OK is returned;
+ *   - all input arrays are copied during the call; the caller keeps ownership;
+ *   - host pointers unless a flag says "device"; device pointers must be
+ *     valid on the current CUDA device and ordered on the handle's stream;
+ *   - amy_last_error() returns a thread-local message for the last failure.
+ *
+ * Index conventions: states and inputs are linearised in C order (last
+ * dimension fastest).  A policy entry is the linear input index; 0xFFFF marks
+ * a state whose value is fixed by the specification (target, avoid, unsafe).
+ */
+#ifndef AMY_H
+#define AMY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AMY_OK = 0,
+    AMY_E_INVALID_ARG = 1,
+    AMY_E_OUT_OF_MEMORY = 2,
+    AMY_E_CUDA = 3,
+    AMY_E_NOT_READY = 4,
+    AMY_E_TIMEOUT = 5,
+    AMY_E_QUEUE_FULL = 6,
+    AMY_E_CANCELLED = 7,
+    AMY_E_UNSUPPORTED = 8,
+    AMY_E_NOT_FOUND = 9
+} amy_status;
+
+#define AMY_MAX_DIMS 8
+#define AMY_MAX_BOXES 16
+#define AMY_POLICY_NONE 0xFFFF
+
+typedef struct amy_handle_s *amy_handle;
+typedef struct amy_server_s *amy_server;
+
+/* Uniform grid (Sec. 3, quantiser Pi_x with Eq. Pi_delta): centre j of dim d is
+ * lb[d] + j*eta[d] for 0 <= j < count[d]; cell j is [centre - eta/2,
+ * centre + eta/2).  periodic[d] != 0 makes dim d wrap modulo count[d]
+ * (periodic may be NULL).  n in 1..8. */
+typedef struct {
+    int32_t n;
+    const double *lb;
+    const double *eta;
+    const int32_t *count;
+    const uint8_t *periodic;
+} amy_grid;
+
+/* System f of Eq. (11a) (no disturbance), evaluated at representative points.
+ * AMY_SYS_AFFINE_PER_INPUT: for each discrete input u (C order over the input
+ *   grid) params holds A_u (n*n, row-major) then c_u (n); the mean is
+ *   mu_i = (sum_j A_u[i][j] * x_j, summed j = 0..n-1 from 0.0) + c_u[i],
+ *   every product and sum rounded separately in FP64 (no fused multiply-add).
+ *   n_params must be n_u * (n*n + n).
+ * AMY_SYS_UNICYCLE: n = 3, m = 2, params = {tau}; with state (x, y, th) and
+ *   input (v, w): mu = (x + (tau*v)*cos(th), y + (tau*v)*sin(th), th + tau*w). */
+typedef enum { AMY_SYS_AFFINE_PER_INPUT = 0, AMY_SYS_UNICYCLE = 1 } amy_sys_kind;
+typedef struct {
+    int32_t kind;
+    int32_t n;
+    int32_t m;
+    const double *params;
+    int64_t n_params;
+} amy_system;
+
+/* Cutting region (Sec. 4.2 and its Remark on constructing the region).
+ * window == NULL, gamma > 0: per dim the 1-D density equals gamma at +-xs,
+ *   xs = sigma*sqrt(2*log(1/(gamma*sigma*sqrt(2*pi)))), width W = floor(2*xs/eta)+1,
+ *   origin o = ceil(((mu - xs) - lb)/eta); slot o+k (k < W) is kept iff its
+ *   centre lb + (o+k)*eta <= mu + xs and it lies on the grid (or the dim is
+ *   periodic).  gamma at or above the peak density -> AMY_E_INVALID_ARG.
+ * window == NULL, gamma == 0: dense rows, W = count, o = 0 (non-periodic only).
+ * window != NULL: explicit odd widths; o = floor((mu - lb)/eta + 0.5) - (W-1)/2.
+ * All origin arithmetic is FP64 in exactly this order, so the kept set is
+ * reproducible bit for bit. */
+typedef struct {
+    double gamma;
+    const int32_t *window;
+} amy_cut;
+
+/* T storage (Sec. 4.3 stored rows; Sec. 5.1 on-the-fly abstraction). */
+typedef enum {
+    AMY_T_ON_THE_FLY = 0,      /* no T in memory; rows recomputed every backup */
+    AMY_T_STORED_FULL = 1,     /* T[slot][pair] products, built once */
+    AMY_T_STORED_FACTORED = 2  /* per-dim masses F[sum W][pair], built once */
+} amy_tmode;
+
+/* Arithmetic: FP64 everywhere, or FP32 cell masses/products with FP64 only for
+ * the mean and the window origin; FP32_KAHAN adds compensated accumulation of
+ * the window sum.  V_out is double for FP64, float otherwise. */
+typedef enum { AMY_PREC_FP64 = 0, AMY_PREC_FP32 = 1, AMY_PREC_FP32_KAHAN = 2 } amy_prec;
+
+/* Storage of V_k between backups (FP32 precisions only).  AMY_V_BF16 halves
+ * the bytes of every V gather; its rounding error (up to 2^-9 per backup) is
+ * biased upwards by the max over inputs and grows about linearly with the
+ * horizon.  AMY_V_UNORM16 stores round(V * 65535) in 16 bits (V lies in
+ * [0, 1]): same bytes, error at most 2^-17 per backup. */
+typedef enum { AMY_V_NATIVE = 0, AMY_V_BF16 = 1, AMY_V_UNORM16 = 2 } amy_vstore;
+
+typedef struct {
+    int32_t tmode;              /* amy_tmode */
+    int32_t prec;               /* amy_prec */
+    int32_t v_store;            /* amy_vstore */
+    int64_t device_mem_budget;  /* bytes the handle may allocate; 0 = unlimited */
+    void *cuda_stream;          /* cudaStream_t for all work (cudaStreamLegacy and
+                                   cudaStreamPerThread accepted); NULL = a
+                                   non-blocking stream owned by the handle */
+} amy_opts;
+
+/* Closed box tested on representative points: lb[d] <= centre_d <= ub[d]. */
+typedef struct {
+    const double *lb;
+    const double *ub;
+} amy_box;
+
+/* Specifications of Algorithm 3 / Algorithm 4.
+ * SAFETY: V_N = 1 on `safe`, V_k = 1_safe * max_u sum (safe == NULL: whole grid).
+ * REACH / REACH_AVOID: V = 1 on the target boxes, 0 on the avoid boxes, and
+ * V_k = max_u sum elsewhere.  A grid state in both a target and an avoid box
+ * -> AMY_E_INVALID_ARG.  At most AMY_MAX_BOXES boxes of each kind. */
+typedef enum { AMY_SAFETY = 0, AMY_REACH = 1, AMY_REACH_AVOID = 2 } amy_spec_kind;
+typedef struct {
+    int32_t kind;
+    const amy_box *safe;
+    const amy_box *target;
+    int32_t n_target;
+    const amy_box *avoid;
+    int32_t n_avoid;
+} amy_spec;
+
+typedef struct {
+    int64_t n_states;
+    int64_t n_inputs;
+    int32_t n;
+    int32_t window[AMY_MAX_DIMS];
+    int64_t window_slots;       /* prod W */
+    int32_t window_sum;         /* sum W */
+    double cut_half_width[AMY_MAX_DIMS];  /* xs per dim (INFINITY outside gamma mode) */
+    int64_t device_bytes;       /* bytes owned by the handle */
+    int32_t tmode;
+    int32_t prec;
+    int32_t v_store;
+} amy_info_t;
+
+/* Points per dim of [lb, ub] with step eta: floor((ub-lb)/eta + 1e-9) + 1
+ * (the grids of Sec. 6-7 give the pair counts printed in Table 4). */
+int64_t amy_grid_count(double lb, double ub, double eta);
+
+/* Build the abstraction (Algorithm 2 for the stored modes): validates the
+ * problem, derives the window shape, copies the system to the device and, in
+ * the stored modes, launches the T construction kernel once.  sigma[n] is the
+ * per-dim noise standard deviation (diagonal covariance).  The handle is
+ * independent of the specification, so it serves any number of
+ * amy_synthesize calls.  Errors: INVALID_ARG (bad grid, system, cut, n_u >
+ * 65535, more than 2^31-1 states), OUT_OF_MEMORY (budget or cudaMalloc),
+ * UNSUPPORTED (window too large for the kernels), CUDA. */
+amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_grid *inputs,
+                     const double *sigma, const amy_cut *cut, const amy_opts *opts,
+                     amy_handle *out);
+
+/* Finite-horizon synthesis (Algorithm 4; on-the-fly rows per Sec. 5.1 in
+ * AMY_T_ON_THE_FLY).  `horizon` backups from V_N; V_out[n_states] receives
+ * V_0 (double for AMY_PREC_FP64, float otherwise).  policy_out receives
+ * pi_0 [n_states] or, with policy_all_steps, pi_k for k = 0..horizon-1 as
+ * [horizon][n_states]; it may be NULL.  outputs_on_device != 0: V_out and
+ * policy_out are device pointers and the call returns once the work is
+ * enqueued on the handle's stream; otherwise they are host pointers and the
+ * call returns after the copy. */
+amy_status amy_synthesize(amy_handle h, const amy_spec *spec, int32_t horizon, void *V_out,
+                          uint16_t *policy_out, int32_t policy_all_steps,
+                          int32_t outputs_on_device);
+
+/* One Bellman backup (one iteration of the time loop of Algorithm 4) from a
+ * caller-given V_next[n_states] (double for FP64, float otherwise) to
+ * V_out[n_states] and policy_out[n_states] (may be NULL).  on_device selects
+ * device or host pointers for all three, as in amy_synthesize. */
+amy_status amy_backup_step(amy_handle h, const amy_spec *spec, const void *V_next, void *V_out,
+                           uint16_t *policy_out, int32_t on_device);
+
+/* Transition rows as the engine uses them (Algorithm 2): for each of `count`
+ * host-given pairs (x[i], u[i]) the window origin origin_out[i*n + d] and the
+ * prod-W probabilities probs_out[i*prod W + slot] in C order over the window
+ * box (0 for dropped slots), as double.  Host pointers. */
+amy_status amy_query_rows(amy_handle h, const int64_t *x, const int64_t *u, int64_t count,
+                          int32_t *origin_out, double *probs_out);
+
+amy_status amy_info(amy_handle h, amy_info_t *out);
+void amy_destroy(amy_handle h);
+const char *amy_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of independent synthesis requests.
+ * A scheduler thread admits queued requests while slots and device memory
+ * allow, keeps each admitted problem's V ping-pong buffers resident, and
+ * every tick advances every admitted problem by one backup -- in one
+ * persistent kernel launch over a table of problems (batched = 1) or one
+ * launch per problem (batched = 0).  Results are copied out as problems
+ * finish; their slots and memory are then reused by queued requests.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t device_mem_budget;  /* bytes for resident problems; 0 = 4 GiB */
+    int32_t max_slots;          /* problems resident at once; 0 = 64 */
+    int32_t max_queue;          /* queued + running requests; 0 = 4096 */
+    int32_t batched;            /* 1: one persistent kernel per tick; 0: per problem */
+    int32_t use_graphs;         /* 1: replay captured CUDA graphs for the tick */
+    int32_t device;             /* CUDA device ordinal */
+} amy_server_opts;
+
+typedef struct {
+    amy_system sys;
+    amy_grid states;
+    amy_grid inputs;
+    const double *sigma;
+    amy_cut cut;
+    int32_t prec;               /* AMY_PREC_FP32 or AMY_PREC_FP32_KAHAN */
+    int32_t v_store;            /* amy_vstore */
+    amy_spec spec;
+    int32_t horizon;
+} amy_request;
+
+typedef struct {
+    amy_status status;          /* AMY_OK or the failure of this request */
+    int64_t n_states;
+    float *V;                   /* V_0 [n_states], library-owned */
+    uint16_t *policy;           /* pi_0 [n_states], library-owned */
+    double submit_us;           /* times on the server's monotonic clock */
+    double admit_us;
+    double finish_us;
+} amy_result;
+
+amy_status amy_server_create(const amy_server_opts *opts, amy_server *out);
+/* Queue a request (copied).  QUEUE_FULL when max_queue is reached; the
+ * request is validated at once (INVALID_ARG / UNSUPPORTED). */
+amy_status amy_submit(amy_server s, const amy_request *req, uint64_t *ticket);
+/* AMY_E_NOT_READY until the result exists; then fills *out once (the ticket
+ * is retired).  NOT_FOUND for unknown or retired tickets. */
+amy_status amy_poll(amy_server s, uint64_t ticket, amy_result *out);
+/* As amy_poll but blocks up to timeout_us (< 0: forever); TIMEOUT if not done. */
+amy_status amy_wait(amy_server s, uint64_t ticket, int64_t timeout_us, amy_result *out);
+/* Cancel a queued or running request; its result reports AMY_E_CANCELLED. */
+amy_status amy_cancel(amy_server s, uint64_t ticket);
+/* Counters: completed requests, ticks, kernel launches, current resident problems. */
+amy_status amy_server_stats(amy_server s, int64_t *completed, int64_t *ticks, int64_t *launches,
+                            int32_t *resident);
+void amy_server_destroy(amy_server s);
+void amy_result_free(amy_result *r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

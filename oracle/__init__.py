@@ -79,6 +79,7 @@ def _load():
         lib.orc_spec_mask.argtypes = [P, S, C.c_void_p]
         lib.orc_backup_states.argtypes = [P, S, C.c_void_p, C.c_void_p, C.c_int64,
                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        lib.orc_action_values.argtypes = [P, C.c_void_p, C.c_int64, C.c_void_p]
         lib.orc_synthesize.argtypes = [P, S, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_int]
         _lib = lib
@@ -198,6 +199,16 @@ def backup_states(p, sp, V_next, states: Sequence[int], nthreads: int = 0):
     if rc != 0:
         raise ValueError("orc_backup_states failed")
     return V, pi, gap
+
+
+def action_values(p, V_next, x: int) -> np.ndarray:
+    """Window sums s_u for every input u at state x (no masking)."""
+    lib, keep = _load(), _Keep()
+    Vn = np.ascontiguousarray(np.asarray(V_next, dtype=np.float64))
+    out = np.zeros(p.n_inputs, np.float64)
+    if lib.orc_action_values(C.byref(_problem(p, keep)), Vn.ctypes.data, int(x), out.ctypes.data) != 0:
+        raise ValueError("orc_action_values failed")
+    return out
 
 
 def synthesize(p, sp, horizon: int, want_all: bool = False, nthreads: int = 0) -> dict:

@@ -346,6 +346,49 @@ static void backup_one(const orc_problem *p, const orc_shape *sh, const orc_spec
     *gap = (sh->nu > 1) ? best - best2 : INFINITY;
 }
 
+/* The window sum of Algorithm 4 (V_in for one state and every input). */
+int orc_action_values(const orc_problem *p, const double *V_next, int64_t x, double *out) {
+    orc_shape sh;
+    if (shape_of(p, &sh) != 0 || x < 0 || x >= sh.nx) return -1;
+    double *fac = (double *)malloc(sizeof(double) * sh.wsum);
+    int64_t *cell = (int64_t *)malloc(sizeof(int64_t) * sh.wsum);
+    if (!fac || !cell) {
+        free(fac);
+        free(cell);
+        return -1;
+    }
+    const int n = p->n;
+    for (int64_t u = 0; u < sh.nu; ++u) {
+        pair_factors(p, &sh, x, u, NULL, fac, cell);
+        int32_t k[ORC_MAXD] = {0};
+        double acc = 0.0;
+        for (int64_t t = 0; t < sh.wtot; ++t) {
+            double w = 1.0;
+            int64_t lin = 0;
+            int off = 0, drop = 0;
+            for (int d = 0; d < n; ++d) {
+                int64_t cidx = cell[off + k[d]];
+                if (cidx < 0) {
+                    drop = 1;
+                    break;
+                }
+                w = w * fac[off + k[d]];
+                lin += cidx * sh.stride[d];
+                off += sh.W[d];
+            }
+            if (!drop) acc += w * V_next[lin];
+            for (int d = n - 1; d >= 0; --d) {
+                if (++k[d] < sh.W[d]) break;
+                k[d] = 0;
+            }
+        }
+        out[u] = acc;
+    }
+    free(fac);
+    free(cell);
+    return 0;
+}
+
 int orc_backup_states(const orc_problem *p, const orc_spec *s, const double *V_next,
                       const int64_t *states, int64_t n_states, double *V_out,
                       uint16_t *pi_out, double *gap_out, int nthreads) {

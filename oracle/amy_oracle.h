@@ -93,6 +93,10 @@ int orc_backup_states(const orc_problem *p, const orc_spec *s, const double *V_n
                       const int64_t *states, int64_t n_states,
                       double *V_out, uint16_t *pi_out, double *gap_out, int nthreads);
 
+/* Action values s_u = sum over the window of T(x'|x,u) * V_next[x'] for every
+ * input u at one (unmasked) state x: out[n_u]. */
+int orc_action_values(const orc_problem *p, const double *V_next, int64_t x, double *out);
+
 /* Full synthesis over `horizon` backups.  V_out[n_x] = V_0.
  * pi_out: [horizon][n_x] (pi_k for k = 0..horizon-1) or NULL.
  * gap_out: [horizon][n_x] or NULL.  V_all: [(horizon+1)][n_x] (V_k, k=0..horizon) or NULL. */

@@ -1,0 +1,274 @@
+"""GB300 engine for the data-parallel hot path of AMYTISS (arxiv 2005.06191).
+
+Thin Python binding over the C ABI of include/amy.h: the functions below carry
+the C names and only marshal arguments; every step of the path (masks, row
+construction, backup, max/argmax, batching, serving) runs in libamy.so's CUDA
+kernels.  Device buffers may be torch CUDA tensors (data_ptr is passed through);
+otherwise numpy arrays are used and the library copies to/from the device.
+
+Problem and spec arguments are duck-typed: any object with the attributes of
+workloads.Problem / workloads.Spec (grids, system kind and parameters, sigma,
+gamma or window; spec kind and boxes) can be passed.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional
+
+import numpy as np
+
+from . import _abi
+from ._abi import STATUS_NAMES
+
+TMODES = {"otf": 0, "stored_full": 1, "stored_factored": 2}
+PRECS = {"fp64": 0, "fp32": 1, "fp32_kahan": 2}
+SYS_KINDS = {"affine": 0, "unicycle": 1}
+SPEC_KINDS = {"safety": 0, "reach": 1, "reach_avoid": 2}
+VSTORES = {"native": 0, "bf16": 1, "u16": 2}
+POLICY_NONE = 0xFFFF
+
+
+class AmyError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _lib():
+    return _abi.load()
+
+
+def _check(st: int):
+    if st != 0:
+        msg = _lib().amy_last_error()
+        raise AmyError(st, msg.decode() if msg else "")
+
+
+class _Keep:
+    """Keeps the numpy buffers behind ctypes structs alive for one call."""
+
+    def __init__(self):
+        self.bufs = []
+
+    def f64(self, v):
+        a = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+        self.bufs.append(a)
+        return a.ctypes.data_as(_abi.DP)
+
+    def i32(self, v):
+        a = np.ascontiguousarray(np.asarray(v, dtype=np.int32))
+        self.bufs.append(a)
+        return a.ctypes.data_as(_abi.IP)
+
+    def u8(self, v):
+        a = np.ascontiguousarray(np.asarray(v, dtype=np.uint8))
+        self.bufs.append(a)
+        return a.ctypes.data_as(_abi.U8P)
+
+    def obj(self, o):
+        self.bufs.append(o)
+        return o
+
+
+def _grid(k: _Keep, lb, eta, count, periodic=None) -> _abi.amy_grid:
+    g = _abi.amy_grid()
+    g.n = len(count)
+    g.lb, g.eta, g.count = k.f64(lb), k.f64(eta), k.i32(count)
+    g.periodic = k.u8(periodic) if periodic is not None else _abi.U8P()
+    return g
+
+
+def _problem_structs(k: _Keep, p):
+    sysd = _abi.amy_system()
+    sysd.kind = SYS_KINDS[p.sys_kind]
+    sysd.n, sysd.m = p.n, p.m
+    sysd.params = k.f64(p.params)
+    sysd.n_params = int(np.asarray(p.params).size)
+    states = _grid(k, p.x_lb, p.x_eta, p.x_count, p.x_periodic)
+    inputs = _grid(k, p.u_lb, p.u_eta, p.u_count)
+    cut = _abi.amy_cut()
+    cut.gamma = float(p.gamma)
+    cut.window = k.i32(p.window) if p.window is not None else _abi.IP()
+    sigma = k.f64(p.sigma)
+    return sysd, states, inputs, sigma, cut
+
+
+def _box(k: _Keep, b) -> _abi.amy_box:
+    x = _abi.amy_box()
+    x.lb, x.ub = k.f64(b[0]), k.f64(b[1])
+    return x
+
+
+def _spec_struct(k: _Keep, sp) -> _abi.amy_spec:
+    s = _abi.amy_spec()
+    s.kind = SPEC_KINDS[sp.kind]
+    if sp.safe is not None:
+        s.safe = C.pointer(k.obj(_box(k, sp.safe)))
+    nt, na = len(sp.targets), len(sp.avoids)
+    if nt:
+        arr = k.obj((_abi.amy_box * nt)(*[_box(k, b) for b in sp.targets]))
+        s.target = C.cast(arr, C.POINTER(_abi.amy_box))
+    if na:
+        arr = k.obj((_abi.amy_box * na)(*[_box(k, b) for b in sp.avoids]))
+        s.avoid = C.cast(arr, C.POINTER(_abi.amy_box))
+    s.n_target, s.n_avoid = nt, na
+    return s
+
+
+def _is_cuda_tensor(t) -> bool:
+    return hasattr(t, "is_cuda") and bool(t.is_cuda)
+
+
+def _current_stream_ptr():
+    """torch's current stream; its legacy default stream (handle 0) is passed
+    as cudaStreamLegacy so that the library does not create its own stream."""
+    import torch
+    if torch.cuda.is_available():
+        s = torch.cuda.current_stream().cuda_stream
+        return C.c_void_p(s if s else 1)
+    return C.c_void_p(0)
+
+
+class AmyHandle:
+    """Owns an amy_handle (device rows, V ping-pong, masks)."""
+
+    def __init__(self, ptr: int, prec: str, n_states: int, n_inputs: int):
+        self.ptr = C.c_void_p(ptr)
+        self.prec = prec
+        self.n_states = n_states
+        self.n_inputs = n_inputs
+
+    @property
+    def out_dtype(self):
+        return np.float64 if self.prec == "fp64" else np.float32
+
+    def close(self):
+        if self.ptr and self.ptr.value:
+            _lib().amy_destroy(self.ptr)
+            self.ptr = C.c_void_p(0)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def amy_grid_count(lb: float, ub: float, eta: float) -> int:
+    return int(_lib().amy_grid_count(lb, ub, eta))
+
+
+def amy_last_error() -> str:
+    m = _lib().amy_last_error()
+    return m.decode() if m else ""
+
+
+def amy_build(problem, tmode: str = "otf", prec: str = "fp32", v_store: str = "native",
+              device_mem_budget: int = 0, stream=None) -> AmyHandle:
+    """amy_build: validate, derive the window and (stored modes) build T on the GPU.
+
+    `stream` is a cudaStream_t as int; None uses torch's current stream."""
+    k = _Keep()
+    sysd, states, inputs, sigma, cut = _problem_structs(k, problem)
+    o = _abi.amy_opts()
+    o.tmode, o.prec, o.v_store = TMODES[tmode], PRECS[prec], VSTORES[v_store]
+    o.device_mem_budget = int(device_mem_budget)
+    o.cuda_stream = C.c_void_p(stream) if stream is not None else _current_stream_ptr()
+    out = C.c_void_p(0)
+    _check(_lib().amy_build(C.byref(sysd), C.byref(states), C.byref(inputs), sigma, C.byref(cut),
+                            C.byref(o), C.byref(out)))
+    info = _abi.amy_info_t()
+    _check(_lib().amy_info(out, C.byref(info)))
+    return AmyHandle(out.value, prec, int(info.n_states), int(info.n_inputs))
+
+
+def amy_info(h: AmyHandle) -> dict:
+    info = _abi.amy_info_t()
+    _check(_lib().amy_info(h.ptr, C.byref(info)))
+    n = info.n
+    return {
+        "n_states": int(info.n_states), "n_inputs": int(info.n_inputs), "n": n,
+        "window": [int(info.window[d]) for d in range(n)],
+        "window_slots": int(info.window_slots), "window_sum": int(info.window_sum),
+        "cut_half_width": [float(info.cut_half_width[d]) for d in range(n)],
+        "device_bytes": int(info.device_bytes), "tmode": int(info.tmode), "prec": int(info.prec),
+        "v_store": int(info.v_store),
+    }
+
+
+def amy_synthesize(h: AmyHandle, spec, horizon: int, V_out=None, policy_out=None,
+                   policy_all_steps: bool = False, want_policy: bool = True):
+    """amy_synthesize: `horizon` backups; returns (V_0, policy).
+
+    With torch CUDA tensors for V_out (and policy_out) the outputs stay on the
+    device (work enqueued on the handle's stream); otherwise numpy arrays are
+    returned."""
+    k = _Keep()
+    s = _spec_struct(k, spec)
+    nx = h.n_states
+    if V_out is not None and _is_cuda_tensor(V_out):
+        vp = C.c_void_p(V_out.data_ptr())
+        pp = C.c_void_p(policy_out.data_ptr()) if policy_out is not None else C.c_void_p(0)
+        _check(_lib().amy_synthesize(h.ptr, C.byref(s), int(horizon), vp, pp, int(bool(policy_all_steps)), 1))
+        return V_out, policy_out
+    V = np.zeros(nx, dtype=h.out_dtype)
+    pi = None
+    if want_policy and horizon > 0:
+        pi = np.zeros((horizon, nx) if policy_all_steps else nx, dtype=np.uint16)
+    _check(_lib().amy_synthesize(h.ptr, C.byref(s), int(horizon), C.c_void_p(V.ctypes.data),
+                                 C.c_void_p(pi.ctypes.data) if pi is not None else C.c_void_p(0),
+                                 int(bool(policy_all_steps)), 0))
+    return V, pi
+
+
+def amy_backup_step(h: AmyHandle, spec, V_next, V_out=None, policy_out=None):
+    """amy_backup_step: one backup from a caller-given V_{k+1}; returns (V_k, pi_k)."""
+    k = _Keep()
+    s = _spec_struct(k, spec)
+    if _is_cuda_tensor(V_next):
+        _check(_lib().amy_backup_step(h.ptr, C.byref(s), C.c_void_p(V_next.data_ptr()),
+                                      C.c_void_p(V_out.data_ptr()),
+                                      C.c_void_p(policy_out.data_ptr()) if policy_out is not None else C.c_void_p(0),
+                                      1))
+        return V_out, policy_out
+    Vn = np.ascontiguousarray(np.asarray(V_next, dtype=h.out_dtype))
+    assert Vn.size == h.n_states
+    V = np.zeros(h.n_states, dtype=h.out_dtype)
+    pi = np.zeros(h.n_states, dtype=np.uint16)
+    _check(_lib().amy_backup_step(h.ptr, C.byref(s), C.c_void_p(Vn.ctypes.data), C.c_void_p(V.ctypes.data),
+                                  C.c_void_p(pi.ctypes.data), 0))
+    return V, pi
+
+
+def amy_query_rows(h: AmyHandle, xs, us):
+    """amy_query_rows: (origins [count, n], probs [count, prod W]) as the engine computes them."""
+    info = amy_info(h)
+    x = np.ascontiguousarray(np.asarray(xs, dtype=np.int64))
+    u = np.ascontiguousarray(np.asarray(us, dtype=np.int64))
+    assert x.shape == u.shape
+    org = np.zeros((x.size, info["n"]), dtype=np.int32)
+    probs = np.zeros((x.size, info["window_slots"]), dtype=np.float64)
+    _check(_lib().amy_query_rows(h.ptr, C.c_void_p(x.ctypes.data), C.c_void_p(u.ctypes.data), x.size,
+                                 C.c_void_p(org.ctypes.data), C.c_void_p(probs.ctypes.data)))
+    return org, probs
+
+
+def amy_destroy(h: AmyHandle) -> None:
+    h.close()
+
+
+from .serving import (AmyServer, amy_cancel, amy_poll, amy_result_free,  # noqa: E402
+                      amy_server_create, amy_server_destroy, amy_server_stats, amy_submit, amy_wait)
+
+__all__ = [
+    "AmyError", "AmyHandle", "AmyServer", "amy_build", "amy_synthesize", "amy_backup_step",
+    "amy_query_rows", "amy_info", "amy_destroy", "amy_grid_count", "amy_last_error",
+    "amy_server_create", "amy_submit", "amy_poll", "amy_wait", "amy_cancel", "amy_server_stats",
+    "amy_server_destroy", "amy_result_free", "TMODES", "PRECS", "VSTORES", "POLICY_NONE",
+]

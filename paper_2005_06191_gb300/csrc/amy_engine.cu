@@ -1,0 +1,684 @@
+// amy_engine.cu -- C ABI of the single-problem path (amy_build,
+// amy_synthesize, amy_backup_step, amy_query_rows, amy_info, amy_destroy).
+//
+// Host side: validation, window shape (Sec. 4.2 Remark, scalars per dim),
+// device allocation and kernel launches.  Every per-state and per-pair step
+// runs in the kernels of amy_kernels.cuh.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/amy.h"
+#include "amy_internal.h"
+#include "amy_kernels.cuh"
+
+using namespace amy;
+
+namespace amy {
+
+static thread_local std::string g_last_error;
+
+amy_status set_error(amy_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+amy_status cuda_error(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return set_error(AMY_E_OUT_OF_MEMORY, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return set_error(AMY_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int64_t grid_count(double lb, double ub, double eta) {
+    return (int64_t)std::floor((ub - lb) / eta + 1e-9) + 1;
+}
+
+// Window shape per dim (Sec. 4.2 and the Remark on the cutting region): the
+// 1-D density of N(0, sigma^2) equals gamma at +-xs; the row keeps
+// floor(2 xs / eta) + 1 slots.  Same FP64 expression as documented in amy.h.
+amy_status make_geom(const amy_system *sys, const amy_grid *st, const amy_grid *in,
+                     const double *sigma, const amy_cut *cut, Geom &g, std::vector<double> &params) {
+    if (!sys || !st || !in || !sigma || !cut) return set_error(AMY_E_INVALID_ARG, "null argument");
+    const int n = st->n, m = in->n;
+    if (n < 1 || n > MAXD || m < 1 || m > MAXD) return set_error(AMY_E_INVALID_ARG, "dims must be 1..8");
+    if (sys->n != n || sys->m != m) return set_error(AMY_E_INVALID_ARG, "system dims differ from grids");
+    if (!st->lb || !st->eta || !st->count || !in->lb || !in->eta || !in->count)
+        return set_error(AMY_E_INVALID_ARG, "null grid array");
+    memset(&g, 0, sizeof g);
+    g.n = n;
+    g.m = m;
+    int64_t nx = 1, nu = 1;
+    for (int d = 0; d < n; ++d) {
+        if (st->count[d] < 1 || !(st->eta[d] > 0.0) || !std::isfinite(st->lb[d]) || !std::isfinite(st->eta[d]))
+            return set_error(AMY_E_INVALID_ARG, "bad state grid in dim %d", d);
+        if (!(sigma[d] > 0.0) || !std::isfinite(sigma[d]))
+            return set_error(AMY_E_INVALID_ARG, "sigma[%d] must be positive", d);
+        g.N[d] = st->count[d];
+        g.lb[d] = st->lb[d];
+        g.eta[d] = st->eta[d];
+        if (st->periodic && st->periodic[d]) g.periodic |= 1u << d;
+        nx *= st->count[d];
+        if (nx > 2147483647LL) return set_error(AMY_E_INVALID_ARG, "more than 2^31-1 states");
+    }
+    for (int d = 0; d < m; ++d) {
+        if (in->count[d] < 1 || !(in->eta[d] > 0.0)) return set_error(AMY_E_INVALID_ARG, "bad input grid in dim %d", d);
+        g.ucount[d] = in->count[d];
+        g.ulb[d] = in->lb[d];
+        g.ueta[d] = in->eta[d];
+        nu *= in->count[d];
+        if (nu > 65535) return set_error(AMY_E_INVALID_ARG, "more than 65535 inputs");
+    }
+    g.nx = (int32_t)nx;
+    g.nu = (int32_t)nu;
+    int64_t s = 1;
+    for (int d = n - 1; d >= 0; --d) {
+        g.stride[d] = (int32_t)s;
+        s *= g.N[d];
+    }
+    // system
+    if (sys->kind == AMY_SYS_AFFINE_PER_INPUT) {
+        if (!sys->params || sys->n_params != nu * (int64_t)(n * n + n))
+            return set_error(AMY_E_INVALID_ARG, "affine system needs n_u*(n*n+n) params");
+        g.sys = SYS_AFFINE;
+    } else if (sys->kind == AMY_SYS_UNICYCLE) {
+        if (n != 3 || m != 2 || !sys->params || sys->n_params < 1)
+            return set_error(AMY_E_INVALID_ARG, "unicycle needs n=3, m=2, params={tau}");
+        g.sys = SYS_UNICYCLE;
+    } else {
+        return set_error(AMY_E_INVALID_ARG, "unknown system kind %d", sys->kind);
+    }
+    params.assign(sys->params, sys->params + sys->n_params);
+    for (double v : params)
+        if (!std::isfinite(v)) return set_error(AMY_E_INVALID_ARG, "non-finite system parameter");
+    // window
+    int64_t wtot = 1;
+    int32_t wsum = 0;
+    for (int d = 0; d < n; ++d) {
+        const bool per = (g.periodic >> d) & 1u;
+        g.k2[d] = sigma[d] * std::sqrt(2.0);
+        g.rk2f[d] = (float)(1.0 / (sigma[d] * std::sqrt(2.0)));
+        if (cut->window) {
+            g.wmode = WM_EXPLICIT;
+            const int32_t W = cut->window[d];
+            if (W < 1 || (W % 2) == 0) return set_error(AMY_E_INVALID_ARG, "explicit window must be odd (dim %d)", d);
+            if (per && W > g.N[d]) return set_error(AMY_E_INVALID_ARG, "window wider than periodic dim %d", d);
+            g.W[d] = W;
+            g.xs[d] = INFINITY;
+        } else if (cut->gamma == 0.0) {
+            g.wmode = WM_DENSE;
+            if (per) return set_error(AMY_E_INVALID_ARG, "dense rows need non-periodic dims");
+            g.W[d] = g.N[d];
+            g.xs[d] = INFINITY;
+        } else {
+            g.wmode = WM_GAMMA;
+            if (!(cut->gamma > 0.0) || !std::isfinite(cut->gamma)) return set_error(AMY_E_INVALID_ARG, "bad gamma");
+            const double arg = 1.0 / (cut->gamma * sigma[d] * std::sqrt(2.0 * M_PI));
+            if (!(arg > 1.0)) return set_error(AMY_E_INVALID_ARG, "gamma at or above the peak density (dim %d)", d);
+            const double xs = sigma[d] * std::sqrt(2.0 * std::log(arg));
+            const double w = std::floor(2.0 * xs / g.eta[d]) + 1.0;
+            if (!(w >= 1.0) || w > 1.0e6) return set_error(AMY_E_INVALID_ARG, "bad window width (dim %d)", d);
+            g.W[d] = (int32_t)w;
+            if (per && g.W[d] > g.N[d]) return set_error(AMY_E_INVALID_ARG, "window wider than periodic dim %d", d);
+            g.xs[d] = xs;
+        }
+        wtot *= g.W[d];
+        wsum += g.W[d];
+        if (wtot > (1LL << 30)) return set_error(AMY_E_UNSUPPORTED, "window box too large");
+    }
+    if (wsum > MAXWS) return set_error(AMY_E_UNSUPPORTED, "sum of window widths %d exceeds %d", wsum, MAXWS);
+    g.wtot = (int32_t)wtot;
+    g.wsum = wsum;
+    return AMY_OK;
+}
+
+// Spec boxes -> device struct; checks that no grid state is both target and
+// avoid (per dim: some centre inside the intersection of the two boxes).
+amy_status make_spec(const Geom &g, const amy_spec *spec, SpecDev &s) {
+    if (!spec) return set_error(AMY_E_INVALID_ARG, "null spec");
+    memset(&s, 0, sizeof s);
+    s.kind = spec->kind;
+    if (spec->kind != AMY_SAFETY && spec->kind != AMY_REACH && spec->kind != AMY_REACH_AVOID)
+        return set_error(AMY_E_INVALID_ARG, "unknown spec kind");
+    if (spec->n_target < 0 || spec->n_target > MAX_BOXES || spec->n_avoid < 0 || spec->n_avoid > MAX_BOXES)
+        return set_error(AMY_E_INVALID_ARG, "at most %d boxes of each kind", MAX_BOXES);
+    if (spec->kind != AMY_SAFETY && spec->n_target < 1) return set_error(AMY_E_INVALID_ARG, "reach needs a target");
+    if (spec->kind == AMY_REACH && spec->n_avoid != 0) return set_error(AMY_E_INVALID_ARG, "reach takes no avoid set");
+    s.n_target = spec->n_target;
+    s.n_avoid = spec->kind == AMY_REACH_AVOID ? spec->n_avoid : 0;
+    for (int b = 0; b < s.n_target; ++b) {
+        if (!spec->target || !spec->target[b].lb || !spec->target[b].ub) return set_error(AMY_E_INVALID_ARG, "null target box");
+        for (int d = 0; d < g.n; ++d) {
+            s.t_lb[b][d] = spec->target[b].lb[d];
+            s.t_ub[b][d] = spec->target[b].ub[d];
+        }
+    }
+    for (int b = 0; b < s.n_avoid; ++b) {
+        if (!spec->avoid || !spec->avoid[b].lb || !spec->avoid[b].ub) return set_error(AMY_E_INVALID_ARG, "null avoid box");
+        for (int d = 0; d < g.n; ++d) {
+            s.a_lb[b][d] = spec->avoid[b].lb[d];
+            s.a_ub[b][d] = spec->avoid[b].ub[d];
+        }
+    }
+    if (spec->kind == AMY_SAFETY && spec->safe) {
+        if (!spec->safe->lb || !spec->safe->ub) return set_error(AMY_E_INVALID_ARG, "null safe box");
+        s.has_safe = 1;
+        for (int d = 0; d < g.n; ++d) {
+            s.safe_lb[d] = spec->safe->lb[d];
+            s.safe_ub[d] = spec->safe->ub[d];
+        }
+    }
+    for (int bt = 0; bt < s.n_target; ++bt)
+        for (int ba = 0; ba < s.n_avoid; ++ba) {
+            bool all = true;
+            for (int d = 0; d < g.n && all; ++d) {
+                const double lo = std::fmax(s.t_lb[bt][d], s.a_lb[ba][d]);
+                const double hi = std::fmin(s.t_ub[bt][d], s.a_ub[ba][d]);
+                bool any = false;
+                for (int j = 0; j < g.N[d] && !any; ++j) {
+                    const double c = g.lb[d] + (double)j * g.eta[d];
+                    any = (lo <= c && c <= hi);
+                }
+                all = any;
+            }
+            if (all) return set_error(AMY_E_INVALID_ARG, "target box %d and avoid box %d share a grid state", bt, ba);
+        }
+    return AMY_OK;
+}
+
+int choose_tile(int32_t nx, int32_t nu, int sm_count) {
+    int tx = 256;
+    while (tx > 1 && (int64_t)tx * nu > 4096) tx >>= 1;
+    while (tx > 8 && ((int64_t)nx + tx - 1) / tx < 4LL * sm_count) tx >>= 1;
+    return tx;
+}
+
+}  // namespace amy
+
+struct amy_handle_s {
+    Geom g;
+    int32_t tmode, prec, v_store;
+    cudaStream_t stream;
+    bool own_stream;
+    int device;
+    int sm_count;
+    int64_t budget;
+    int64_t bytes;
+    double *d_params;
+    void *d_T;
+    int16_t *d_O;
+    int64_t npairs;
+    void *d_V[2];
+    uint8_t *d_mask;
+    int tileX;
+    amy_info_t info;
+};
+
+namespace {
+
+size_t rsize(const amy_handle_s *h) { return h->prec == AMY_PREC_FP64 ? 8 : 4; }
+size_t vsize(const amy_handle_s *h) { return h->prec == AMY_PREC_FP64 ? 8 : (h->v_store ? 2 : 4); }
+
+amy_status dev_alloc(amy_handle_s *h, void **p, size_t bytes, const char *what) {
+    if (h->budget > 0 && h->bytes + (int64_t)bytes > h->budget)
+        return set_error(AMY_E_OUT_OF_MEMORY, "%s: %zu bytes exceed the device memory budget", what, bytes);
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) return cuda_error(e, what);
+    h->bytes += (int64_t)bytes;
+    return AMY_OK;
+}
+
+void free_handle(amy_handle_s *h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    cudaFree(h->d_params);
+    cudaFree(h->d_T);
+    cudaFree(h->d_O);
+    cudaFree(h->d_V[0]);
+    cudaFree(h->d_V[1]);
+    cudaFree(h->d_mask);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+#define AMY_CUDA(call, what)                          \
+    do {                                              \
+        cudaError_t e__ = (call);                     \
+        if (e__ != cudaSuccess) return cuda_error(e__, what); \
+    } while (0)
+
+template <class R, class VT>
+amy_status launch_mask(amy_handle_s *h, const SpecDev &s, VT *VN) {
+    const int blocks = (int)std::min<int64_t>((h->g.nx + 255) / 256, 65535);
+    k_spec_mask<R, VT><<<blocks, 256, 0, h->stream>>>(h->g, s, h->d_mask, VN);
+    AMY_CUDA(cudaGetLastError(), "spec mask launch");
+    return AMY_OK;
+}
+
+template <class R, class VT, int TM, bool KAHAN>
+amy_status launch_backup_t(amy_handle_s *h, int spec_kind, const VT *Vn, VT *Vo, R *Vfinal, uint16_t *pi) {
+    BackupArgs<R, VT> a;
+    a.Vn = Vn;
+    a.Vo = Vo;
+    a.Vfinal = Vfinal;
+    a.pi = pi;
+    a.mask = h->d_mask;
+    a.spec_kind = spec_kind;
+    a.tileX = h->tileX;
+    a.T = (const R *)h->d_T;
+    a.O = h->d_O;
+    a.npairs = h->npairs;
+    const int blocks = (h->g.nx + h->tileX - 1) / h->tileX;
+    const size_t smem = (size_t)h->tileX * h->g.nu * sizeof(R);
+    k_backup<R, VT, TM, KAHAN><<<blocks, 256, smem, h->stream>>>(h->g, a);
+    AMY_CUDA(cudaGetLastError(), "backup launch");
+    return AMY_OK;
+}
+
+template <class R, class VT, bool KAHAN>
+amy_status launch_backup_k(amy_handle_s *h, int spec_kind, const VT *Vn, VT *Vo, R *Vfinal, uint16_t *pi) {
+    switch (h->tmode) {
+        case AMY_T_ON_THE_FLY: return launch_backup_t<R, VT, TM_OTF, KAHAN>(h, spec_kind, Vn, Vo, Vfinal, pi);
+        case AMY_T_STORED_FULL: return launch_backup_t<R, VT, TM_FULL, KAHAN>(h, spec_kind, Vn, Vo, Vfinal, pi);
+        default: return launch_backup_t<R, VT, TM_FACTORED, KAHAN>(h, spec_kind, Vn, Vo, Vfinal, pi);
+    }
+}
+
+// One backup V_{k+1} (Vn) -> V_k (Vo) with the handle's precision.
+amy_status launch_backup(amy_handle_s *h, int spec_kind, const void *Vn, void *Vo, void *Vfinal, uint16_t *pi) {
+    if (h->prec == AMY_PREC_FP64)
+        return launch_backup_k<double, double, false>(h, spec_kind, (const double *)Vn, (double *)Vo,
+                                                      (double *)Vfinal, pi);
+    const bool kahan = h->prec == AMY_PREC_FP32_KAHAN;
+    if (h->v_store == AMY_V_BF16) {
+        if (kahan)
+            return launch_backup_k<float, __nv_bfloat16, true>(h, spec_kind, (const __nv_bfloat16 *)Vn,
+                                                               (__nv_bfloat16 *)Vo, (float *)Vfinal, pi);
+        return launch_backup_k<float, __nv_bfloat16, false>(h, spec_kind, (const __nv_bfloat16 *)Vn,
+                                                            (__nv_bfloat16 *)Vo, (float *)Vfinal, pi);
+    }
+    if (h->v_store == AMY_V_UNORM16) {
+        if (kahan)
+            return launch_backup_k<float, unorm16, true>(h, spec_kind, (const unorm16 *)Vn, (unorm16 *)Vo,
+                                                         (float *)Vfinal, pi);
+        return launch_backup_k<float, unorm16, false>(h, spec_kind, (const unorm16 *)Vn, (unorm16 *)Vo,
+                                                      (float *)Vfinal, pi);
+    }
+    if (kahan)
+        return launch_backup_k<float, float, true>(h, spec_kind, (const float *)Vn, (float *)Vo, (float *)Vfinal, pi);
+    return launch_backup_k<float, float, false>(h, spec_kind, (const float *)Vn, (float *)Vo, (float *)Vfinal, pi);
+}
+
+amy_status launch_mask_any(amy_handle_s *h, const SpecDev &s, void *VN) {
+    if (h->prec == AMY_PREC_FP64) return launch_mask<double, double>(h, s, (double *)VN);
+    if (h->v_store == AMY_V_BF16) return launch_mask<float, __nv_bfloat16>(h, s, (__nv_bfloat16 *)VN);
+    if (h->v_store == AMY_V_UNORM16) return launch_mask<float, unorm16>(h, s, (unorm16 *)VN);
+    return launch_mask<float, float>(h, s, (float *)VN);
+}
+
+template <class R>
+amy_status launch_build(amy_handle_s *h) {
+    const int blocks = (int)std::min<int64_t>((h->npairs + 127) / 128, (int64_t)h->sm_count * 32);
+    if (h->tmode == AMY_T_STORED_FULL)
+        k_build<R, TM_FULL><<<blocks, 128, 0, h->stream>>>(h->g, (R *)h->d_T, h->d_O, h->npairs);
+    else
+        k_build<R, TM_FACTORED><<<blocks, 128, 0, h->stream>>>(h->g, (R *)h->d_T, h->d_O, h->npairs);
+    AMY_CUDA(cudaGetLastError(), "build launch");
+    return AMY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *amy_last_error(void) { return amy::g_last_error.c_str(); }
+
+int64_t amy_grid_count(double lb, double ub, double eta) { return amy::grid_count(lb, ub, eta); }
+
+amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_grid *inputs,
+                     const double *sigma, const amy_cut *cut, const amy_opts *opts, amy_handle *out) {
+    if (!out || !opts) return set_error(AMY_E_INVALID_ARG, "null argument");
+    *out = nullptr;
+    Geom g;
+    std::vector<double> params;
+    amy_status st = make_geom(sys, states, inputs, sigma, cut, g, params);
+    if (st != AMY_OK) return st;
+    if (opts->tmode < AMY_T_ON_THE_FLY || opts->tmode > AMY_T_STORED_FACTORED)
+        return set_error(AMY_E_INVALID_ARG, "unknown tmode");
+    if (opts->prec < AMY_PREC_FP64 || opts->prec > AMY_PREC_FP32_KAHAN)
+        return set_error(AMY_E_INVALID_ARG, "unknown precision");
+    if (opts->v_store < AMY_V_NATIVE || opts->v_store > AMY_V_UNORM16)
+        return set_error(AMY_E_INVALID_ARG, "unknown V storage");
+    if (opts->v_store != AMY_V_NATIVE && opts->prec == AMY_PREC_FP64)
+        return set_error(AMY_E_INVALID_ARG, "16-bit V storage needs an FP32 precision");
+    if (opts->tmode != AMY_T_ON_THE_FLY)
+        for (int d = 0; d < g.n; ++d)
+            if (g.N[d] + g.W[d] + 2 > 32767)
+                return set_error(AMY_E_UNSUPPORTED, "stored origins are int16: dim %d too large", d);
+    amy_handle_s *h = new (std::nothrow) amy_handle_s();
+    if (!h) return set_error(AMY_E_OUT_OF_MEMORY, "host allocation");
+    h->g = g;
+    h->tmode = opts->tmode;
+    h->prec = opts->prec;
+    h->v_store = opts->v_store;
+    h->budget = opts->device_mem_budget;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_error(e, "device query");
+    }
+    if (opts->cuda_stream) {
+        h->stream = (cudaStream_t)opts->cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_error(e, "stream create");
+        }
+        h->own_stream = true;
+    }
+    h->tileX = choose_tile(g.nx, g.nu, h->sm_count);
+    h->npairs = (int64_t)g.nx * g.nu;
+#define TRY(x)                 \
+    do {                       \
+        amy_status s__ = (x);  \
+        if (s__ != AMY_OK) {   \
+            free_handle(h);    \
+            return s__;        \
+        }                      \
+    } while (0)
+    TRY(dev_alloc(h, (void **)&h->d_params, params.size() * sizeof(double), "params"));
+    h->g.params = h->d_params;
+    TRY(dev_alloc(h, &h->d_V[0], (size_t)g.nx * vsize(h), "V"));
+    TRY(dev_alloc(h, &h->d_V[1], (size_t)g.nx * vsize(h), "V"));
+    TRY(dev_alloc(h, (void **)&h->d_mask, (size_t)g.nx, "mask"));
+    if (h->tmode != AMY_T_ON_THE_FLY) {
+        const int64_t per_pair = (h->tmode == AMY_T_STORED_FULL) ? g.wtot : g.wsum;
+        TRY(dev_alloc(h, &h->d_T, (size_t)(h->npairs * per_pair) * rsize(h), "stored T"));
+        TRY(dev_alloc(h, (void **)&h->d_O, (size_t)(h->npairs * g.n) * sizeof(int16_t), "stored origins"));
+    }
+    e = cudaMemcpyAsync(h->d_params, params.data(), params.size() * sizeof(double), cudaMemcpyHostToDevice,
+                        h->stream);
+    if (e != cudaSuccess) {
+        free_handle(h);
+        return cuda_error(e, "params upload");
+    }
+    if (h->tmode != AMY_T_ON_THE_FLY) {
+        if (h->prec == AMY_PREC_FP64)
+            TRY(launch_build<double>(h));
+        else
+            TRY(launch_build<float>(h));
+    }
+    // The params upload reads pageable host memory owned by `params`: make
+    // sure it has completed before that vector goes away.
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        free_handle(h);
+        return cuda_error(e, "build");
+    }
+#undef TRY
+    amy_info_t &inf = h->info;
+    memset(&inf, 0, sizeof inf);
+    inf.n_states = g.nx;
+    inf.n_inputs = g.nu;
+    inf.n = g.n;
+    for (int d = 0; d < g.n; ++d) {
+        inf.window[d] = g.W[d];
+        inf.cut_half_width[d] = g.xs[d];
+    }
+    inf.window_slots = g.wtot;
+    inf.window_sum = g.wsum;
+    inf.tmode = h->tmode;
+    inf.prec = h->prec;
+    inf.v_store = h->v_store;
+    *out = h;
+    return AMY_OK;
+}
+
+amy_status amy_info(amy_handle h, amy_info_t *out) {
+    if (!h || !out) return set_error(AMY_E_INVALID_ARG, "null argument");
+    *out = h->info;
+    out->device_bytes = h->bytes;
+    return AMY_OK;
+}
+
+void amy_destroy(amy_handle h) { free_handle(h); }
+
+amy_status amy_synthesize(amy_handle h, const amy_spec *spec, int32_t horizon, void *V_out,
+                          uint16_t *policy_out, int32_t policy_all_steps, int32_t outputs_on_device) {
+    if (!h || !V_out) return set_error(AMY_E_INVALID_ARG, "null argument");
+    if (horizon < 0) return set_error(AMY_E_INVALID_ARG, "negative horizon");
+    SpecDev s;
+    amy_status st = make_spec(h->g, spec, s);
+    if (st != AMY_OK) return st;
+    const int64_t nx = h->g.nx;
+    const size_t osz = rsize(h);
+    // Outputs: V_0 is written by the last backup straight into the output
+    // buffer (device) or a staging buffer (host).
+    void *d_Vout = nullptr;
+    uint16_t *d_pi = nullptr;
+    bool own_out = false, own_pi = false;
+    if (outputs_on_device) {
+        d_Vout = V_out;
+        d_pi = policy_out;
+    } else {
+        AMY_CUDA(cudaMallocAsync(&d_Vout, (size_t)nx * osz, h->stream), "output staging");
+        own_out = true;
+        if (policy_out && horizon > 0) {
+            const size_t pbytes = (size_t)nx * sizeof(uint16_t) * (policy_all_steps ? horizon : 1);
+            cudaError_t e = cudaMallocAsync((void **)&d_pi, pbytes, h->stream);
+            if (e != cudaSuccess) {
+                cudaFreeAsync(d_Vout, h->stream);
+                return cuda_error(e, "policy staging");
+            }
+            own_pi = true;
+        }
+    }
+    auto cleanup = [&]() {
+        if (own_out) cudaFreeAsync(d_Vout, h->stream);
+        if (own_pi) cudaFreeAsync(d_pi, h->stream);
+    };
+    st = launch_mask_any(h, s, h->d_V[0]);
+    if (st != AMY_OK) {
+        cleanup();
+        return st;
+    }
+    int cur = 0;
+    for (int32_t k = horizon - 1; k >= 0; --k) {
+        uint16_t *pk = nullptr;
+        if (d_pi) pk = policy_all_steps ? d_pi + (int64_t)k * nx : (k == 0 ? d_pi : nullptr);
+        void *vfinal = (k == 0) ? d_Vout : nullptr;
+        st = launch_backup(h, s.kind, h->d_V[cur], h->d_V[cur ^ 1], vfinal, pk);
+        if (st != AMY_OK) {
+            cleanup();
+            return st;
+        }
+        cur ^= 1;
+    }
+    if (horizon == 0) {
+        // V_0 = V_N: convert the initial vector into the output type.
+        if (h->prec == AMY_PREC_FP64 || h->v_store == AMY_V_NATIVE) {
+            cudaError_t e = cudaMemcpyAsync(d_Vout, h->d_V[0], (size_t)nx * osz, cudaMemcpyDeviceToDevice, h->stream);
+            if (e != cudaSuccess) {
+                cleanup();
+                return cuda_error(e, "copy V_N");
+            }
+        } else {
+            st = launch_v16_to_f32(h->d_V[0], h->v_store, (float *)d_Vout, nx, h->stream);
+            if (st != AMY_OK) {
+                cleanup();
+                return st;
+            }
+        }
+    }
+    if (!outputs_on_device) {
+        cudaError_t e = cudaMemcpyAsync(V_out, d_Vout, (size_t)nx * osz, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && policy_out && horizon > 0)
+            e = cudaMemcpyAsync(policy_out, d_pi, (size_t)nx * sizeof(uint16_t) * (policy_all_steps ? horizon : 1),
+                                cudaMemcpyDeviceToHost, h->stream);
+        cleanup();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_error(e, "copy out");
+        if (policy_out && horizon == 0) {
+            // no backup: no policy entries to report
+        }
+    } else {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_error(e, "synthesize");
+    }
+    return AMY_OK;
+}
+
+amy_status amy_backup_step(amy_handle h, const amy_spec *spec, const void *V_next, void *V_out,
+                           uint16_t *policy_out, int32_t on_device) {
+    if (!h || !V_next || !V_out) return set_error(AMY_E_INVALID_ARG, "null argument");
+    SpecDev s;
+    amy_status st = make_spec(h->g, spec, s);
+    if (st != AMY_OK) return st;
+    const int64_t nx = h->g.nx;
+    const size_t osz = rsize(h);
+    // The mask kernel also writes V_N into d_V[1]; the caller's V_next then
+    // replaces it in d_V[0] (converted to the storage type).
+    st = launch_mask_any(h, s, h->d_V[1]);
+    if (st != AMY_OK) return st;
+    const void *src = V_next;
+    void *staging = nullptr;
+    if (!on_device) {
+        AMY_CUDA(cudaMallocAsync(&staging, (size_t)nx * osz, h->stream), "staging");
+        cudaError_t e = cudaMemcpyAsync(staging, V_next, (size_t)nx * osz, cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(staging, h->stream);
+            return cuda_error(e, "V_next upload");
+        }
+        src = staging;
+    }
+    cudaError_t e = cudaSuccess;
+    if (h->prec == AMY_PREC_FP64 || h->v_store == AMY_V_NATIVE)
+        e = cudaMemcpyAsync(h->d_V[0], src, (size_t)nx * osz, cudaMemcpyDeviceToDevice, h->stream);
+    else
+        st = launch_f32_to_v16((const float *)src, h->d_V[0], h->v_store, nx, h->stream);
+    if (e != cudaSuccess || st != AMY_OK) {
+        if (staging) cudaFreeAsync(staging, h->stream);
+        return e != cudaSuccess ? cuda_error(e, "V_next copy") : st;
+    }
+    void *d_out = V_out;
+    uint16_t *d_pi = policy_out;
+    void *own_out = nullptr;
+    uint16_t *own_pi = nullptr;
+    if (!on_device) {
+        e = cudaMallocAsync(&own_out, (size_t)nx * osz, h->stream);
+        if (e == cudaSuccess && policy_out) e = cudaMallocAsync((void **)&own_pi, (size_t)nx * 2, h->stream);
+        if (e != cudaSuccess) {
+            if (staging) cudaFreeAsync(staging, h->stream);
+            if (own_out) cudaFreeAsync(own_out, h->stream);
+            return cuda_error(e, "output staging");
+        }
+        d_out = own_out;
+        d_pi = own_pi;
+    }
+    st = launch_backup(h, s.kind, h->d_V[0], h->d_V[1], d_out, d_pi);
+    if (st == AMY_OK && !on_device) {
+        e = cudaMemcpyAsync(V_out, d_out, (size_t)nx * osz, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && policy_out)
+            e = cudaMemcpyAsync(policy_out, d_pi, (size_t)nx * 2, cudaMemcpyDeviceToHost, h->stream);
+    }
+    if (staging) cudaFreeAsync(staging, h->stream);
+    if (own_out) cudaFreeAsync(own_out, h->stream);
+    if (own_pi) cudaFreeAsync(own_pi, h->stream);
+    if (st != AMY_OK) return st;
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_error(e, "backup step");
+    return AMY_OK;
+}
+
+amy_status amy_query_rows(amy_handle h, const int64_t *x, const int64_t *u, int64_t count,
+                          int32_t *origin_out, double *probs_out) {
+    if (!h || !x || !u || !origin_out || !probs_out || count < 0) return set_error(AMY_E_INVALID_ARG, "null argument");
+    if (count == 0) return AMY_OK;
+    for (int64_t i = 0; i < count; ++i)
+        if (x[i] < 0 || x[i] >= h->g.nx || u[i] < 0 || u[i] >= h->g.nu)
+            return set_error(AMY_E_INVALID_ARG, "pair %lld out of range", (long long)i);
+    const Geom &g = h->g;
+    int64_t *dx = nullptr, *du = nullptr;
+    int32_t *dor = nullptr;
+    double *dpr = nullptr;
+    const size_t prb = (size_t)count * g.wtot * sizeof(double);
+    cudaError_t e = cudaMallocAsync((void **)&dx, count * 8, h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&du, count * 8, h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dor, count * g.n * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dpr, prb, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x, count * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(du, u, count * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) {
+        const int blocks = (int)std::min<int64_t>((count + 127) / 128, 4096);
+        if (h->prec == AMY_PREC_FP64)
+            k_query_rows<double><<<blocks, 128, 0, h->stream>>>(g, h->tmode, (const double *)h->d_T, h->d_O, h->npairs,
+                                                                dx, du, count, dor, dpr);
+        else
+            k_query_rows<float><<<blocks, 128, 0, h->stream>>>(g, h->tmode, (const float *)h->d_T, h->d_O, h->npairs,
+                                                               dx, du, count, dor, dpr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(origin_out, dor, count * g.n * 4, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(probs_out, dpr, prb, cudaMemcpyDeviceToHost, h->stream);
+    if (dx) cudaFreeAsync(dx, h->stream);
+    if (du) cudaFreeAsync(du, h->stream);
+    if (dor) cudaFreeAsync(dor, h->stream);
+    if (dpr) cudaFreeAsync(dpr, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_error(e, "query rows");
+    return AMY_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// 16-bit V storage <-> float (used only at the boundary of a call: V_N output
+// with horizon 0, caller-given V_next with 16-bit storage).
+// ---------------------------------------------------------------------------
+namespace amy {
+
+template <class VT>
+__global__ void k_v16_to_f32(const VT *__restrict__ s, float *__restrict__ d, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        d[i] = vload<float, VT>(s + i);
+}
+
+template <class VT>
+__global__ void k_f32_to_v16(const float *__restrict__ s, VT *__restrict__ d, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        d[i] = vstore_cast<VT, float>(s[i]);
+}
+
+amy_status launch_v16_to_f32(const void *src, int32_t v_store, float *dst, int64_t n, cudaStream_t s) {
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8192);
+    if (v_store == AMY_V_BF16)
+        k_v16_to_f32<__nv_bfloat16><<<blocks, 256, 0, s>>>((const __nv_bfloat16 *)src, dst, n);
+    else
+        k_v16_to_f32<unorm16><<<blocks, 256, 0, s>>>((const unorm16 *)src, dst, n);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AMY_OK : cuda_error(e, "16-bit V -> f32");
+}
+
+amy_status launch_f32_to_v16(const float *src, void *dst, int32_t v_store, int64_t n, cudaStream_t s) {
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8192);
+    if (v_store == AMY_V_BF16)
+        k_f32_to_v16<__nv_bfloat16><<<blocks, 256, 0, s>>>(src, (__nv_bfloat16 *)dst, n);
+    else
+        k_f32_to_v16<unorm16><<<blocks, 256, 0, s>>>(src, (unorm16 *)dst, n);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AMY_OK : cuda_error(e, "f32 -> 16-bit V");
+}
+
+}  // namespace amy

@@ -1,0 +1,380 @@
+// amy_kernels.cuh -- kernels of the single-problem path: spec mask + V_N,
+// stored-T construction (Algorithm 2), the fused backup + max/argmax
+// (Algorithm 4, stored or on-the-fly per Sec. 5.1) and a row query used to
+// check rows against an independent implementation.
+#pragma once
+
+#include "amy_core.cuh"
+
+namespace amy {
+
+// Storage types of V between backups: native FP32/FP64, bfloat16, or a
+// 16-bit fixed-point code round(V * 65535) (V is a probability in [0, 1]).
+template <class R, class VT> __device__ __forceinline__ R vload(const VT *p);
+template <> __device__ __forceinline__ double vload<double, double>(const double *p) { return __ldg(p); }
+template <> __device__ __forceinline__ float vload<float, float>(const float *p) { return __ldg(p); }
+template <> __device__ __forceinline__ float vload<float, __nv_bfloat16>(const __nv_bfloat16 *p) {
+    return __bfloat162float(__ldg(p));
+}
+template <> __device__ __forceinline__ float vload<float, unorm16>(const unorm16 *p) {
+    return (float)__ldg(&p->bits) * (1.0f / 65535.0f);
+}
+
+template <class VT, class R> __device__ __forceinline__ VT vstore_cast(R v);
+template <> __device__ __forceinline__ double vstore_cast<double, double>(double v) { return v; }
+template <> __device__ __forceinline__ float vstore_cast<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 vstore_cast<__nv_bfloat16, float>(float v) {
+    return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ unorm16 vstore_cast<unorm16, float>(float v) {
+    unorm16 r;
+    r.bits = (uint16_t)__float2uint_rn(fminf(fmaxf(v, 0.0f), 1.0f) * 65535.0f);
+    return r;
+}
+
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
+
+// Compensated (Kahan) or plain accumulation of one term.
+template <class R, bool KAHAN>
+__device__ __forceinline__ void accum(R &acc, R &comp, R term) {
+    if (KAHAN) {
+        const R y = term - comp;
+        const R t = acc + y;
+        comp = (t - acc) - y;
+        acc = t;
+    } else {
+        acc += term;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Spec sets (Algorithm 3, initial value function) on representative points.
+// ---------------------------------------------------------------------------
+template <class R, class VT>
+__global__ void k_spec_mask(const __grid_constant__ Geom g, const __grid_constant__ SpecDev s,
+                            uint8_t *__restrict__ mask, VT *__restrict__ VN) {
+    for (int64_t xl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xl < g.nx;
+         xl += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = (int32_t)xl;
+        int32_t xi[MAXD];
+        decode_state(g, x, xi);
+        double c[MAXD];
+        for (int d = 0; d < g.n; ++d) c[d] = state_centre(g, d, xi[d]);
+        uint8_t f = 0;
+        for (int b = 0; b < s.n_target; ++b) {
+            bool in = true;
+            for (int d = 0; d < g.n; ++d) in = in && (s.t_lb[b][d] <= c[d] && c[d] <= s.t_ub[b][d]);
+            if (in) f |= F_TARGET;
+        }
+        for (int b = 0; b < s.n_avoid; ++b) {
+            bool in = true;
+            for (int d = 0; d < g.n; ++d) in = in && (s.a_lb[b][d] <= c[d] && c[d] <= s.a_ub[b][d]);
+            if (in) f |= F_AVOID;
+        }
+        if (s.kind == SPEC_SAFETY) {
+            bool in = true;
+            if (s.has_safe)
+                for (int d = 0; d < g.n; ++d) in = in && (s.safe_lb[d] <= c[d] && c[d] <= s.safe_ub[d]);
+            if (in) f |= F_SAFE;
+        } else {
+            f |= F_SAFE;
+        }
+        mask[x] = f;
+        R v;
+        if (s.kind == SPEC_SAFETY)
+            v = (f & F_SAFE) ? R(1) : R(0);
+        else
+            v = (f & F_TARGET) ? R(1) : R(0);
+        VN[x] = vstore_cast<VT, R>(v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row setup for one (x, u) pair: per-dim masses `fac` and cell offsets `off`
+// (each dim d occupies W[d] consecutive entries).
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void row_setup_otf(const Geom &g, int32_t x, int32_t u, R *fac,
+                                              int32_t *off, int32_t *origin) {
+    double mu[MAXD];
+    mean_of(g, x, u, mu);
+    int b = 0;
+    for (int d = 0; d < g.n; ++d) {
+        const int32_t o = origin_of(g, d, mu[d]);
+        if (origin) origin[d] = o;
+        dim_masses<R>(g, d, mu[d], o, fac + b, off + b);
+        b += g.W[d];
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void row_setup_stored(const Geom &g, const R *__restrict__ T,
+                                                 const int16_t *__restrict__ O, int64_t npairs,
+                                                 int64_t pair, bool factored, R *fac, int32_t *off,
+                                                 int32_t *origin) {
+    int b = 0;
+    for (int d = 0; d < g.n; ++d) {
+        const int32_t o = __ldg(O + d * npairs + pair);
+        if (origin) origin[d] = o;
+        dim_offsets(g, d, o, off + b);
+        if (factored)
+            for (int k = 0; k < g.W[d]; ++k) fac[b + k] = __ldg(T + (int64_t)(b + k) * npairs + pair);
+        b += g.W[d];
+    }
+}
+
+// Window sum of a factored row: sum over the window box (C order) of
+// prod_d fac_d[k_d] * V[sum_d off_d[k_d]].  The last dimension is the inner
+// run; the outer dims carry prefix products and prefix offsets.
+template <class R, class VT, bool KAHAN>
+__device__ __forceinline__ R window_sum_factored(const Geom &g, const R *fac, const int32_t *off,
+                                                 const VT *__restrict__ V) {
+    const int n = g.n;
+    const int WL = g.W[n - 1];
+    const int bL = g.wsum - WL;
+    int k[MAXD], fb[MAXD];
+    R pp[MAXD];
+    int32_t po[MAXD];
+    int acc_fb = 0;
+    for (int d = 0; d < n; ++d) {
+        fb[d] = acc_fb;
+        acc_fb += g.W[d];
+        k[d] = 0;
+    }
+    R p = R(1);
+    int32_t q = 0;
+    for (int d = 0; d < n - 1; ++d) {
+        p *= fac[fb[d]];
+        q += off[fb[d]];
+        pp[d] = p;
+        po[d] = q;
+    }
+    R acc = R(0), comp = R(0);
+    const int rows = g.wtot / WL;
+    for (int r = 0; r < rows; ++r) {
+        const R w = (n > 1) ? pp[n - 2] : R(1);
+        const int32_t base = (n > 1) ? po[n - 2] : 0;
+        if (w != R(0)) {
+            R inner = R(0);
+            for (int j = 0; j < WL; ++j) inner = fma_r(fac[bL + j], vload<R, VT>(V + base + off[bL + j]), inner);
+            accum<R, KAHAN>(acc, comp, w * inner);
+        }
+        int d = n - 2;
+        while (d >= 0) {
+            if (++k[d] < g.W[d]) break;
+            k[d] = 0;
+            --d;
+        }
+        if (d < 0) break;
+        for (int e = d; e < n - 1; ++e) {
+            pp[e] = (e > 0 ? pp[e - 1] : R(1)) * fac[fb[e] + k[e]];
+            po[e] = (e > 0 ? po[e - 1] : 0) + off[fb[e] + k[e]];
+        }
+    }
+    return acc;
+}
+
+// Window sum of a stored full row T[slot][pair] (slot in C order).
+template <class R, class VT, bool KAHAN>
+__device__ __forceinline__ R window_sum_full(const Geom &g, const R *__restrict__ Trow, int64_t npairs,
+                                             const int32_t *off, const VT *__restrict__ V) {
+    const int n = g.n;
+    const int WL = g.W[n - 1];
+    const int bL = g.wsum - WL;
+    int k[MAXD], fb[MAXD];
+    int32_t po[MAXD];
+    int acc_fb = 0;
+    for (int d = 0; d < n; ++d) {
+        fb[d] = acc_fb;
+        acc_fb += g.W[d];
+        k[d] = 0;
+    }
+    int32_t q = 0;
+    for (int d = 0; d < n - 1; ++d) {
+        q += off[fb[d]];
+        po[d] = q;
+    }
+    R acc = R(0), comp = R(0);
+    const int rows = g.wtot / WL;
+    int64_t t = 0;
+    for (int r = 0; r < rows; ++r) {
+        const int32_t base = (n > 1) ? po[n - 2] : 0;
+        R inner = R(0);
+        for (int j = 0; j < WL; ++j, ++t)
+            inner = fma_r(__ldg(Trow + t * npairs), vload<R, VT>(V + base + off[bL + j]), inner);
+        accum<R, KAHAN>(acc, comp, inner);
+        int d = n - 2;
+        while (d >= 0) {
+            if (++k[d] < g.W[d]) break;
+            k[d] = 0;
+            --d;
+        }
+        if (d < 0) break;
+        for (int e = d; e < n - 1; ++e) po[e] = (e > 0 ? po[e - 1] : 0) + off[fb[e] + k[e]];
+    }
+    return acc;
+}
+
+template <class R, class VT> struct BackupArgs {
+    const VT *Vn;       // V_{k+1}
+    VT *Vo;             // V_k
+    R *Vfinal;          // optional unrounded copy of V_k (output precision)
+    uint16_t *pi;       // optional policy of this step
+    const uint8_t *mask;
+    int32_t spec_kind;
+    int32_t tileX;      // states per block
+    const R *T;         // stored rows (full or factored)
+    const int16_t *O;   // stored origins [n][pairs]
+    int64_t npairs;
+};
+
+__device__ __forceinline__ bool state_masked(int32_t spec_kind, uint8_t f) {
+    return (spec_kind == SPEC_SAFETY) ? !(f & F_SAFE) : ((f & (F_TARGET | F_AVOID)) != 0);
+}
+
+// Fused backup + max/argmax (Algorithm 4, collect step included).  A block
+// owns tileX consecutive states and all their inputs: items q = u*tileX + xl
+// (consecutive lanes -> consecutive states of one input, so stored rows and V
+// windows are read coalesced).  Window sums land in shared memory, then one
+// thread per state takes the max and the lowest maximising input.
+template <class R, class VT, int TM, bool KAHAN>
+__global__ void __launch_bounds__(256) k_backup(const __grid_constant__ Geom g, const BackupArgs<R, VT> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sbuf = reinterpret_cast<R *>(smem_raw);
+    const int TX = a.tileX;
+    const int32_t x0 = (int32_t)blockIdx.x * TX;
+    const int nitems = TX * g.nu;
+    R fac[MAXWS];
+    int32_t off[MAXWS];
+    for (int q = threadIdx.x; q < nitems; q += blockDim.x) {
+        const int u = q / TX;
+        const int xl = q - u * TX;
+        const int32_t x = x0 + xl;
+        R s = R(-1);
+        if (x < g.nx && !state_masked(a.spec_kind, a.mask[x])) {
+            const int64_t pair = (int64_t)u * g.nx + x;
+            if (TM == TM_OTF) {
+                row_setup_otf<R>(g, x, u, fac, off, nullptr);
+                s = window_sum_factored<R, VT, KAHAN>(g, fac, off, a.Vn);
+            } else if (TM == TM_FACTORED) {
+                row_setup_stored<R>(g, a.T, a.O, a.npairs, pair, true, fac, off, nullptr);
+                s = window_sum_factored<R, VT, KAHAN>(g, fac, off, a.Vn);
+            } else {
+                row_setup_stored<R>(g, a.T, a.O, a.npairs, pair, false, fac, off, nullptr);
+                s = window_sum_full<R, VT, KAHAN>(g, a.T + pair, a.npairs, off, a.Vn);
+            }
+        }
+        sbuf[q] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < TX; t += blockDim.x) {
+        const int32_t x = x0 + t;
+        if (x >= g.nx) continue;
+        const uint8_t f = a.mask[x];
+        R best;
+        uint16_t arg;
+        if (state_masked(a.spec_kind, f)) {
+            best = (a.spec_kind != SPEC_SAFETY && (f & F_TARGET)) ? R(1) : R(0);
+            arg = 0xFFFF;
+        } else {
+            best = R(-1);
+            arg = 0;
+            for (int u = 0; u < g.nu; ++u) {
+                const R s = sbuf[u * TX + t];
+                if (s > best) {
+                    best = s;
+                    arg = (uint16_t)u;
+                }
+            }
+        }
+        a.Vo[x] = vstore_cast<VT, R>(best);
+        if (a.Vfinal) a.Vfinal[x] = best;
+        if (a.pi) a.pi[x] = arg;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stored T construction (Algorithm 2): one thread per (x, u) pair.
+// ---------------------------------------------------------------------------
+template <class R, int TM>
+__global__ void __launch_bounds__(128) k_build(const __grid_constant__ Geom g, R *__restrict__ T,
+                                               int16_t *__restrict__ O, int64_t npairs) {
+    R fac[MAXWS];
+    int32_t off[MAXWS];
+    int32_t org[MAXD];
+    for (int64_t pair = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pair < npairs;
+         pair += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = (int32_t)(pair / g.nx);
+        const int32_t x = (int32_t)(pair - (int64_t)u * g.nx);
+        row_setup_otf<R>(g, x, u, fac, off, org);
+        for (int d = 0; d < g.n; ++d) O[d * npairs + pair] = (int16_t)org[d];
+        if (TM == TM_FACTORED) {
+            for (int j = 0; j < g.wsum; ++j) T[(int64_t)j * npairs + pair] = fac[j];
+        } else {
+            int k[MAXD], fb[MAXD];
+            int acc = 0;
+            for (int d = 0; d < g.n; ++d) {
+                fb[d] = acc;
+                acc += g.W[d];
+                k[d] = 0;
+            }
+            for (int t = 0; t < g.wtot; ++t) {
+                R v = R(1);
+                for (int d = 0; d < g.n; ++d) v = v * fac[fb[d] + k[d]];
+                T[(int64_t)t * npairs + pair] = v;
+                for (int d = g.n - 1; d >= 0; --d) {
+                    if (++k[d] < g.W[d]) break;
+                    k[d] = 0;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row query: origin and window probabilities (double) of listed pairs.
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void k_query_rows(const __grid_constant__ Geom g, int32_t tmode, const R *__restrict__ T,
+                             const int16_t *__restrict__ O, int64_t npairs, const int64_t *__restrict__ qx,
+                             const int64_t *__restrict__ qu, int64_t count, int32_t *__restrict__ origin_out,
+                             double *__restrict__ probs_out) {
+    R fac[MAXWS];
+    int32_t off[MAXWS];
+    int32_t org[MAXD];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = (int32_t)qx[i], u = (int32_t)qu[i];
+        const int64_t pair = (int64_t)u * g.nx + x;
+        if (tmode == TM_OTF)
+            row_setup_otf<R>(g, x, u, fac, off, org);
+        else
+            row_setup_stored<R>(g, T, O, npairs, pair, tmode == TM_FACTORED, fac, off, org);
+        for (int d = 0; d < g.n; ++d) origin_out[i * g.n + d] = org[d];
+        int k[MAXD], fb[MAXD];
+        int acc = 0;
+        for (int d = 0; d < g.n; ++d) {
+            fb[d] = acc;
+            acc += g.W[d];
+            k[d] = 0;
+        }
+        for (int t = 0; t < g.wtot; ++t) {
+            double v;
+            if (tmode == TM_FULL) {
+                v = (double)T[(int64_t)t * npairs + pair];
+            } else {
+                R pr = R(1);
+                for (int d = 0; d < g.n; ++d) pr = pr * fac[fb[d] + k[d]];
+                v = (double)pr;
+            }
+            probs_out[i * (int64_t)g.wtot + t] = v;
+            for (int d = g.n - 1; d >= 0; --d) {
+                if (++k[d] < g.W[d]) break;
+                k[d] = 0;
+            }
+        }
+    }
+}
+
+}  // namespace amy

@@ -1,0 +1,190 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs (all five workloads, reduced and full sizes, every T mode
+and precision, ragged shapes and edge cases)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from parity_util import GAP, TOL, compare_one_step, compare_rows, compare_synthesis, load_engine
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amy():
+    return load_engine()
+
+
+# ---- robot_lin: dense 41x41 rows, reach-avoid, horizon 8 -------------------
+@pytest.fixture(scope="module")
+def robot_ref():
+    w = W.robot_lin()
+    return w, oracle.synthesize(w.problem, w.spec, w.horizon, want_all=True)
+
+
+@pytest.mark.parametrize("tmode", ["stored_full", "otf", "stored_factored"])
+def test_robot_lin_fp64(amy, robot_ref, tmode):
+    w, ref = robot_ref
+    compare_synthesis(amy, w, tmode, "fp64", ref=ref)
+
+
+@pytest.mark.parametrize("tmode", ["stored_full", "otf", "stored_factored"])
+@pytest.mark.parametrize("prec", ["fp32", "fp32_kahan"])
+def test_robot_lin_fp32(amy, robot_ref, tmode, prec):
+    w, ref = robot_ref
+    compare_synthesis(amy, w, tmode, prec, ref=ref)
+
+
+def test_robot_lin_rows(amy):
+    w = W.robot_lin()
+    for tmode, prec, tol in [("stored_full", "fp64", 1e-14), ("otf", "fp32", 2e-6)]:
+        mism, worst = compare_rows(amy, w, tmode, prec)
+        assert mism == 0
+        assert worst <= tol, (tmode, prec, worst)
+
+
+# ---- unicycle: full size (51x51x30, 45 inputs, gamma 1e-6, horizon 32) -----
+@pytest.fixture(scope="module")
+def unicycle_ref():
+    w = W.unicycle()
+    return w, oracle.synthesize(w.problem, w.spec, w.horizon, want_all=True)
+
+
+@pytest.mark.parametrize("tmode,prec", [("stored_factored", "fp32"), ("stored_full", "fp32_kahan"),
+                                        ("otf", "fp32"), ("otf", "fp64")])
+def test_unicycle_full(amy, unicycle_ref, tmode, prec):
+    w, ref = unicycle_ref
+    compare_synthesis(amy, w, tmode, prec, ref=ref)
+
+
+@pytest.mark.parametrize("v_store", ["u16", "bf16"])
+def test_unicycle_16bit_v(amy, unicycle_ref, v_store):
+    w, ref = unicycle_ref
+    compare_synthesis(amy, w, "stored_factored", "fp32", v_store=v_store, ref=ref)
+
+
+def test_unicycle_rows_origins_exact(amy):
+    w = W.unicycle()
+    mism, worst = compare_rows(amy, w, "otf", "fp64", n_pairs=4096)
+    # cos/sin of CUDA and of the host libm may differ in the last bit; an origin
+    # can then differ only if the mean sits within an ulp of a slot boundary.
+    assert mism == 0
+    assert worst <= 1e-13
+
+
+# ---- rooms7: reduced to 5 points per dim, horizon 3; full size one step ----
+def test_rooms7_reduced(amy):
+    w = W.rooms7(n_per_dim=5, horizon=3)
+    ref = oracle.synthesize(w.problem, w.spec, w.horizon, want_all=True)
+    for tmode, prec in [("otf", "fp32_kahan"), ("stored_factored", "fp32"), ("otf", "fp32")]:
+        compare_synthesis(amy, w, tmode, prec, ref=ref)
+
+
+def test_rooms7_full_one_step(amy):
+    w = W.rooms7()
+    rng = np.random.default_rng(W.SEED)
+    V_next = rng.uniform(0.0, 1.0, size=w.problem.n_states)
+    states = rng.choice(w.problem.n_states, size=3000, replace=False)
+    compare_one_step(amy, w, "otf", "fp32_kahan", "native", states, V_next)
+
+
+# ---- traffic6: reduced to 6 points per dim, horizon 2; full size one step ---
+def test_traffic6_reduced(amy):
+    w = W.traffic6(n_per_dim=6, horizon=2)
+    ref = oracle.synthesize(w.problem, w.spec, w.horizon, want_all=True)
+    compare_synthesis(amy, w, "otf", "fp32_kahan", ref=ref)
+    compare_synthesis(amy, w, "otf", "fp32", v_store="u16", ref=ref)
+    compare_synthesis(amy, w, "otf", "fp32", v_store="bf16", ref=ref)
+
+
+def test_traffic6_full_one_step(amy):
+    w = W.traffic6()
+    rng = np.random.default_rng(W.SEED + 5)
+    V_next = rng.uniform(0.0, 1.0, size=w.problem.n_states)
+    states = rng.choice(w.problem.n_states, size=400, replace=False)
+    compare_one_step(amy, w, "otf", "fp32_kahan", "native", states, V_next)
+
+
+# ---- served-stream problems, one by one through amy_synthesize ---------------
+def test_served_requests_individually(amy):
+    reqs = W.served_stream(12)
+    for w in reqs:
+        w.horizon = min(w.horizon, 12)
+        compare_synthesis(amy, w, "otf", "fp32")
+
+
+# ---- ragged shapes, every dimension count, periodic dims, all specs ---------
+@pytest.mark.parametrize("n,per_dim,window,gamma,periodic", [
+    (1, [37], None, 5e-2, None),
+    (2, [13, 29], [3, 5], 0.0, [0, 1]),
+    (3, [7, 9, 11], None, 1e-2, [1, 0, 0]),
+    (4, [5, 6, 7, 5], [3, 3, 3, 3], 0.0, None),
+    (5, [4, 5, 4, 5, 3], None, 0.2, None),
+    (6, [3, 4, 3, 4, 3, 4], [3, 1, 3, 1, 3, 1], 0.0, None),
+    (7, [3, 3, 3, 3, 3, 3, 4], None, 0.3, None),
+    (8, [3, 3, 3, 3, 3, 3, 3, 3], [3] * 8, 0.0, None),
+])
+@pytest.mark.parametrize("kind", [W.SAFETY, W.REACH, W.REACH_AVOID])
+def test_random_shapes(amy, n, per_dim, window, gamma, periodic, kind):
+    rng = np.random.default_rng(100 + n)
+    w = W.random_affine(rng, n, per_dim, 3, gamma=gamma, window=window, periodic=periodic,
+                        kind=kind, horizon=3)
+    if window is None and gamma == 0.0:
+        w.problem.gamma = 0.0
+    for tmode in ["otf", "stored_factored", "stored_full"]:
+        compare_synthesis(amy, w, tmode, "fp32_kahan")
+    compare_synthesis(amy, w, "otf", "fp64")
+
+
+def test_horizon_zero_and_single_input(amy):
+    rng = np.random.default_rng(9)
+    w = W.random_affine(rng, 2, [9, 7], 1, gamma=1e-2, horizon=0)
+    compare_synthesis(amy, w, "otf", "fp32")
+    w.horizon = 4
+    compare_synthesis(amy, w, "stored_full", "fp32")
+
+
+def test_single_state_grid(amy):
+    rng = np.random.default_rng(4)
+    w = W.random_affine(rng, 2, [1, 1], 3, window=[3, 3], kind=W.SAFETY, horizon=3)
+    w.problem.x_eta = [1.0, 1.0]
+    w.spec = W.Spec(W.SAFETY, safe=([-10.0, -10.0], [10.0, 10.0]))
+    compare_synthesis(amy, w, "otf", "fp32")
+
+
+def test_backup_step_matches_synthesize(amy):
+    w = W.unicycle(nxy=21, horizon=1, target=(2.0, 3.0))
+    with amy.amy_build(w.problem, tmode="stored_factored", prec="fp32") as h:
+        V1, pi1 = amy.amy_synthesize(h, w.spec, 1)
+        mask = oracle.spec_mask(w.problem, w.spec)
+        VN = ((mask & 1) != 0).astype(np.float32)
+        V2, pi2 = amy.amy_backup_step(h, w.spec, VN)
+    assert np.array_equal(V1, V2) and np.array_equal(pi1, pi2)
+
+
+def test_deterministic_reruns(amy):
+    w = W.rooms7(n_per_dim=4, horizon=3)
+    with amy.amy_build(w.problem, tmode="otf", prec="fp32_kahan") as h:
+        a = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
+        b = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_device_outputs(amy):
+    import torch
+    w = W.unicycle(nxy=21, horizon=6, target=(2.0, 3.0))
+    ref = oracle.synthesize(w.problem, w.spec, w.horizon)
+    with amy.amy_build(w.problem, tmode="otf", prec="fp32") as h:
+        V = torch.empty(w.problem.n_states, dtype=torch.float32, device="cuda")
+        pi = torch.empty(w.problem.n_states, dtype=torch.int16, device="cuda")
+        amy.amy_synthesize(h, w.spec, w.horizon, V_out=V, policy_out=pi)
+        torch.cuda.synchronize()
+    assert np.max(np.abs(V.cpu().numpy() - ref["V"])) <= TOL["fp32"]
+
+
+def test_memory_budget_rejected(amy):
+    w = W.unicycle()
+    with pytest.raises(amy.AmyError) as e:
+        amy.amy_build(w.problem, tmode="stored_full", prec="fp32", device_mem_budget=1 << 20)
+    assert "OUT_OF_MEMORY" in str(e.value)

@@ -84,7 +84,7 @@ class Workload:
     horizon: int
     precision: str = "fp32"     # "fp64", "fp32", "fp32_kahan"
     tmode: str = "otf"          # "otf", "stored_full", "stored_factored"
-    v_bf16: bool = False
+    v_store: str = "native"     # "native", "bf16", "u16" (16-bit storage of V between backups)
 
 
 def input_centres(p: Problem) -> np.ndarray:
@@ -137,7 +137,7 @@ def robot_lin(n_per_dim: int = 41, horizon: int = 8, precision: str = "fp64") ->
 # unicycle: 3-D nonlinear unicycle, theta periodic
 # ---------------------------------------------------------------------------
 def unicycle(nxy: int = 51, nth: int = 30, horizon: int = 32, precision: str = "fp32",
-             tmode: str = "stored_factored") -> Workload:
+             tmode: str = "stored_factored", target=(8.0, 10.0)) -> Workload:
     p = Problem(
         name=f"unicycle_{nxy}x{nxy}x{nth}",
         x_lb=[0.0, 0.0, -math.pi], x_eta=[0.2, 0.2, 2.0 * math.pi / nth],
@@ -145,7 +145,8 @@ def unicycle(nxy: int = 51, nth: int = 30, horizon: int = 32, precision: str = "
         u_lb=[0.0, -1.0], u_eta=[0.25, 0.25], u_count=[5, 9],
         sys_kind=UNICYCLE, params=np.array([0.1]), sigma=[0.05, 0.05, 0.05],
         gamma=1e-6, window=None)
-    spec = Spec(REACH, targets=[([8.0, 8.0, -10.0], [10.0, 10.0, 10.0])])
+    lo, hi = target
+    spec = Spec(REACH, targets=[([lo, lo, -10.0], [hi, hi, 10.0])])
     return Workload(p, spec, horizon, precision=precision, tmode=tmode)
 
 
@@ -182,7 +183,7 @@ def rooms7(n_per_dim: int = 9, horizon: int = 10, n_rooms: int = 7,
 # traffic6: 6-D linear traffic ring, two binary on-ramp lights
 # ---------------------------------------------------------------------------
 def traffic6(n_per_dim: int = 21, horizon: int = 8, n_cells: int = 6, window: int = 5,
-             v_bf16: bool = False, wrap: bool = True) -> Workload:
+             v_store: str = "native", wrap: bool = True) -> Workload:
     A = np.zeros((n_cells, n_cells))
     for i in range(n_cells):
         A[i, i] = 0.6
@@ -203,7 +204,7 @@ def traffic6(n_per_dim: int = 21, horizon: int = 8, n_cells: int = 6, window: in
     p.params = linear_system_params(A, B, input_centres(p))
     safe_hi = float(min(18.0, n_per_dim - 1 - 2))
     spec = Spec(SAFETY, safe=([0.0] * n_cells, [safe_hi] * n_cells))
-    return Workload(p, spec, horizon, precision="fp32_kahan", tmode="otf", v_bf16=v_bf16)
+    return Workload(p, spec, horizon, precision="fp32_kahan", tmode="otf", v_store=v_store)
 
 
 # ---------------------------------------------------------------------------
@@ -282,7 +283,7 @@ def random_affine(rng: np.random.Generator, n: int, per_dim: Sequence[int], n_u:
                   periodic: Optional[List[int]] = None, kind: str = REACH_AVOID,
                   horizon: int = 4) -> Workload:
     lo, hi = -3.0, 3.0
-    etas = [(hi - lo) / (c - 1) for c in per_dim]
+    etas = [(hi - lo) / (c - 1) if c > 1 else 1.0 for c in per_dim]
     A = rng.standard_normal((n, n))
     A = A * (rng.uniform(0.6, 1.0) / max(abs(np.linalg.eigvals(A))))
     B = rng.normal(0.0, 0.6, size=(n, 1))
