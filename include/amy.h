@@ -90,11 +90,22 @@ typedef struct {
     const int32_t *window;
 } amy_cut;
 
-/* T storage (Sec. 4.3 stored rows; Sec. 5.1 on-the-fly abstraction). */
+/* T storage (Sec. 4.3 stored rows; Sec. 5.1 on-the-fly abstraction).
+ * AMY_T_STORED_SEPARABLE tabulates, per state dim d, the window origin and the
+ * W[d] masses of mean component d over only the state and input coordinates
+ * that component depends on (affine: non-zero columns of A_u[d][:] and input
+ * coordinates that change row d; unicycle: x on (x, th, v), y on (y, th, v),
+ * th on (th, w)).  The values are bit-identical to the per-pair masses of
+ * AMY_T_STORED_FACTORED; FP32 precisions only. */
 typedef enum {
-    AMY_T_ON_THE_FLY = 0,      /* no T in memory; rows recomputed every backup */
-    AMY_T_STORED_FULL = 1,     /* T[slot][pair] products, built once */
-    AMY_T_STORED_FACTORED = 2  /* per-dim masses F[sum W][pair], built once */
+    AMY_T_ON_THE_FLY = 0,       /* no T in memory; rows recomputed every backup */
+    AMY_T_STORED_FULL = 1,      /* T[slot][pair] products, built once */
+    AMY_T_STORED_FACTORED = 2,  /* per-dim masses F[sum W][pair], built once */
+    AMY_T_STORED_SEPARABLE = 3, /* per-dim tables over each component's dependencies */
+    AMY_T_AUTO = 4              /* separable tables when they take at most 8 MiB (and a
+                                   quarter of the budget), else stored factored when it
+                                   takes at most 1 GiB (and a quarter of the budget), else
+                                   on the fly; amy_info reports the choice */
 } amy_tmode;
 
 /* Arithmetic: FP64 everywhere, or FP32 cell masses/products with FP64 only for
@@ -117,6 +128,9 @@ typedef struct {
     void *cuda_stream;          /* cudaStream_t for all work (cudaStreamLegacy and
                                    cudaStreamPerThread accepted); NULL = a
                                    non-blocking stream owned by the handle */
+    int32_t use_graphs;         /* 1: amy_synthesize with device outputs captures its
+                                   horizon loop into a CUDA graph and replays it while
+                                   spec, horizon and output pointers repeat */
 } amy_opts;
 
 /* Closed box tested on representative points: lb[d] <= centre_d <= ub[d]. */
@@ -195,6 +209,21 @@ amy_status amy_backup_step(amy_handle h, const amy_spec *spec, const void *V_nex
  * box (0 for dropped slots), as double.  Host pointers. */
 amy_status amy_query_rows(amy_handle h, const int64_t *x, const int64_t *u, int64_t count,
                           int32_t *origin_out, double *probs_out);
+
+/* Rebuild the stored rows in place (Algorithm 2 again) after replacing the
+ * system parameters (params may be NULL to keep them): same grid, cut and
+ * storage, no allocation.  Asynchronous on the handle's stream.  For
+ * AMY_T_STORED_SEPARABLE the new parameters must keep the dependency sets
+ * (else INVALID_ARG).  A no-op for AMY_T_ON_THE_FLY apart from the upload. */
+amy_status amy_rebuild(amy_handle h, const double *params, int64_t n_params);
+
+/* Kernel timing: while on, every backup and build kernel of this handle is
+ * bracketed by CUDA events on the handle's stream.  amy_kernel_times waits
+ * for the recorded events, returns the summed durations (ms) and launch
+ * counts since the previous call, and resets them. */
+amy_status amy_set_profiling(amy_handle h, int32_t on);
+amy_status amy_kernel_times(amy_handle h, double *backup_ms, int64_t *backup_launches, double *build_ms,
+                            int64_t *build_launches);
 
 amy_status amy_info(amy_handle h, amy_info_t *out);
 void amy_destroy(amy_handle h);

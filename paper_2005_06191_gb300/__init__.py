@@ -20,7 +20,7 @@ import numpy as np
 from . import _abi
 from ._abi import STATUS_NAMES
 
-TMODES = {"otf": 0, "stored_full": 1, "stored_factored": 2}
+TMODES = {"otf": 0, "stored_full": 1, "stored_factored": 2, "stored_separable": 3, "auto": 4}
 PRECS = {"fp64": 0, "fp32": 1, "fp32_kahan": 2}
 SYS_KINDS = {"affine": 0, "unicycle": 1}
 SPEC_KINDS = {"safety": 0, "reach": 1, "reach_avoid": 2}
@@ -170,7 +170,7 @@ def amy_last_error() -> str:
 
 
 def amy_build(problem, tmode: str = "otf", prec: str = "fp32", v_store: str = "native",
-              device_mem_budget: int = 0, stream=None) -> AmyHandle:
+              device_mem_budget: int = 0, stream=None, use_graphs: bool = True) -> AmyHandle:
     """amy_build: validate, derive the window and (stored modes) build T on the GPU.
 
     `stream` is a cudaStream_t as int; None uses torch's current stream."""
@@ -179,6 +179,7 @@ def amy_build(problem, tmode: str = "otf", prec: str = "fp32", v_store: str = "n
     o = _abi.amy_opts()
     o.tmode, o.prec, o.v_store = TMODES[tmode], PRECS[prec], VSTORES[v_store]
     o.device_mem_budget = int(device_mem_budget)
+    o.use_graphs = int(bool(use_graphs))
     o.cuda_stream = C.c_void_p(stream) if stream is not None else _current_stream_ptr()
     out = C.c_void_p(0)
     _check(_lib().amy_build(C.byref(sysd), C.byref(states), C.byref(inputs), sigma, C.byref(cut),
@@ -259,6 +260,27 @@ def amy_query_rows(h: AmyHandle, xs, us):
     return org, probs
 
 
+def amy_rebuild(h: AmyHandle, params=None) -> None:
+    """amy_rebuild: rebuild the stored rows in place (optionally with new system parameters)."""
+    if params is None:
+        _check(_lib().amy_rebuild(h.ptr, C.c_void_p(0), 0))
+        return
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    _check(_lib().amy_rebuild(h.ptr, C.c_void_p(p.ctypes.data), p.size))
+
+
+def amy_set_profiling(h: AmyHandle, on: bool = True) -> None:
+    _check(_lib().amy_set_profiling(h.ptr, int(bool(on))))
+
+
+def amy_kernel_times(h: AmyHandle) -> dict:
+    """Summed CUDA-event durations (ms) and counts of backup / build kernels since the last call."""
+    bms, bn, cms, cn = C.c_double(0), C.c_int64(0), C.c_double(0), C.c_int64(0)
+    _check(_lib().amy_kernel_times(h.ptr, C.byref(bms), C.byref(bn), C.byref(cms), C.byref(cn)))
+    return {"backup_ms": bms.value, "backup_launches": bn.value, "build_ms": cms.value,
+            "build_launches": cn.value}
+
+
 def amy_destroy(h: AmyHandle) -> None:
     h.close()
 
@@ -269,6 +291,7 @@ from .serving import (AmyServer, amy_cancel, amy_poll, amy_result_free,  # noqa:
 __all__ = [
     "AmyError", "AmyHandle", "AmyServer", "amy_build", "amy_synthesize", "amy_backup_step",
     "amy_query_rows", "amy_info", "amy_destroy", "amy_grid_count", "amy_last_error",
+    "amy_rebuild", "amy_set_profiling", "amy_kernel_times",
     "amy_server_create", "amy_submit", "amy_poll", "amy_wait", "amy_cancel", "amy_server_stats",
     "amy_server_destroy", "amy_result_free", "TMODES", "PRECS", "VSTORES", "POLICY_NONE",
 ]

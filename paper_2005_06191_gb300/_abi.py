@@ -35,7 +35,7 @@ class amy_cut(C.Structure):
 
 class amy_opts(C.Structure):
     _fields_ = [("tmode", C.c_int32), ("prec", C.c_int32), ("v_store", C.c_int32),
-                ("device_mem_budget", C.c_int64), ("cuda_stream", C.c_void_p)]
+                ("device_mem_budget", C.c_int64), ("cuda_stream", C.c_void_p), ("use_graphs", C.c_int32)]
 
 
 class amy_box(C.Structure):
@@ -83,6 +83,10 @@ PROTOTYPES = {
                                     C.c_int32]),
     "amy_query_rows": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "amy_info": (C.c_int32, [C.c_void_p, C.POINTER(amy_info_t)]),
+    "amy_rebuild": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "amy_set_profiling": (C.c_int32, [C.c_void_p, C.c_int32]),
+    "amy_kernel_times": (C.c_int32, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "amy_destroy": (None, [C.c_void_p]),
     "amy_last_error": (C.c_char_p, []),
     "amy_server_create": (C.c_int32, [C.POINTER(amy_server_opts), C.POINTER(C.c_void_p)]),

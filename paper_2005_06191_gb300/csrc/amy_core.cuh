@@ -22,7 +22,7 @@ constexpr int MAXWS = 160;  // largest sum of window widths a kernel keeps per r
 enum WindowMode : int32_t { WM_DENSE = 0, WM_GAMMA = 1, WM_EXPLICIT = 2 };
 enum SysKind : int32_t { SYS_AFFINE = 0, SYS_UNICYCLE = 1 };
 enum SpecKind : int32_t { SPEC_SAFETY = 0, SPEC_REACH = 1, SPEC_REACH_AVOID = 2 };
-enum TMode : int32_t { TM_OTF = 0, TM_FULL = 1, TM_FACTORED = 2 };
+enum TMode : int32_t { TM_OTF = 0, TM_FULL = 1, TM_FACTORED = 2, TM_SEPARABLE = 3 };
 
 // 16-bit fixed-point storage of a probability: value = bits / 65535.
 struct unorm16 {
@@ -49,6 +49,21 @@ struct Geom {
     int32_t ucount[MAXD];
     double ulb[MAXD], ueta[MAXD];
     const double *params;        // device copy of the system parameters
+    // Dependency-compressed per-dimension tables (separable stored mode):
+    // mean component d depends only on the state dims j with tsx[d][j] != 0
+    // and the input dims i with tsu[d][i] != 0, so its window origin and
+    // masses are tabulated over those coordinates.  Record e of table d sits
+    // at word toff[d] + e*trw[d]: the origin (int32), W[d] masses (FP32), then
+    // the W[d] cell offsets (cell index * stride, clamped or wrapped; int32).
+    // The input part of every table index, sum_i u_i * tsu[d][i], is stored
+    // per input u at word uoff + u*urw (one int32 per dim).
+    int32_t tsx[MAXD][MAXD];
+    int32_t tsu[MAXD][MAXD];
+    int64_t toff[MAXD];
+    int32_t trw[MAXD];
+    int32_t tent[MAXD];
+    int64_t uoff;
+    int32_t urw;
 };
 
 struct SpecDev {

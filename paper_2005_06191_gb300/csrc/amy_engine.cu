@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/amy.h"
@@ -196,6 +197,98 @@ amy_status make_spec(const Geom &g, const amy_spec *spec, SpecDev &s) {
     return AMY_OK;
 }
 
+// Separable stored mode: which state and input coordinates each mean
+// component depends on.  Affine systems: state dim j matters for component d
+// iff some A_u[d][j] is non-zero (a zero coefficient adds an exact zero in
+// FP64); input dim i matters iff two inputs differing only in that coordinate
+// have bitwise different rows (A_u[d][:], c_u[d]).  Unicycle: x on (x, th, v),
+// y on (y, th, v), th on (th, w).
+amy_status plan_sep_tables(Geom &g, const std::vector<double> &params, int64_t &words,
+                           std::vector<int32_t> *upart) {
+    const int n = g.n, m = g.m;
+    uint32_t Sx[MAXD] = {0}, Su[MAXD] = {0};
+    if (g.sys == SYS_UNICYCLE) {
+        Sx[0] = (1u << 0) | (1u << 2);
+        Su[0] = 1u << 0;
+        Sx[1] = (1u << 1) | (1u << 2);
+        Su[1] = 1u << 0;
+        Sx[2] = 1u << 2;
+        Su[2] = 1u << 1;
+    } else {
+        const int rec = n * n + n;
+        int32_t ustr[MAXD];
+        int32_t s = 1;
+        for (int i = m - 1; i >= 0; --i) {
+            ustr[i] = s;
+            s *= g.ucount[i];
+        }
+        for (int u = 0; u < g.nu; ++u) {
+            const double *A = params.data() + (size_t)u * rec;
+            for (int d = 0; d < n; ++d)
+                for (int j = 0; j < n; ++j)
+                    if (A[d * n + j] != 0.0) Sx[d] |= 1u << j;
+            int32_t r = u;
+            for (int i = m - 1; i >= 0; --i) {
+                const int32_t ui = r % g.ucount[i];
+                r /= g.ucount[i];
+                if (ui == 0) continue;
+                const double *B = params.data() + (size_t)(u - ustr[i]) * rec;
+                for (int d = 0; d < n; ++d) {
+                    if (Su[d] & (1u << i)) continue;
+                    bool same = memcmp(A + n * n + d, B + n * n + d, sizeof(double)) == 0;
+                    for (int j = 0; j < n && same; ++j) same = memcmp(A + d * n + j, B + d * n + j, sizeof(double)) == 0;
+                    if (!same) Su[d] |= 1u << i;
+                }
+            }
+        }
+    }
+    int64_t off = 0;
+    for (int d = 0; d < n; ++d) {
+        int64_t st = 1;
+        for (int i = m - 1; i >= 0; --i) {
+            g.tsu[d][i] = 0;
+            if (Su[d] & (1u << i)) {
+                g.tsu[d][i] = (int32_t)st;
+                st *= g.ucount[i];
+            }
+        }
+        for (int j = n - 1; j >= 0; --j) {
+            g.tsx[d][j] = 0;
+            if (Sx[d] & (1u << j)) {
+                if (st > 2147483647LL) return set_error(AMY_E_UNSUPPORTED, "table of dim %d too large", d);
+                g.tsx[d][j] = (int32_t)st;
+                st *= g.N[j];
+            }
+        }
+        if (st > 2147483647LL) return set_error(AMY_E_UNSUPPORTED, "table of dim %d too large", d);
+        g.tent[d] = (int32_t)st;
+        g.trw[d] = ((1 + 2 * g.W[d]) + 3) / 4 * 4;
+        g.toff[d] = off;
+        off += st * g.trw[d];
+    }
+    // input part of each table index, one record of urw words per input
+    g.uoff = off;
+    g.urw = (n + 3) / 4 * 4;
+    if (upart) {
+        upart->assign((size_t)g.nu * g.urw, 0);
+        for (int u = 0; u < g.nu; ++u) {
+            int32_t ui[MAXD];
+            int32_t r = u;
+            for (int i = m - 1; i >= 0; --i) {
+                ui[i] = r % g.ucount[i];
+                r /= g.ucount[i];
+            }
+            for (int d = 0; d < n; ++d) {
+                int64_t e = 0;
+                for (int i = 0; i < m; ++i) e += (int64_t)ui[i] * g.tsu[d][i];
+                (*upart)[(size_t)u * g.urw + d] = (int32_t)e;
+            }
+        }
+    }
+    words = off + (int64_t)g.nu * g.urw;
+    return AMY_OK;
+}
+
 int choose_tile(int32_t nx, int32_t nu, int sm_count) {
     int tx = 256;
     while (tx > 1 && (int64_t)tx * nu > 4096) tx >>= 1;
@@ -220,7 +313,25 @@ struct amy_handle_s {
     int64_t npairs;
     void *d_V[2];
     uint8_t *d_mask;
+    uint32_t *d_tab;      // per-dimension tables (separable stored mode)
+    int64_t tab_words;
     int tileX;
+    int fast_wm;          // width bound of the register-resident backup, 0 = generic kernel
+    std::vector<double> host_params;
+    // kernel timing: CUDA events around every backup / build kernel when profiling
+    bool profiling;
+    // CUDA graph of the horizon loop (a spec-mask launch + `horizon` backups),
+    // replayed while the spec, horizon and output pointers repeat
+    int use_graphs;
+    cudaStream_t cap_stream;
+    cudaGraphExec_t graph_exec;
+    bool graph_valid;
+    SpecDev g_spec;
+    int32_t g_horizon, g_all;
+    void *g_vout;
+    uint16_t *g_pi;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_backup, ev_build;
     amy_info_t info;
 };
 
@@ -247,6 +358,12 @@ void free_handle(amy_handle_s *h) {
     cudaFree(h->d_V[0]);
     cudaFree(h->d_V[1]);
     cudaFree(h->d_mask);
+    cudaFree(h->d_tab);
+    for (auto &p : h->ev_backup) h->ev_pool.push_back(p.first), h->ev_pool.push_back(p.second);
+    for (auto &p : h->ev_build) h->ev_pool.push_back(p.first), h->ev_pool.push_back(p.second);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -278,6 +395,7 @@ amy_status launch_backup_t(amy_handle_s *h, int spec_kind, const VT *Vn, VT *Vo,
     a.T = (const R *)h->d_T;
     a.O = h->d_O;
     a.npairs = h->npairs;
+    a.tab = h->d_tab;
     const int blocks = (h->g.nx + h->tileX - 1) / h->tileX;
     const size_t smem = (size_t)h->tileX * h->g.nu * sizeof(R);
     k_backup<R, VT, TM, KAHAN><<<blocks, 256, smem, h->stream>>>(h->g, a);
@@ -290,12 +408,76 @@ amy_status launch_backup_k(amy_handle_s *h, int spec_kind, const VT *Vn, VT *Vo,
     switch (h->tmode) {
         case AMY_T_ON_THE_FLY: return launch_backup_t<R, VT, TM_OTF, KAHAN>(h, spec_kind, Vn, Vo, Vfinal, pi);
         case AMY_T_STORED_FULL: return launch_backup_t<R, VT, TM_FULL, KAHAN>(h, spec_kind, Vn, Vo, Vfinal, pi);
+        case AMY_T_STORED_SEPARABLE:
+            return launch_backup_t<R, VT, TM_SEPARABLE, KAHAN>(h, spec_kind, Vn, Vo, Vfinal, pi);
         default: return launch_backup_t<R, VT, TM_FACTORED, KAHAN>(h, spec_kind, Vn, Vo, Vfinal, pi);
     }
 }
 
-// One backup V_{k+1} (Vn) -> V_k (Vo) with the handle's precision.
+cudaEvent_t pooled_event(amy_handle_s *h) {
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Brackets one kernel launch with CUDA events on the handle's stream when
+// profiling is on.
+struct KernelTimer {
+    amy_handle_s *h;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *list;
+    cudaEvent_t a = nullptr, b = nullptr;
+    KernelTimer(amy_handle_s *hh, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *l) : h(hh), list(l) {
+        if (!h->profiling) return;
+        a = pooled_event(h);
+        b = pooled_event(h);
+        if (a && b) cudaEventRecord(a, h->stream);
+    }
+    void done() {
+        if (!h->profiling || !a || !b) return;
+        cudaEventRecord(b, h->stream);
+        list->push_back({a, b});
+    }
+};
+
+amy_status launch_backup_generic(amy_handle_s *h, int spec_kind, const void *Vn, void *Vo, void *Vfinal,
+                                 uint16_t *pi);
+
+// One backup V_{k+1} (Vn) -> V_k (Vo) with the handle's precision: the
+// register-resident kernel when the window fits it, the generic one otherwise.
 amy_status launch_backup(amy_handle_s *h, int spec_kind, const void *Vn, void *Vo, void *Vfinal, uint16_t *pi) {
+    KernelTimer tm(h, &h->ev_backup);
+    amy_status st;
+    if (h->fast_wm > 0 && h->tmode != AMY_T_STORED_FULL) {
+        FastCall c;
+        c.Vn = Vn;
+        c.Vo = Vo;
+        c.Vfinal = (float *)Vfinal;
+        c.pi = pi;
+        c.mask = h->d_mask;
+        c.spec_kind = spec_kind;
+        c.kahan = h->prec == AMY_PREC_FP32_KAHAN;
+        c.T = (const float *)h->d_T;
+        c.O = h->d_O;
+        c.npairs = h->npairs;
+        c.tab = h->d_tab;
+        c.ulanes = 0;
+        const int tm_kind = h->tmode == AMY_T_ON_THE_FLY ? TM_OTF
+                            : h->tmode == AMY_T_STORED_FACTORED ? TM_FACTORED : TM_SEPARABLE;
+        st = launch_backup_fast(h->g, tm_kind, h->v_store, c, h->sm_count, h->stream);
+    } else {
+        st = launch_backup_generic(h, spec_kind, Vn, Vo, Vfinal, pi);
+    }
+    tm.done();
+    return st;
+}
+
+amy_status launch_backup_generic(amy_handle_s *h, int spec_kind, const void *Vn, void *Vo, void *Vfinal,
+                                 uint16_t *pi) {
     if (h->prec == AMY_PREC_FP64)
         return launch_backup_k<double, double, false>(h, spec_kind, (const double *)Vn, (double *)Vo,
                                                       (double *)Vfinal, pi);
@@ -328,11 +510,18 @@ amy_status launch_mask_any(amy_handle_s *h, const SpecDev &s, void *VN) {
 
 template <class R>
 amy_status launch_build(amy_handle_s *h) {
+    KernelTimer tm(h, &h->ev_build);
+    if (h->tmode == AMY_T_STORED_SEPARABLE) {
+        amy_status st = launch_build_sep(h->g, h->d_tab, h->sm_count, h->stream);
+        tm.done();
+        return st;
+    }
     const int blocks = (int)std::min<int64_t>((h->npairs + 127) / 128, (int64_t)h->sm_count * 32);
     if (h->tmode == AMY_T_STORED_FULL)
         k_build<R, TM_FULL><<<blocks, 128, 0, h->stream>>>(h->g, (R *)h->d_T, h->d_O, h->npairs);
     else
         k_build<R, TM_FACTORED><<<blocks, 128, 0, h->stream>>>(h->g, (R *)h->d_T, h->d_O, h->npairs);
+    tm.done();
     AMY_CUDA(cudaGetLastError(), "build launch");
     return AMY_OK;
 }
@@ -353,22 +542,28 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     std::vector<double> params;
     amy_status st = make_geom(sys, states, inputs, sigma, cut, g, params);
     if (st != AMY_OK) return st;
-    if (opts->tmode < AMY_T_ON_THE_FLY || opts->tmode > AMY_T_STORED_FACTORED)
+    if (opts->tmode < AMY_T_ON_THE_FLY || opts->tmode > AMY_T_AUTO)
         return set_error(AMY_E_INVALID_ARG, "unknown tmode");
+    if (opts->prec < AMY_PREC_FP64 || opts->prec > AMY_PREC_FP32_KAHAN)
+        return set_error(AMY_E_INVALID_ARG, "unknown precision");
+    const int32_t tmode =
+        opts->tmode == AMY_T_AUTO ? choose_tmode(g, params, opts->prec, opts->device_mem_budget) : opts->tmode;
+    if (tmode == AMY_T_STORED_SEPARABLE && opts->prec == AMY_PREC_FP64)
+        return set_error(AMY_E_UNSUPPORTED, "separable tables hold FP32 masses");
     if (opts->prec < AMY_PREC_FP64 || opts->prec > AMY_PREC_FP32_KAHAN)
         return set_error(AMY_E_INVALID_ARG, "unknown precision");
     if (opts->v_store < AMY_V_NATIVE || opts->v_store > AMY_V_UNORM16)
         return set_error(AMY_E_INVALID_ARG, "unknown V storage");
     if (opts->v_store != AMY_V_NATIVE && opts->prec == AMY_PREC_FP64)
         return set_error(AMY_E_INVALID_ARG, "16-bit V storage needs an FP32 precision");
-    if (opts->tmode != AMY_T_ON_THE_FLY)
+    if (tmode == AMY_T_STORED_FULL || tmode == AMY_T_STORED_FACTORED)
         for (int d = 0; d < g.n; ++d)
             if (g.N[d] + g.W[d] + 2 > 32767)
                 return set_error(AMY_E_UNSUPPORTED, "stored origins are int16: dim %d too large", d);
     amy_handle_s *h = new (std::nothrow) amy_handle_s();
     if (!h) return set_error(AMY_E_OUT_OF_MEMORY, "host allocation");
     h->g = g;
-    h->tmode = opts->tmode;
+    h->tmode = tmode;
     h->prec = opts->prec;
     h->v_store = opts->v_store;
     h->budget = opts->device_mem_budget;
@@ -390,6 +585,9 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     }
     h->tileX = choose_tile(g.nx, g.nu, h->sm_count);
     h->npairs = (int64_t)g.nx * g.nu;
+    h->fast_wm = fast_wm(g, h->prec);
+    h->use_graphs = opts->use_graphs;
+    h->host_params = params;
 #define TRY(x)                 \
     do {                       \
         amy_status s__ = (x);  \
@@ -403,7 +601,16 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     TRY(dev_alloc(h, &h->d_V[0], (size_t)g.nx * vsize(h), "V"));
     TRY(dev_alloc(h, &h->d_V[1], (size_t)g.nx * vsize(h), "V"));
     TRY(dev_alloc(h, (void **)&h->d_mask, (size_t)g.nx, "mask"));
-    if (h->tmode != AMY_T_ON_THE_FLY) {
+    if (h->tmode == AMY_T_STORED_SEPARABLE) {
+        std::vector<int32_t> upart;
+        TRY(plan_sep_tables(h->g, params, h->tab_words, &upart));
+        TRY(dev_alloc(h, (void **)&h->d_tab, (size_t)h->tab_words * 4, "separable tables"));
+        e = cudaMemcpy(h->d_tab + h->g.uoff, upart.data(), upart.size() * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            free_handle(h);
+            return cuda_error(e, "table index upload");
+        }
+    } else if (h->tmode != AMY_T_ON_THE_FLY) {
         const int64_t per_pair = (h->tmode == AMY_T_STORED_FULL) ? g.wtot : g.wsum;
         TRY(dev_alloc(h, &h->d_T, (size_t)(h->npairs * per_pair) * rsize(h), "stored T"));
         TRY(dev_alloc(h, (void **)&h->d_O, (size_t)(h->npairs * g.n) * sizeof(int16_t), "stored origins"));
@@ -455,6 +662,139 @@ amy_status amy_info(amy_handle h, amy_info_t *out) {
 
 void amy_destroy(amy_handle h) { free_handle(h); }
 
+amy_status amy_rebuild(amy_handle h, const double *params, int64_t n_params) {
+    if (!h) return set_error(AMY_E_INVALID_ARG, "null handle");
+    if (params) {
+        if (n_params != (int64_t)h->host_params.size())
+            return set_error(AMY_E_INVALID_ARG, "rebuild needs %lld parameters", (long long)h->host_params.size());
+        for (int64_t i = 0; i < n_params; ++i)
+            if (!std::isfinite(params[i])) return set_error(AMY_E_INVALID_ARG, "non-finite system parameter");
+        if (h->tmode == AMY_T_STORED_SEPARABLE) {
+            // the dependency sets (hence the table layout) must not change
+            Geom g2 = h->g;
+            std::vector<double> p2(params, params + n_params);
+            int64_t words = 0;
+            amy_status st = plan_sep_tables(g2, p2, words, nullptr);
+            if (st != AMY_OK) return st;
+            if (words != h->tab_words || memcmp(g2.tsx, h->g.tsx, sizeof g2.tsx) != 0 ||
+                memcmp(g2.tsu, h->g.tsu, sizeof g2.tsu) != 0)
+                return set_error(AMY_E_INVALID_ARG, "new parameters change the table layout; build a new handle");
+        }
+        h->host_params.assign(params, params + n_params);
+        AMY_CUDA(cudaMemcpyAsync(h->d_params, h->host_params.data(), n_params * sizeof(double),
+                                 cudaMemcpyHostToDevice, h->stream), "params upload");
+    }
+    if (h->tmode == AMY_T_ON_THE_FLY) return AMY_OK;
+    if (h->prec == AMY_PREC_FP64) return launch_build<double>(h);
+    return launch_build<float>(h);
+}
+
+amy_status amy_set_profiling(amy_handle h, int32_t on) {
+    if (!h) return set_error(AMY_E_INVALID_ARG, "null handle");
+    h->profiling = on != 0;
+    return AMY_OK;
+}
+
+amy_status amy_kernel_times(amy_handle h, double *backup_ms, int64_t *backup_launches, double *build_ms,
+                            int64_t *build_launches) {
+    if (!h) return set_error(AMY_E_INVALID_ARG, "null handle");
+    auto drain = [&](std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &l, double *ms, int64_t *cnt) -> amy_status {
+        double tot = 0.0;
+        for (auto &p : l) {
+            cudaError_t e = cudaEventSynchronize(p.second);
+            float t = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, p.first, p.second);
+            if (e != cudaSuccess) return cuda_error(e, "kernel timing");
+            tot += t;
+        }
+        if (ms) *ms = tot;
+        if (cnt) *cnt = (int64_t)l.size();
+        for (auto &p : l) h->ev_pool.push_back(p.first), h->ev_pool.push_back(p.second);
+        l.clear();
+        return AMY_OK;
+    };
+    amy_status st = drain(h->ev_backup, backup_ms, backup_launches);
+    if (st != AMY_OK) return st;
+    return drain(h->ev_build, build_ms, build_launches);
+}
+
+}  // extern "C"
+
+namespace {
+
+// The horizon loop of Algorithm 4 on the handle's stream: spec mask and V_N,
+// then backups k = N-1..0 ping-ponging between the two resident V vectors;
+// the last one writes V_0 into d_Vout.
+amy_status enqueue_synthesis(amy_handle_s *h, const SpecDev &s, int32_t horizon, void *d_Vout, uint16_t *d_pi,
+                             int32_t all_steps) {
+    const int64_t nx = h->g.nx;
+    amy_status st = launch_mask_any(h, s, h->d_V[0]);
+    if (st != AMY_OK) return st;
+    int cur = 0;
+    for (int32_t k = horizon - 1; k >= 0; --k) {
+        uint16_t *pk = nullptr;
+        if (d_pi) pk = all_steps ? d_pi + (int64_t)k * nx : (k == 0 ? d_pi : nullptr);
+        void *vfinal = (k == 0) ? d_Vout : nullptr;
+        st = launch_backup(h, s.kind, h->d_V[cur], h->d_V[cur ^ 1], vfinal, pk);
+        if (st != AMY_OK) return st;
+        cur ^= 1;
+    }
+    if (horizon == 0) {
+        // V_0 = V_N: convert the initial vector into the output type.
+        if (h->prec == AMY_PREC_FP64 || h->v_store == AMY_V_NATIVE) {
+            AMY_CUDA(cudaMemcpyAsync(d_Vout, h->d_V[0], (size_t)nx * rsize(h), cudaMemcpyDeviceToDevice, h->stream),
+                     "copy V_N");
+        } else {
+            st = launch_v16_to_f32(h->d_V[0], h->v_store, (float *)d_Vout, nx, h->stream);
+            if (st != AMY_OK) return st;
+        }
+    }
+    return AMY_OK;
+}
+
+// Replays the cached graph of the horizon loop when the call repeats the
+// previous one (same spec, horizon, outputs); otherwise captures a new one on
+// a private stream and instantiates it.
+amy_status synthesize_graph(amy_handle_s *h, const SpecDev &s, int32_t horizon, void *d_Vout, uint16_t *d_pi,
+                            int32_t all_steps) {
+    const bool hit = h->graph_valid && memcmp(&h->g_spec, &s, sizeof s) == 0 && h->g_horizon == horizon &&
+                     h->g_vout == d_Vout && h->g_pi == d_pi && h->g_all == all_steps;
+    if (!hit) {
+        if (!h->cap_stream) AMY_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "capture stream");
+        if (h->graph_exec) {
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+        }
+        h->graph_valid = false;
+        cudaStream_t user = h->stream;
+        AMY_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed), "begin capture");
+        h->stream = h->cap_stream;
+        amy_status st = enqueue_synthesis(h, s, horizon, d_Vout, d_pi, all_steps);
+        h->stream = user;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (st != AMY_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_error(e, "graph capture");
+        h->graph_valid = true;
+        h->g_spec = s;
+        h->g_horizon = horizon;
+        h->g_vout = d_Vout;
+        h->g_pi = d_pi;
+        h->g_all = all_steps;
+    }
+    AMY_CUDA(cudaGraphLaunch(h->graph_exec, h->stream), "graph launch");
+    return AMY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 amy_status amy_synthesize(amy_handle h, const amy_spec *spec, int32_t horizon, void *V_out,
                           uint16_t *policy_out, int32_t policy_all_steps, int32_t outputs_on_device) {
     if (!h || !V_out) return set_error(AMY_E_INVALID_ARG, "null argument");
@@ -489,38 +829,14 @@ amy_status amy_synthesize(amy_handle h, const amy_spec *spec, int32_t horizon, v
         if (own_out) cudaFreeAsync(d_Vout, h->stream);
         if (own_pi) cudaFreeAsync(d_pi, h->stream);
     };
-    st = launch_mask_any(h, s, h->d_V[0]);
+    if (outputs_on_device && h->use_graphs && !h->profiling) {
+        st = synthesize_graph(h, s, horizon, d_Vout, d_pi, policy_all_steps);
+    } else {
+        st = enqueue_synthesis(h, s, horizon, d_Vout, d_pi, policy_all_steps);
+    }
     if (st != AMY_OK) {
         cleanup();
         return st;
-    }
-    int cur = 0;
-    for (int32_t k = horizon - 1; k >= 0; --k) {
-        uint16_t *pk = nullptr;
-        if (d_pi) pk = policy_all_steps ? d_pi + (int64_t)k * nx : (k == 0 ? d_pi : nullptr);
-        void *vfinal = (k == 0) ? d_Vout : nullptr;
-        st = launch_backup(h, s.kind, h->d_V[cur], h->d_V[cur ^ 1], vfinal, pk);
-        if (st != AMY_OK) {
-            cleanup();
-            return st;
-        }
-        cur ^= 1;
-    }
-    if (horizon == 0) {
-        // V_0 = V_N: convert the initial vector into the output type.
-        if (h->prec == AMY_PREC_FP64 || h->v_store == AMY_V_NATIVE) {
-            cudaError_t e = cudaMemcpyAsync(d_Vout, h->d_V[0], (size_t)nx * osz, cudaMemcpyDeviceToDevice, h->stream);
-            if (e != cudaSuccess) {
-                cleanup();
-                return cuda_error(e, "copy V_N");
-            }
-        } else {
-            st = launch_v16_to_f32(h->d_V[0], h->v_store, (float *)d_Vout, nx, h->stream);
-            if (st != AMY_OK) {
-                cleanup();
-                return st;
-            }
-        }
     }
     if (!outputs_on_device) {
         cudaError_t e = cudaMemcpyAsync(V_out, d_Vout, (size_t)nx * osz, cudaMemcpyDeviceToHost, h->stream);
@@ -624,9 +940,11 @@ amy_status amy_query_rows(amy_handle h, const int64_t *x, const int64_t *u, int6
         const int blocks = (int)std::min<int64_t>((count + 127) / 128, 4096);
         if (h->prec == AMY_PREC_FP64)
             k_query_rows<double><<<blocks, 128, 0, h->stream>>>(g, h->tmode, (const double *)h->d_T, h->d_O, h->npairs,
+                                                                h->d_tab,
                                                                 dx, du, count, dor, dpr);
         else
             k_query_rows<float><<<blocks, 128, 0, h->stream>>>(g, h->tmode, (const float *)h->d_T, h->d_O, h->npairs,
+                                                               h->d_tab,
                                                                dx, du, count, dor, dpr);
         e = cudaGetLastError();
     }
@@ -679,6 +997,93 @@ amy_status launch_f32_to_v16(const float *src, void *dst, int32_t v_store, int64
         k_f32_to_v16<unorm16><<<blocks, 256, 0, s>>>(src, (unorm16 *)dst, n);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? AMY_OK : cuda_error(e, "f32 -> 16-bit V");
+}
+
+}  // namespace amy
+
+// ---------------------------------------------------------------------------
+// Launchers used by the serving scheduler (problems without a handle).
+// ---------------------------------------------------------------------------
+namespace amy {
+
+amy_status launch_spec_mask(const Geom &g, const SpecDev &s, uint8_t *mask, void *VN, int v_store, cudaStream_t st) {
+    const int blocks = (int)std::min<int64_t>((g.nx + 255) / 256, 65535);
+    if (v_store == AMY_V_BF16)
+        k_spec_mask<float, __nv_bfloat16><<<blocks, 256, 0, st>>>(g, s, mask, (__nv_bfloat16 *)VN);
+    else if (v_store == AMY_V_UNORM16)
+        k_spec_mask<float, unorm16><<<blocks, 256, 0, st>>>(g, s, mask, (unorm16 *)VN);
+    else
+        k_spec_mask<float, float><<<blocks, 256, 0, st>>>(g, s, mask, (float *)VN);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AMY_OK : cuda_error(e, "spec mask launch");
+}
+
+namespace {
+template <class VT, int TM, bool KAHAN>
+amy_status generic_fp32_t(const Geom &g, const FastCall &c, int sm_count, cudaStream_t st) {
+    BackupArgs<float, VT> a;
+    a.Vn = (const VT *)c.Vn;
+    a.Vo = (VT *)c.Vo;
+    a.Vfinal = c.Vfinal;
+    a.pi = c.pi;
+    a.mask = c.mask;
+    a.spec_kind = c.spec_kind;
+    a.tileX = choose_tile(g.nx, g.nu, sm_count);
+    a.T = nullptr;
+    a.O = nullptr;
+    a.npairs = 0;
+    a.tab = c.tab;
+    const int blocks = (g.nx + a.tileX - 1) / a.tileX;
+    const size_t smem = (size_t)a.tileX * g.nu * sizeof(float);
+    k_backup<float, VT, TM, KAHAN><<<blocks, 256, smem, st>>>(g, a);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AMY_OK : cuda_error(e, "backup launch");
+}
+
+template <int TM>
+amy_status generic_fp32_tm(const Geom &g, const FastCall &c, int v_store, int sm_count, cudaStream_t st) {
+    if (v_store == AMY_V_BF16)
+        return c.kahan ? generic_fp32_t<__nv_bfloat16, TM, true>(g, c, sm_count, st)
+                       : generic_fp32_t<__nv_bfloat16, TM, false>(g, c, sm_count, st);
+    if (v_store == AMY_V_UNORM16)
+        return c.kahan ? generic_fp32_t<unorm16, TM, true>(g, c, sm_count, st)
+                       : generic_fp32_t<unorm16, TM, false>(g, c, sm_count, st);
+    return c.kahan ? generic_fp32_t<float, TM, true>(g, c, sm_count, st)
+                   : generic_fp32_t<float, TM, false>(g, c, sm_count, st);
+}
+}  // namespace
+
+amy_status launch_backup_generic_fp32(const Geom &g, int tm, const FastCall &c, int v_store, int sm_count,
+                                      cudaStream_t st) {
+    if (tm == TM_OTF) return generic_fp32_tm<TM_OTF>(g, c, v_store, sm_count, st);
+    return generic_fp32_tm<TM_SEPARABLE>(g, c, v_store, sm_count, st);
+}
+
+}  // namespace amy
+
+namespace amy {
+
+int choose_tmode(const Geom &g, const std::vector<double> &params, int prec, int64_t budget) {
+    const int64_t cap = budget > 0 ? budget / 4 : INT64_MAX;
+    if (prec != AMY_PREC_FP64) {
+        Geom g2 = g;
+        int64_t words = 0;
+        if (plan_sep_tables(g2, params, words, nullptr) == AMY_OK && words * 4 <= std::min(kAutoTableBytes, cap))
+            return TM_SEPARABLE;
+    }
+    bool fits16 = true;
+    for (int d = 0; d < g.n; ++d) fits16 = fits16 && (g.N[d] + g.W[d] + 2 <= 32767);
+    const int64_t rsz = prec == AMY_PREC_FP64 ? 8 : 4;
+    const int64_t fact = (int64_t)g.nx * g.nu * ((int64_t)g.wsum * rsz + 2 * g.n);
+    if (fits16 && fact <= std::min(kAutoFactoredBytes, cap)) return TM_FACTORED;
+    return TM_OTF;
+}
+
+amy_status launch_build_factored(const Geom &g, float *T, int16_t *O, int64_t npairs, int sm_count, cudaStream_t st) {
+    const int blocks = (int)std::min<int64_t>((npairs + 127) / 128, (int64_t)sm_count * 32);
+    k_build<float, TM_FACTORED><<<std::max(blocks, 1), 128, 0, st>>>(g, T, O, npairs);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AMY_OK : cuda_error(e, "factored build launch");
 }
 
 }  // namespace amy

@@ -1,0 +1,49 @@
+// amy_fast.cu -- dispatch of the register-resident fused backup
+// (amy_fast.cuh) and launch of the per-dimension table build.
+#include <algorithm>
+
+#include "amy_fast.cuh"
+#include "amy_internal.h"
+
+namespace amy {
+
+template <class VT>
+amy_status launch_fast_vt(const Geom &g, int wm, bool exact, int tmode, const FastCall &c, int sm_count,
+                          cudaStream_t st);
+extern template amy_status launch_fast_vt<float>(const Geom &, int, bool, int, const FastCall &, int, cudaStream_t);
+extern template amy_status launch_fast_vt<unorm16>(const Geom &, int, bool, int, const FastCall &, int,
+                                                   cudaStream_t);
+extern template amy_status launch_fast_vt<__nv_bfloat16>(const Geom &, int, bool, int, const FastCall &, int,
+                                                         cudaStream_t);
+
+int fast_wm(const Geom &g, int prec) {
+    if (prec == AMY_PREC_FP64) return 0;
+    int wmax = 0;
+    for (int d = 0; d < g.n; ++d) wmax = std::max(wmax, g.W[d]);
+    const int wm = wmax <= 3 ? 3 : (wmax <= 5 ? 5 : (wmax <= 8 ? 8 : 0));
+    if (wm == 0) return 0;
+    if (fast_smem_bytes(g.n, wm) > 200 * 1024) return 0;
+    return wm;
+}
+
+amy_status launch_backup_fast(const Geom &g, int tmode, int v_store, const FastCall &c, int sm_count,
+                              cudaStream_t st) {
+    const int wm = fast_wm(g, AMY_PREC_FP32);
+    if (wm == 0 || tmode == TM_FULL) return set_error(AMY_E_UNSUPPORTED, "fast backup not applicable");
+    bool exact = true;
+    for (int d = 0; d < g.n; ++d) exact = exact && g.W[d] == wm;
+    if (v_store == AMY_V_BF16) return launch_fast_vt<__nv_bfloat16>(g, wm, exact, tmode, c, sm_count, st);
+    if (v_store == AMY_V_UNORM16) return launch_fast_vt<unorm16>(g, wm, exact, tmode, c, sm_count, st);
+    return launch_fast_vt<float>(g, wm, exact, tmode, c, sm_count, st);
+}
+
+amy_status launch_build_sep(const Geom &g, uint32_t *tab, int sm_count, cudaStream_t st) {
+    int64_t total = 0;
+    for (int d = 0; d < g.n; ++d) total += g.tent[d];
+    const int blocks = (int)std::min<int64_t>((total + 127) / 128, (int64_t)sm_count * 16);
+    k_build_sep<<<std::max(blocks, 1), 128, 0, st>>>(g, tab, total);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AMY_OK : cuda_error(e, "table build launch");
+}
+
+}  // namespace amy

@@ -1,0 +1,10 @@
+// amy_fast_f32.cu -- register-resident backup kernels (single problem and
+// grouped persistent batch) with V stored as float.
+#include "amy_batch.cuh"
+#include "amy_fast_launch.cuh"
+
+namespace amy {
+template amy_status launch_fast_vt<float>(const Geom &, int, bool, int, const FastCall &, int, cudaStream_t);
+template amy_status launch_group_vt<float>(int, int, bool, const BatchEntry *, int32_t, int64_t, int32_t *, int, int,
+                                         cudaStream_t);
+}  // namespace amy

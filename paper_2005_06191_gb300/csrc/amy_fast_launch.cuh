@@ -1,0 +1,74 @@
+// amy_fast_launch.cuh -- launcher of the register-resident backup for one V
+// storage type; instantiated once per storage type in its own translation
+// unit (amy_fast_f32.cu, amy_fast_u16.cu, amy_fast_bf16.cu) so the variants
+// compile in parallel.
+#pragma once
+
+#include "amy_fast.cuh"
+#include "amy_internal.h"
+
+namespace amy {
+
+template <class VT>
+amy_status launch_fast_vt(const Geom &g, int wm, bool exact, int tmode, const FastCall &c, int sm_count,
+                          cudaStream_t st);
+
+namespace fastimpl {
+
+template <class VT, int WM, int TM, bool EXACT>
+amy_status launch_t(const Geom &g, const FastCall &c, int sm_count, cudaStream_t st) {
+    FastArgs<VT> a;
+    a.Vn = (const VT *)c.Vn;
+    a.Vo = (VT *)c.Vo;
+    a.Vfinal = c.Vfinal;
+    a.pi = c.pi;
+    a.mask = c.mask;
+    a.spec_kind = c.spec_kind;
+    a.kahan = c.kahan;
+    a.T = c.T;
+    a.O = c.O;
+    a.npairs = c.npairs;
+    a.tab = c.tab;
+    // Input lanes per state: one when the grid alone fills the GPU several
+    // times over, otherwise up to 8 (power of two) to expose parallelism.
+    a.ulanes = c.ulanes > 0 ? c.ulanes : fast_default_ulanes(g, sm_count);
+    a.tileX = FAST_THREADS / a.ulanes;
+    const size_t smem = fast_smem_bytes(g.n, WM);
+    auto kern = k_backup_fast<VT, WM, TM, EXACT>;
+    if (smem > 48 * 1024) {
+        static bool raised = false;
+        if (!raised) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            if (e != cudaSuccess) return cuda_error(e, "fast backup smem attribute");
+            raised = true;
+        }
+    }
+    const int64_t blocks = ((int64_t)g.nx + a.tileX - 1) / a.tileX;
+    kern<<<(unsigned)blocks, FAST_THREADS, smem, st>>>(g, a);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AMY_OK : cuda_error(e, "fast backup launch");
+}
+
+template <class VT, int WM>
+amy_status launch_tm(const Geom &g, bool exact, int tmode, const FastCall &c, int sm, cudaStream_t st) {
+    switch (tmode) {
+        case TM_OTF:
+            return exact ? launch_t<VT, WM, TM_OTF, true>(g, c, sm, st) : launch_t<VT, WM, TM_OTF, false>(g, c, sm, st);
+        case TM_FACTORED: return launch_t<VT, WM, TM_FACTORED, false>(g, c, sm, st);
+        default:
+            return exact ? launch_t<VT, WM, TM_SEPARABLE, true>(g, c, sm, st)
+                         : launch_t<VT, WM, TM_SEPARABLE, false>(g, c, sm, st);
+    }
+}
+
+}  // namespace fastimpl
+
+template <class VT>
+amy_status launch_fast_vt(const Geom &g, int wm, bool exact, int tmode, const FastCall &c, int sm_count,
+                          cudaStream_t st) {
+    if (wm == 3) return fastimpl::launch_tm<VT, 3>(g, exact, tmode, c, sm_count, st);
+    if (wm == 5) return fastimpl::launch_tm<VT, 5>(g, exact, tmode, c, sm_count, st);
+    return fastimpl::launch_tm<VT, 8>(g, exact, tmode, c, sm_count, st);
+}
+
+}  // namespace amy

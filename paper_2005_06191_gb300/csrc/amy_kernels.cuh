@@ -124,6 +124,32 @@ __device__ __forceinline__ void row_setup_stored(const Geom &g, const R *__restr
     }
 }
 
+// Row setup from the per-dimension tables of the separable stored mode.
+__device__ __forceinline__ void row_setup_sep(const Geom &g, const uint32_t *__restrict__ tab, int32_t x,
+                                              int32_t u, float *fac, int32_t *off, int32_t *origin) {
+    int32_t xi[MAXD], ui[MAXD];
+    decode_state(g, x, xi);
+    uint32_t r = (uint32_t)u;
+    for (int i = g.m - 1; i >= 0; --i) {
+        ui[i] = (int32_t)(r % (uint32_t)g.ucount[i]);
+        r /= (uint32_t)g.ucount[i];
+    }
+    int b = 0;
+    for (int d = 0; d < g.n; ++d) {
+        int64_t e = 0;
+        for (int j = 0; j < g.n; ++j) e += (int64_t)xi[j] * g.tsx[d][j];
+        for (int i = 0; i < g.m; ++i) e += (int64_t)ui[i] * g.tsu[d][i];
+        const uint32_t *rec = tab + g.toff[d] + e * g.trw[d];
+        const int32_t o = (int32_t)__ldg(rec);
+        if (origin) origin[d] = o;
+        for (int k = 0; k < g.W[d]; ++k) {
+            fac[b + k] = __uint_as_float(__ldg(rec + 1 + k));
+            off[b + k] = (int32_t)__ldg(rec + 1 + g.W[d] + k);
+        }
+        b += g.W[d];
+    }
+}
+
 // Window sum of a factored row: sum over the window box (C order) of
 // prod_d fac_d[k_d] * V[sum_d off_d[k_d]].  The last dimension is the inner
 // run; the outer dims carry prefix products and prefix offsets.
@@ -227,6 +253,7 @@ template <class R, class VT> struct BackupArgs {
     const R *T;         // stored rows (full or factored)
     const int16_t *O;   // stored origins [n][pairs]
     int64_t npairs;
+    const uint32_t *tab;  // per-dimension tables (separable stored mode)
 };
 
 __device__ __forceinline__ bool state_masked(int32_t spec_kind, uint8_t f) {
@@ -254,12 +281,17 @@ __global__ void __launch_bounds__(256) k_backup(const __grid_constant__ Geom g, 
         R s = R(-1);
         if (x < g.nx && !state_masked(a.spec_kind, a.mask[x])) {
             const int64_t pair = (int64_t)u * g.nx + x;
-            if (TM == TM_OTF) {
+            if constexpr (TM == TM_OTF) {
                 row_setup_otf<R>(g, x, u, fac, off, nullptr);
                 s = window_sum_factored<R, VT, KAHAN>(g, fac, off, a.Vn);
-            } else if (TM == TM_FACTORED) {
+            } else if constexpr (TM == TM_FACTORED) {
                 row_setup_stored<R>(g, a.T, a.O, a.npairs, pair, true, fac, off, nullptr);
                 s = window_sum_factored<R, VT, KAHAN>(g, fac, off, a.Vn);
+            } else if constexpr (TM == TM_SEPARABLE) {
+                if constexpr (sizeof(R) == 4) {
+                    row_setup_sep(g, a.tab, x, u, fac, off, nullptr);
+                    s = window_sum_factored<R, VT, KAHAN>(g, fac, off, a.Vn);
+                }
             } else {
                 row_setup_stored<R>(g, a.T, a.O, a.npairs, pair, false, fac, off, nullptr);
                 s = window_sum_full<R, VT, KAHAN>(g, a.T + pair, a.npairs, off, a.Vn);
@@ -337,7 +369,8 @@ __global__ void __launch_bounds__(128) k_build(const __grid_constant__ Geom g, R
 // ---------------------------------------------------------------------------
 template <class R>
 __global__ void k_query_rows(const __grid_constant__ Geom g, int32_t tmode, const R *__restrict__ T,
-                             const int16_t *__restrict__ O, int64_t npairs, const int64_t *__restrict__ qx,
+                             const int16_t *__restrict__ O, int64_t npairs, const uint32_t *__restrict__ tab,
+                             const int64_t *__restrict__ qx,
                              const int64_t *__restrict__ qu, int64_t count, int32_t *__restrict__ origin_out,
                              double *__restrict__ probs_out) {
     R fac[MAXWS];
@@ -349,7 +382,9 @@ __global__ void k_query_rows(const __grid_constant__ Geom g, int32_t tmode, cons
         const int64_t pair = (int64_t)u * g.nx + x;
         if (tmode == TM_OTF)
             row_setup_otf<R>(g, x, u, fac, off, org);
-        else
+        else if (tmode == TM_SEPARABLE) {
+            if constexpr (sizeof(R) == 4) row_setup_sep(g, tab, x, u, fac, off, org);
+        } else
             row_setup_stored<R>(g, T, O, npairs, pair, tmode == TM_FACTORED, fac, off, org);
         for (int d = 0; d < g.n; ++d) origin_out[i * g.n + d] = org[d];
         int k[MAXD], fb[MAXD];

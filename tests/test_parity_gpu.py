@@ -188,3 +188,105 @@ def test_memory_budget_rejected(amy):
     with pytest.raises(amy.AmyError) as e:
         amy.amy_build(w.problem, tmode="stored_full", prec="fp32", device_mem_budget=1 << 20)
     assert "OUT_OF_MEMORY" in str(e.value)
+
+
+# ---- separable per-dimension tables ------------------------------------------
+@pytest.mark.parametrize("prec,v_store", [("fp32", "native"), ("fp32_kahan", "native"), ("fp32", "u16")])
+def test_unicycle_separable(amy, unicycle_ref, prec, v_store):
+    w, ref = unicycle_ref
+    compare_synthesis(amy, w, "stored_separable", prec, v_store=v_store, ref=ref)
+
+
+def test_separable_tables_match_factored_bitwise(amy):
+    """Tabulating each component over its dependencies changes no value."""
+    for w in [W.unicycle(nxy=31, horizon=6, target=(3.0, 5.0)), W.rooms7(n_per_dim=4, horizon=3),
+              W.traffic6(n_per_dim=5, horizon=2), W.served_stream(3)[2]]:
+        out = {}
+        for tmode in ["stored_factored", "stored_separable"]:
+            with amy.amy_build(w.problem, tmode=tmode, prec="fp32") as h:
+                out[tmode] = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
+        assert np.array_equal(out["stored_factored"][0], out["stored_separable"][0])
+        assert np.array_equal(out["stored_factored"][1], out["stored_separable"][1])
+
+
+def test_separable_rows_and_other_workloads(amy, robot_ref):
+    w, ref = robot_ref
+    compare_synthesis(amy, w, "stored_separable", "fp32", ref=ref)   # 41-wide rows: generic kernel
+    mism, worst = compare_rows(amy, W.unicycle(), "stored_separable", "fp32", n_pairs=2048)
+    assert mism == 0 and worst <= 2e-6
+    w3 = W.rooms7(n_per_dim=5, horizon=3)
+    compare_synthesis(amy, w3, "stored_separable", "fp32_kahan")
+    w5 = W.traffic6(n_per_dim=6, horizon=2)
+    compare_synthesis(amy, w5, "stored_separable", "fp32_kahan")
+    for w4 in W.served_stream(6):
+        w4.horizon = min(w4.horizon, 10)
+        compare_synthesis(amy, w4, "stored_separable", "fp32")
+
+
+@pytest.mark.parametrize("tmode", ["stored_full", "stored_factored", "stored_separable", "otf"])
+def test_rebuild_with_new_parameters(amy, tmode):
+    rng = np.random.default_rng(21)
+    w = W.random_affine(rng, 3, [9, 8, 7], 4, gamma=2e-2, horizon=4)
+    w2 = W.random_affine(np.random.default_rng(22), 3, [9, 8, 7], 4, gamma=2e-2, horizon=4)
+    w2.problem.sigma = w.problem.sigma
+    ref2 = oracle.synthesize(w2.problem, w.spec, w.horizon)
+    with amy.amy_build(w.problem, tmode=tmode, prec="fp32") as h:
+        amy.amy_synthesize(h, w.spec, w.horizon)
+        amy.amy_rebuild(h, w2.problem.params)
+        V, _ = amy.amy_synthesize(h, w.spec, w.horizon)
+    assert np.max(np.abs(V - ref2["V"])) <= TOL["fp32"]
+
+
+def test_random_shapes_separable(amy):
+    for n, per_dim, window, gamma in [(1, [37], None, 5e-2), (4, [5, 6, 7, 5], [3, 3, 3, 3], 0.0),
+                                      (5, [4, 5, 4, 5, 3], None, 0.2), (8, [3] * 8, [3] * 8, 0.0),
+                                      (2, [11, 13], [7, 5], 0.0)]:
+        for kind in [W.SAFETY, W.REACH_AVOID]:
+            w = W.random_affine(np.random.default_rng(300 + n), n, per_dim, 3, gamma=gamma, window=window,
+                                kind=kind, horizon=3)
+            compare_synthesis(amy, w, "stored_separable", "fp32")
+            compare_synthesis(amy, w, "otf", "fp32_kahan", v_store="u16")
+
+
+def test_graph_replay_matches_direct_launches(amy):
+    import torch
+    w = W.unicycle(nxy=31, horizon=9, target=(3.0, 5.0))
+    w2 = W.unicycle(nxy=31, horizon=9, target=(1.0, 2.0))
+    with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32", use_graphs=True) as h:
+        Vh, pih = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)   # host path, no graph
+        V = torch.empty(w.problem.n_states, dtype=torch.float32, device="cuda")
+        PI = torch.empty((w.horizon, w.problem.n_states), dtype=torch.int16, device="cuda")
+        for _ in range(3):   # capture once, replay twice
+            amy.amy_synthesize(h, w.spec, w.horizon, V_out=V, policy_out=PI, policy_all_steps=True)
+            torch.cuda.synchronize()
+            assert np.array_equal(V.cpu().numpy(), Vh)
+            assert np.array_equal(PI.cpu().numpy().view(np.uint16), pih)
+        # a different spec must not replay the cached graph
+        V2h, _ = amy.amy_synthesize(h, w2.spec, w2.horizon)
+        amy.amy_synthesize(h, w2.spec, w2.horizon, V_out=V, policy_out=PI, policy_all_steps=True)
+        torch.cuda.synchronize()
+        assert np.array_equal(V.cpu().numpy(), V2h)
+
+
+def test_profiling_counts_kernels(amy):
+    w = W.unicycle(nxy=21, horizon=5, target=(2.0, 3.0))
+    with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32") as h:
+        amy.amy_set_profiling(h, True)
+        amy.amy_rebuild(h)
+        amy.amy_synthesize(h, w.spec, w.horizon)
+        kt = amy.amy_kernel_times(h)
+    assert kt["backup_launches"] == 5 and kt["build_launches"] == 1
+    assert kt["backup_ms"] > 0 and kt["build_ms"] > 0
+
+
+def test_auto_mode_picks_and_matches(amy):
+    """AMY_T_AUTO: tables for few dependencies, factored rows for dense systems."""
+    picks = {}
+    for w in W.served_stream(8, seed=W.SEED + 21):
+        w.horizon = min(w.horizon, 8)
+        with amy.amy_build(w.problem, tmode="auto", prec="fp32", device_mem_budget=4 << 30) as h:
+            picks[w.problem.name] = amy.amy_info(h)["tmode"]
+        compare_synthesis(amy, w, "auto", "fp32")
+    assert set(picks.values()) <= {0, 2, 3}
+    with amy.amy_build(W.unicycle().problem, tmode="auto", prec="fp32") as h:
+        assert amy.amy_info(h)["tmode"] == 3
