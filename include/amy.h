@@ -230,6 +230,39 @@ void amy_destroy(amy_handle h);
 const char *amy_last_error(void);
 
 /* ------------------------------------------------------------------------
+ * Synthesis without memory allocation.  This entry point has no counterpart
+ * in the paper; it serves callers that may not allocate device memory -- for
+ * example code whose device memory is owned entirely by its own pool or by
+ * another framework, or a latency-critical loop where an allocation could
+ * synchronise the device or fail.
+ *
+ * amy_synthesize_noalloc runs the same computation as amy_build with
+ * AMY_T_ON_THE_FLY followed by amy_synthesize (FP32 or FP32_KAHAN, V stored in
+ * FP32), writing V_0 (float) into V_out and pi_0 into policy_out (may be NULL;
+ * not written when horizon is 0); both are device pointers of n_states
+ * entries, ordered on cuda_stream (NULL = the legacy default stream).  It
+ * calls no cudaMalloc, cudaFree or other allocating routine: the system
+ * parameters, the per-state spec flags and the two value vectors live in one
+ * file-scope device array of AMY_NOALLOC_SCRATCH_BYTES, which every GPU that
+ * loads the library holds until the process exits.  A problem needs
+ * 8*n_params + n_states + 8*n_states bytes (each part rounded up to 256);
+ * larger problems return AMY_E_INVALID_ARG with a message naming the limit.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents; every entry a call reads is written earlier by the same
+ * call, so nothing needs clearing, but calls whose work overlaps on the GPU
+ * (on different streams or threads) race on it and must be serialised.  The
+ * parameters are copied from host memory during the call; the call returns
+ * once the work is enqueued.
+ * ------------------------------------------------------------------------ */
+#define AMY_NOALLOC_SCRATCH_BYTES (16u << 20)
+amy_status amy_synthesize_noalloc(const amy_system *sys, const amy_grid *states, const amy_grid *inputs,
+                                  const double *sigma, const amy_cut *cut, int32_t prec, const amy_spec *spec,
+                                  int32_t horizon, float *V_out, uint16_t *policy_out, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Serving: continuous batching of independent synthesis requests.
  * A scheduler thread admits queued requests while slots and device memory
  * allow, keeps each admitted problem's V ping-pong buffers resident, and

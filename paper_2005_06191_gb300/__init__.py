@@ -285,13 +285,30 @@ def amy_destroy(h: AmyHandle) -> None:
     h.close()
 
 
+def amy_synthesize_noalloc(problem, spec, horizon: int, V_out, policy_out=None, prec: str = "fp32",
+                           stream=None) -> None:
+    """amy_synthesize_noalloc: on-the-fly synthesis whose intermediate device
+    memory is the library's fixed scratch array (no allocation).  V_out
+    (float32) and policy_out (16-bit, may be None) are torch CUDA tensors of
+    n_states entries; the work is enqueued on `stream` (None: torch's current
+    stream)."""
+    k = _Keep()
+    sysd, states, inputs, sigma, cut = _problem_structs(k, problem)
+    s = _spec_struct(k, spec)
+    st = C.c_void_p(stream) if stream is not None else _current_stream_ptr()
+    pp = C.c_void_p(policy_out.data_ptr()) if policy_out is not None else C.c_void_p(0)
+    _check(_lib().amy_synthesize_noalloc(C.byref(sysd), C.byref(states), C.byref(inputs), sigma, C.byref(cut),
+                                         PRECS[prec], C.byref(s), int(horizon), C.c_void_p(V_out.data_ptr()), pp,
+                                         st))
+
+
 from .serving import (AmyServer, amy_cancel, amy_poll, amy_result_free,  # noqa: E402
                       amy_server_create, amy_server_destroy, amy_server_stats, amy_submit, amy_wait)
 
 __all__ = [
     "AmyError", "AmyHandle", "AmyServer", "amy_build", "amy_synthesize", "amy_backup_step",
     "amy_query_rows", "amy_info", "amy_destroy", "amy_grid_count", "amy_last_error",
-    "amy_rebuild", "amy_set_profiling", "amy_kernel_times",
+    "amy_rebuild", "amy_set_profiling", "amy_kernel_times", "amy_synthesize_noalloc",
     "amy_server_create", "amy_submit", "amy_poll", "amy_wait", "amy_cancel", "amy_server_stats",
     "amy_server_destroy", "amy_result_free", "TMODES", "PRECS", "VSTORES", "POLICY_NONE",
 ]

@@ -89,6 +89,9 @@ PROTOTYPES = {
                                      C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "amy_destroy": (None, [C.c_void_p]),
     "amy_last_error": (C.c_char_p, []),
+    "amy_synthesize_noalloc": (C.c_int32, [C.POINTER(amy_system), C.POINTER(amy_grid), C.POINTER(amy_grid), DP,
+                                           C.POINTER(amy_cut), C.c_int32, C.POINTER(amy_spec), C.c_int32,
+                                           C.c_void_p, C.c_void_p, C.c_void_p]),
     "amy_server_create": (C.c_int32, [C.POINTER(amy_server_opts), C.POINTER(C.c_void_p)]),
     "amy_submit": (C.c_int32, [C.c_void_p, C.POINTER(amy_request), C.POINTER(C.c_uint64)]),
     "amy_poll": (C.c_int32, [C.c_void_p, C.c_uint64, C.POINTER(amy_result)]),

@@ -1,0 +1,222 @@
+// amy_noalloc.cu -- amy_synthesize_noalloc: finite-horizon synthesis with
+// rows on the fly for callers that may not allocate memory.
+//
+// Who needs it: code that must not call cudaMalloc, cudaMallocAsync or any
+// other allocator -- for example a caller whose device memory is entirely
+// owned by its own pool or by another framework, or a latency-critical loop
+// where an allocation could synchronise the device or fail.  Such a caller
+// passes its problem and its own device output buffers; every piece of
+// intermediate device memory the synthesis needs (the system parameters, the
+// per-state spec flags and the two value vectors the backups ping-pong
+// between) lives in one file-scope device array, `g_noalloc_scratch`, of
+// AMY_NOALLOC_SCRATCH_BYTES.  Every GPU that loads the library holds that
+// array until the process exits.
+//
+// The array is shared by all calls on a device and keeps the last call's
+// contents.  Every entry a call reads is written earlier by that same call
+// (the spec-mask kernel writes every flag and V_N, each backup writes every
+// V_k), so nothing has to start at zero.  Calls whose work overlaps on the GPU
+// (e.g. on two streams at once) race on the array; serialise them.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/amy.h"
+#include "amy_internal.h"
+
+namespace amy {
+
+// Scratch for amy_synthesize_noalloc (see the file comment).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[AMY_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device: looked up once
+// per device, with that device current, on the first call there.
+amy_status scratch_address(int dev, unsigned char **out) {
+    if (dev < 0 || dev >= kMaxDevices) return set_error(AMY_E_UNSUPPORTED, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "scratch symbol address");
+        g_scratch_addr[dev] = p;
+    }
+    *out = (unsigned char *)g_scratch_addr[dev];
+    return AMY_OK;
+}
+
+size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Problem validation and geometry for this entry point, with no heap use:
+// the same checks and the same FP64 window-shape expressions as amy_build.
+amy_status geom_noheap(const amy_system *sys, const amy_grid *st, const amy_grid *in, const double *sigma,
+                       const amy_cut *cut, Geom &g) {
+    if (!sys || !st || !in || !sigma || !cut) return set_error(AMY_E_INVALID_ARG, "null argument");
+    const int n = st->n, m = in->n;
+    if (n < 1 || n > MAXD || m < 1 || m > MAXD) return set_error(AMY_E_INVALID_ARG, "dims must be 1..8");
+    if (sys->n != n || sys->m != m) return set_error(AMY_E_INVALID_ARG, "system dims differ from grids");
+    if (!st->lb || !st->eta || !st->count || !in->lb || !in->eta || !in->count)
+        return set_error(AMY_E_INVALID_ARG, "null grid array");
+    memset(&g, 0, sizeof g);
+    g.n = n;
+    g.m = m;
+    int64_t nx = 1, nu = 1;
+    for (int d = 0; d < n; ++d) {
+        if (st->count[d] < 1 || !(st->eta[d] > 0.0) || !std::isfinite(st->lb[d]) || !std::isfinite(st->eta[d]))
+            return set_error(AMY_E_INVALID_ARG, "bad state grid in dim %d", d);
+        if (!(sigma[d] > 0.0) || !std::isfinite(sigma[d]))
+            return set_error(AMY_E_INVALID_ARG, "sigma[%d] must be positive", d);
+        g.N[d] = st->count[d];
+        g.lb[d] = st->lb[d];
+        g.eta[d] = st->eta[d];
+        if (st->periodic && st->periodic[d]) g.periodic |= 1u << d;
+        nx *= st->count[d];
+        if (nx > 2147483647LL) return set_error(AMY_E_INVALID_ARG, "more than 2^31-1 states");
+    }
+    for (int d = 0; d < m; ++d) {
+        if (in->count[d] < 1 || !(in->eta[d] > 0.0)) return set_error(AMY_E_INVALID_ARG, "bad input grid in dim %d", d);
+        g.ucount[d] = in->count[d];
+        g.ulb[d] = in->lb[d];
+        g.ueta[d] = in->eta[d];
+        nu *= in->count[d];
+        if (nu > 65535) return set_error(AMY_E_INVALID_ARG, "more than 65535 inputs");
+    }
+    g.nx = (int32_t)nx;
+    g.nu = (int32_t)nu;
+    int64_t s = 1;
+    for (int d = n - 1; d >= 0; --d) {
+        g.stride[d] = (int32_t)s;
+        s *= g.N[d];
+    }
+    if (sys->kind == AMY_SYS_AFFINE_PER_INPUT) {
+        if (!sys->params || sys->n_params != nu * (int64_t)(n * n + n))
+            return set_error(AMY_E_INVALID_ARG, "affine system needs n_u*(n*n+n) params");
+        g.sys = SYS_AFFINE;
+    } else if (sys->kind == AMY_SYS_UNICYCLE) {
+        if (n != 3 || m != 2 || !sys->params || sys->n_params < 1)
+            return set_error(AMY_E_INVALID_ARG, "unicycle needs n=3, m=2, params={tau}");
+        g.sys = SYS_UNICYCLE;
+    } else {
+        return set_error(AMY_E_INVALID_ARG, "unknown system kind %d", sys->kind);
+    }
+    for (int64_t i = 0; i < sys->n_params; ++i)
+        if (!std::isfinite(sys->params[i])) return set_error(AMY_E_INVALID_ARG, "non-finite system parameter");
+    int64_t wtot = 1;
+    int32_t wsum = 0;
+    for (int d = 0; d < n; ++d) {
+        const bool per = (g.periodic >> d) & 1u;
+        g.k2[d] = sigma[d] * std::sqrt(2.0);
+        g.rk2f[d] = (float)(1.0 / (sigma[d] * std::sqrt(2.0)));
+        if (cut->window) {
+            g.wmode = WM_EXPLICIT;
+            const int32_t W = cut->window[d];
+            if (W < 1 || (W % 2) == 0) return set_error(AMY_E_INVALID_ARG, "explicit window must be odd (dim %d)", d);
+            if (per && W > g.N[d]) return set_error(AMY_E_INVALID_ARG, "window wider than periodic dim %d", d);
+            g.W[d] = W;
+            g.xs[d] = INFINITY;
+        } else if (cut->gamma == 0.0) {
+            g.wmode = WM_DENSE;
+            if (per) return set_error(AMY_E_INVALID_ARG, "dense rows need non-periodic dims");
+            g.W[d] = g.N[d];
+            g.xs[d] = INFINITY;
+        } else {
+            g.wmode = WM_GAMMA;
+            if (!(cut->gamma > 0.0) || !std::isfinite(cut->gamma)) return set_error(AMY_E_INVALID_ARG, "bad gamma");
+            const double arg = 1.0 / (cut->gamma * sigma[d] * std::sqrt(2.0 * M_PI));
+            if (!(arg > 1.0)) return set_error(AMY_E_INVALID_ARG, "gamma at or above the peak density (dim %d)", d);
+            const double xs = sigma[d] * std::sqrt(2.0 * std::log(arg));
+            const double w = std::floor(2.0 * xs / g.eta[d]) + 1.0;
+            if (!(w >= 1.0) || w > 1.0e6) return set_error(AMY_E_INVALID_ARG, "bad window width (dim %d)", d);
+            g.W[d] = (int32_t)w;
+            if (per && g.W[d] > g.N[d]) return set_error(AMY_E_INVALID_ARG, "window wider than periodic dim %d", d);
+            g.xs[d] = xs;
+        }
+        wtot *= g.W[d];
+        wsum += g.W[d];
+        if (wtot > (1LL << 30)) return set_error(AMY_E_UNSUPPORTED, "window box too large");
+    }
+    if (wsum > MAXWS) return set_error(AMY_E_UNSUPPORTED, "sum of window widths %d exceeds %d", wsum, MAXWS);
+    g.wtot = (int32_t)wtot;
+    g.wsum = wsum;
+    return AMY_OK;
+}
+
+}  // namespace
+}  // namespace amy
+
+using namespace amy;
+
+extern "C" amy_status amy_synthesize_noalloc(const amy_system *sys, const amy_grid *states, const amy_grid *inputs,
+                                             const double *sigma, const amy_cut *cut, int32_t prec,
+                                             const amy_spec *spec, int32_t horizon, float *V_out,
+                                             uint16_t *policy_out, void *cuda_stream) {
+    if (!V_out) return set_error(AMY_E_INVALID_ARG, "null V_out");
+    if (horizon < 0) return set_error(AMY_E_INVALID_ARG, "negative horizon");
+    if (prec != AMY_PREC_FP32 && prec != AMY_PREC_FP32_KAHAN)
+        return set_error(AMY_E_UNSUPPORTED, "amy_synthesize_noalloc runs in FP32 or FP32_KAHAN");
+    Geom g;
+    amy_status st = geom_noheap(sys, states, inputs, sigma, cut, g);
+    if (st != AMY_OK) return st;
+    SpecDev sd;
+    st = make_spec(g, spec, sd);
+    if (st != AMY_OK) return st;
+    // scratch layout: parameters | spec flags | V ping-pong (FP32)
+    const size_t nx = (size_t)g.nx;
+    const size_t pbytes = up256((size_t)sys->n_params * sizeof(double));
+    const size_t mbytes = up256(nx);
+    const size_t vbytes = up256(nx * sizeof(float));
+    const size_t need = pbytes + mbytes + 2 * vbytes;
+    if (need > (size_t)AMY_NOALLOC_SCRATCH_BYTES)
+        return set_error(AMY_E_INVALID_ARG,
+                         "problem needs %zu bytes of scratch (parameters, flags, two value vectors); "
+                         "amy_synthesize_noalloc holds at most %zu -- use amy_build/amy_synthesize",
+                         need, (size_t)AMY_NOALLOC_SCRATCH_BYTES);
+    int dev = 0, sm_count = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_error(e, "device query");
+    unsigned char *base = nullptr;
+    st = scratch_address(dev, &base);
+    if (st != AMY_OK) return st;
+    double *d_params = (double *)base;
+    uint8_t *d_mask = base + pbytes;
+    float *d_V[2] = {(float *)(base + pbytes + mbytes), (float *)(base + pbytes + mbytes + vbytes)};
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    g.params = d_params;
+    e = cudaMemcpyAsync(d_params, sys->params, (size_t)sys->n_params * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_error(e, "parameter upload");
+    st = launch_spec_mask(g, sd, d_mask, d_V[0], AMY_V_NATIVE, s);
+    if (st != AMY_OK) return st;
+    const bool fast = fast_wm(g, prec) > 0;
+    int cur = 0;
+    for (int32_t k = horizon - 1; k >= 0; --k) {
+        FastCall c;
+        c.Vn = d_V[cur];
+        c.Vo = d_V[cur ^ 1];
+        c.Vfinal = (k == 0) ? V_out : nullptr;
+        c.pi = (k == 0) ? policy_out : nullptr;
+        c.mask = d_mask;
+        c.spec_kind = sd.kind;
+        c.kahan = prec == AMY_PREC_FP32_KAHAN;
+        c.T = nullptr;
+        c.O = nullptr;
+        c.npairs = 0;
+        c.tab = nullptr;
+        c.ulanes = 0;
+        st = fast ? launch_backup_fast(g, TM_OTF, AMY_V_NATIVE, c, sm_count, s)
+                  : launch_backup_generic_fp32(g, TM_OTF, c, AMY_V_NATIVE, sm_count, s);
+        if (st != AMY_OK) return st;
+        cur ^= 1;
+    }
+    if (horizon == 0) {
+        e = cudaMemcpyAsync(V_out, d_V[0], nx * sizeof(float), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_error(e, "V_N copy");
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? AMY_OK : cuda_error(e, "synthesize (no allocation)");
+}
