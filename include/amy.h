@@ -245,15 +245,17 @@ const char *amy_last_error(void);
  * parameters, the per-state spec flags and the two value vectors live in one
  * file-scope device array of AMY_NOALLOC_SCRATCH_BYTES, which every GPU that
  * loads the library holds until the process exits.  A problem needs
- * 8*n_params + n_states + 8*n_states bytes (each part rounded up to 256);
- * larger problems return AMY_E_INVALID_ARG with a message naming the limit.
+ * 8*n_params + n_states + 2*4*(n_states + 32) bytes (each part rounded up to
+ * 256); larger problems return AMY_E_INVALID_ARG with a message naming the
+ * limit.
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
  * before any stream capture.  All calls share the array and it keeps the last
  * call's contents; every entry a call reads is written earlier by the same
- * call, so nothing needs clearing, but calls whose work overlaps on the GPU
- * (on different streams or threads) race on it and must be serialised.  The
+ * call (it clears the few guard cells around its value vectors itself), but
+ * calls whose work overlaps on the GPU (on different streams or threads) race
+ * on it and must be serialised.  The
  * parameters are copied from host memory during the call; the call returns
  * once the work is enqueued.
  * ------------------------------------------------------------------------ */

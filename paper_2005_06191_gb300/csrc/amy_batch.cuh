@@ -19,7 +19,7 @@ namespace amy {
 
 constexpr size_t kGeomSmemBytes = (sizeof(Geom) + 15) / 16 * 16;
 
-template <class VT, int WM, int TM, bool EXACT>
+template <class VT, int WM, int TM, int VAR>
 __global__ void __launch_bounds__(FAST_THREADS) k_step_group(const BatchEntry *__restrict__ entries, int32_t n_entries,
                                                              int64_t total_tiles, int32_t *__restrict__ counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -72,16 +72,16 @@ __global__ void __launch_bounds__(FAST_THREADS) k_step_group(const BatchEntry *_
         a.O = e.O;
         a.npairs = e.npairs;
         a.tab = e.tab;
-        backup_tile<VT, WM, TM, EXACT>(sg, a, t - e.tile_begin, work);
+        backup_tile<VT, WM, TM, VAR>(sg, a, t - e.tile_begin, work);
         __syncthreads();
     }
 }
 
-template <class VT, int WM, int TM, bool EXACT>
+template <class VT, int WM, int TM, int VAR>
 amy_status launch_group_t(const BatchEntry *d_entries, int32_t n, int64_t tiles, int32_t *counter, int max_n,
                           int sm_count, cudaStream_t st) {
     const size_t smem = kGeomSmemBytes + fast_smem_bytes(max_n, WM);
-    auto kern = k_step_group<VT, WM, TM, EXACT>;
+    auto kern = k_step_group<VT, WM, TM, VAR>;
     static size_t raised = 48 * 1024;
     if (smem > raised) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -100,24 +100,30 @@ amy_status launch_group_t(const BatchEntry *d_entries, int32_t n, int64_t tiles,
     return e == cudaSuccess ? AMY_OK : cuda_error(e, "batched step launch");
 }
 
+template <class VT, int WM, int TM>
+amy_status launch_group_var(int var, const BatchEntry *d, int32_t n, int64_t tiles, int32_t *counter, int max_n,
+                            int sm, cudaStream_t st) {
+    if (var == VAR_EXACT_CONTIG) return launch_group_t<VT, WM, TM, VAR_EXACT_CONTIG>(d, n, tiles, counter, max_n, sm, st);
+    if (var == VAR_EXACT) return launch_group_t<VT, WM, TM, VAR_EXACT>(d, n, tiles, counter, max_n, sm, st);
+    return launch_group_t<VT, WM, TM, VAR_GENERAL>(d, n, tiles, counter, max_n, sm, st);
+}
+
 template <class VT, int WM>
-amy_status launch_group_tm(int tm, bool exact, const BatchEntry *d, int32_t n, int64_t tiles, int32_t *counter,
+amy_status launch_group_tm(int tm, int var, const BatchEntry *d, int32_t n, int64_t tiles, int32_t *counter,
                            int max_n, int sm, cudaStream_t st) {
-    if (tm == TM_OTF)
-        return exact ? launch_group_t<VT, WM, TM_OTF, true>(d, n, tiles, counter, max_n, sm, st)
-                     : launch_group_t<VT, WM, TM_OTF, false>(d, n, tiles, counter, max_n, sm, st);
-    if (tm == TM_FACTORED) return launch_group_t<VT, WM, TM_FACTORED, false>(d, n, tiles, counter, max_n, sm, st);
-    return exact ? launch_group_t<VT, WM, TM_SEPARABLE, true>(d, n, tiles, counter, max_n, sm, st)
-                 : launch_group_t<VT, WM, TM_SEPARABLE, false>(d, n, tiles, counter, max_n, sm, st);
+    if (tm == TM_OTF) return launch_group_var<VT, WM, TM_OTF>(var, d, n, tiles, counter, max_n, sm, st);
+    if (tm == TM_FACTORED)
+        return launch_group_t<VT, WM, TM_FACTORED, VAR_GENERAL>(d, n, tiles, counter, max_n, sm, st);
+    return launch_group_var<VT, WM, TM_SEPARABLE>(var, d, n, tiles, counter, max_n, sm, st);
 }
 
 template <class VT>
-amy_status launch_group_vt(int wm, int tm, bool exact, const BatchEntry *d, int32_t n, int64_t tiles,
+amy_status launch_group_vt(int wm, int tm, int var, const BatchEntry *d, int32_t n, int64_t tiles,
                            int32_t *counter, int max_n, int sm, cudaStream_t st) {
     if (n <= 0 || tiles <= 0) return AMY_OK;
-    if (wm == 3) return launch_group_tm<VT, 3>(tm, exact, d, n, tiles, counter, max_n, sm, st);
-    if (wm == 5) return launch_group_tm<VT, 5>(tm, exact, d, n, tiles, counter, max_n, sm, st);
-    return launch_group_tm<VT, 8>(tm, exact, d, n, tiles, counter, max_n, sm, st);
+    if (wm == 3) return launch_group_tm<VT, 3>(tm, var, d, n, tiles, counter, max_n, sm, st);
+    if (wm == 5) return launch_group_tm<VT, 5>(tm, var, d, n, tiles, counter, max_n, sm, st);
+    return launch_group_tm<VT, 8>(tm, var, d, n, tiles, counter, max_n, sm, st);
 }
 
 }  // namespace amy

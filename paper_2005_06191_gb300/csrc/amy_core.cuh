@@ -53,8 +53,8 @@ struct Geom {
     // mean component d depends only on the state dims j with tsx[d][j] != 0
     // and the input dims i with tsu[d][i] != 0, so its window origin and
     // masses are tabulated over those coordinates.  Record e of table d sits
-    // at word toff[d] + e*trw[d]: the origin (int32), W[d] masses (FP32), then
-    // the W[d] cell offsets (cell index * stride, clamped or wrapped; int32).
+    // at word toff[d] + e*trw[d]: the window origin (int32) then the W[d]
+    // masses (FP32), padded to a multiple of 4 words.
     // The input part of every table index, sum_i u_i * tsu[d][i], is stored
     // per input u at word uoff + u*urw (one int32 per dim).
     int32_t tsx[MAXD][MAXD];

@@ -244,25 +244,28 @@ amy_status plan_sep_tables(Geom &g, const std::vector<double> &params, int64_t &
     }
     int64_t off = 0;
     for (int d = 0; d < n; ++d) {
+        // state coordinates fastest: lanes of a warp (consecutive states, one
+        // input) then read consecutive records
         int64_t st = 1;
+        for (int j = n - 1; j >= 0; --j) {
+            g.tsx[d][j] = 0;
+            if (Sx[d] & (1u << j)) {
+                g.tsx[d][j] = (int32_t)st;
+                st *= g.N[j];
+                if (st > 2147483647LL) return set_error(AMY_E_UNSUPPORTED, "table of dim %d too large", d);
+            }
+        }
         for (int i = m - 1; i >= 0; --i) {
             g.tsu[d][i] = 0;
             if (Su[d] & (1u << i)) {
+                if (st > 2147483647LL) return set_error(AMY_E_UNSUPPORTED, "table of dim %d too large", d);
                 g.tsu[d][i] = (int32_t)st;
                 st *= g.ucount[i];
             }
         }
-        for (int j = n - 1; j >= 0; --j) {
-            g.tsx[d][j] = 0;
-            if (Sx[d] & (1u << j)) {
-                if (st > 2147483647LL) return set_error(AMY_E_UNSUPPORTED, "table of dim %d too large", d);
-                g.tsx[d][j] = (int32_t)st;
-                st *= g.N[j];
-            }
-        }
         if (st > 2147483647LL) return set_error(AMY_E_UNSUPPORTED, "table of dim %d too large", d);
         g.tent[d] = (int32_t)st;
-        g.trw[d] = ((1 + 2 * g.W[d]) + 3) / 4 * 4;
+        g.trw[d] = ((1 + g.W[d]) + 3) / 4 * 4;
         g.toff[d] = off;
         off += st * g.trw[d];
     }
@@ -311,7 +314,8 @@ struct amy_handle_s {
     void *d_T;
     int16_t *d_O;
     int64_t npairs;
-    void *d_V[2];
+    void *d_V[2];         // V ping-pong (interior start)
+    void *d_Vbase[2];     // allocations: kVGuard finite guard cells on each side
     uint8_t *d_mask;
     uint32_t *d_tab;      // per-dimension tables (separable stored mode)
     int64_t tab_words;
@@ -355,8 +359,8 @@ void free_handle(amy_handle_s *h) {
     cudaFree(h->d_params);
     cudaFree(h->d_T);
     cudaFree(h->d_O);
-    cudaFree(h->d_V[0]);
-    cudaFree(h->d_V[1]);
+    cudaFree(h->d_Vbase[0]);
+    cudaFree(h->d_Vbase[1]);
     cudaFree(h->d_mask);
     cudaFree(h->d_tab);
     for (auto &p : h->ev_backup) h->ev_pool.push_back(p.first), h->ev_pool.push_back(p.second);
@@ -598,8 +602,16 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     } while (0)
     TRY(dev_alloc(h, (void **)&h->d_params, params.size() * sizeof(double), "params"));
     h->g.params = h->d_params;
-    TRY(dev_alloc(h, &h->d_V[0], (size_t)g.nx * vsize(h), "V"));
-    TRY(dev_alloc(h, &h->d_V[1], (size_t)g.nx * vsize(h), "V"));
+    for (int i = 0; i < 2; ++i) {
+        const size_t vb = (size_t)(g.nx + 2 * kVGuard) * vsize(h);
+        TRY(dev_alloc(h, &h->d_Vbase[i], vb, "V"));
+        e = cudaMemsetAsync(h->d_Vbase[i], 0, vb, h->stream);
+        if (e != cudaSuccess) {
+            free_handle(h);
+            return cuda_error(e, "V guard init");
+        }
+        h->d_V[i] = (char *)h->d_Vbase[i] + kVGuard * vsize(h);
+    }
     TRY(dev_alloc(h, (void **)&h->d_mask, (size_t)g.nx, "mask"));
     if (h->tmode == AMY_T_STORED_SEPARABLE) {
         std::vector<int32_t> upart;

@@ -8,12 +8,12 @@
 namespace amy {
 
 template <class VT>
-amy_status launch_fast_vt(const Geom &g, int wm, bool exact, int tmode, const FastCall &c, int sm_count,
+amy_status launch_fast_vt(const Geom &g, int wm, int var, int tmode, const FastCall &c, int sm_count,
                           cudaStream_t st);
-extern template amy_status launch_fast_vt<float>(const Geom &, int, bool, int, const FastCall &, int, cudaStream_t);
-extern template amy_status launch_fast_vt<unorm16>(const Geom &, int, bool, int, const FastCall &, int,
+extern template amy_status launch_fast_vt<float>(const Geom &, int, int, int, const FastCall &, int, cudaStream_t);
+extern template amy_status launch_fast_vt<unorm16>(const Geom &, int, int, int, const FastCall &, int,
                                                    cudaStream_t);
-extern template amy_status launch_fast_vt<__nv_bfloat16>(const Geom &, int, bool, int, const FastCall &, int,
+extern template amy_status launch_fast_vt<__nv_bfloat16>(const Geom &, int, int, int, const FastCall &, int,
                                                          cudaStream_t);
 
 int fast_wm(const Geom &g, int prec) {
@@ -26,15 +26,22 @@ int fast_wm(const Geom &g, int prec) {
     return wm;
 }
 
+int fast_variant(const Geom &g, int wm, int tmode) {
+    if (tmode == TM_FACTORED) return VAR_GENERAL;
+    bool exact = true;
+    for (int d = 0; d < g.n; ++d) exact = exact && g.W[d] == wm;
+    if (!exact) return VAR_GENERAL;
+    return ((g.periodic >> (g.n - 1)) & 1u) ? VAR_EXACT : VAR_EXACT_CONTIG;
+}
+
 amy_status launch_backup_fast(const Geom &g, int tmode, int v_store, const FastCall &c, int sm_count,
                               cudaStream_t st) {
     const int wm = fast_wm(g, AMY_PREC_FP32);
     if (wm == 0 || tmode == TM_FULL) return set_error(AMY_E_UNSUPPORTED, "fast backup not applicable");
-    bool exact = true;
-    for (int d = 0; d < g.n; ++d) exact = exact && g.W[d] == wm;
-    if (v_store == AMY_V_BF16) return launch_fast_vt<__nv_bfloat16>(g, wm, exact, tmode, c, sm_count, st);
-    if (v_store == AMY_V_UNORM16) return launch_fast_vt<unorm16>(g, wm, exact, tmode, c, sm_count, st);
-    return launch_fast_vt<float>(g, wm, exact, tmode, c, sm_count, st);
+    const int var = fast_variant(g, wm, tmode);
+    if (v_store == AMY_V_BF16) return launch_fast_vt<__nv_bfloat16>(g, wm, var, tmode, c, sm_count, st);
+    if (v_store == AMY_V_UNORM16) return launch_fast_vt<unorm16>(g, wm, var, tmode, c, sm_count, st);
+    return launch_fast_vt<float>(g, wm, var, tmode, c, sm_count, st);
 }
 
 amy_status launch_build_sep(const Geom &g, uint32_t *tab, int sm_count, cudaStream_t st) {

@@ -18,6 +18,7 @@
 namespace amy {
 
 constexpr int FAST_THREADS = 256;
+enum FastVariant : int { VAR_GENERAL = 0, VAR_EXACT = 1, VAR_EXACT_CONTIG = 2 };
 
 template <class VT> struct FastArgs {
     const VT *Vn;        // V_{k+1}
@@ -80,12 +81,41 @@ __device__ __forceinline__ void dim_masses_reg(const Geom &g, int d, double mu, 
     }
 }
 
+// Cell offsets of a window starting at slot o: clamped on a bounded dim
+// (the clamped slots carry zero mass), wrapped on a periodic one (a single
+// modulo per dim, then at most one subtraction per slot since W <= N).
 template <int WM>
 __device__ __forceinline__ void dim_offsets_reg(const Geom &g, int d, int32_t o, int W, int32_t (&off)[WM]) {
+    const int32_t N = g.N[d], st = g.stride[d];
+    if ((g.periodic >> d) & 1u) {
+        int32_t w = o % N;
+        w = w < 0 ? w + N : w;
 #pragma unroll
-    for (int k = 0; k < WM; ++k) {
-        bool on;
-        off[k] = (k < W) ? cell_of(g, d, o + k, on) * g.stride[d] : 0;
+        for (int k = 0; k < WM; ++k) {
+            int32_t c = w + k;
+            c = c >= N ? c - N : c;
+            off[k] = (k < W) ? c * st : 0;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < WM; ++k) {
+            const int32_t c = min(max(o + k, 0), N - 1);
+            off[k] = (k < W) ? c * st : 0;
+        }
+    }
+}
+
+// Adds one window row's contribution with explicit rounding (no contraction
+// into a fused multiply-add), plainly or Kahan-compensated, so that every
+// kernel variant sums in exactly the same arithmetic.
+__device__ __forceinline__ void accum_row(float &acc, float &comp, float term, int kahan) {
+    if (kahan) {
+        const float y = __fsub_rn(term, comp);
+        const float t = __fadd_rn(acc, y);
+        comp = __fsub_rn(__fsub_rn(t, acc), y);
+        acc = t;
+    } else {
+        acc = __fadd_rn(acc, term);
     }
 }
 
@@ -120,11 +150,17 @@ __device__ __forceinline__ float inner_block(const VT *__restrict__ V, int32_t b
 }
 
 // One tile (tileX consecutive states, all inputs) of the fused backup.
-// EXACT: every window width equals WM, so all width guards fold away.
+// Kernel variants: VAR_GENERAL (widths up to WM), VAR_EXACT (every width
+// equals WM, so all width guards fold away), VAR_EXACT_CONTIG (also a bounded
+// innermost dim: its window row is read unclamped -- off-grid slots have zero
+// mass and the V buffers carry kVGuard finite guard cells on each side -- so
+// one base address plus immediate offsets reads the whole row).
 // g may live in kernel parameters or in shared memory (batched kernel).
-template <class VT, int WM, int TM, bool EXACT>
+template <class VT, int WM, int TM, int VAR>
 __device__ __forceinline__ void backup_tile(const Geom &g, const FastArgs<VT> &a, int64_t tile,
                                             unsigned char *smem_raw) {
+    constexpr bool EXACT = VAR >= VAR_EXACT;
+    constexpr bool CONTIG = VAR == VAR_EXACT_CONTIG;
     constexpr int BT = FAST_THREADS;
     const int tid = threadIdx.x;
     const int TX = a.tileX, UL = a.ulanes;
@@ -237,43 +273,40 @@ __device__ __forceinline__ void backup_tile(const Geom &g, const FastArgs<VT> &a
                     const int Wd = EXACT ? WM : g.W[d];
                     float fk[WM];
                     int32_t ok[WM];
+                    int32_t od = 0;  // window origin of this dim
                     if (TM == TM_OTF) {
-                        const int32_t o = origin_of(g, d, mu[d]);
-                        dim_masses_reg<WM>(g, d, mu[d], o, Wd, fk, ok);
+                        od = origin_of(g, d, mu[d]);
+                        dim_masses_reg<WM>(g, d, mu[d], od, Wd, fk, ok);
                     } else if (TM == TM_SEPARABLE) {
                         const int32_t e = es[d] + ui[d];
                         const uint4 *rec = reinterpret_cast<const uint4 *>(a.tab + g.toff[d] + (int64_t)e * g.trw[d]);
-                        constexpr int NQ = (2 * WM + 1 + 3) / 4;
+                        constexpr int NQ = (WM + 1 + 3) / 4;
                         uint32_t wds[NQ * 4];
 #pragma unroll
                         for (int q = 0; q < NQ; ++q) {
                             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                            if (q * 4 < 2 * Wd + 1) v = __ldg(rec + q);
+                            if (q * 4 < Wd + 1) v = __ldg(rec + q);
                             wds[q * 4 + 0] = v.x;
                             wds[q * 4 + 1] = v.y;
                             wds[q * 4 + 2] = v.z;
                             wds[q * 4 + 3] = v.w;
                         }
-                        // masses at words 1..Wd, offsets at words 1+Wd..2Wd (Wd <= WM)
+                        // origin at word 0, masses at words 1..Wd
 #pragma unroll
-                        for (int k = 0; k < WM; ++k) {
-                            fk[k] = (k < Wd) ? __uint_as_float(wds[1 + k]) : 0.0f;
-                            uint32_t ov = 0u;
-                            if (EXACT) {
-                                ov = wds[1 + WM + k];
-                            } else {
-#pragma unroll
-                                for (int w = 1; w <= WM; ++w)
-                                    if (w == Wd && k < Wd) ov = wds[1 + w + k];
-                            }
-                            ok[k] = (int32_t)ov;
-                        }
+                        for (int k = 0; k < WM; ++k) fk[k] = (k < Wd) ? __uint_as_float(wds[1 + k]) : 0.0f;
+                        od = (int32_t)wds[0];
+                        dim_offsets_reg<WM>(g, d, od, Wd, ok);
                     } else {  // TM_FACTORED
-                        const int32_t o = __ldg(a.O + d * a.npairs + pair);
+                        od = __ldg(a.O + d * a.npairs + pair);
 #pragma unroll
                         for (int k = 0; k < WM; ++k)
                             fk[k] = (k < Wd) ? __ldg(a.T + (int64_t)(fb + k) * a.npairs + pair) : 0.0f;
-                        dim_offsets_reg<WM>(g, d, o, Wd, ok);
+                        dim_offsets_reg<WM>(g, d, od, Wd, ok);
+                    }
+                    if (CONTIG && d == n - 1) {
+                        // bounded innermost dim (stride 1): unclamped, contiguous row
+#pragma unroll
+                        for (int k = 0; k < WM; ++k) ok[k] = od + k;
                     }
                     fb += Wd;
                     if (d < n - 3) {
@@ -316,7 +349,7 @@ __device__ __forceinline__ void backup_tile(const Geom &g, const FastArgs<VT> &a
                 // higher levels 0..DO-2 keep (k, prefix product, prefix offset) in shared memory
                 for (int e = 0; e < DH; ++e) {
                     sK[e * BT + tid] = 0;
-                    const float pe = (e > 0 ? sP[(e - 1) * BT + tid] : 1.0f) * sF[(e * WM) * BT + tid];
+                    const float pe = __fmul_rn(e > 0 ? sP[(e - 1) * BT + tid] : 1.0f, sF[(e * WM) * BT + tid]);
                     const int32_t be = (e > 0 ? sB[(e - 1) * BT + tid] : 0) + sO[(e * WM) * BT + tid];
                     sP[e * BT + tid] = pe;
                     sB[e * BT + tid] = be;
@@ -334,33 +367,19 @@ __device__ __forceinline__ void backup_tile(const Geom &g, const FastArgs<VT> &a
 #pragma unroll
                             for (int k = 0; k < WM; ++k) {
                                 if (k < WL) {
-                                    const float w = pw * tL[k];
-                                    const float term = w * inner_block<VT, WM>(
-                                                                a.Vn, pb + oL[k], tA, oA, WA, tB, oB, WB);
-                                    if (a.kahan) {
-                                        const float y = term - comp;
-                                        const float t = acc + y;
-                                        comp = (t - acc) - y;
-                                        acc = t;
-                                    } else {
-                                        acc += term;
-                                    }
+                                    const float w = __fmul_rn(pw, tL[k]);
+                                    const float term = __fmul_rn(w, inner_block<VT, WM>(
+                                                                          a.Vn, pb + oL[k], tA, oA, WA, tB, oB, WB));
+                                    accum_row(acc, comp, term, a.kahan);
                                 }
                             }
                         } else {
                             for (int k = 0; k < WL; ++k) {
-                                const float w = pw * sel_reg<WM>(tL, k);
+                                const float w = __fmul_rn(pw, sel_reg<WM>(tL, k));
                                 if (w != 0.0f) {
-                                    const float term = w * inner_block<VT, WM>(
-                                                                a.Vn, pb + sel_reg<WM>(oL, k), tA, oA, WA, tB, oB, WB);
-                                    if (a.kahan) {
-                                        const float y = term - comp;
-                                        const float t = acc + y;
-                                        comp = (t - acc) - y;
-                                        acc = t;
-                                    } else {
-                                        acc += term;
-                                    }
+                                    const float term = __fmul_rn(w, inner_block<VT, WM>(
+                                                                          a.Vn, pb + sel_reg<WM>(oL, k), tA, oA, WA, tB, oB, WB));
+                                    accum_row(acc, comp, term, a.kahan);
                                 }
                             }
                         }
@@ -378,7 +397,7 @@ __device__ __forceinline__ void backup_tile(const Geom &g, const FastArgs<VT> &a
                     if (e < 0) break;
                     for (int q = e; q < DH; ++q) {
                         const int kq = sK[q * BT + tid];
-                        sP[q * BT + tid] = (q > 0 ? sP[(q - 1) * BT + tid] : 1.0f) * sF[(q * WM + kq) * BT + tid];
+                        sP[q * BT + tid] = __fmul_rn(q > 0 ? sP[(q - 1) * BT + tid] : 1.0f, sF[(q * WM + kq) * BT + tid]);
                         sB[q * BT + tid] = (q > 0 ? sB[(q - 1) * BT + tid] : 0) + sO[(q * WM + kq) * BT + tid];
                     }
                 }
@@ -415,11 +434,11 @@ __device__ __forceinline__ void backup_tile(const Geom &g, const FastArgs<VT> &a
     }
 }
 
-template <class VT, int WM, int TM, bool EXACT>
+template <class VT, int WM, int TM, int VAR>
 __global__ void __launch_bounds__(FAST_THREADS) k_backup_fast(const __grid_constant__ Geom g,
                                                               const FastArgs<VT> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    backup_tile<VT, WM, TM, EXACT>(g, a, blockIdx.x, smem_raw);
+    backup_tile<VT, WM, TM, VAR>(g, a, blockIdx.x, smem_raw);
 }
 
 // Per-dimension table construction (separable stored mode): record e of
@@ -460,11 +479,8 @@ static __global__ void k_build_sep(const __grid_constant__ Geom g, uint32_t *__r
         uint32_t *rec = tab + g.toff[d] + e * g.trw[d];
         const int Wd = g.W[d];
         rec[0] = (uint32_t)o;
-        for (int k = 0; k < Wd; ++k) {
-            rec[1 + k] = __float_as_uint(fac[k]);
-            rec[1 + Wd + k] = (uint32_t)off[k];
-        }
-        for (int k = 1 + 2 * Wd; k < g.trw[d]; ++k) rec[k] = 0u;
+        for (int k = 0; k < Wd; ++k) rec[1 + k] = __float_as_uint(fac[k]);
+        for (int k = 1 + Wd; k < g.trw[d]; ++k) rec[k] = 0u;
     }
 }
 

@@ -6,16 +6,17 @@
 
 #include "amy_fast.cuh"
 #include "amy_internal.h"
+#include "amy_staged.cuh"
 
 namespace amy {
 
 template <class VT>
-amy_status launch_fast_vt(const Geom &g, int wm, bool exact, int tmode, const FastCall &c, int sm_count,
+amy_status launch_fast_vt(const Geom &g, int wm, int var, int tmode, const FastCall &c, int sm_count,
                           cudaStream_t st);
 
 namespace fastimpl {
 
-template <class VT, int WM, int TM, bool EXACT>
+template <class VT, int WM, int TM, int VAR>
 amy_status launch_t(const Geom &g, const FastCall &c, int sm_count, cudaStream_t st) {
     FastArgs<VT> a;
     a.Vn = (const VT *)c.Vn;
@@ -34,7 +35,7 @@ amy_status launch_t(const Geom &g, const FastCall &c, int sm_count, cudaStream_t
     a.ulanes = c.ulanes > 0 ? c.ulanes : fast_default_ulanes(g, sm_count);
     a.tileX = FAST_THREADS / a.ulanes;
     const size_t smem = fast_smem_bytes(g.n, WM);
-    auto kern = k_backup_fast<VT, WM, TM, EXACT>;
+    auto kern = k_backup_fast<VT, WM, TM, VAR>;
     if (smem > 48 * 1024) {
         static bool raised = false;
         if (!raised) {
@@ -49,26 +50,69 @@ amy_status launch_t(const Geom &g, const FastCall &c, int sm_count, cudaStream_t
     return e == cudaSuccess ? AMY_OK : cuda_error(e, "fast backup launch");
 }
 
+// Staged variant (low-dimensional problems, exact widths): window boxes in
+// shared memory.
+template <class VT, int WM, int TM, int NS>
+amy_status launch_staged_ns(const Geom &g, const FastCall &c, int sm_count, cudaStream_t st) {
+    FastArgs<VT> a;
+    a.Vn = (const VT *)c.Vn;
+    a.Vo = (VT *)c.Vo;
+    a.Vfinal = c.Vfinal;
+    a.pi = c.pi;
+    a.mask = c.mask;
+    a.spec_kind = c.spec_kind;
+    a.kahan = c.kahan;
+    a.T = c.T;
+    a.O = c.O;
+    a.npairs = c.npairs;
+    a.tab = c.tab;
+    a.ulanes = c.ulanes > 0 ? c.ulanes : fast_default_ulanes(g, sm_count);
+    a.tileX = FAST_THREADS / a.ulanes;
+    const size_t smem = staged_smem_bytes(g.n, WM);
+    auto kern = k_backup_staged<VT, WM, TM, NS>;
+    static bool raised = false;
+    if (!raised) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return cuda_error(e, "staged backup smem attribute");
+        raised = true;
+    }
+    const int64_t blocks = ((int64_t)g.nx + a.tileX - 1) / a.tileX;
+    kern<<<(unsigned)blocks, FAST_THREADS, smem, st>>>(g, a);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AMY_OK : cuda_error(e, "staged backup launch");
+}
+
+template <class VT, int WM, int TM>
+amy_status launch_var(const Geom &g, int var, const FastCall &c, int sm, cudaStream_t st) {
+    if constexpr (WM <= 5 && TM == TM_SEPARABLE) {
+        if (var >= VAR_EXACT && g.n <= 3 && !c.no_stage) {
+            if (g.n == 1) return launch_staged_ns<VT, WM, TM, 1>(g, c, sm, st);
+            if (g.n == 2) return launch_staged_ns<VT, WM, TM, 2>(g, c, sm, st);
+            return launch_staged_ns<VT, WM, TM, 3>(g, c, sm, st);
+        }
+    }
+    if (var == VAR_EXACT_CONTIG) return launch_t<VT, WM, TM, VAR_EXACT_CONTIG>(g, c, sm, st);
+    if (var == VAR_EXACT) return launch_t<VT, WM, TM, VAR_EXACT>(g, c, sm, st);
+    return launch_t<VT, WM, TM, VAR_GENERAL>(g, c, sm, st);
+}
+
 template <class VT, int WM>
-amy_status launch_tm(const Geom &g, bool exact, int tmode, const FastCall &c, int sm, cudaStream_t st) {
+amy_status launch_tm(const Geom &g, int var, int tmode, const FastCall &c, int sm, cudaStream_t st) {
     switch (tmode) {
-        case TM_OTF:
-            return exact ? launch_t<VT, WM, TM_OTF, true>(g, c, sm, st) : launch_t<VT, WM, TM_OTF, false>(g, c, sm, st);
-        case TM_FACTORED: return launch_t<VT, WM, TM_FACTORED, false>(g, c, sm, st);
-        default:
-            return exact ? launch_t<VT, WM, TM_SEPARABLE, true>(g, c, sm, st)
-                         : launch_t<VT, WM, TM_SEPARABLE, false>(g, c, sm, st);
+        case TM_OTF: return launch_var<VT, WM, TM_OTF>(g, var, c, sm, st);
+        case TM_FACTORED: return launch_t<VT, WM, TM_FACTORED, VAR_GENERAL>(g, c, sm, st);
+        default: return launch_var<VT, WM, TM_SEPARABLE>(g, var, c, sm, st);
     }
 }
 
 }  // namespace fastimpl
 
 template <class VT>
-amy_status launch_fast_vt(const Geom &g, int wm, bool exact, int tmode, const FastCall &c, int sm_count,
+amy_status launch_fast_vt(const Geom &g, int wm, int var, int tmode, const FastCall &c, int sm_count,
                           cudaStream_t st) {
-    if (wm == 3) return fastimpl::launch_tm<VT, 3>(g, exact, tmode, c, sm_count, st);
-    if (wm == 5) return fastimpl::launch_tm<VT, 5>(g, exact, tmode, c, sm_count, st);
-    return fastimpl::launch_tm<VT, 8>(g, exact, tmode, c, sm_count, st);
+    if (wm == 3) return fastimpl::launch_tm<VT, 3>(g, var, tmode, c, sm_count, st);
+    if (wm == 5) return fastimpl::launch_tm<VT, 5>(g, var, tmode, c, sm_count, st);
+    return fastimpl::launch_tm<VT, 8>(g, var, tmode, c, sm_count, st);
 }
 
 }  // namespace amy

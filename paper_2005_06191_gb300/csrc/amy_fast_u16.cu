@@ -4,7 +4,7 @@
 #include "amy_fast_launch.cuh"
 
 namespace amy {
-template amy_status launch_fast_vt<unorm16>(const Geom &, int, bool, int, const FastCall &, int, cudaStream_t);
-template amy_status launch_group_vt<unorm16>(int, int, bool, const BatchEntry *, int32_t, int64_t, int32_t *, int, int,
+template amy_status launch_fast_vt<unorm16>(const Geom &, int, int, int, const FastCall &, int, cudaStream_t);
+template amy_status launch_group_vt<unorm16>(int, int, int, const BatchEntry *, int32_t, int64_t, int32_t *, int, int,
                                          cudaStream_t);
 }  // namespace amy

@@ -33,6 +33,7 @@ struct FastCall {
     int64_t npairs;
     const uint32_t *tab;
     int32_t ulanes;   // input lanes per state (1, 2, 4, 8); 0 = heuristic
+    int32_t no_stage = 0;  // 1: never use the shared-memory staged variant
 };
 
 // Input lanes per state: one when the grid alone fills the GPU several times
@@ -46,6 +47,13 @@ inline int fast_default_ulanes(const Geom &g, int sm_count) {
 
 // Width bound (3, 5, 8) of the fast backup for this geometry, 0 if it does not apply.
 int fast_wm(const Geom &g, int prec);
+// Kernel variant of the fast backup (general, exact widths, exact widths with
+// a contiguous bounded innermost row).
+int fast_variant(const Geom &g, int wm, int tmode);
+// Finite guard cells on each side of every V buffer the fast kernels read:
+// the contiguous-row variant reads a bounded innermost row unclamped (the
+// off-grid slots have zero mass), up to kVGuard cells past either end.
+constexpr int64_t kVGuard = 16;
 amy_status launch_backup_fast(const Geom &g, int tmode, int v_store, const FastCall &c, int sm_count,
                               cudaStream_t st);
 amy_status launch_build_sep(const Geom &g, uint32_t *tab, int sm_count, cudaStream_t st);
@@ -80,7 +88,7 @@ struct BatchEntry {
 size_t batched_smem_bytes(int n, int wm);
 // One persistent launch over problems sharing a kernel variant (storage type,
 // width bound, row mode, exact widths); max_n = largest state dimension.
-amy_status launch_step_group(int vt, int wm, int tm, bool exact, const BatchEntry *d_entries, int32_t n_entries,
+amy_status launch_step_group(int vt, int wm, int tm, int var, const BatchEntry *d_entries, int32_t n_entries,
                              int64_t total_tiles, int32_t *d_counter, int max_n, int sm_count, cudaStream_t st);
 // Row mode picked automatically: separable tables when they stay small,
 // per-pair factored rows when they fit the budget, otherwise on the fly.

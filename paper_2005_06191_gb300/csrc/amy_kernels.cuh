@@ -142,10 +142,8 @@ __device__ __forceinline__ void row_setup_sep(const Geom &g, const uint32_t *__r
         const uint32_t *rec = tab + g.toff[d] + e * g.trw[d];
         const int32_t o = (int32_t)__ldg(rec);
         if (origin) origin[d] = o;
-        for (int k = 0; k < g.W[d]; ++k) {
-            fac[b + k] = __uint_as_float(__ldg(rec + 1 + k));
-            off[b + k] = (int32_t)__ldg(rec + 1 + g.W[d] + k);
-        }
+        dim_offsets(g, d, o, off + b);
+        for (int k = 0; k < g.W[d]; ++k) fac[b + k] = __uint_as_float(__ldg(rec + 1 + k));
         b += g.W[d];
     }
 }

@@ -13,9 +13,11 @@
 // array until the process exits.
 //
 // The array is shared by all calls on a device and keeps the last call's
-// contents.  Every entry a call reads is written earlier by that same call
-// (the spec-mask kernel writes every flag and V_N, each backup writes every
-// V_k), so nothing has to start at zero.  Calls whose work overlaps on the GPU
+// contents.  Every entry a call reads is written earlier by that same call:
+// the spec-mask kernel writes every flag and V_N, each backup writes every
+// V_k, and the few guard cells around each value vector (read with zero
+// mass by the contiguous-row kernels, so they must hold finite values) are
+// cleared at the start of every call.  Calls whose work overlaps on the GPU
 // (e.g. on two streams at once) race on the array; serialise them.
 #include <cmath>
 #include <cstring>
@@ -169,7 +171,7 @@ extern "C" amy_status amy_synthesize_noalloc(const amy_system *sys, const amy_gr
     const size_t nx = (size_t)g.nx;
     const size_t pbytes = up256((size_t)sys->n_params * sizeof(double));
     const size_t mbytes = up256(nx);
-    const size_t vbytes = up256(nx * sizeof(float));
+    const size_t vbytes = up256((nx + 2 * kVGuard) * sizeof(float));
     const size_t need = pbytes + mbytes + 2 * vbytes;
     if (need > (size_t)AMY_NOALLOC_SCRATCH_BYTES)
         return set_error(AMY_E_INVALID_ARG,
@@ -185,10 +187,16 @@ extern "C" amy_status amy_synthesize_noalloc(const amy_system *sys, const amy_gr
     if (st != AMY_OK) return st;
     double *d_params = (double *)base;
     uint8_t *d_mask = base + pbytes;
-    float *d_V[2] = {(float *)(base + pbytes + mbytes), (float *)(base + pbytes + mbytes + vbytes)};
+    // each value vector carries kVGuard finite guard cells on both sides
+    float *d_V[2] = {(float *)(base + pbytes + mbytes) + kVGuard, (float *)(base + pbytes + mbytes + vbytes) + kVGuard};
     cudaStream_t s = (cudaStream_t)cuda_stream;
     g.params = d_params;
     e = cudaMemcpyAsync(d_params, sys->params, (size_t)sys->n_params * sizeof(double), cudaMemcpyHostToDevice, s);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        // guard cells must hold finite values: cleared on every call
+        e = cudaMemsetAsync(d_V[i] - kVGuard, 0, kVGuard * sizeof(float), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_V[i] + nx, 0, kVGuard * sizeof(float), s);
+    }
     if (e != cudaSuccess) return cuda_error(e, "parameter upload");
     st = launch_spec_mask(g, sd, d_mask, d_V[0], AMY_V_NATIVE, s);
     if (st != AMY_OK) return st;

@@ -77,7 +77,7 @@ struct Req {
     int32_t k_left = 0;
     int tm = TM_SEPARABLE;  // row mode: separable tables, factored per-pair rows, or on the fly
     int wm = 0;
-    bool exact = false;
+    int var = 0;  // fast-kernel variant (general / exact widths / exact + contiguous row)
     bool batched = false;
     int ulanes = 1;
     int64_t ntiles = 0;
@@ -99,7 +99,7 @@ size_t device_bytes(const Req *r) {
     const size_t fT = r->tm == TM_FACTORED ? npairs_of(r) * r->g.wsum * 4 : 0;
     const size_t fO = r->tm == TM_FACTORED ? npairs_of(r) * r->g.n * 2 : 0;
     return align256(sizeof(Geom)) + align256(r->params.size() * 8) + align256(tab) + align256(fT) + align256(fO) +
-           2 * align256(nx * vbytes(r)) + align256(nx) + align256(nx * 4) + align256(nx * 2);
+           2 * align256((nx + 2 * kVGuard) * vbytes(r)) + align256(nx) + align256(nx * 4) + align256(nx * 2);
 }
 
 }  // namespace
@@ -305,10 +305,10 @@ void carve(Req *r) {
     p += align256(r->tm == TM_FACTORED ? npairs_of(r) * r->g.wsum * 4 : 0);
     r->d_O = (int16_t *)p;
     p += align256(r->tm == TM_FACTORED ? npairs_of(r) * r->g.n * 2 : 0);
-    r->d_V[0] = p;
-    p += align256(nx * vbytes(r));
-    r->d_V[1] = p;
-    p += align256(nx * vbytes(r));
+    r->d_V[0] = p + kVGuard * vbytes(r);
+    p += align256((nx + 2 * kVGuard) * vbytes(r));
+    r->d_V[1] = p + kVGuard * vbytes(r);
+    p += align256((nx + 2 * kVGuard) * vbytes(r));
     r->d_mask = (uint8_t *)p;
     p += align256(nx);
     r->d_Vout = (float *)p;
@@ -325,6 +325,10 @@ amy_status admit(amy_server_s *s, Req *r) {
     cudaError_t e = cudaMallocAsync(&r->dmem, r->dbytes, s->stream);
     if (e != cudaSuccess) return cuda_error(e, "request memory");
     carve(r);
+    // finite guard cells around both V buffers (read with zero mass)
+    e = cudaMemsetAsync((char *)r->d_V[0] - kVGuard * vbytes(r), 0, align256((r->g.nx + 2 * kVGuard) * vbytes(r)) * 2,
+                        s->stream);
+    if (e != cudaSuccess) return cuda_error(e, "guard init");
     const size_t pbytes = r->params.size() * 8;
     const size_t ubytes = r->tm == TM_SEPARABLE ? r->upart.size() * 4 : 0;
     r->h_up_bytes = sizeof(Geom) + pbytes + ubytes;
@@ -352,9 +356,7 @@ amy_status admit(amy_server_s *s, Req *r) {
     if (st != AMY_OK) return st;
     s->launches += 1;
     r->wm = fast_wm(r->g, AMY_PREC_FP32);
-    r->exact = r->wm > 0;
-    for (int d = 0; d < r->g.n; ++d) r->exact = r->exact && r->g.W[d] == r->wm;
-    if (r->tm == TM_FACTORED) r->exact = false;
+    r->var = r->wm > 0 ? fast_variant(r->g, r->wm, r->tm) : 0;
     r->batched = r->wm > 0 && batched_smem_bytes(r->g.n, r->wm) <= 100 * 1024;
     if (r->wm > 0) {
         st = autotune(s, r);
@@ -455,8 +457,7 @@ amy_status tick(amy_server_s *s) {
     }
     // group the batched problems by kernel variant; the rest launch one by one
     struct Group {
-        int vt, wm, tm;
-        bool exact;
+        int vt, wm, tm, var;
         std::vector<Req *> rs;
     };
     std::vector<Group> groups;
@@ -468,9 +469,9 @@ amy_status tick(amy_server_s *s) {
         if (s->opts.batched && r->batched) {
             Group *gp = nullptr;
             for (Group &gg : groups)
-                if (gg.vt == r->v_store && gg.wm == r->wm && gg.tm == r->tm && gg.exact == r->exact) gp = &gg;
+                if (gg.vt == r->v_store && gg.wm == r->wm && gg.tm == r->tm && gg.var == r->var) gp = &gg;
             if (!gp) {
-                groups.push_back({r->v_store, r->wm, r->tm, r->exact, {}});
+                groups.push_back({r->v_store, r->wm, r->tm, r->var, {}});
                 gp = &groups.back();
             }
             gp->rs.push_back(r);
@@ -515,7 +516,7 @@ amy_status tick(amy_server_s *s) {
         cudaError_t e = cudaMemcpyAsync(slot.d + first, slot.h + first, sizeof(BatchEntry) * (ne - first),
                                         cudaMemcpyHostToDevice, s->stream);
         if (e != cudaSuccess) return cuda_error(e, "step table upload");
-        amy_status st = launch_step_group(gg.vt, gg.wm, gg.tm, gg.exact, slot.d + first, ne - first, tiles,
+        amy_status st = launch_step_group(gg.vt, gg.wm, gg.tm, gg.var, slot.d + first, ne - first, tiles,
                                           slot.counter + gi, max_n, s->sm_count, s->stream);
         if (st != AMY_OK) return st;
         s->launches += 1;
