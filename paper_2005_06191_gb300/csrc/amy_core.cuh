@@ -64,6 +64,11 @@ struct Geom {
     int32_t tent[MAXD];
     int64_t uoff;
     int32_t urw;
+    // After the index parts, at word boff: per dim d the smallest and largest
+    // window origin minus the state's own coordinate d over the table
+    // (words boff + d and boff + MAXD + d), then a bit mask of the dims for
+    // which that bound exists (component d depends on coordinate d).
+    int64_t boff;
 };
 
 struct SpecDev {

@@ -288,7 +288,8 @@ amy_status plan_sep_tables(Geom &g, const std::vector<double> &params, int64_t &
             }
         }
     }
-    words = off + (int64_t)g.nu * g.urw;
+    g.boff = off + (int64_t)g.nu * g.urw;
+    words = g.boff + 2 * MAXD + 4;
     return AMY_OK;
 }
 

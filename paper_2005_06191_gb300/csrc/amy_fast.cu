@@ -48,6 +48,7 @@ amy_status launch_build_sep(const Geom &g, uint32_t *tab, int sm_count, cudaStre
     int64_t total = 0;
     for (int d = 0; d < g.n; ++d) total += g.tent[d];
     const int blocks = (int)std::min<int64_t>((total + 127) / 128, (int64_t)sm_count * 16);
+    k_build_sep_bounds_init<<<1, 32, 0, st>>>(g, tab);
     k_build_sep<<<std::max(blocks, 1), 128, 0, st>>>(g, tab, total);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? AMY_OK : cuda_error(e, "table build launch");

@@ -13,6 +13,8 @@
 // input are kept in registers per lane and merged across lanes at the end.
 #pragma once
 
+#include <climits>
+
 #include "amy_kernels.cuh"
 
 namespace amy {
@@ -481,6 +483,28 @@ static __global__ void k_build_sep(const __grid_constant__ Geom g, uint32_t *__r
         rec[0] = (uint32_t)o;
         for (int k = 0; k < Wd; ++k) rec[1 + k] = __float_as_uint(fac[k]);
         for (int k = 1 + Wd; k < g.trw[d]; ++k) rec[k] = 0u;
+        // origin bounds relative to the state's own coordinate d
+        if (g.tsx[d][d] != 0) {
+            const int32_t xd = (int32_t)((e / g.tsx[d][d]) % g.N[d]);
+            int32_t *b = reinterpret_cast<int32_t *>(tab + g.boff);
+            atomicMin(b + d, o - xd);
+            atomicMax(b + MAXD + d, o - xd);
+        }
+    }
+}
+
+static __global__ void k_build_sep_bounds_init(const __grid_constant__ Geom g, uint32_t *__restrict__ tab) {
+    int32_t *b = reinterpret_cast<int32_t *>(tab + g.boff);
+    const int d = threadIdx.x;
+    if (d < MAXD) {
+        b[d] = INT_MAX;
+        b[MAXD + d] = INT_MIN;
+    }
+    if (d == 0) {
+        int32_t m = 0;
+        for (int q = 0; q < g.n; ++q)
+            if (g.tsx[q][q] != 0) m |= 1 << q;
+        b[2 * MAXD] = m;
     }
 }
 

@@ -144,17 +144,28 @@ __global__ void __launch_bounds__(FAST_THREADS) k_backup_staged(const __grid_con
         }
     };
 
-    // pass 1: the tile's window box
+    // pass 1: the tile's window box -- from the tables' bounds on (origin -
+    // own coordinate) when every dim has one, else from the items' origins
+    const int32_t *rb = TM == TM_SEPARABLE ? reinterpret_cast<const int32_t *>(a.tab + g.boff) : nullptr;
+    const bool analytic = rb && ((__ldg(rb + 2 * MAXD) & ((1 << NS) - 1)) == ((1 << NS) - 1));
     int32_t lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
     if (work_items) {
-        for (int32_t u = c; u < g.nu; u += UL) {
-            int32_t o[3];
-            float t[3][WM];
-            item(u, o, t, false);
+        if (analytic) {
 #pragma unroll
             for (int d = 0; d < NS; ++d) {
-                lo[d] = min(lo[d], o[d]);
-                hi[d] = max(hi[d], o[d]);
+                lo[d] = xi[d] + __ldg(rb + d);
+                hi[d] = xi[d] + __ldg(rb + MAXD + d);
+            }
+        } else {
+            for (int32_t u = c; u < g.nu; u += UL) {
+                int32_t o[3];
+                float t[3][WM];
+                item(u, o, t, false);
+#pragma unroll
+                for (int d = 0; d < NS; ++d) {
+                    lo[d] = min(lo[d], o[d]);
+                    hi[d] = max(hi[d], o[d]);
+                }
             }
         }
     }
@@ -182,27 +193,36 @@ __global__ void __launch_bounds__(FAST_THREADS) k_backup_staged(const __grid_con
         return;
     }
     {
+        // row stride padded to a multiple of 32 floats when it fits: lanes whose
+        // windows differ by whole rows then still hit distinct banks
+        int32_t inner = bn[NS - 1];
+        const int32_t padded = (inner + 31) / 32 * 32;
+        if (NS > 1 && (vol / inner) * padded <= STAGE_BOX_FLOATS) inner = padded;
         int32_t s = 1;
 #pragma unroll
         for (int d = NS - 1; d >= 0; --d) {
             bs[d] = s;
-            s *= bn[d];
+            s *= (d == NS - 1) ? inner : bn[d];
         }
     }
     // stage the box: periodic dims wrap, off-grid cells hold 0 (zero mass there)
     if (any) {
         for (int32_t i = tid; i < (int32_t)vol; i += BT) {
             int64_t lin = 0;
+            int32_t sidx = 0;
             bool on = true;
+            int32_t r = i;
 #pragma unroll
-            for (int d = 0; d < NS; ++d) {
-                const int32_t cd = blo[d] + (i / bs[d]) % bn[d];
+            for (int d = NS - 1; d >= 0; --d) {
+                const int32_t kd = r % bn[d];
+                r /= bn[d];
                 bool ond;
-                const int32_t cell = cell_of(g, d, cd, ond);
+                const int32_t cell = cell_of(g, d, blo[d] + kd, ond);
                 on = on && ond;
                 lin += (int64_t)cell * g.stride[d];
+                sidx += kd * bs[d];
             }
-            sbox[i] = on ? vload<float, VT>(a.Vn + lin) : 0.0f;
+            sbox[sidx] = on ? vload<float, VT>(a.Vn + lin) : 0.0f;
         }
     }
     __syncthreads();
