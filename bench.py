@@ -40,6 +40,36 @@ METRIC = "Bellman transitions/s (x*u*x' window slots * horizon)"
 UNIT = "transitions/s"
 
 
+# DRAM traffic of the dominant kernel per launch, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum).  A figure holds only for the
+# kernel sources it was captured on, so each entry carries the digest of the
+# csrc/ tree at capture time and is reported as null once the sources change.
+# key: (workload, tmode, prec, v_store) -> (digest, bytes per launch, states in
+# the captured launch, profile summary).  A capture on a reduced grid is scaled
+# to the full launch by the number of states (the traffic is V in/out, pi and
+# the mask per state; the tables are a few hundred KB at most).
+MEASURED_TRAFFIC = {
+}
+
+
+def csrc_digest() -> str:
+    import hashlib
+    d = os.path.join(ROOT, "paper_2005_06191_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(args, n_states: int):
+    e = MEASURED_TRAFFIC.get((args.workload, args.tmode, args.prec, args.v_store))
+    if e is None or e[0] != csrc_digest():
+        return None, None
+    return int(round(e[1] * n_states / e[2])), e[3]
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -133,21 +163,30 @@ def barrier(world: int):
 
 
 WORKLOADS = {
-    # name: (constructor, default T mode, default precision, description)
-    "unicycle": (lambda: W.unicycle(), "stored_separable", "fp32", WORKLOAD_NAME),
-    "robot": (lambda: W.robot_lin(), "stored_full", "fp64",
+    # name: (constructor(size or None), default T mode, default precision, description)
+    "unicycle": (lambda s: W.unicycle(nxy=s or 51), "stored_separable", "fp32", WORKLOAD_NAME),
+    "robot": (lambda s: W.robot_lin(n_per_dim=s or 41), "stored_full", "fp64",
               "2-D linear robot 41x41 states, 25 inputs, sigma 0.2, dense rows, reach-avoid, horizon 8"),
-    "rooms7": (lambda: W.rooms7(), "stored_separable", "fp32_kahan",
+    "rooms7": (lambda s: W.rooms7(n_per_dim=s or 9), "stored_separable", "fp32_kahan",
                "7-room temperature ring 9^7 states, 5 inputs, sigma 0.02, window 3^7, safety, horizon 10"),
-    "traffic6": (lambda: W.traffic6(), "stored_separable", "fp32_kahan",
+    "traffic6": (lambda s: W.traffic6(n_per_dim=s or 21), "stored_separable", "fp32_kahan",
                  "6-D traffic ring 21^6 states, 4 inputs, sigma 0.5, window 5^6, safety [0,18]^6, horizon 8"),
 }
 
 
 def workload(args):
-    w = WORKLOADS[args.workload][0]()
+    w = WORKLOADS[args.workload][0](args.size)
     w.tmode, w.precision = args.tmode, args.prec
+    if args.horizon is not None:
+        w.horizon = args.horizon
     return w
+
+
+def workload_name(args) -> str:
+    name = WORKLOADS[args.workload][3]
+    if args.size is not None or args.horizon is not None:
+        name += f" [reduced: size {args.size}, horizon {args.horizon}]"
+    return name
 
 
 def transitions_per_step(w, window_slots: int) -> int:
@@ -203,7 +242,10 @@ def run_amy(args, rank, world):
     ms_max = barrier_max(ms, world)
     value = trans * args.steps * world / (ms_max / 1e3)
     # kernel-level roofline of the dominant kernel (the fused backup)
-    launches = kt["backup_launches"] + kt["build_launches"] + args.steps  # + one spec-mask per step
+    # kernels per timed step: the backups, one spec-mask kernel, and the build
+    # (two kernels for the per-dimension tables: bounds reset + tables)
+    per_build = 2 if args.tmode == "stored_separable" else 1
+    launches = kt["backup_launches"] + per_build * kt["build_launches"] + args.steps
     bk_ms = kt["backup_ms"] / max(kt["backup_launches"], 1)
     build_ms = kt["build_ms"] / max(kt["build_launches"], 1)
     V_host = V.cpu().numpy()
@@ -213,26 +255,29 @@ def run_amy(args, rank, world):
 
     # end to end through the C ABI with host buffers: build (H2D of the
     # problem), synthesize with host outputs (D2H of V_0 and every pi_k), destroy
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 5))
     h2d = (np.asarray(p.params).nbytes + 8 * 4 * p.n + 8 * 2 * p.m + 4 * (p.n + p.m) + p.n + 8 * 2 * p.n)
     d2h = p.n_states * 4 + N * p.n_states * 2
-    for _ in range(2):
-        with amy.amy_build(p, tmode=args.tmode, prec=args.prec, v_store=args.v_store) as he:
-            amy.amy_synthesize(he, spec, N, policy_all_steps=True)
-    torch.cuda.synchronize()
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        with amy.amy_build(p, tmode=args.tmode, prec=args.prec, v_store=args.v_store) as he:
-            Ve, PIe = amy.amy_synthesize(he, spec, N, policy_all_steps=True)
-    e2e_s = barrier_max(time.perf_counter() - t0, world)
-    e2e_value = trans * e2e_steps * world / e2e_s
+    Ve, e2e = None, None
+    if e2e_steps:
+        for _ in range(2):
+            with amy.amy_build(p, tmode=args.tmode, prec=args.prec, v_store=args.v_store) as he:
+                amy.amy_synthesize(he, spec, N, policy_all_steps=True)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            with amy.amy_build(p, tmode=args.tmode, prec=args.prec, v_store=args.v_store) as he:
+                Ve, PIe = amy.amy_synthesize(he, spec, N, policy_all_steps=True)
+        e2e_s = barrier_max(time.perf_counter() - t0, world)
+        e2e = {"value": trans * e2e_steps * world / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
     amy.amy_destroy(h)
     clocks = clk.summary()
     return {
         "value": value, "ms_per_step": ms_max / args.steps, "trans": trans, "info": info,
         "backup_ms": bk_ms, "build_ms": build_ms, "launches": launches, "roofline": roof,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "e2e": e2e,
         "clocks": clocks, "V": V_host, "V_e2e": Ve,
         "synth_only_value": trans * args.steps * world / ((ms_max - build_ms * args.steps) / 1e3),
     }
@@ -254,14 +299,16 @@ def roofline(args, w, info, backup_ms, free):
         algo = free * nu * per_pair + nx * per_state
         achieved = algo / (backup_ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "frac": achieved / pk["hbm_gbs"], "traffic": measured_traffic(args, nx)[0],
                 "peak_source": pk["source"], "algorithmic_bytes_per_launch": int(algo)}
+    traffic, src = measured_traffic(args, nx)
     sms = 152
     lane_loads = free * nu * info["window_slots"]
     achieved = lane_loads / (backup_ms / 1e3) / 1e9
     peak = sms * 32 * pk["sm_max_mhz"] * 1e6 / 1e9
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G lane-loads/s",
-            "frac": achieved / peak, "traffic": None, "peak_source": "152 SMs x 32 load lanes/clk x max SM clock",
+            "frac": achieved / peak, "traffic": traffic, "traffic_source": src,
+            "peak_source": "152 SMs x 32 load lanes/clk x max SM clock",
             "algorithmic_lane_loads_per_launch": int(lane_loads)}
 
 
@@ -295,29 +342,39 @@ def window_slots_of(w) -> int:
     return int(np.prod(Wd))
 
 
+def oracle_step(args, w):
+    """One timed step of the oracle and its description: the whole workload
+    where the oracle finishes it in seconds (robot, unicycle), else one
+    backup at a bounded set of seeded states with full rows."""
+    if args.workload in ("unicycle", "robot"):
+        slots = window_slots_of(w)
+        trans = w.problem.n_states * w.problem.n_inputs * slots * w.horizon
+        return (lambda: time_oracle(w, w.horizon)[0], trans,
+                f"the whole workload per step (full grid, {w.horizon} backups), FP64")
+    n_s = 2000 if args.workload == "rooms7" else 100
+
+    def run():
+        return time_oracle_sample(w, n_s)[0]
+    trans = min(n_s, w.problem.n_states) * w.problem.n_inputs * window_slots_of(w)
+    return run, trans, f"one backup at {n_s} seeded states (full rows) per step, FP64"
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
     w = workload(args)
-    sample_h = 4  # each step: the full grid over 4 backups (a bounded sample of the 32)
-    slots = window_slots_of(w)
-    trans = w.problem.n_states * w.problem.n_inputs * slots * sample_h
+    run, trans, sample = oracle_step(args, w)
     for _ in range(args.warmup):
-        time_oracle(w, sample_h)
-    times = []
-    for _ in range(args.steps):
-        dt, _ = time_oracle(w, sample_h)
-        times.append(dt)
-    tot = sum(times)
+        run()
+    tot = sum(run() for _ in range(args.steps))
     value = trans * args.steps / tot
     cores = os.cpu_count()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "sample": f"full grid, {sample_h} of 32 backups"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"full grid, {sample_h} backups per step"},
+        "data": "synthetic", "config": {"workload": workload_name(args), "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -437,6 +494,11 @@ def main():
     ap.add_argument("--served-n", dest="served_n", type=int, default=256)
     ap.add_argument("--v-store", dest="v_store", default="native", choices=["native", "u16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", dest="no_e2e", action="store_true",
+                    help="skip the end-to-end (host buffer) measurement, e.g. under a profiler")
+    ap.add_argument("--size", type=int, default=None,
+                    help="grid points per dimension (x/y for the unicycle) instead of the workload's own")
+    ap.add_argument("--horizon", type=int, default=None, help="horizon instead of the workload's own")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -472,10 +534,10 @@ def main():
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload][3], "tmode": args.tmode, "prec": args.prec,
+        "config": {"workload": workload_name(args), "tmode": args.tmode, "prec": args.prec,
                    "v_store": args.v_store,
                    "l2": "flushed (256 MB write) between timed iterations",
-                   "step": "rebuild stored rows + spec mask + 32 fused backups (all pi_k written)"},
+                   "step": f"rebuild stored rows + spec mask + {w.horizon} fused backups (all pi_k written)"},
         "roofline": r["roofline"],
         "cpu_baseline": cpu,
         "e2e": r["e2e"],

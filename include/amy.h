@@ -46,7 +46,7 @@ typedef enum {
 typedef struct amy_handle_s *amy_handle;
 typedef struct amy_server_s *amy_server;
 
-/* Uniform grid (Sec. 3, quantiser Pi_x with Eq. Pi_delta): centre j of dim d is
+/* Uniform grid (Sec. 4, quantiser Pi_x with Eq. 7): centre j of dim d is
  * lb[d] + j*eta[d] for 0 <= j < count[d]; cell j is [centre - eta/2,
  * centre + eta/2).  periodic[d] != 0 makes dim d wrap modulo count[d]
  * (periodic may be NULL).  n in 1..8. */
@@ -58,7 +58,7 @@ typedef struct {
     const uint8_t *periodic;
 } amy_grid;
 
-/* System f of Eq. (11a) (no disturbance), evaluated at representative points.
+/* System f of Eq. 4 (no disturbance), evaluated at representative points.
  * AMY_SYS_AFFINE_PER_INPUT: for each discrete input u (C order over the input
  *   grid) params holds A_u (n*n, row-major) then c_u (n); the mean is
  *   mu_i = (sum_j A_u[i][j] * x_j, summed j = 0..n-1 from 0.0) + c_u[i],
@@ -75,7 +75,7 @@ typedef struct {
     int64_t n_params;
 } amy_system;
 
-/* Cutting region (Sec. 4.2 and its Remark on constructing the region).
+/* Cutting region (Sec. 5.2 and its Remark on constructing the region).
  * window == NULL, gamma > 0: per dim the 1-D density equals gamma at +-xs,
  *   xs = sigma*sqrt(2*log(1/(gamma*sigma*sqrt(2*pi)))), width W = floor(2*xs/eta)+1,
  *   origin o = ceil(((mu - xs) - lb)/eta); slot o+k (k < W) is kept iff its
@@ -90,7 +90,7 @@ typedef struct {
     const int32_t *window;
 } amy_cut;
 
-/* T storage (Sec. 4.3 stored rows; Sec. 5.1 on-the-fly abstraction).
+/* T storage (Sec. 5.3 stored rows; Sec. 6.1 on-the-fly abstraction).
  * AMY_T_STORED_SEPARABLE tabulates, per state dim d, the window origin and the
  * W[d] masses of mean component d over only the state and input coordinates
  * that component depends on (affine: non-zero columns of A_u[d][:] and input
@@ -169,7 +169,7 @@ typedef struct {
 } amy_info_t;
 
 /* Points per dim of [lb, ub] with step eta: floor((ub-lb)/eta + 1e-9) + 1
- * (the grids of Sec. 6-7 give the pair counts printed in Table 4). */
+ * (the grids of Sec. 7-8 give the pair counts printed in Table 4). */
 int64_t amy_grid_count(double lb, double ub, double eta);
 
 /* Build the abstraction (Algorithm 2 for the stored modes): validates the
@@ -184,7 +184,7 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
                      const double *sigma, const amy_cut *cut, const amy_opts *opts,
                      amy_handle *out);
 
-/* Finite-horizon synthesis (Algorithm 4; on-the-fly rows per Sec. 5.1 in
+/* Finite-horizon synthesis (Algorithm 4; on-the-fly rows per Sec. 6.1 in
  * AMY_T_ON_THE_FLY).  `horizon` backups from V_N; V_out[n_states] receives
  * V_0 (double for AMY_PREC_FP64, float otherwise).  policy_out receives
  * pi_0 [n_states] or, with policy_all_steps, pi_k for k = 0..horizon-1 as

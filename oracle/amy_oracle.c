@@ -5,16 +5,16 @@
  * It shares no code with the CUDA library.  Every step follows the paper
  * (arxiv 2005.06191, "AMYTISS") in its own order and notation:
  *
- *   Sec. 3 (finite MDP, Eq. trans_prob):  T^(x'|x,u) = T(Xi(x')|x,u), the
+ *   Sec. 4 (finite MDP, Eq. 5):  T^(x'|x,u) = T(Xi(x')|x,u), the
  *       probability that f(x,u) + noise lands in the cell of x'.
  *   Algorithm 1:  T entry = integral of the Gaussian density over the cell;
  *       for a diagonal covariance this is a product of 1-D masses.
- *   Sec. 4.2 + Remark on constructing the cutting region:  per dimension the
+ *   Sec. 5.2 + Remark on constructing the cutting region:  per dimension the
  *       1-D density equals gamma at +-xs, and the kept post states are the
  *       grid centres inside [mu - xs, mu + xs]; the row has a fixed width.
  *   Algorithm 3 / Algorithm 4:  backward recursion over the horizon, V_in as
  *       the window sum of T * V_{k+1}, then max (and lowest argmax) over u.
- *   Sec. 5.1 (OFA):  rows are recomputed where needed; the oracle does so for
+ *   Sec. 6.1 (OFA):  rows are recomputed where needed; the oracle does so for
  *       every state and step, which is the same arithmetic as storing them.
  *
  * Readings of points the paper leaves open (kept identical in the CUDA path,
@@ -65,12 +65,12 @@ static int is_periodic(const orc_problem *p, int d) {
     return p->x_periodic != NULL && p->x_periodic[d] != 0;
 }
 
-/* Grid quantiser, Sec. 3 (map Pi_x and Eq. Pi_delta): points per dimension. */
+/* Grid quantiser, Sec. 4 (map Pi_x and Eq. 7): points per dimension. */
 int64_t orc_grid_count(double lb, double ub, double eta) {
     return (int64_t)floor((ub - lb) / eta + 1e-9) + 1;
 }
 
-/* Cutting region size, Sec. 4.2 and its Remark: solve the 1-D density = gamma
+/* Cutting region size, Sec. 5.2 and its Remark: solve the 1-D density = gamma
  * per dimension, then the fixed number of slots per dimension. */
 int orc_window_shape(const orc_problem *p, int32_t *W, double *xstar) {
     for (int d = 0; d < p->n; ++d) {

@@ -8,14 +8,14 @@
  * paper independently.
  *
  * What it computes (paper sections cited per function in amy_oracle.c):
- *   - grid quantiser (Sec. 3, Eq. (Pi_delta)): centres lb + j*eta, j < N,
+ *   - grid quantiser (Sec. 4, Eq. 7): centres lb + j*eta, j < N,
  *     N = floor((ub-lb)/eta + 1e-9) + 1;
- *   - cutting region (Sec. 4.2, Remark "constructing the cutting region"):
+ *   - cutting region (Sec. 5.2, Remark "constructing the cutting region"):
  *     per-dimension 1-D density cut, window widths and origins;
  *   - transition probabilities (Algorithm 1 / Algorithm 2): Gaussian mass of
  *     each post-state cell, a product of per-dimension masses for diagonal
  *     covariance;
- *   - Bellman synthesis (Algorithm 3 / Algorithm 4, OFA semantics of Sec. 5.1):
+ *   - Bellman synthesis (Algorithm 3 / Algorithm 4, OFA semantics of Sec. 6.1):
  *     safety, reachability and reach-avoid value functions with the
  *     lowest-index argmax policy.
  *

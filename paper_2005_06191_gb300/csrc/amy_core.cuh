@@ -3,7 +3,7 @@
 // engine.  Host code fills a Geom once per problem; kernels take it by value.
 //
 // What a row is (Algorithm 1 / Algorithm 2): for a state x and an input u the
-// mean mu = f(centre(x), centre(u)) (Eq. 11a), the cutting window of Sec. 4.2
+// mean mu = f(centre(x), centre(u)) (Eq. 4), the cutting window of Sec. 5.2
 // (Remark on constructing the cutting region) and, per dimension, the Gaussian
 // mass of each window cell; for a diagonal covariance the row entry is the
 // product of the per-dimension masses.
@@ -103,7 +103,7 @@ __device__ __forceinline__ double state_centre(const Geom &g, int d, int32_t j) 
 }
 
 // Mean of the post state, Algorithm 2 "Set mu = f(x, nu, w)" for the
-// disturbance-free system of Eq. (11a).
+// disturbance-free system of Eq. 4.
 __device__ __forceinline__ void mean_of(const Geom &g, int32_t x, int32_t u, double *mu) {
     int32_t xi[MAXD];
     double xc[MAXD];

@@ -1,7 +1,7 @@
 // amy_engine.cu -- C ABI of the single-problem path (amy_build,
 // amy_synthesize, amy_backup_step, amy_query_rows, amy_info, amy_destroy).
 //
-// Host side: validation, window shape (Sec. 4.2 Remark, scalars per dim),
+// Host side: validation, window shape (Sec. 5.2 Remark, scalars per dim),
 // device allocation and kernel launches.  Every per-state and per-pair step
 // runs in the kernels of amy_kernels.cuh.
 #include <cmath>
@@ -45,7 +45,7 @@ int64_t grid_count(double lb, double ub, double eta) {
     return (int64_t)std::floor((ub - lb) / eta + 1e-9) + 1;
 }
 
-// Window shape per dim (Sec. 4.2 and the Remark on the cutting region): the
+// Window shape per dim (Sec. 5.2 and the Remark on the cutting region): the
 // 1-D density of N(0, sigma^2) equals gamma at +-xs; the row keeps
 // floor(2 xs / eta) + 1 slots.  Same FP64 expression as documented in amy.h.
 amy_status make_geom(const amy_system *sys, const amy_grid *st, const amy_grid *in,

@@ -1,6 +1,6 @@
 // amy_fast.cuh -- register-resident fused backup + max/argmax (Algorithm 4)
 // for windows whose per-dimension width is at most WM (3, 5 or 8), FP32
-// arithmetic, rows on the fly (Sec. 5.1), stored per pair, or tabulated per
+// arithmetic, rows on the fly (Sec. 6.1), stored per pair, or tabulated per
 // dimension over the coordinates each mean component depends on.
 //
 // Thread mapping: a block owns TX consecutive states; thread tid handles

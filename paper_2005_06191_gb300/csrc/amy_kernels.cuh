@@ -1,6 +1,6 @@
 // amy_kernels.cuh -- kernels of the single-problem path: spec mask + V_N,
 // stored-T construction (Algorithm 2), the fused backup + max/argmax
-// (Algorithm 4, stored or on-the-fly per Sec. 5.1) and a row query used to
+// (Algorithm 4, stored or on-the-fly per Sec. 6.1) and a row query used to
 // check rows against an independent implementation.
 #pragma once
 

@@ -5,8 +5,8 @@ cutting rule, specification boxes, request streams).  It holds none of the
 method's arithmetic: no means, windows, cell masses or backups are computed
 here, so both the CUDA path and the CPU oracle receive identical inputs.
 
-The five workloads follow the paper's case studies (robot Sec. 6, room
-temperature and road traffic Sec. 7) reshaped to the sizes the engine is
+The five workloads follow the paper's case studies (robot Sec. 7, room
+temperature and road traffic Sec. 8) reshaped to the sizes the engine is
 measured on:
 
   robot_lin    2-D x+ = x + u, dense rows, reach-avoid, horizon 8 (FP64)
@@ -118,7 +118,7 @@ def linear_system_params(A: np.ndarray, B: np.ndarray, ucs: np.ndarray,
 
 
 # ---------------------------------------------------------------------------
-# robot_lin: 2-D linear robot (shape of the paper's Sec. 6 robot example)
+# robot_lin: 2-D linear robot (shape of the paper's Sec. 7 robot example)
 # ---------------------------------------------------------------------------
 def robot_lin(n_per_dim: int = 41, horizon: int = 8, precision: str = "fp64") -> Workload:
     lb, eta = -5.0, 0.25
