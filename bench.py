@@ -210,7 +210,9 @@ def run_amy(args, rank, world):
     w = workload(args)
     p, spec, N = w.problem, w.spec, w.horizon
     stream = torch.cuda.current_stream()
-    h = amy.amy_build(p, tmode=args.tmode, prec=args.prec, v_store=args.v_store)
+    shape = [int(v) for v in args.shape.split(",")] if args.shape else None
+    h = amy.amy_build(p, tmode=args.tmode, prec=args.prec, v_store=args.v_store, autotune=shape is None,
+                      launch_shape=shape)
     info = amy.amy_info(h)
     trans = transitions_per_step(w, info["window_slots"])
     V = torch.empty(p.n_states, dtype=torch.float64 if args.prec == "fp64" else torch.float32, device="cuda")
@@ -499,6 +501,9 @@ def main():
     ap.add_argument("--size", type=int, default=None,
                     help="grid points per dimension (x/y for the unicycle) instead of the workload's own")
     ap.add_argument("--horizon", type=int, default=None, help="horizon instead of the workload's own")
+    ap.add_argument("--shape", default=None,
+                    help="fixed backup launch shape 'lanes,states_per_block,rows(1)|consecutive(2),box_floats' "
+                         "(0 = automatic) instead of the build-time autotuner")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -536,6 +541,10 @@ def main():
         "data": "synthetic",
         "config": {"workload": workload_name(args), "tmode": args.tmode, "prec": args.prec,
                    "v_store": args.v_store,
+                   "launch_shape": {"input_lanes": r["info"]["input_lanes"], "states_per_block": r["info"]["block_states"],
+                                    "row_tiles": r["info"]["row_tiles"], "grouped_inputs": r["info"]["grouped_inputs"],
+                                    "chosen_by": ("fixed: " + args.shape) if args.shape else
+                                    "amy_build autotune (timed at build, outside the timed region)"},
                    "l2": "flushed (256 MB write) between timed iterations",
                    "step": f"rebuild stored rows + spec mask + {w.horizon} fused backups (all pi_k written)"},
         "roofline": r["roofline"],

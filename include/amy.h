@@ -131,6 +131,19 @@ typedef struct {
     int32_t use_graphs;         /* 1: amy_synthesize with device outputs captures its
                                    horizon loop into a CUDA graph and replays it while
                                    spec, horizon and output pointers repeat */
+    int32_t autotune;           /* 1: amy_build times the backup kernel's launch
+                                   shapes (input lanes per state, row-aligned or
+                                   linear state tiles) on the handle's own buffers
+                                   and keeps the fastest; results do not depend on
+                                   the choice.  Skipped (heuristic shapes) when one
+                                   backup exceeds 4e9 window slots.  0: heuristic. */
+    int32_t launch_shape[4];    /* fixed backup launch shape, each entry 0 = automatic:
+                                   [0] input lanes per state (1..8), [1] states per
+                                   block of the staged variant (multiple of 32,
+                                   [0]*[1] <= 256), [2] 1 = row tiles, 2 = tiles of
+                                   consecutive states, [3] staged box budget in floats
+                                   (256..6144).  Entries that do not apply are ignored;
+                                   the autotuner, when on, overrides them. */
 } amy_opts;
 
 /* Closed box tested on representative points: lb[d] <= centre_d <= ub[d]. */
@@ -166,6 +179,11 @@ typedef struct {
     int32_t tmode;
     int32_t prec;
     int32_t v_store;
+    int32_t input_lanes;        /* backup launch shape: threads per state (1,2,4,8; 0 = generic kernel) */
+    int32_t row_tiles;          /* 1: staged backup tiles are whole innermost-dim rows */
+    int32_t block_states;       /* states (lane columns) per block of the backup */
+    int32_t grouped_inputs;     /* 1: runs of inputs sharing every outer dim's masses
+                                   are served by one outer contraction per run */
 } amy_info_t;
 
 /* Points per dim of [lb, ub] with step eta: floor((ub-lb)/eta + 1e-9) + 1

@@ -170,16 +170,23 @@ def amy_last_error() -> str:
 
 
 def amy_build(problem, tmode: str = "otf", prec: str = "fp32", v_store: str = "native",
-              device_mem_budget: int = 0, stream=None, use_graphs: bool = True) -> AmyHandle:
+              device_mem_budget: int = 0, stream=None, use_graphs: bool = True,
+              autotune: bool = False, launch_shape=None) -> AmyHandle:
     """amy_build: validate, derive the window and (stored modes) build T on the GPU.
 
-    `stream` is a cudaStream_t as int; None uses torch's current stream."""
+    `stream` is a cudaStream_t as int; None uses torch's current stream.
+    `autotune` times the backup's launch shapes at build and keeps the fastest;
+    `launch_shape` = (input lanes, states per block, row tiles 1 / consecutive 2,
+    box floats) fixes them instead (0 entries = automatic)."""
     k = _Keep()
     sysd, states, inputs, sigma, cut = _problem_structs(k, problem)
     o = _abi.amy_opts()
     o.tmode, o.prec, o.v_store = TMODES[tmode], PRECS[prec], VSTORES[v_store]
     o.device_mem_budget = int(device_mem_budget)
     o.use_graphs = int(bool(use_graphs))
+    o.autotune = int(bool(autotune))
+    for i, v in enumerate(launch_shape or ()):
+        o.launch_shape[i] = int(v)
     o.cuda_stream = C.c_void_p(stream) if stream is not None else _current_stream_ptr()
     out = C.c_void_p(0)
     _check(_lib().amy_build(C.byref(sysd), C.byref(states), C.byref(inputs), sigma, C.byref(cut),
@@ -199,7 +206,8 @@ def amy_info(h: AmyHandle) -> dict:
         "window_slots": int(info.window_slots), "window_sum": int(info.window_sum),
         "cut_half_width": [float(info.cut_half_width[d]) for d in range(n)],
         "device_bytes": int(info.device_bytes), "tmode": int(info.tmode), "prec": int(info.prec),
-        "v_store": int(info.v_store),
+        "v_store": int(info.v_store), "input_lanes": int(info.input_lanes), "row_tiles": int(info.row_tiles), "block_states": int(info.block_states),
+        "grouped_inputs": int(info.grouped_inputs),
     }
 
 

@@ -10,6 +10,8 @@
 // the single-problem register-resident kernel.
 #pragma once
 
+#include <climits>
+
 #include <algorithm>
 
 #include "amy_fast.cuh"
@@ -72,7 +74,12 @@ __global__ void __launch_bounds__(FAST_THREADS) k_step_group(const BatchEntry *_
         a.O = e.O;
         a.npairs = e.npairs;
         a.tab = e.tab;
-        backup_tile<VT, WM, TM, VAR>(sg, a, t - e.tile_begin, work);
+        a.rowtile = 0;
+        a.grouped = 0;
+        a.box_floats = 0;
+        a.stage_tab = 0;
+        const int64_t x = (t - e.tile_begin) * e.tileX + threadIdx.x % e.tileX;
+        backup_tile<VT, WM, TM, VAR>(sg, a, (int32_t)min(x, (int64_t)INT_MAX), work);
         __syncthreads();
     }
 }

@@ -293,6 +293,23 @@ amy_status plan_sep_tables(Geom &g, const std::vector<double> &params, int64_t &
     return AMY_OK;
 }
 
+int32_t input_outer_runs(const Geom &g, const std::vector<int32_t> &upart) {
+    if (g.n < 2 || upart.size() < (size_t)g.nu * g.urw) return g.nu;
+    int32_t runs = 0;
+    for (int32_t u = 0; u < g.nu; ++u) {
+        bool same = u > 0;
+        for (int d = 0; d < g.n - 1 && same; ++d)
+            same = upart[(size_t)u * g.urw + d] == upart[(size_t)(u - 1) * g.urw + d];
+        if (!same) ++runs;
+    }
+    return runs;
+}
+
+bool input_runs_share_outer(const Geom &g, const std::vector<int32_t> &upart) {
+    if (g.n < 2 || g.n > 3) return false;
+    return 2 * (int64_t)input_outer_runs(g, upart) <= g.nu;
+}
+
 int choose_tile(int32_t nx, int32_t nu, int sm_count) {
     int tx = 256;
     while (tx > 1 && (int64_t)tx * nu > 4096) tx >>= 1;
@@ -322,6 +339,12 @@ struct amy_handle_s {
     int64_t tab_words;
     int tileX;
     int fast_wm;          // width bound of the register-resident backup, 0 = generic kernel
+    int ulanes;           // its input lanes per state (0 = heuristic)
+    int rows;             // staged variant: row-aligned tiles allowed
+    int grouped;          // staged variant: outer dims contracted once per input run
+    int runs;             // number of those runs
+    int tilex;            // staged variant: lane columns per block (0 = default)
+    int box_floats;       // staged variant: box budget (0 = default)
     std::vector<double> host_params;
     // kernel timing: CUDA events around every backup / build kernel when profiling
     bool profiling;
@@ -452,12 +475,18 @@ struct KernelTimer {
 amy_status launch_backup_generic(amy_handle_s *h, int spec_kind, const void *Vn, void *Vo, void *Vfinal,
                                  uint16_t *pi);
 
+int tm_kind_of(const amy_handle_s *h) {
+    return h->tmode == AMY_T_ON_THE_FLY ? TM_OTF : h->tmode == AMY_T_STORED_FACTORED ? TM_FACTORED : TM_SEPARABLE;
+}
+
+bool fast_path(const amy_handle_s *h) { return h->fast_wm > 0 && h->tmode != AMY_T_STORED_FULL; }
+
 // One backup V_{k+1} (Vn) -> V_k (Vo) with the handle's precision: the
 // register-resident kernel when the window fits it, the generic one otherwise.
 amy_status launch_backup(amy_handle_s *h, int spec_kind, const void *Vn, void *Vo, void *Vfinal, uint16_t *pi) {
     KernelTimer tm(h, &h->ev_backup);
     amy_status st;
-    if (h->fast_wm > 0 && h->tmode != AMY_T_STORED_FULL) {
+    if (fast_path(h)) {
         FastCall c;
         c.Vn = Vn;
         c.Vo = Vo;
@@ -470,10 +499,13 @@ amy_status launch_backup(amy_handle_s *h, int spec_kind, const void *Vn, void *V
         c.O = h->d_O;
         c.npairs = h->npairs;
         c.tab = h->d_tab;
-        c.ulanes = 0;
-        const int tm_kind = h->tmode == AMY_T_ON_THE_FLY ? TM_OTF
-                            : h->tmode == AMY_T_STORED_FACTORED ? TM_FACTORED : TM_SEPARABLE;
-        st = launch_backup_fast(h->g, tm_kind, h->v_store, c, h->sm_count, h->stream);
+        c.ulanes = h->ulanes;
+        c.rows = h->rows;
+        c.grouped = h->grouped;
+        c.runs = h->runs;
+        c.tilex = h->tilex;
+        c.box_floats = h->box_floats;
+        st = launch_backup_fast(h->g, tm_kind_of(h), h->v_store, c, h->sm_count, h->stream);
     } else {
         st = launch_backup_generic(h, spec_kind, Vn, Vo, Vfinal, pi);
     }
@@ -539,6 +571,91 @@ const char *amy_last_error(void) { return amy::g_last_error.c_str(); }
 
 int64_t amy_grid_count(double lb, double ub, double eta) { return amy::grid_count(lb, ub, eta); }
 
+namespace {
+
+// Launch-shape autotuner (amy_opts.autotune).  Times the register-resident
+// backup for every input-lane count and, where the staged variant runs, both
+// tile mappings, on the handle's own V buffers with every state free, and
+// keeps the fastest.  The results do not depend on the shape: each (state,
+// input) sum is formed by the same arithmetic whatever thread owns it, and
+// the merge over input lanes keeps the lowest maximising input.
+amy_status autotune_shape(amy_handle_s *h) {
+    const double slots = (double)h->g.nx * (double)h->g.nu * (double)h->g.wtot;
+    if (!fast_path(h) || slots > 4e9) return AMY_OK;
+    AMY_CUDA(cudaMemsetAsync(h->d_mask, 0, (size_t)h->g.nx, h->stream), "autotune mask");
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    AMY_CUDA(cudaEventCreate(&ea), "autotune event");
+    if (cudaEventCreate(&eb) != cudaSuccess) {
+        cudaEventDestroy(ea);
+        return set_error(AMY_E_CUDA, "autotune event");
+    }
+    FastCall c;
+    c.Vn = h->d_V[0];
+    c.Vo = h->d_V[1];
+    c.Vfinal = nullptr;
+    c.pi = nullptr;
+    c.mask = h->d_mask;
+    c.spec_kind = SPEC_REACH;  // a zero mask leaves every state free
+    c.kahan = h->prec == AMY_PREC_FP32_KAHAN;
+    c.T = (const float *)h->d_T;
+    c.O = h->d_O;
+    c.npairs = h->npairs;
+    c.tab = h->d_tab;
+    c.grouped = h->grouped;
+    c.runs = h->runs;
+    const bool staged = fast_shape(h->g, tm_kind_of(h), c, h->sm_count).staged;
+    // candidates: power-of-two input lanes, plus one lane per input run; the
+    // staged variant also varies the states per block and the tile mapping
+    std::vector<int> uls = {1, 2, 4, 8};
+    if (staged && h->grouped && h->runs >= 2 && h->runs <= 8 && (h->runs & (h->runs - 1)) != 0)
+        uls.push_back(h->runs);
+    float best = 3.4e38f;
+    int best_ul = h->ulanes, best_tx = h->tilex, best_rows = h->rows, best_box = h->box_floats;
+    amy_status st = AMY_OK;
+    for (int ul : uls) {
+        if (ul > 1 && ul > h->g.nu) continue;
+        for (int tx = 32; tx <= 256 && st == AMY_OK; tx <<= 1) {
+            if (tx * ul > 256) break;
+            if (!staged && tx * ul != 256) continue;
+            for (int cand = 0; cand < (staged ? 4 : 1) && st == AMY_OK; ++cand) {
+                const int rows = cand & 1;
+                c.ulanes = ul;
+                c.tilex = staged ? tx : 0;
+                c.rows = rows;
+                c.box_floats = (cand >> 1) ? 3072 : 0;
+                if (rows == 1 && fast_shape(h->g, tm_kind_of(h), c, h->sm_count).rowtile == 0) continue;
+                st = launch_backup_fast(h->g, tm_kind_of(h), h->v_store, c, h->sm_count, h->stream);
+                cudaError_t e = cudaSuccess;
+                if (st == AMY_OK) e = cudaEventRecord(ea, h->stream);
+                for (int rep = 0; rep < 3 && st == AMY_OK && e == cudaSuccess; ++rep)
+                    st = launch_backup_fast(h->g, tm_kind_of(h), h->v_store, c, h->sm_count, h->stream);
+                if (st == AMY_OK && e == cudaSuccess) e = cudaEventRecord(eb, h->stream);
+                if (st == AMY_OK && e == cudaSuccess) e = cudaEventSynchronize(eb);
+                float ms = 0.0f;
+                if (st == AMY_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, ea, eb);
+                if (st == AMY_OK && e != cudaSuccess) st = cuda_error(e, "autotune timing");
+                if (st == AMY_OK && ms < best) {
+                    best = ms;
+                    best_ul = ul;
+                    best_tx = c.tilex;
+                    best_rows = rows;
+                    best_box = c.box_floats;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
+    if (st != AMY_OK) return st;
+    h->ulanes = best_ul;
+    h->tilex = best_tx;
+    h->rows = best_rows;
+    h->box_floats = best_box;
+    return AMY_OK;
+}
+
+}  // namespace
+
 amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_grid *inputs,
                      const double *sigma, const amy_cut *cut, const amy_opts *opts, amy_handle *out) {
     if (!out || !opts) return set_error(AMY_E_INVALID_ARG, "null argument");
@@ -591,6 +708,25 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     h->tileX = choose_tile(g.nx, g.nu, h->sm_count);
     h->npairs = (int64_t)g.nx * g.nu;
     h->fast_wm = fast_wm(g, h->prec);
+    h->ulanes = 0;
+    h->rows = 1;
+    h->grouped = 0;
+    h->runs = 0;
+    h->tilex = 0;
+    h->box_floats = 0;
+    {
+        const int32_t *ls = opts->launch_shape;
+        if (ls[0] < 0 || ls[0] > 8 || ls[1] < 0 || ls[1] > 256 || ls[1] % 32 != 0 ||
+            (ls[0] > 0 && ls[1] > 0 && ls[0] * ls[1] > 256) || ls[2] < 0 || ls[2] > 2 ||
+            (ls[3] != 0 && (ls[3] < 256 || ls[3] > 6144))) {
+            free_handle(h);
+            return set_error(AMY_E_INVALID_ARG, "bad launch shape");
+        }
+        h->ulanes = ls[0];
+        h->tilex = ls[1];
+        h->rows = ls[2] == 2 ? 0 : 1;
+        h->box_floats = ls[3];
+    }
     h->use_graphs = opts->use_graphs;
     h->host_params = params;
 #define TRY(x)                 \
@@ -617,6 +753,8 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     if (h->tmode == AMY_T_STORED_SEPARABLE) {
         std::vector<int32_t> upart;
         TRY(plan_sep_tables(h->g, params, h->tab_words, &upart));
+        h->grouped = input_runs_share_outer(h->g, upart);
+        h->runs = h->grouped ? input_outer_runs(h->g, upart) : 0;
         TRY(dev_alloc(h, (void **)&h->d_tab, (size_t)h->tab_words * 4, "separable tables"));
         e = cudaMemcpy(h->d_tab + h->g.uoff, upart.data(), upart.size() * 4, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
@@ -647,6 +785,7 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
         free_handle(h);
         return cuda_error(e, "build");
     }
+    if (opts->autotune) TRY(autotune_shape(h));
 #undef TRY
     amy_info_t &inf = h->info;
     memset(&inf, 0, sizeof inf);
@@ -662,6 +801,20 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     inf.tmode = h->tmode;
     inf.prec = h->prec;
     inf.v_store = h->v_store;
+    if (fast_path(h)) {
+        FastCall c;
+        c.ulanes = h->ulanes;
+        c.rows = h->rows;
+        c.grouped = h->grouped;
+        c.runs = h->runs;
+        c.tilex = h->tilex;
+        c.box_floats = h->box_floats;
+        const FastShape sh = fast_shape(h->g, tm_kind_of(h), c, h->sm_count);
+        inf.input_lanes = sh.ulanes;
+        inf.row_tiles = sh.rowtile > 0;
+        inf.block_states = sh.tilex;
+        inf.grouped_inputs = sh.staged && h->grouped;
+    }
     *out = h;
     return AMY_OK;
 }

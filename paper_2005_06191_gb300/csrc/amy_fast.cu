@@ -34,6 +34,21 @@ int fast_variant(const Geom &g, int wm, int tmode) {
     return ((g.periodic >> (g.n - 1)) & 1u) ? VAR_EXACT : VAR_EXACT_CONTIG;
 }
 
+FastShape fast_shape(const Geom &g, int tmode, const FastCall &c, int sm_count) {
+    FastShape sh;
+    const int wm = fast_wm(g, AMY_PREC_FP32);
+    const int var = wm ? fast_variant(g, wm, tmode) : VAR_GENERAL;
+    sh.staged = wm > 0 && wm <= 5 && tmode == TM_SEPARABLE && var >= VAR_EXACT && g.n <= 3 && !c.no_stage;
+    if (sh.staged) {
+        staged_default_shape(g, c, sm_count, sh.ulanes, sh.tilex);
+    } else {
+        sh.ulanes = (c.ulanes > 0 && FAST_THREADS % c.ulanes == 0) ? c.ulanes : fast_default_ulanes(g, sm_count);
+        sh.tilex = FAST_THREADS / sh.ulanes;
+    }
+    sh.rowtile = sh.staged ? staged_rowtile(g, sh.tilex, c.rows) : 0;
+    return sh;
+}
+
 amy_status launch_backup_fast(const Geom &g, int tmode, int v_store, const FastCall &c, int sm_count,
                               cudaStream_t st) {
     const int wm = fast_wm(g, AMY_PREC_FP32);

@@ -31,6 +31,10 @@ template <class VT> struct FastArgs {
     int32_t spec_kind;
     int32_t tileX;       // states per block
     int32_t ulanes;      // input lanes per state (tileX * ulanes == 256)
+    int32_t rowtile;     // staged kernel: innermost-dim rows per tile (0 = consecutive states)
+    int32_t grouped;     // staged kernel: inputs come in runs sharing their outer-dim records
+    int32_t box_floats;  // staged kernel: shared-memory box budget (floats)
+    int32_t stage_tab;   // staged kernel: words of the innermost dim's table to stage (0 = none)
     int32_t kahan;       // compensated accumulation over window rows
     const float *T;      // per-pair masses [sum W][pairs] (stored factored)
     const int16_t *O;    // per-pair origins [n][pairs]
@@ -151,7 +155,9 @@ __device__ __forceinline__ float inner_block(const VT *__restrict__ V, int32_t b
     return s;
 }
 
-// One tile (tileX consecutive states, all inputs) of the fused backup.
+// One tile (tileX states, all inputs) of the fused backup; x is the state of
+// this thread's lane column (xl = tid % tileX), any value >= nx when the
+// column is idle.
 // Kernel variants: VAR_GENERAL (widths up to WM), VAR_EXACT (every width
 // equals WM, so all width guards fold away), VAR_EXACT_CONTIG (also a bounded
 // innermost dim: its window row is read unclamped -- off-grid slots have zero
@@ -159,7 +165,7 @@ __device__ __forceinline__ float inner_block(const VT *__restrict__ V, int32_t b
 // one base address plus immediate offsets reads the whole row).
 // g may live in kernel parameters or in shared memory (batched kernel).
 template <class VT, int WM, int TM, int VAR>
-__device__ __forceinline__ void backup_tile(const Geom &g, const FastArgs<VT> &a, int64_t tile,
+__device__ __forceinline__ void backup_tile(const Geom &g, const FastArgs<VT> &a, int32_t x,
                                             unsigned char *smem_raw) {
     constexpr bool EXACT = VAR >= VAR_EXACT;
     constexpr bool CONTIG = VAR == VAR_EXACT_CONTIG;
@@ -168,7 +174,6 @@ __device__ __forceinline__ void backup_tile(const Geom &g, const FastArgs<VT> &a
     const int TX = a.tileX, UL = a.ulanes;
     const int xl = tid % TX;
     const int c = tid / TX;
-    const int32_t x = (int32_t)(tile * TX + xl);
     const int n = g.n;
     const int DO = n > 2 ? n - 2 : 0;   // outer dims walked by the odometer
     const int DH = DO > 1 ? DO - 1 : 0; // outer dims above the last outer one
@@ -182,7 +187,7 @@ __device__ __forceinline__ void backup_tile(const Geom &g, const FastArgs<VT> &a
 
     float best = -1.0f;
     int32_t arg = 0x7fffffff;
-    const bool active = x < g.nx;
+    const bool active = x >= 0 && x < g.nx;
     const uint8_t f = active ? a.mask[x] : (uint8_t)0;
     const bool masked = active && state_masked(a.spec_kind, f);
     if (active && !masked) {
@@ -440,7 +445,8 @@ template <class VT, int WM, int TM, int VAR>
 __global__ void __launch_bounds__(FAST_THREADS) k_backup_fast(const __grid_constant__ Geom g,
                                                               const FastArgs<VT> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    backup_tile<VT, WM, TM, VAR>(g, a, blockIdx.x, smem_raw);
+    const int64_t x = (int64_t)blockIdx.x * a.tileX + threadIdx.x % a.tileX;
+    backup_tile<VT, WM, TM, VAR>(g, a, (int32_t)min(x, (int64_t)INT_MAX), smem_raw);
 }
 
 // Per-dimension table construction (separable stored mode): record e of

@@ -4,6 +4,8 @@
 // compile in parallel.
 #pragma once
 
+#include <algorithm>
+
 #include "amy_fast.cuh"
 #include "amy_internal.h"
 #include "amy_staged.cuh"
@@ -30,9 +32,13 @@ amy_status launch_t(const Geom &g, const FastCall &c, int sm_count, cudaStream_t
     a.O = c.O;
     a.npairs = c.npairs;
     a.tab = c.tab;
+    a.rowtile = 0;
+    a.grouped = 0;
+    a.box_floats = 0;
+    a.stage_tab = 0;
     // Input lanes per state: one when the grid alone fills the GPU several
     // times over, otherwise up to 8 (power of two) to expose parallelism.
-    a.ulanes = c.ulanes > 0 ? c.ulanes : fast_default_ulanes(g, sm_count);
+    a.ulanes = (c.ulanes > 0 && FAST_THREADS % c.ulanes == 0) ? c.ulanes : fast_default_ulanes(g, sm_count);
     a.tileX = FAST_THREADS / a.ulanes;
     const size_t smem = fast_smem_bytes(g.n, WM);
     auto kern = k_backup_fast<VT, WM, TM, VAR>;
@@ -66,9 +72,19 @@ amy_status launch_staged_ns(const Geom &g, const FastCall &c, int sm_count, cuda
     a.O = c.O;
     a.npairs = c.npairs;
     a.tab = c.tab;
-    a.ulanes = c.ulanes > 0 ? c.ulanes : fast_default_ulanes(g, sm_count);
-    a.tileX = FAST_THREADS / a.ulanes;
-    const size_t smem = staged_smem_bytes(g.n, WM);
+    int ul = 0, tx = 0;
+    staged_default_shape(g, c, sm_count, ul, tx);
+    if (ul < 1 || tx < 32 || tx % 32 != 0 || tx * ul > FAST_THREADS)
+        return set_error(AMY_E_INVALID_ARG, "staged backup shape %d x %d", tx, ul);
+    a.ulanes = ul;
+    a.tileX = tx;
+    a.rowtile = staged_rowtile(g, a.tileX, c.rows);
+    a.grouped = c.grouped;
+    a.box_floats = c.box_floats > 0 ? std::min(std::max(c.box_floats, 256), STAGE_BOX_FLOATS) : STAGE_BOX_FLOATS;
+    const int64_t tabw = (int64_t)g.tent[g.n - 1] * g.trw[g.n - 1];
+    a.stage_tab = (c.grouped && tabw <= STAGE_TAB_WORDS) ? (int32_t)tabw : 0;
+    const int64_t blocks = staged_blocks(g, a.tileX, a.rowtile);
+    const size_t smem = staged_smem_bytes(g.n, WM, a.box_floats, g.nu, a.stage_tab);
     auto kern = k_backup_staged<VT, WM, TM, NS>;
     static bool raised = false;
     if (!raised) {
@@ -76,8 +92,7 @@ amy_status launch_staged_ns(const Geom &g, const FastCall &c, int sm_count, cuda
         if (e != cudaSuccess) return cuda_error(e, "staged backup smem attribute");
         raised = true;
     }
-    const int64_t blocks = ((int64_t)g.nx + a.tileX - 1) / a.tileX;
-    kern<<<(unsigned)blocks, FAST_THREADS, smem, st>>>(g, a);
+    kern<<<(unsigned)blocks, (unsigned)(a.tileX * a.ulanes), smem, st>>>(g, a);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? AMY_OK : cuda_error(e, "staged backup launch");
 }

@@ -34,7 +34,23 @@ struct FastCall {
     const uint32_t *tab;
     int32_t ulanes;   // input lanes per state (1, 2, 4, 8); 0 = heuristic
     int32_t no_stage = 0;  // 1: never use the shared-memory staged variant
+    int32_t rows = 1;      // staged variant: 1 = tiles of whole innermost-dim rows
+                           // (when most lanes stay busy), 0 = consecutive states
+    int32_t grouped = 0;   // staged variant: inputs come in runs that share every
+                           // outer dim's table record (see input_runs_share_outer)
+    int32_t runs = 0;      // number of such runs (0 = not grouped)
+    int32_t tilex = 0;     // staged variant: lane columns (states) per block, a
+                           // multiple of 32 with tilex * ulanes <= 256; 0 = 256 / ulanes
+    int32_t box_floats = 0;  // staged variant: box budget in floats (0 = 6144)
 };
+
+// Whether consecutive inputs form runs (at least two inputs per run on
+// average) whose table records agree on every dim but the innermost one, so
+// that the staged backup may contract the outer dims once per run.  upart
+// holds each input's table-index part per dim (urw words per input).
+bool input_runs_share_outer(const Geom &g, const std::vector<int32_t> &upart);
+// Number of runs of consecutive inputs with equal outer-dim table records.
+int32_t input_outer_runs(const Geom &g, const std::vector<int32_t> &upart);
 
 // Input lanes per state: one when the grid alone fills the GPU several times
 // over, otherwise up to 8 (power of two) to expose parallelism.
@@ -44,6 +60,53 @@ inline int fast_default_ulanes(const Geom &g, int sm_count) {
     while (ul < 8 && ul < g.nu && (int64_t)g.nx * ul < want) ul <<= 1;
     return ul;
 }
+
+// Rows per tile of the staged backup's row-aligned mapping for tileX lane
+// columns: each warp takes up to 32 consecutive states of one innermost-dim
+// row (chunks of 32 when the row is longer), so the lanes of a warp differ in
+// the innermost coordinate only and their reads of the staged window box fall
+// in distinct banks.  0 (consecutive states instead) when the mapping is off,
+// n < 2, or fewer than three quarters of the lanes would stay busy.
+inline int staged_rowtile(const Geom &g, int tileX, int rows) {
+    if (!rows || g.n < 2 || g.n > 3) return 0;
+    const int R = g.N[g.n - 1];
+    int ch = 1;
+    while (ch * 32 < R) ch <<= 1;
+    const int rw = tileX / (32 * ch);
+    return (rw >= 1 && 4 * R >= 3 * 32 * ch) ? rw : 0;
+}
+// Grid of the staged backup: row tiles (within one outermost index when n = 3)
+// or tiles of tileX consecutive states.
+inline int64_t staged_blocks(const Geom &g, int tileX, int rowtile) {
+    if (rowtile == 0) return ((int64_t)g.nx + tileX - 1) / tileX;
+    if (g.n == 3) return (int64_t)g.N[0] * ((g.N[1] + rowtile - 1) / rowtile);
+    return ((int64_t)g.N[0] + rowtile - 1) / rowtile;
+}
+// Launch shape the register-resident backup takes for these arguments.
+struct FastShape {
+    int ulanes;   // input lanes per state
+    int tilex;    // lane columns (states) per block
+    int rowtile;  // staged variant's rows per tile (0 = consecutive states)
+    int staged;   // 1 = shared-memory staged variant
+};
+// Default input lanes and lane columns of the staged variant: with input runs
+// (grouped), one lane per run when there are at most 8 runs, so that every
+// lane contracts the outer dims once; otherwise the register-resident default.
+inline void staged_default_shape(const Geom &g, const FastCall &c, int sm_count, int &ulanes, int &tilex) {
+    if (c.ulanes > 0)
+        ulanes = c.ulanes;
+    else if (c.grouped && c.runs >= 1 && c.runs <= 8)
+        ulanes = c.runs;
+    else
+        ulanes = fast_default_ulanes(g, sm_count);
+    if (c.tilex > 0)
+        tilex = c.tilex;
+    else if (256 % ulanes == 0)
+        tilex = 256 / ulanes;
+    else
+        tilex = 32 * (8 / ulanes);
+}
+FastShape fast_shape(const Geom &g, int tmode, const FastCall &c, int sm_count);
 
 // Width bound (3, 5, 8) of the fast backup for this geometry, 0 if it does not apply.
 int fast_wm(const Geom &g, int prec);

@@ -233,6 +233,8 @@ FastCall fast_call(const Req *r, const void *Vn, void *Vo, float *Vfinal, uint16
     c.npairs = (int64_t)npairs_of(r);
     c.tab = r->d_tab;
     c.ulanes = ulanes;
+    c.grouped = r->tm == TM_SEPARABLE && input_runs_share_outer(r->g, r->upart);
+    c.runs = c.grouped ? input_outer_runs(r->g, r->upart) : 0;
     return c;
 }
 

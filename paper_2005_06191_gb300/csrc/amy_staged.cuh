@@ -20,10 +20,16 @@
 
 namespace amy {
 
-constexpr int STAGE_BOX_FLOATS = 6144;  // 24 KiB staging box per block
+constexpr int STAGE_BOX_FLOATS = 6144;  // default staging box per block (24 KiB)
+constexpr int STAGE_UP_MAX = 512;       // inputs whose table-index parts are staged too
+constexpr int STAGE_TAB_WORDS = 4096;   // inner-dim table staged when at most this many words
 
-__host__ __device__ inline size_t staged_smem_bytes(int n, int WM) {
-    return (size_t)STAGE_BOX_FLOATS * 4 + fast_smem_bytes(n, WM);
+// Shared memory of one block: the staging box, the register-resident body's
+// area (also the lane-merge arrays), the inputs' table-index parts and, for
+// the per-run pass, the innermost dim's table (tab_words, 0 = not staged).
+__host__ __device__ inline size_t staged_smem_bytes(int n, int WM, int box_floats, int nu, int tab_words) {
+    return (size_t)box_floats * 4 + fast_smem_bytes(n, WM) + (nu <= STAGE_UP_MAX ? (size_t)nu * 16 : 0) +
+           (size_t)tab_words * 4;
 }
 
 // Mean of one (state, input) pair from the state's precomputed FP64 centres
@@ -58,13 +64,169 @@ __device__ __forceinline__ void item_mean(const Geom &g, int32_t u, const double
     }
 }
 
+// Extra inner-dim slots, beyond the window width, that one cached outer
+// contraction may span (inputs whose inner windows start up to this many
+// cells apart share it).
+constexpr int STAGE_KX = 3;
+
+// Window sums of one state for the inputs [u0, u1) when inputs come in runs
+// that share every outer dim's record (same masses and origins; e.g. the
+// unicycle's speed fixes the x and y rows and only the turn rate moves the
+// heading window).  For a run, the outer dims are contracted once over the K
+// inner slots [r0, r0 + K) that any input's inner window can reach,
+//   R[k] = sum_i t0_i * (sum_j t1_j * V[o0 + i, o1 + j, r0 + k])   (NS = 3),
+// and each input then needs only its inner row: s = sum_k tL_k * R[oL - r0 + k].
+// R depends only on the state and the run's records, so the result does not
+// depend on how inputs are split over threads.  BOX: V from the staged
+// shared-memory box; otherwise from global memory with clamped / wrapped
+// cells (off-grid cells carry zero mass either way, so both give the same
+// bits).
+template <class VT, int WM, int NS, bool BOX>
+__device__ __forceinline__ void grouped_items(const Geom &g, const FastArgs<VT> &a, const int4 *up,
+                                              const uint4 *tabL, const int32_t (&xi)[MAXD], const int32_t (&es)[3], int32_t u0,
+                                              int32_t u1, int32_t dminL, int32_t K, const float *sbox,
+                                              const int32_t (&blo)[3], const int32_t (&bs)[3], float &best,
+                                              int32_t &arg) {
+    constexpr int L = NS - 1;
+    constexpr int KM = WM + STAGE_KX;
+    constexpr int NQ = (WM + 1 + 3) / 4;  // uint4 words of one record (origin + WM masses)
+    if (u0 >= u1) return;
+    float R[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) R[k] = 0.0f;
+    int32_t key0 = INT_MIN, key1 = INT_MIN;
+    const int32_t r0 = xi[L] + dminL;  // first inner slot of R (unwrapped)
+    // this state's records of the inner dim: record es[L] + ui[L] of table L
+    const uint4 *recL = tabL + (int64_t)es[L] * NQ;
+    // one input ahead: its table-index parts and its inner record are loaded
+    // while the current input is summed
+    int4 uv_n = up[u0];
+    uint4 rq_n[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) rq_n[q] = recL[(int64_t)(NS == 3 ? uv_n.z : uv_n.y) * NQ + q];
+    for (int32_t u = u0; u < u1; ++u) {
+        const int4 uv = uv_n;
+        uint4 rq[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) rq[q] = rq_n[q];
+        if (u + 1 < u1) {
+            uv_n = up[u + 1];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) rq_n[q] = recL[(int64_t)(NS == 3 ? uv_n.z : uv_n.y) * NQ + q];
+        }
+        const int32_t k0 = es[0] + uv.x;
+        const int32_t k1 = NS == 3 ? es[1] + uv.y : 0;
+        if (k0 != key0 || k1 != key1) {
+            key0 = k0;
+            key1 = k1;
+            int32_t o[2] = {0, 0};
+            float t[2][WM];
+#pragma unroll
+            for (int d = 0; d < L; ++d) {
+                const uint4 *rec = reinterpret_cast<const uint4 *>(a.tab + g.toff[d]) + (int64_t)(d == 0 ? k0 : k1) * NQ;
+                uint32_t wds[NQ * 4];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const uint4 v = __ldg(rec + q);
+                    wds[q * 4 + 0] = v.x;
+                    wds[q * 4 + 1] = v.y;
+                    wds[q * 4 + 2] = v.z;
+                    wds[q * 4 + 3] = v.w;
+                }
+                o[d] = (int32_t)wds[0];
+#pragma unroll
+                for (int k = 0; k < WM; ++k) t[d][k] = __uint_as_float(wds[1 + k]);
+            }
+            if (BOX) {
+                int32_t base = r0 - blo[L];
+#pragma unroll
+                for (int d = 0; d < L; ++d) base += (o[d] - blo[d]) * bs[d];
+#pragma unroll
+                for (int kk = 0; kk < KM; ++kk) {
+                    if (kk < K) {
+                        float acc = 0.0f, comp = 0.0f;
+#pragma unroll
+                        for (int i = 0; i < WM; ++i) {
+                            const float *pr = sbox + base + i * bs[0] + kk;
+                            float inner;
+                            if (NS == 3) {
+                                inner = 0.0f;
+#pragma unroll
+                                for (int j = 0; j < WM; ++j) inner = fmaf(t[1][j], pr[j * bs[1]], inner);
+                            } else {
+                                inner = pr[0];
+                            }
+                            accum_row(acc, comp, __fmul_rn(t[0][i], inner), a.kahan);
+                        }
+                        R[kk] = acc;
+                    }
+                }
+            } else {
+                int32_t of0[WM], of1[WM], ofL[KM];
+                dim_offsets_reg<WM>(g, 0, o[0], WM, of0);
+                if (NS == 3) dim_offsets_reg<WM>(g, 1, o[1], WM, of1);
+                dim_offsets_reg<KM>(g, L, r0, K, ofL);
+#pragma unroll
+                for (int kk = 0; kk < KM; ++kk) {
+                    if (kk < K) {
+                        float acc = 0.0f, comp = 0.0f;
+#pragma unroll
+                        for (int i = 0; i < WM; ++i) {
+                            float inner;
+                            if (NS == 3) {
+                                inner = 0.0f;
+#pragma unroll
+                                for (int j = 0; j < WM; ++j)
+                                    inner = fmaf(t[1][j], vload<float, VT>(a.Vn + (of0[i] + of1[j] + ofL[kk])), inner);
+                            } else {
+                                inner = vload<float, VT>(a.Vn + (of0[i] + ofL[kk]));
+                            }
+                            accum_row(acc, comp, __fmul_rn(t[0][i], inner), a.kahan);
+                        }
+                        R[kk] = acc;
+                    }
+                }
+            }
+        }
+        // the input's own inner row: s = sum_k tL_k * R[sh + k], sh = oL - r0 in [0, K - WM]
+        uint32_t wds[NQ * 4];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            wds[q * 4 + 0] = rq[q].x;
+            wds[q * 4 + 1] = rq[q].y;
+            wds[q * 4 + 2] = rq[q].z;
+            wds[q * 4 + 3] = rq[q].w;
+        }
+        const int32_t sh = (int32_t)wds[0] - r0;
+        float w[WM];
+#pragma unroll
+        for (int k = 0; k < WM; ++k) w[k] = R[k];
+#pragma unroll
+        for (int q = 1; q <= STAGE_KX; ++q) {
+            if (sh >= q) {
+#pragma unroll
+                for (int k = 0; k < WM; ++k) w[k] = R[q + k];
+            }
+        }
+        float sum = 0.0f;
+#pragma unroll
+        for (int k = 0; k < WM; ++k) sum = fmaf(__uint_as_float(wds[1 + k]), w[k], sum);
+        if (sum > best) {
+            best = sum;
+            arg = u;
+        }
+    }
+}
+
 template <class VT, int WM, int TM, int NS>
 __global__ void __launch_bounds__(FAST_THREADS) k_backup_staged(const __grid_constant__ Geom g,
                                                                 const FastArgs<VT> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int BT = FAST_THREADS;
     float *sbox = reinterpret_cast<float *>(smem_raw);
-    unsigned char *work = smem_raw + (size_t)STAGE_BOX_FLOATS * 4;  // also the fallback's area
+    unsigned char *work = smem_raw + (size_t)a.box_floats * 4;  // also the fallback's area
+    int4 *s_up = reinterpret_cast<int4 *>(work + fast_smem_bytes(NS, WM));
+    uint4 *s_tabL = reinterpret_cast<uint4 *>(s_up + (g.nu <= STAGE_UP_MAX ? g.nu : 0));
     float *cBest = reinterpret_cast<float *>(work);
     int32_t *cArg = reinterpret_cast<int32_t *>(cBest + BT);
     __shared__ int32_t s_lo[3], s_hi[3];
@@ -73,12 +235,35 @@ __global__ void __launch_bounds__(FAST_THREADS) k_backup_staged(const __grid_con
     const int TX = a.tileX, UL = a.ulanes;
     const int xl = tid % TX;
     const int c = tid / TX;
-    const int32_t x = (int32_t)blockIdx.x * TX + xl;
+    int32_t x;
+    if (NS >= 2 && a.rowtile > 0) {
+        // row-aligned tile: lane column xl = (row r, chunk ch, lane) of rowtile
+        // consecutive innermost-dim rows (within one outermost index when NS = 3)
+        const int RW = a.rowtile;
+        const int CHU = TX / (32 * RW);
+        const int32_t R = g.N[NS - 1];
+        const int r = (xl >> 5) / CHU;
+        const int32_t k_in = ((xl >> 5) % CHU) * 32 + (xl & 31);
+        int32_t row;
+        bool ok;
+        if (NS == 3) {
+            const int32_t t1 = (g.N[1] + RW - 1) / RW;
+            const int32_t i1 = (int32_t)(blockIdx.x % t1) * RW + r;
+            row = (int32_t)(blockIdx.x / t1) * g.N[1] + i1;
+            ok = i1 < g.N[1];
+        } else {
+            row = (int32_t)blockIdx.x * RW + r;
+            ok = row < g.N[0];
+        }
+        x = (ok && k_in < R) ? row * R + k_in : INT_MAX;
+    } else {
+        x = (int32_t)blockIdx.x * TX + xl;
+    }
     if (tid < 3) {
         s_lo[tid] = INT_MAX;
         s_hi[tid] = INT_MIN;
     }
-    const bool active = x < g.nx;
+    const bool active = x >= 0 && x < g.nx;
     const uint8_t f = active ? a.mask[x] : (uint8_t)0;
     const bool masked = active && state_masked(a.spec_kind, f);
     const bool work_items = active && !masked;
@@ -187,17 +372,33 @@ __global__ void __launch_bounds__(FAST_THREADS) k_backup_staged(const __grid_con
         bn[d] = any ? (s_hi[d] - s_lo[d] + WM) : 1;
         vol *= bn[d];
     }
-    if (vol > STAGE_BOX_FLOATS) {
+    // inputs in runs sharing their outer records: contract the outer dims
+    // once per run (decided per launch from the tables, the same in every block)
+    constexpr int L = NS - 1;
+    int32_t dminL = 0, KL = 0;
+    bool grouped = false;
+    if (TM == TM_SEPARABLE && NS >= 2 && a.grouped && analytic) {
+        dminL = __ldg(rb + L);
+        KL = __ldg(rb + MAXD + L) - dminL + WM;
+        // (K <= N keeps a wrapped row of K cells to one lap of a periodic dim)
+        // (records of 4*NQ words and 4-word table-index parts are assumed)
+        bool strides = g.urw == 4;
+#pragma unroll
+        for (int d = 0; d < NS; ++d) strides = strides && g.trw[d] == 4 * ((WM + 1 + 3) / 4);
+        grouped = strides && KL >= WM && KL <= WM + STAGE_KX && KL <= g.N[L];
+    }
+    const bool fits = vol <= a.box_floats;
+    if (!fits && !grouped) {
         // this tile's windows spread too far: the register-resident body
-        backup_tile<VT, WM, TM, VAR_EXACT>(g, a, blockIdx.x, work);
+        backup_tile<VT, WM, TM, VAR_EXACT>(g, a, x, work);
         return;
     }
-    {
+    if (fits) {
         // row stride padded to a multiple of 32 floats when it fits: lanes whose
         // windows differ by whole rows then still hit distinct banks
         int32_t inner = bn[NS - 1];
         const int32_t padded = (inner + 31) / 32 * 32;
-        if (NS > 1 && (vol / inner) * padded <= STAGE_BOX_FLOATS) inner = padded;
+        if (NS > 1 && (vol / inner) * padded <= a.box_floats) inner = padded;
         int32_t s = 1;
 #pragma unroll
         for (int d = NS - 1; d >= 0; --d) {
@@ -205,32 +406,80 @@ __global__ void __launch_bounds__(FAST_THREADS) k_backup_staged(const __grid_con
             s *= (d == NS - 1) ? inner : bn[d];
         }
     }
-    // stage the box: periodic dims wrap, off-grid cells hold 0 (zero mass there)
-    if (any) {
-        for (int32_t i = tid; i < (int32_t)vol; i += BT) {
+    // stage the box: periodic dims wrap, off-grid cells hold 0 (zero mass
+    // there).  A warp takes one box row (outer coordinates decoded once per
+    // row) and its lanes walk the innermost extent; the innermost cell wraps
+    // or clips with a compare per element.
+    if (any && fits) {
+        const int32_t inner = bn[NS - 1];
+        const int32_t nrows = (int32_t)(vol / inner);
+        const int d_in = NS - 1;
+        const int32_t Nin = g.N[d_in], st_in = g.stride[d_in];
+        const bool per_in = (g.periodic >> d_in) & 1u;
+        const int lane = tid & 31;
+        for (int32_t rr = tid >> 5; rr < nrows; rr += (int32_t)(blockDim.x >> 5)) {
             int64_t lin = 0;
             int32_t sidx = 0;
             bool on = true;
-            int32_t r = i;
+            int32_t q = rr;
 #pragma unroll
-            for (int d = NS - 1; d >= 0; --d) {
-                const int32_t kd = r % bn[d];
-                r /= bn[d];
+            for (int d = NS - 2; d >= 0; --d) {
+                const int32_t kd = q % bn[d];
+                q /= bn[d];
                 bool ond;
                 const int32_t cell = cell_of(g, d, blo[d] + kd, ond);
                 on = on && ond;
                 lin += (int64_t)cell * g.stride[d];
                 sidx += kd * bs[d];
             }
-            sbox[sidx] = on ? vload<float, VT>(a.Vn + lin) : 0.0f;
+            for (int32_t k = lane; k < inner; k += 32) {
+                int32_t cin = blo[d_in] + k;
+                bool onk = on;
+                if ((uint32_t)cin >= (uint32_t)Nin) {
+                    if (per_in) {
+                        cin %= Nin;
+                        cin = cin < 0 ? cin + Nin : cin;
+                    } else {
+                        onk = false;
+                        cin = 0;
+                    }
+                }
+                sbox[sidx + k] = onk ? vload<float, VT>(a.Vn + lin + (int64_t)cin * st_in) : 0.0f;
+            }
+        }
+    }
+    // the inputs' table-index parts and the innermost dim's table, for the
+    // per-run pass (read through generic pointers: shared or global)
+    const int4 *up = reinterpret_cast<const int4 *>(a.tab + g.uoff);
+    const uint4 *tabL = reinterpret_cast<const uint4 *>(a.tab + g.toff[L]);
+    if (TM == TM_SEPARABLE && grouped) {
+        if (g.nu <= STAGE_UP_MAX) {
+            for (int32_t u = tid; u < g.nu; u += (int32_t)blockDim.x) s_up[u] = __ldg(up + u);
+            up = s_up;
+        }
+        if (a.stage_tab > 0) {
+            for (int32_t i = tid; i < a.stage_tab / 4; i += (int32_t)blockDim.x) s_tabL[i] = __ldg(tabL + i);
+            tabL = s_tabL;
         }
     }
     __syncthreads();
 
-    // pass 2: window sums from the box (summation order of amy_fast.cuh)
+    // pass 2: window sums from the box (summation order of amy_fast.cuh), or
+    // per run of inputs sharing their outer records
     float best = -1.0f;
     int32_t arg = 0x7fffffff;
-    if (work_items) {
+    if (work_items && grouped) {
+        if constexpr (TM == TM_SEPARABLE && NS >= 2) {
+            const int32_t chunk = (g.nu + UL - 1) / UL;
+            const int32_t u0 = c * chunk, u1 = min(g.nu, u0 + chunk);
+            if (fits)
+                grouped_items<VT, WM, NS, true>(g, a, up, tabL, xi, es, u0, u1, dminL, KL, sbox, blo, bs, best,
+                                                arg);
+            else
+                grouped_items<VT, WM, NS, false>(g, a, up, tabL, xi, es, u0, u1, dminL, KL, sbox, blo, bs, best,
+                                                 arg);
+        }
+    } else if (work_items) {
         for (int32_t u = c; u < g.nu; u += UL) {
             int32_t o[3];
             float t[3][WM];

@@ -198,15 +198,82 @@ def test_unicycle_separable(amy, unicycle_ref, prec, v_store):
 
 
 def test_separable_tables_match_factored_bitwise(amy):
-    """Tabulating each component over its dependencies changes no value."""
+    """Tabulating each component over its dependencies changes no value.  (The
+    unicycle's inputs come in runs sharing the x and y rows; there the tables'
+    kernel contracts those rows once per run, a different summation order, so
+    it is compared within the FP32 tolerance instead.)"""
     for w in [W.unicycle(nxy=31, horizon=6, target=(3.0, 5.0)), W.rooms7(n_per_dim=4, horizon=3),
               W.traffic6(n_per_dim=5, horizon=2), W.served_stream(3)[2]]:
-        out = {}
+        out, grouped = {}, False
         for tmode in ["stored_factored", "stored_separable"]:
             with amy.amy_build(w.problem, tmode=tmode, prec="fp32") as h:
+                grouped = grouped or amy.amy_info(h)["grouped_inputs"] == 1
                 out[tmode] = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
+        if grouped:
+            assert w.problem.name.startswith("unicycle")
+            assert np.max(np.abs(out["stored_factored"][0] - out["stored_separable"][0])) <= 2e-6
+            continue
         assert np.array_equal(out["stored_factored"][0], out["stored_separable"][0])
         assert np.array_equal(out["stored_factored"][1], out["stored_separable"][1])
+
+
+def _steer_problem():
+    """2-D affine system whose second input only moves the inner dim (runs of 5
+    inputs share the outer row) and whose outer dim spreads its windows over
+    the whole grid, so that every row tile's box overflows shared memory."""
+    p = W.Problem(name="steer2", x_lb=[-3.0, -3.0], x_eta=[6.0 / 63, 6.0 / 29], x_count=[64, 30],
+                  x_periodic=[0, 0], u_lb=[-1.0, -1.0], u_eta=[1.0, 0.5], u_count=[3, 5],
+                  sys_kind=W.AFFINE, params=np.zeros(0), sigma=[0.3, 0.25], gamma=0.0, window=[3, 3])
+    A = np.array([[3.0, 0.0], [0.0, 1.0]])
+    B = np.array([[0.5, 0.0], [0.0, 0.1]])
+    p.params = W.linear_system_params(A, B, W.input_centres(p))
+    spec = W.Spec(W.REACH_AVOID, targets=[([0.2, 1.0], [0.6, 2.5])], avoids=[([-0.5, -1.0], [0.0, 0.0])])
+    return W.Workload(p, spec, 6, precision="fp32")
+
+
+def test_grouped_inputs_box_and_global_paths(amy):
+    """The per-run outer contraction: staged (unicycle) and from global memory
+    when the window box overflows (steer2) both match the oracle."""
+    for w in [W.unicycle(nxy=31, horizon=6, target=(3.0, 5.0)), _steer_problem()]:
+        with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32") as h:
+            assert amy.amy_info(h)["grouped_inputs"] == 1
+        compare_synthesis(amy, w, "stored_separable", "fp32")
+        compare_synthesis(amy, w, "stored_separable", "fp32_kahan")
+        compare_synthesis(amy, w, "stored_separable", "fp32", v_store="u16")
+
+
+def test_launch_shapes_agree_bitwise(amy):
+    """Any launch shape (input lanes per state; staged tiles of whole rows or of
+    consecutive states; boxes too wide for shared memory falling back to the
+    register-resident body) gives the same values and policies."""
+    rng = np.random.default_rng(5)
+    cases = [
+        W.unicycle(nxy=31, horizon=6, target=(3.0, 5.0)),                          # rows of 30, periodic
+        W.random_affine(rng, 2, [37, 30], 6, window=[3, 3], horizon=5),             # 2-D rows of 30
+        W.random_affine(rng, 3, [6, 7, 60], 5, window=[5, 5, 5], horizon=3),        # rows of 60: 2 chunks
+        W.random_affine(rng, 3, [5, 6, 29], 3, window=[3, 3, 3], periodic=[0, 0, 1], horizon=4),
+    ]
+    # fixed shapes: (input lanes, states per block, rows 1 / consecutive 2, box floats);
+    # a 256-float box overflows for most tiles and takes the global-memory path
+    fixed = [(1, 256, 2, 0), (5, 32, 1, 0), (2, 64, 1, 256), (3, 64, 2, 0), (8, 32, 0, 1024)]
+    for i, w in enumerate(cases):
+        out, shapes = [], []
+        runs = [dict(autotune=False), dict(autotune=True)] + [dict(launch_shape=f) for f in fixed]
+        for kw in runs:
+            with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32", **kw) as h:
+                info = amy.amy_info(h)
+                shapes.append((info["input_lanes"], info["block_states"], info["row_tiles"]))
+                out.append(amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True))
+        for k in range(1, len(runs)):
+            assert np.array_equal(out[0][0], out[k][0]), (i, shapes[k])
+            assert np.array_equal(out[0][1], out[k][1]), (i, shapes[k])
+        if i == 0:
+            assert shapes[0][2] == 1   # the default shape of the unicycle uses row tiles
+        compare_synthesis(amy, w, "stored_separable", "fp32")
+    for bad in [(9, 0, 0, 0), (0, 48, 0, 0), (4, 128, 0, 0), (0, 0, 3, 0), (0, 0, 0, 100)]:
+        with pytest.raises(amy.AmyError) as e:
+            amy.amy_build(cases[0].problem, tmode="stored_separable", prec="fp32", launch_shape=bad)
+        assert "INVALID_ARG" in str(e.value)
 
 
 def test_separable_rows_and_other_workloads(amy, robot_ref):
