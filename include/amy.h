@@ -140,7 +140,7 @@ typedef struct {
     int32_t launch_shape[4];    /* fixed backup launch shape, each entry 0 = automatic:
                                    [0] input lanes per state (1..8), [1] states per
                                    block of the staged variant (multiple of 32,
-                                   [0]*[1] <= 256), [2] 1 = row tiles, 2 = tiles of
+                                   [0]*[1] <= 512), [2] 1 = row tiles, 2 = tiles of
                                    consecutive states, [3] staged box budget in floats
                                    (256..6144).  Entries that do not apply are ignored;
                                    the autotuner, when on, overrides them. */
@@ -263,7 +263,7 @@ const char *amy_last_error(void);
  * parameters, the per-state spec flags and the two value vectors live in one
  * file-scope device array of AMY_NOALLOC_SCRATCH_BYTES, which every GPU that
  * loads the library holds until the process exits.  A problem needs
- * 8*n_params + n_states + 2*4*(n_states + 32) bytes (each part rounded up to
+ * 8*n_params + n_states + 2*4*(n_states + 64) bytes (each part rounded up to
  * 256); larger problems return AMY_E_INVALID_ARG with a message naming the
  * limit.
  *

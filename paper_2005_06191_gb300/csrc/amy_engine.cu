@@ -607,15 +607,16 @@ amy_status autotune_shape(amy_handle_s *h) {
     // candidates: power-of-two input lanes, plus one lane per input run; the
     // staged variant also varies the states per block and the tile mapping
     std::vector<int> uls = {1, 2, 4, 8};
-    if (staged && h->grouped && h->runs >= 2 && h->runs <= 8 && (h->runs & (h->runs - 1)) != 0)
-        uls.push_back(h->runs);
+    if (staged && h->grouped && h->runs >= 2)  // lanes take whole runs: any count up to the runs
+        for (int ul = 3; ul <= std::min(h->runs, 8); ++ul)
+            if ((ul & (ul - 1)) != 0) uls.push_back(ul);
     float best = 3.4e38f;
     int best_ul = h->ulanes, best_tx = h->tilex, best_rows = h->rows, best_box = h->box_floats;
     amy_status st = AMY_OK;
     for (int ul : uls) {
         if (ul > 1 && ul > h->g.nu) continue;
-        for (int tx = 32; tx <= 256 && st == AMY_OK; tx <<= 1) {
-            if (tx * ul > 256) break;
+        for (int tx = 32; tx <= 512 && st == AMY_OK; tx <<= 1) {
+            if (tx * ul > (staged ? 512 : 256)) break;
             if (!staged && tx * ul != 256) continue;
             for (int cand = 0; cand < (staged ? 4 : 1) && st == AMY_OK; ++cand) {
                 const int rows = cand & 1;
@@ -716,8 +717,8 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     h->box_floats = 0;
     {
         const int32_t *ls = opts->launch_shape;
-        if (ls[0] < 0 || ls[0] > 8 || ls[1] < 0 || ls[1] > 256 || ls[1] % 32 != 0 ||
-            (ls[0] > 0 && ls[1] > 0 && ls[0] * ls[1] > 256) || ls[2] < 0 || ls[2] > 2 ||
+        if (ls[0] < 0 || ls[0] > 8 || ls[1] < 0 || ls[1] > 512 || ls[1] % 32 != 0 ||
+            (ls[0] > 0 && ls[1] > 0 && ls[0] * ls[1] > 512) || ls[2] < 0 || ls[2] > 2 ||
             (ls[3] != 0 && (ls[3] < 256 || ls[3] > 6144))) {
             free_handle(h);
             return set_error(AMY_E_INVALID_ARG, "bad launch shape");

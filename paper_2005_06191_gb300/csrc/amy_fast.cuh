@@ -183,7 +183,7 @@ __device__ __forceinline__ void backup_tile(const Geom &g, const FastArgs<VT> &a
     float *sP = reinterpret_cast<float *>(sK + DH * BT);
     int32_t *sB = reinterpret_cast<int32_t *>(sP + DH * BT);
     float *cBest = reinterpret_cast<float *>(sB + DH * BT);
-    int32_t *cArg = reinterpret_cast<int32_t *>(cBest + BT);
+    int32_t *cArg = reinterpret_cast<int32_t *>(cBest + blockDim.x);  // one entry per thread
 
     float best = -1.0f;
     int32_t arg = 0x7fffffff;

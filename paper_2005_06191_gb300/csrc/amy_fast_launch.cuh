@@ -74,7 +74,7 @@ amy_status launch_staged_ns(const Geom &g, const FastCall &c, int sm_count, cuda
     a.tab = c.tab;
     int ul = 0, tx = 0;
     staged_default_shape(g, c, sm_count, ul, tx);
-    if (ul < 1 || tx < 32 || tx % 32 != 0 || tx * ul > FAST_THREADS)
+    if (ul < 1 || tx < 32 || tx % 32 != 0 || tx * ul > STAGE_MAX_THREADS)
         return set_error(AMY_E_INVALID_ARG, "staged backup shape %d x %d", tx, ul);
     a.ulanes = ul;
     a.tileX = tx;
@@ -84,7 +84,7 @@ amy_status launch_staged_ns(const Geom &g, const FastCall &c, int sm_count, cuda
     const int64_t tabw = (int64_t)g.tent[g.n - 1] * g.trw[g.n - 1];
     a.stage_tab = (c.grouped && tabw <= STAGE_TAB_WORDS) ? (int32_t)tabw : 0;
     const int64_t blocks = staged_blocks(g, a.tileX, a.rowtile);
-    const size_t smem = staged_smem_bytes(g.n, WM, a.box_floats, g.nu, a.stage_tab);
+    const size_t smem = staged_smem_bytes(g.n, WM, a.box_floats, g.nu, a.stage_tab, a.tileX * a.ulanes);
     auto kern = k_backup_staged<VT, WM, TM, NS>;
     static bool raised = false;
     if (!raised) {

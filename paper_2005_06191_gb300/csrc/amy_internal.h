@@ -2,6 +2,7 @@
 // engine (error reporting, problem validation, small conversion kernels).
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 #include <vector>
 
@@ -40,7 +41,7 @@ struct FastCall {
                            // outer dim's table record (see input_runs_share_outer)
     int32_t runs = 0;      // number of such runs (0 = not grouped)
     int32_t tilex = 0;     // staged variant: lane columns (states) per block, a
-                           // multiple of 32 with tilex * ulanes <= 256; 0 = 256 / ulanes
+                           // multiple of 32 with tilex * ulanes <= 512; 0 = default
     int32_t box_floats = 0;  // staged variant: box budget in floats (0 = 6144)
 };
 
@@ -101,10 +102,8 @@ inline void staged_default_shape(const Geom &g, const FastCall &c, int sm_count,
         ulanes = fast_default_ulanes(g, sm_count);
     if (c.tilex > 0)
         tilex = c.tilex;
-    else if (256 % ulanes == 0)
-        tilex = 256 / ulanes;
     else
-        tilex = 32 * (8 / ulanes);
+        tilex = std::min(256, 32 * std::max(1, 16 / ulanes));
 }
 FastShape fast_shape(const Geom &g, int tmode, const FastCall &c, int sm_count);
 
@@ -115,8 +114,9 @@ int fast_wm(const Geom &g, int prec);
 int fast_variant(const Geom &g, int wm, int tmode);
 // Finite guard cells on each side of every V buffer the fast kernels read:
 // the contiguous-row variant reads a bounded innermost row unclamped (the
-// off-grid slots have zero mass), up to kVGuard cells past either end.
-constexpr int64_t kVGuard = 16;
+// off-grid slots have zero mass; origins are clamped to [-(W+1), N+1], so a
+// row reaches at most W + 1 <= 9 cells past either end of the buffer).
+constexpr int64_t kVGuard = 32;
 amy_status launch_backup_fast(const Geom &g, int tmode, int v_store, const FastCall &c, int sm_count,
                               cudaStream_t st);
 amy_status launch_build_sep(const Geom &g, uint32_t *tab, int sm_count, cudaStream_t st);

@@ -15,6 +15,7 @@
 #pragma once
 
 #include <climits>
+#include <type_traits>
 
 #include "amy_fast.cuh"
 
@@ -23,13 +24,22 @@ namespace amy {
 constexpr int STAGE_BOX_FLOATS = 6144;  // default staging box per block (24 KiB)
 constexpr int STAGE_UP_MAX = 512;       // inputs whose table-index parts are staged too
 constexpr int STAGE_TAB_WORDS = 4096;   // inner-dim table staged when at most this many words
+constexpr int STAGE_MAX_THREADS = 512;  // threads per block of the staged kernel
 
-// Shared memory of one block: the staging box, the register-resident body's
-// area (also the lane-merge arrays), the inputs' table-index parts and, for
-// the per-run pass, the innermost dim's table (tab_words, 0 = not staged).
-__host__ __device__ inline size_t staged_smem_bytes(int n, int WM, int box_floats, int nu, int tab_words) {
-    return (size_t)box_floats * 4 + fast_smem_bytes(n, WM) + (nu <= STAGE_UP_MAX ? (size_t)nu * 16 : 0) +
-           (size_t)tab_words * 4;
+// The register-resident body's area (its odometer arrays, laid out for
+// FAST_THREADS, and the lane-merge arrays, one entry per thread).
+__host__ __device__ inline size_t staged_work_bytes(int n, int WM, int threads) {
+    const size_t a = fast_smem_bytes(n, WM), b = (size_t)threads * 8;
+    return a > b ? a : b;
+}
+
+// Shared memory of one block: the staging box, the work area, the inputs'
+// table-index parts and, for the per-run pass, the innermost dim's table
+// (tab_words, 0 = not staged).
+__host__ __device__ inline size_t staged_smem_bytes(int n, int WM, int box_floats, int nu, int tab_words,
+                                                    int threads) {
+    return (size_t)box_floats * 4 + staged_work_bytes(n, WM, threads) +
+           (nu <= STAGE_UP_MAX ? (size_t)nu * 16 : 0) + (size_t)tab_words * 4;
 }
 
 // Mean of one (state, input) pair from the state's precomputed FP64 centres
@@ -63,6 +73,15 @@ __device__ __forceinline__ void item_mean(const Geom &g, int32_t u, const double
         mu[2] = dadd(xc[2], dmul(tau, w));
     }
 }
+
+// Asynchronous global -> shared copy of one 4-byte word (cp.async, cached in
+// L1) and the wait for all of this thread's outstanding copies.
+__device__ __forceinline__ void cp_async4(float *smem_dst, const float *gmem_src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    const size_t gsrc = __cvta_generic_to_global(gmem_src);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Extra inner-dim slots, beyond the window width, that one cached outer
 // contraction may span (inputs whose inner windows start up to this many
@@ -219,13 +238,13 @@ __device__ __forceinline__ void grouped_items(const Geom &g, const FastArgs<VT> 
 }
 
 template <class VT, int WM, int TM, int NS>
-__global__ void __launch_bounds__(FAST_THREADS) k_backup_staged(const __grid_constant__ Geom g,
+__global__ void __launch_bounds__(STAGE_MAX_THREADS) k_backup_staged(const __grid_constant__ Geom g,
                                                                 const FastArgs<VT> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int BT = FAST_THREADS;
+    const int BT = blockDim.x;
     float *sbox = reinterpret_cast<float *>(smem_raw);
     unsigned char *work = smem_raw + (size_t)a.box_floats * 4;  // also the fallback's area
-    int4 *s_up = reinterpret_cast<int4 *>(work + fast_smem_bytes(NS, WM));
+    int4 *s_up = reinterpret_cast<int4 *>(work + staged_work_bytes(NS, WM, BT));
     uint4 *s_tabL = reinterpret_cast<uint4 *>(s_up + (g.nu <= STAGE_UP_MAX ? g.nu : 0));
     float *cBest = reinterpret_cast<float *>(work);
     int32_t *cArg = reinterpret_cast<int32_t *>(cBest + BT);
@@ -444,9 +463,19 @@ __global__ void __launch_bounds__(FAST_THREADS) k_backup_staged(const __grid_con
                         cin = 0;
                     }
                 }
-                sbox[sidx + k] = onk ? vload<float, VT>(a.Vn + lin + (int64_t)cin * st_in) : 0.0f;
+                if constexpr (std::is_same<VT, float>::value) {
+                    // FP32 V: asynchronous 4-byte copies, all of this thread's
+                    // cells in flight at once (completed before the barrier)
+                    if (onk)
+                        cp_async4(sbox + sidx + k, a.Vn + lin + (int64_t)cin * st_in);
+                    else
+                        sbox[sidx + k] = 0.0f;
+                } else {
+                    sbox[sidx + k] = onk ? vload<float, VT>(a.Vn + lin + (int64_t)cin * st_in) : 0.0f;
+                }
             }
         }
+        if constexpr (std::is_same<VT, float>::value) cp_async_wait_all();
     }
     // the inputs' table-index parts and the innermost dim's table, for the
     // per-run pass (read through generic pointers: shared or global)
@@ -470,8 +499,17 @@ __global__ void __launch_bounds__(FAST_THREADS) k_backup_staged(const __grid_con
     int32_t arg = 0x7fffffff;
     if (work_items && grouped) {
         if constexpr (TM == TM_SEPARABLE && NS >= 2) {
+            // a run belongs to the lane whose share [c*chunk, (c+1)*chunk) holds
+            // its first input, so no lane repeats another's outer contraction
             const int32_t chunk = (g.nu + UL - 1) / UL;
-            const int32_t u0 = c * chunk, u1 = min(g.nu, u0 + chunk);
+            auto run_start = [&](int32_t u) {
+                if (u <= 0 || u >= g.nu) return true;
+                const int4 p = up[u - 1], q = up[u];
+                return p.x != q.x || (NS == 3 && p.y != q.y);
+            };
+            int32_t u0 = min(g.nu, c * chunk), u1 = min(g.nu, u0 + chunk);
+            while (!run_start(u0)) ++u0;
+            while (!run_start(u1)) ++u1;
             if (fits)
                 grouped_items<VT, WM, NS, true>(g, a, up, tabL, xi, es, u0, u1, dminL, KL, sbox, blo, bs, best,
                                                 arg);

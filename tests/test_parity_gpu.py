@@ -255,7 +255,8 @@ def test_launch_shapes_agree_bitwise(amy):
     ]
     # fixed shapes: (input lanes, states per block, rows 1 / consecutive 2, box floats);
     # a 256-float box overflows for most tiles and takes the global-memory path
-    fixed = [(1, 256, 2, 0), (5, 32, 1, 0), (2, 64, 1, 256), (3, 64, 2, 0), (8, 32, 0, 1024)]
+    fixed = [(1, 256, 2, 0), (5, 32, 1, 0), (2, 64, 1, 256), (3, 64, 2, 0), (8, 32, 0, 1024), (5, 96, 1, 0),
+             (1, 512, 2, 0), (4, 128, 1, 0)]
     for i, w in enumerate(cases):
         out, shapes = [], []
         runs = [dict(autotune=False), dict(autotune=True)] + [dict(launch_shape=f) for f in fixed]
@@ -270,7 +271,7 @@ def test_launch_shapes_agree_bitwise(amy):
         if i == 0:
             assert shapes[0][2] == 1   # the default shape of the unicycle uses row tiles
         compare_synthesis(amy, w, "stored_separable", "fp32")
-    for bad in [(9, 0, 0, 0), (0, 48, 0, 0), (4, 128, 0, 0), (0, 0, 3, 0), (0, 0, 0, 100)]:
+    for bad in [(9, 0, 0, 0), (0, 48, 0, 0), (4, 256, 0, 0), (0, 544, 0, 0), (0, 0, 3, 0), (0, 0, 0, 100)]:
         with pytest.raises(amy.AmyError) as e:
             amy.amy_build(cases[0].problem, tmode="stored_separable", prec="fp32", launch_shape=bad)
         assert "INVALID_ARG" in str(e.value)
