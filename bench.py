@@ -226,6 +226,7 @@ def run_amy(args, rank, world):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    lane_peaks = amy.amy_measure_lane_loads()  # roofline denominators (outside the timed region)
     barrier(world)
     amy.amy_kernel_times(h)  # reset
     amy.amy_set_profiling(h, True)
@@ -253,7 +254,7 @@ def run_amy(args, rank, world):
     V_host = V.cpu().numpy()
     # states whose value the spec fixes carry policy 0xFFFF and cost no backup work
     free = int((PI[0] != -1).sum().item())
-    roof = roofline(args, w, info, bk_ms, free)
+    roof = roofline(args, w, info, bk_ms, free, lane_peaks)
 
     # end to end through the C ABI with host buffers: build (H2D of the
     # problem), synthesize with host outputs (D2H of V_0 and every pi_k), destroy
@@ -285,33 +286,52 @@ def run_amy(args, rank, world):
     }
 
 
-def roofline(args, w, info, backup_ms, free):
-    """Roofline of the fused backup kernel.  Stored full / factored rows are
-    streamed from HBM (bound = hbm, algorithmic bytes = rows + V in/out + pi +
-    mask).  Tables and on-the-fly rows keep T out of HBM; the kernel is then
-    bound by the per-transition V gather through the load/store units (one
-    32-bit lane-load per transition, 32 lanes per clock per SM)."""
+def roofline(args, w, info, backup_ms, free, lane_peaks):
+    """Roofline of the fused backup kernel.
+
+    Stored full / factored rows are streamed from HBM: bound = hbm,
+    algorithmic bytes = rows + V in/out + pi + mask.  With per-dimension
+    tables or rows on the fly T stays out of HBM and V_{k+1} is L2-resident
+    (or streamed once); the kernel is then bound by the rate at which lanes
+    receive V values: the shared-memory path for the staged kernels, the
+    L1 path of global loads for the register-resident ones.  Both ceilings
+    are measured on the device (amy_measure_lane_loads).  Algorithmic
+    lane-loads per launch: one per (free state, input, window slot) for the
+    gather kernels; for the per-run kernel, K x W^(n-1) per (free state,
+    input run) -- its outer contraction -- the inner rows then being
+    register arithmetic."""
     pk = peaks()
     p = w.problem
     nx, nu = p.n_states, p.n_inputs
+    slots = info["window_slots"]
     vbytes = 2 if args.v_store != "native" else 4
     per_state = vbytes + vbytes + 2 + 1  # V_{k+1} read once, V_k write, pi write, mask read
     if args.tmode in ("stored_full", "stored_factored"):
-        per_pair = 4 * (info["window_slots"] if args.tmode == "stored_full" else info["window_sum"]) + 2 * info["n"]
+        per_pair = 4 * (slots if args.tmode == "stored_full" else info["window_sum"]) + 2 * info["n"]
         algo = free * nu * per_pair + nx * per_state
         achieved = algo / (backup_ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": measured_traffic(args, nx)[0],
                 "peak_source": pk["source"], "algorithmic_bytes_per_launch": int(algo)}
     traffic, src = measured_traffic(args, nx)
-    sms = 152
-    lane_loads = free * nu * info["window_slots"]
-    achieved = lane_loads / (backup_ms / 1e3) / 1e9
-    peak = sms * 32 * pk["sm_max_mhz"] * 1e6 / 1e9
+    kern = info["backup_kernel"]
+    gather = free * nu * slots
+    if kern == 3:
+        wm = max(info["window"])
+        loads = free * info["input_runs"] * info["inner_span"] * wm ** (info["n"] - 1)
+        path, what = "shared", "K x W^(n-1) shared-memory loads per (free state, input run)"
+    elif kern == 2:
+        loads, path, what = gather, "shared", "one shared-memory load per (free state, input, slot)"
+    else:
+        loads, path, what = gather, "global_l1", "one global (L1) load per (free state, input, slot)"
+    peak = lane_peaks[path] / 1e9
+    achieved = loads / (backup_ms / 1e3) / 1e9
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G lane-loads/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_source": src,
-            "peak_source": "152 SMs x 32 load lanes/clk x max SM clock",
-            "algorithmic_lane_loads_per_launch": int(lane_loads)}
+            "peak_source": f"measured on this GPU by amy_measure_lane_loads ({path} path)",
+            "algorithmic_lane_loads_per_launch": int(loads), "algorithmic_unit": what,
+            "backup_kernel": kern,
+            "window_slot_rate_vs_gather_ceiling": (gather / (backup_ms / 1e3) / 1e9) / peak}
 
 
 # ---------------------------------------------------------------------------

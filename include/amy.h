@@ -179,11 +179,16 @@ typedef struct {
     int32_t tmode;
     int32_t prec;
     int32_t v_store;
-    int32_t input_lanes;        /* backup launch shape: threads per state (1,2,4,8; 0 = generic kernel) */
+    int32_t input_lanes;        /* backup launch shape: threads per state (1..8; 0 = generic kernel) */
     int32_t row_tiles;          /* 1: staged backup tiles are whole innermost-dim rows */
     int32_t block_states;       /* states (lane columns) per block of the backup */
     int32_t grouped_inputs;     /* 1: runs of inputs sharing every outer dim's masses
                                    are served by one outer contraction per run */
+    int32_t backup_kernel;      /* 0 generic (k_backup), 1 register-resident
+                                   (k_backup_fast), 2 shared-memory staged, 3 staged
+                                   with one outer contraction per input run */
+    int32_t input_runs;         /* runs of consecutive inputs sharing outer records */
+    int32_t inner_span;         /* inner slots K one outer contraction covers (kernel 3) */
 } amy_info_t;
 
 /* Points per dim of [lb, ub] with step eta: floor((ub-lb)/eta + 1e-9) + 1
@@ -281,6 +286,15 @@ const char *amy_last_error(void);
 amy_status amy_synthesize_noalloc(const amy_system *sys, const amy_grid *states, const amy_grid *inputs,
                                   const double *sigma, const amy_cut *cut, int32_t prec, const amy_spec *spec,
                                   int32_t horizon, float *V_out, uint16_t *policy_out, void *cuda_stream);
+
+/* ---- Measurement helper (not part of the paper's method) ----------------
+ * Measured ceilings of the two load paths the fused backup kernels gather
+ * V_{k+1} through, for roofline denominators: 32-bit shared-memory loads
+ * (conflict free) and 32-bit global loads that hit L1 (coalesced), both in
+ * lane-loads per second (one 4-byte value delivered to one thread), on the
+ * current device.  Takes a few milliseconds; allocates 16 MiB temporarily.
+ * Errors: INVALID_ARG (null pointer), CUDA. */
+amy_status amy_measure_lane_loads(double *shared_per_s, double *global_per_s);
 
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of independent synthesis requests.

@@ -207,7 +207,8 @@ def amy_info(h: AmyHandle) -> dict:
         "cut_half_width": [float(info.cut_half_width[d]) for d in range(n)],
         "device_bytes": int(info.device_bytes), "tmode": int(info.tmode), "prec": int(info.prec),
         "v_store": int(info.v_store), "input_lanes": int(info.input_lanes), "row_tiles": int(info.row_tiles), "block_states": int(info.block_states),
-        "grouped_inputs": int(info.grouped_inputs),
+        "grouped_inputs": int(info.grouped_inputs), "backup_kernel": int(info.backup_kernel),
+        "input_runs": int(info.input_runs), "inner_span": int(info.inner_span),
     }
 
 
@@ -293,6 +294,15 @@ def amy_destroy(h: AmyHandle) -> None:
     h.close()
 
 
+def amy_measure_lane_loads() -> dict:
+    """amy_measure_lane_loads: measured lane-load ceilings (per second) of
+    conflict-free shared-memory loads and L1-hitting global loads on the
+    current device (roofline denominators)."""
+    sh, gl = C.c_double(0.0), C.c_double(0.0)
+    _check(_lib().amy_measure_lane_loads(C.byref(sh), C.byref(gl)))
+    return {"shared": sh.value, "global_l1": gl.value}
+
+
 def amy_synthesize_noalloc(problem, spec, horizon: int, V_out, policy_out=None, prec: str = "fp32",
                            stream=None) -> None:
     """amy_synthesize_noalloc: on-the-fly synthesis whose intermediate device
@@ -316,7 +326,7 @@ from .serving import (AmyServer, amy_cancel, amy_poll, amy_result_free,  # noqa:
 __all__ = [
     "AmyError", "AmyHandle", "AmyServer", "amy_build", "amy_synthesize", "amy_backup_step",
     "amy_query_rows", "amy_info", "amy_destroy", "amy_grid_count", "amy_last_error",
-    "amy_rebuild", "amy_set_profiling", "amy_kernel_times", "amy_synthesize_noalloc",
+    "amy_rebuild", "amy_set_profiling", "amy_kernel_times", "amy_synthesize_noalloc", "amy_measure_lane_loads",
     "amy_server_create", "amy_submit", "amy_poll", "amy_wait", "amy_cancel", "amy_server_stats",
     "amy_server_destroy", "amy_result_free", "TMODES", "PRECS", "VSTORES", "POLICY_NONE",
 ]

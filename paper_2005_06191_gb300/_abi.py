@@ -54,7 +54,8 @@ class amy_info_t(C.Structure):
                 ("window_sum", C.c_int32), ("cut_half_width", C.c_double * MAX_DIMS),
                 ("device_bytes", C.c_int64), ("tmode", C.c_int32), ("prec", C.c_int32),
                 ("v_store", C.c_int32), ("input_lanes", C.c_int32), ("row_tiles", C.c_int32), ("block_states", C.c_int32),
-                ("grouped_inputs", C.c_int32)]
+                ("grouped_inputs", C.c_int32), ("backup_kernel", C.c_int32), ("input_runs", C.c_int32),
+                ("inner_span", C.c_int32)]
 
 
 class amy_server_opts(C.Structure):
@@ -91,6 +92,7 @@ PROTOTYPES = {
                                      C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "amy_destroy": (None, [C.c_void_p]),
     "amy_last_error": (C.c_char_p, []),
+    "amy_measure_lane_loads": (C.c_int32, [DP, DP]),
     "amy_synthesize_noalloc": (C.c_int32, [C.POINTER(amy_system), C.POINTER(amy_grid), C.POINTER(amy_grid), DP,
                                            C.POINTER(amy_cut), C.c_int32, C.POINTER(amy_spec), C.c_int32,
                                            C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -1,0 +1,103 @@
+// amy_calibrate.cu -- measured ceilings of the two load paths the fused
+// backup kernels gather V through, used as roofline denominators:
+//   - shared memory: 32-bit loads, every warp reading 32 consecutive words
+//     (one wavefront per instruction, no bank conflict);
+//   - global memory hitting L1: 32-bit loads, every warp reading 32
+//     consecutive words of a 16 KiB block-private slice that stays in L1.
+// Each thread keeps four independent sums so that loads, not the adds, set
+// the pace; the sums are written out so that nothing is optimised away.
+// The rates count lane-loads (one 4-byte value delivered to one thread).
+#include <cuda_runtime.h>
+
+#include "../../include/amy.h"
+#include "amy_internal.h"
+
+namespace amy {
+namespace {
+
+constexpr int CAL_THREADS = 512;
+constexpr int CAL_WORDS = 4096;  // per block: 16 KiB
+constexpr int CAL_ITERS = 256;   // passes over the block's words
+
+__global__ void __launch_bounds__(CAL_THREADS) k_cal_shared(const float *__restrict__ src, float *__restrict__ out) {
+    __shared__ float buf[CAL_WORDS];
+    for (int i = threadIdx.x; i < CAL_WORDS; i += blockDim.x) buf[i] = src[i];
+    __syncthreads();
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int it = 0; it < CAL_ITERS; ++it) {
+        const int b = ((warp + it) * 128) & (CAL_WORDS - 1);  // 4 rows of 32 words per step
+        s0 += buf[b + lane];
+        s1 += buf[b + 32 + lane];
+        s2 += buf[b + 64 + lane];
+        s3 += buf[b + 96 + lane];
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = (s0 + s1) + (s2 + s3);
+}
+
+__global__ void __launch_bounds__(CAL_THREADS) k_cal_global(const float *__restrict__ src, float *__restrict__ out) {
+    const float *base = src + (size_t)(blockIdx.x % 1024) * CAL_WORDS;  // block-private, L1-resident slice
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int it = 0; it < CAL_ITERS; ++it) {
+        const int b = ((warp + it) * 128) & (CAL_WORDS - 1);
+        s0 += __ldg(base + b + lane);
+        s1 += __ldg(base + b + 32 + lane);
+        s2 += __ldg(base + b + 64 + lane);
+        s3 += __ldg(base + b + 96 + lane);
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = (s0 + s1) + (s2 + s3);
+}
+
+}  // namespace
+}  // namespace amy
+
+using namespace amy;
+
+extern "C" amy_status amy_measure_lane_loads(double *shared_per_s, double *global_per_s) {
+    if (!shared_per_s || !global_per_s) return set_error(AMY_E_INVALID_ARG, "null argument");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_error(e, "device query");
+    const int blocks = sms * 4 * 8;  // several waves of full blocks
+    float *src = nullptr, *out = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    const size_t src_words = (size_t)1024 * CAL_WORDS;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&src, src_words * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&out, (size_t)blocks * CAL_THREADS * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(src, 0, src_words * 4, st);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    double rate[2] = {0.0, 0.0};
+    for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
+        float best = 3.4e38f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // first pass warms up
+            e = cudaEventRecord(a, st);
+            if (which == 0)
+                k_cal_shared<<<blocks, CAL_THREADS, 0, st>>>(src, out);
+            else
+                k_cal_global<<<blocks, CAL_THREADS, 0, st>>>(src, out);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(b, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+            if (e == cudaSuccess && rep > 0 && ms < best) best = ms;
+        }
+        const double loads = (double)blocks * CAL_THREADS * CAL_ITERS * 4.0;
+        rate[which] = loads / (best * 1e-3);
+    }
+    if (src) cudaFreeAsync(src, st);
+    if (out) cudaFreeAsync(out, st);
+    if (st) cudaStreamSynchronize(st);
+    if (st) cudaStreamDestroy(st);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_error(e, "lane-load calibration");
+    *shared_per_s = rate[0];
+    *global_per_s = rate[1];
+    return AMY_OK;
+}

@@ -755,7 +755,7 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
         std::vector<int32_t> upart;
         TRY(plan_sep_tables(h->g, params, h->tab_words, &upart));
         h->grouped = input_runs_share_outer(h->g, upart);
-        h->runs = h->grouped ? input_outer_runs(h->g, upart) : 0;
+        h->runs = input_outer_runs(h->g, upart);
         TRY(dev_alloc(h, (void **)&h->d_tab, (size_t)h->tab_words * 4, "separable tables"));
         e = cudaMemcpy(h->d_tab + h->g.uoff, upart.data(), upart.size() * 4, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
@@ -824,6 +824,34 @@ amy_status amy_info(amy_handle h, amy_info_t *out) {
     if (!h || !out) return set_error(AMY_E_INVALID_ARG, "null argument");
     *out = h->info;
     out->device_bytes = h->bytes;
+    out->backup_kernel = 0;
+    out->inner_span = 0;
+    if (fast_path(h)) {
+        FastCall c;
+        c.ulanes = h->ulanes;
+        c.rows = h->rows;
+        c.grouped = h->grouped;
+        c.runs = h->runs;
+        c.tilex = h->tilex;
+        const FastShape sh = fast_shape(h->g, tm_kind_of(h), c, h->sm_count);
+        out->backup_kernel = sh.staged ? 2 : 1;
+        if (sh.staged && h->grouped && h->tmode == AMY_T_STORED_SEPARABLE) {
+            // the per-run pass runs when every dim has origin bounds and the
+            // inner dim's bounds span at most WM + 3 slots (the kernel's test)
+            int32_t b[2 * MAXD + 4];
+            AMY_CUDA(cudaMemcpyAsync(b, h->d_tab + h->g.boff, sizeof b, cudaMemcpyDeviceToHost, h->stream),
+                     "bounds read");
+            AMY_CUDA(cudaStreamSynchronize(h->stream), "bounds read");
+            const int L = h->g.n - 1, wm = h->fast_wm;
+            const int32_t K = b[MAXD + L] - b[L] + wm;
+            const bool all = (b[2 * MAXD] & ((1 << h->g.n) - 1)) == ((1 << h->g.n) - 1);
+            if (all && K >= wm && K <= wm + 3 && K <= h->g.N[L]) {
+                out->backup_kernel = 3;
+                out->inner_span = K;
+            }
+        }
+    }
+    out->input_runs = h->runs;
     return AMY_OK;
 }
 

@@ -374,11 +374,18 @@ __global__ void __launch_bounds__(STAGE_MAX_THREADS) k_backup_staged(const __gri
         }
     }
     __syncthreads();
-    if (work_items) {
+    {
+        // one shared atomic per warp and dim (with table bounds, the first
+        // input lane of each state speaks for all of them)
+        const bool contrib = work_items && (!analytic || c == 0);
 #pragma unroll
         for (int d = 0; d < NS; ++d) {
-            atomicMin(&s_lo[d], lo[d]);
-            atomicMax(&s_hi[d], hi[d]);
+            const int32_t l = __reduce_min_sync(0xffffffffu, contrib ? lo[d] : INT_MAX);
+            const int32_t h = __reduce_max_sync(0xffffffffu, contrib ? hi[d] : INT_MIN);
+            if ((tid & 31) == 0 && l != INT_MAX) {
+                atomicMin(&s_lo[d], l);
+                atomicMax(&s_hi[d], h);
+            }
         }
     }
     __syncthreads();

@@ -236,7 +236,13 @@ def test_grouped_inputs_box_and_global_paths(amy):
     when the window box overflows (steer2) both match the oracle."""
     for w in [W.unicycle(nxy=31, horizon=6, target=(3.0, 5.0)), _steer_problem()]:
         with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32") as h:
-            assert amy.amy_info(h)["grouped_inputs"] == 1
+            info = amy.amy_info(h)
+            assert info["grouped_inputs"] == 1 and info["backup_kernel"] == 3
+            if w.problem.name.startswith("unicycle"):
+                # 5 speeds x 9 turn rates; heading windows start at most 1 slot apart
+                assert (info["input_runs"], info["inner_span"]) == (5, 4)
+            else:
+                assert info["input_runs"] == 3 and 3 <= info["inner_span"] <= 6
         compare_synthesis(amy, w, "stored_separable", "fp32")
         compare_synthesis(amy, w, "stored_separable", "fp32_kahan")
         compare_synthesis(amy, w, "stored_separable", "fp32", v_store="u16")
@@ -358,3 +364,16 @@ def test_auto_mode_picks_and_matches(amy):
     assert set(picks.values()) <= {0, 2, 3}
     with amy.amy_build(W.unicycle().problem, tmode="auto", prec="fp32") as h:
         assert amy.amy_info(h)["tmode"] == 3
+
+
+def test_backup_kernel_reported_and_lane_load_ceilings(amy):
+    expect = [(W.rooms7(n_per_dim=4, horizon=1), "stored_separable", 1),   # 7-D: register-resident
+              (W.random_affine(np.random.default_rng(3), 2, [37, 30], 6, window=[3, 3]), "stored_separable", 2),
+              (W.robot_lin(), "stored_full", 0)]                              # dense 41-wide rows: generic
+    for w, tmode, kern in expect:
+        with amy.amy_build(w.problem, tmode=tmode, prec="fp32") as h:
+            assert amy.amy_info(h)["backup_kernel"] == kern, (w.problem.name, tmode)
+    peaks = amy.amy_measure_lane_loads()
+    # 152 SMs x 32 lanes x ~2 GHz is about 1e13 lane-loads/s for either path
+    for k in ("shared", "global_l1"):
+        assert 1e12 < peaks[k] < 3e13, peaks
