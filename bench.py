@@ -246,10 +246,11 @@ def run_amy(args, rank, world):
     value = trans * args.steps * world / (ms_max / 1e3)
     # kernel-level roofline of the dominant kernel (the fused backup)
     # kernels per timed step: the backups, one spec-mask kernel, and the build
-    # (two kernels for the per-dimension tables: bounds reset + tables)
-    per_build = 2 if args.tmode == "stored_separable" else 1
-    launches = kt["backup_launches"] + per_build * kt["build_launches"] + args.steps
-    bk_ms = kt["backup_ms"] / max(kt["backup_launches"], 1)
+    # (for the per-dimension tables: bounds reset + tables [+ shifted inner table])
+    launches = kt["backup_launches"] + info["build_kernels"] * kt["build_launches"] + args.steps
+    # per backup: the persistent kernel performs the whole horizon in one launch
+    bk_ms = kt["backup_ms"] / max(kt["backup_steps"], 1)
+    launch_ms = kt["backup_ms"] / max(kt["backup_launches"], 1)
     build_ms = kt["build_ms"] / max(kt["build_launches"], 1)
     V_host = V.cpu().numpy()
     # states whose value the spec fixes carry policy 0xFFFF and cost no backup work
@@ -316,7 +317,7 @@ def roofline(args, w, info, backup_ms, free, lane_peaks):
     traffic, src = measured_traffic(args, nx)
     kern = info["backup_kernel"]
     gather = free * nu * slots
-    if kern == 3:
+    if kern in (3, 4, 5):
         wm = max(info["window"])
         loads = free * info["input_runs"] * info["inner_span"] * wm ** (info["n"] - 1)
         path, what = "shared", "K x W^(n-1) shared-memory loads per (free state, input run)"

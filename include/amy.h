@@ -186,9 +186,13 @@ typedef struct {
                                    are served by one outer contraction per run */
     int32_t backup_kernel;      /* 0 generic (k_backup), 1 register-resident
                                    (k_backup_fast), 2 shared-memory staged, 3 staged
-                                   with one outer contraction per input run */
+                                   with one outer contraction per input run, 4 the
+                                   per-run kernel on row tiles (k_backup_runs), 5 its
+                                   persistent form: the whole horizon in one
+                                   cooperative launch (k_synth_runs) */
     int32_t input_runs;         /* runs of consecutive inputs sharing outer records */
-    int32_t inner_span;         /* inner slots K one outer contraction covers (kernel 3) */
+    int32_t inner_span;         /* inner slots K one outer contraction covers (kernels 3, 4) */
+    int32_t build_kernels;      /* kernels one table build (amy_build / amy_rebuild) launches */
 } amy_info_t;
 
 /* Points per dim of [lb, ub] with step eta: floor((ub-lb)/eta + 1e-9) + 1
@@ -242,11 +246,15 @@ amy_status amy_rebuild(amy_handle h, const double *params, int64_t n_params);
 
 /* Kernel timing: while on, every backup and build kernel of this handle is
  * bracketed by CUDA events on the handle's stream.  amy_kernel_times waits
- * for the recorded events, returns the summed durations (ms) and launch
- * counts since the previous call, and resets them. */
+ * for the recorded events, returns the summed durations (ms), the launch
+ * counts and the number of backups those launches performed (one per launch,
+ * or the whole horizon for the persistent kernel) since the previous call,
+ * and resets them.  Any argument may be NULL.  It also reports
+ * AMY_E_TIMEOUT when a persistent synthesis since the previous check gave up
+ * waiting at a grid barrier (its outputs are then invalid). */
 amy_status amy_set_profiling(amy_handle h, int32_t on);
-amy_status amy_kernel_times(amy_handle h, double *backup_ms, int64_t *backup_launches, double *build_ms,
-                            int64_t *build_launches);
+amy_status amy_kernel_times(amy_handle h, double *backup_ms, int64_t *backup_launches, int64_t *backup_steps,
+                            double *build_ms, int64_t *build_launches);
 
 amy_status amy_info(amy_handle h, amy_info_t *out);
 void amy_destroy(amy_handle h);

@@ -209,6 +209,7 @@ def amy_info(h: AmyHandle) -> dict:
         "v_store": int(info.v_store), "input_lanes": int(info.input_lanes), "row_tiles": int(info.row_tiles), "block_states": int(info.block_states),
         "grouped_inputs": int(info.grouped_inputs), "backup_kernel": int(info.backup_kernel),
         "input_runs": int(info.input_runs), "inner_span": int(info.inner_span),
+        "build_kernels": int(info.build_kernels),
     }
 
 
@@ -283,11 +284,12 @@ def amy_set_profiling(h: AmyHandle, on: bool = True) -> None:
 
 
 def amy_kernel_times(h: AmyHandle) -> dict:
-    """Summed CUDA-event durations (ms) and counts of backup / build kernels since the last call."""
-    bms, bn, cms, cn = C.c_double(0), C.c_int64(0), C.c_double(0), C.c_int64(0)
-    _check(_lib().amy_kernel_times(h.ptr, C.byref(bms), C.byref(bn), C.byref(cms), C.byref(cn)))
-    return {"backup_ms": bms.value, "backup_launches": bn.value, "build_ms": cms.value,
-            "build_launches": cn.value}
+    """Summed CUDA-event durations (ms) and counts of backup / build kernels since
+    the last call; backup_steps counts the backups those launches performed."""
+    bms, bn, bs, cms, cn = C.c_double(0), C.c_int64(0), C.c_int64(0), C.c_double(0), C.c_int64(0)
+    _check(_lib().amy_kernel_times(h.ptr, C.byref(bms), C.byref(bn), C.byref(bs), C.byref(cms), C.byref(cn)))
+    return {"backup_ms": bms.value, "backup_launches": bn.value, "backup_steps": bs.value,
+            "build_ms": cms.value, "build_launches": cn.value}
 
 
 def amy_destroy(h: AmyHandle) -> None:

@@ -55,7 +55,7 @@ class amy_info_t(C.Structure):
                 ("device_bytes", C.c_int64), ("tmode", C.c_int32), ("prec", C.c_int32),
                 ("v_store", C.c_int32), ("input_lanes", C.c_int32), ("row_tiles", C.c_int32), ("block_states", C.c_int32),
                 ("grouped_inputs", C.c_int32), ("backup_kernel", C.c_int32), ("input_runs", C.c_int32),
-                ("inner_span", C.c_int32)]
+                ("inner_span", C.c_int32), ("build_kernels", C.c_int32)]
 
 
 class amy_server_opts(C.Structure):
@@ -88,7 +88,7 @@ PROTOTYPES = {
     "amy_info": (C.c_int32, [C.c_void_p, C.POINTER(amy_info_t)]),
     "amy_rebuild": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64]),
     "amy_set_profiling": (C.c_int32, [C.c_void_p, C.c_int32]),
-    "amy_kernel_times": (C.c_int32, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+    "amy_kernel_times": (C.c_int32, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "amy_destroy": (None, [C.c_void_p]),
     "amy_last_error": (C.c_char_p, []),

@@ -78,6 +78,21 @@ __global__ void __launch_bounds__(FAST_THREADS) k_step_group(const BatchEntry *_
         a.grouped = 0;
         a.box_floats = 0;
         a.stage_tab = 0;
+        a.stage_recs = 0;
+        a.runs_planes = 0;
+    a.tx_magic = 0;
+    a.chu_shift = 0;
+    a.bnd_known = 0;
+    a.nrs = 0;
+    a.in_stride_b = INT_MIN;
+        a.tx_magic = 0;
+        a.chu_shift = 0;
+    a.bnd_known = 0;
+    a.nrs = 0;
+    a.in_stride_b = INT_MIN;
+        a.bnd_known = 0;
+        a.nrs = 0;
+        a.in_stride_b = INT_MIN;
         const int64_t x = (t - e.tile_begin) * e.tileX + threadIdx.x % e.tileX;
         backup_tile<VT, WM, TM, VAR>(sg, a, (int32_t)min(x, (int64_t)INT_MAX), work);
         __syncthreads();

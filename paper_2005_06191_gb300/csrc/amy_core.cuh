@@ -69,6 +69,13 @@ struct Geom {
     // (words boff + d and boff + MAXD + d), then a bit mask of the dims for
     // which that bound exists (component d depends on coordinate d).
     int64_t boff;
+    // After the bounds block, at word shoff (0 = absent; 2-D and 3-D problems
+    // whose innermost table has at most 4096 records): that table as shifted
+    // weights, 8 floats per record (two planes of 4 at shoff and
+    // shoff + 4 * tent[n - 1]): record e holds its W masses at positions
+    // sh .. sh + W - 1, sh = origin - own coordinate - the smallest such
+    // offset over the table, and zeros elsewhere (all zeros when sh > 7 - W + 1).
+    int64_t shoff;
 };
 
 struct SpecDev {

@@ -290,6 +290,11 @@ amy_status plan_sep_tables(Geom &g, const std::vector<double> &params, int64_t &
     }
     g.boff = off + (int64_t)g.nu * g.urw;
     words = g.boff + 2 * MAXD + 4;
+    g.shoff = 0;
+    if (n >= 2 && n <= 3 && g.tent[n - 1] <= 4096) {
+        g.shoff = (words + 3) / 4 * 4;
+        words = g.shoff + 8 * (int64_t)g.tent[n - 1];
+    }
     return AMY_OK;
 }
 
@@ -303,6 +308,33 @@ int32_t input_outer_runs(const Geom &g, const std::vector<int32_t> &upart) {
         if (!same) ++runs;
     }
     return runs;
+}
+
+void input_run_layout(const Geom &g, const std::vector<int32_t> &upart, std::vector<int32_t> &starts,
+                      int32_t &stride_b) {
+    starts.clear();
+    stride_b = INT_MIN;
+    if (g.n < 2 || upart.size() < (size_t)g.nu * g.urw) return;
+    const int L = g.n - 1;
+    bool have = false, same = true;
+    int32_t step = 0;
+    for (int32_t u = 0; u < g.nu; ++u) {
+        bool start = u == 0;
+        for (int d = 0; d < L && !start; ++d)
+            start = upart[(size_t)u * g.urw + d] != upart[(size_t)(u - 1) * g.urw + d];
+        if (start) {
+            starts.push_back(u);
+            continue;
+        }
+        const int32_t dd = upart[(size_t)u * g.urw + L] - upart[(size_t)(u - 1) * g.urw + L];
+        if (!have) {
+            step = dd;
+            have = true;
+        }
+        same = same && dd == step;
+    }
+    starts.push_back(g.nu);
+    if (same && (int64_t)step * 16 < INT32_MAX && (int64_t)step * 16 > INT32_MIN + 1) stride_b = step * 16;
 }
 
 bool input_runs_share_outer(const Geom &g, const std::vector<int32_t> &upart) {
@@ -343,6 +375,10 @@ struct amy_handle_s {
     int rows;             // staged variant: row-aligned tiles allowed
     int grouped;          // staged variant: outer dims contracted once per input run
     int runs;             // number of those runs
+    std::vector<int32_t> run_starts;  // input runs sharing their outer records (+ input count)
+    int32_t in_stride_b;              // byte step of their shifted inner records (INT_MIN: varies)
+    int bounds_known;     // tables' origin bounds read back after the last build
+    int32_t bnd_lo[MAXD], bnd_hi[MAXD];
     int tilex;            // staged variant: lane columns per block (0 = default)
     int box_floats;       // staged variant: box budget (0 = default)
     std::vector<double> host_params;
@@ -360,6 +396,14 @@ struct amy_handle_s {
     uint16_t *g_pi;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_backup, ev_build;
+    std::vector<int32_t> ev_backup_steps;  // backups performed by each timed backup launch
+    // persistent horizon kernel: applies to this handle's problem and shape
+    // (checked after the shape is fixed), its grid barrier words (arrivals,
+    // generation, error flag) and the polls a barrier wait makes before it
+    // gives up
+    int synth_ok;
+    unsigned *d_bar;
+    int32_t spin_limit;
     amy_info_t info;
 };
 
@@ -387,6 +431,7 @@ void free_handle(amy_handle_s *h) {
     cudaFree(h->d_Vbase[1]);
     cudaFree(h->d_mask);
     cudaFree(h->d_tab);
+    cudaFree(h->d_bar);
     for (auto &p : h->ev_backup) h->ev_pool.push_back(p.first), h->ev_pool.push_back(p.second);
     for (auto &p : h->ev_build) h->ev_pool.push_back(p.first), h->ev_pool.push_back(p.second);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -458,8 +503,10 @@ cudaEvent_t pooled_event(amy_handle_s *h) {
 struct KernelTimer {
     amy_handle_s *h;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *list;
+    int32_t steps;  // backups the bracketed launch performs (backup list only)
     cudaEvent_t a = nullptr, b = nullptr;
-    KernelTimer(amy_handle_s *hh, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *l) : h(hh), list(l) {
+    KernelTimer(amy_handle_s *hh, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *l, int32_t n_steps = 1)
+        : h(hh), list(l), steps(n_steps) {
         if (!h->profiling) return;
         a = pooled_event(h);
         b = pooled_event(h);
@@ -469,11 +516,25 @@ struct KernelTimer {
         if (!h->profiling || !a || !b) return;
         cudaEventRecord(b, h->stream);
         list->push_back({a, b});
+        if (list == &h->ev_backup) h->ev_backup_steps.push_back(steps);
     }
 };
 
 amy_status launch_backup_generic(amy_handle_s *h, int spec_kind, const void *Vn, void *Vo, void *Vfinal,
                                  uint16_t *pi);
+
+// Reads and clears the persistent kernel's error flag (synchronises the
+// handle's stream).
+amy_status check_synth_error(amy_handle_s *h) {
+    if (!h->d_bar) return AMY_OK;
+    int32_t err = 0;
+    AMY_CUDA(cudaMemcpyAsync(&err, h->d_bar + 2, sizeof err, cudaMemcpyDeviceToHost, h->stream), "barrier flag read");
+    AMY_CUDA(cudaStreamSynchronize(h->stream), "barrier flag read");
+    if (err == 0) return AMY_OK;
+    AMY_CUDA(cudaMemsetAsync(h->d_bar + 2, 0, sizeof(int32_t), h->stream), "barrier flag reset");
+    if (err == 1) return set_error(AMY_E_TIMEOUT, "persistent backup: a grid barrier wait gave up");
+    return set_error(AMY_E_CUDA, "persistent backup: launch shape rejected on the device");
+}
 
 int tm_kind_of(const amy_handle_s *h) {
     return h->tmode == AMY_T_ON_THE_FLY ? TM_OTF : h->tmode == AMY_T_STORED_FACTORED ? TM_FACTORED : TM_SEPARABLE;
@@ -481,30 +542,94 @@ int tm_kind_of(const amy_handle_s *h) {
 
 bool fast_path(const amy_handle_s *h) { return h->fast_wm > 0 && h->tmode != AMY_T_STORED_FULL; }
 
+// The tables' bounds on (window origin - own coordinate) as the launch sees them.
+void set_bounds(const amy_handle_s *h, FastCall &c) {
+    c.run_starts = h->run_starts.empty() ? nullptr : h->run_starts.data();
+    c.n_runs = h->run_starts.empty() ? 0 : (int32_t)h->run_starts.size() - 1;
+    c.in_stride_b = h->in_stride_b;
+    c.bounds_known = h->bounds_known;
+    for (int d = 0; d < 3; ++d) {
+        c.bnd_lo[d] = d < h->g.n ? h->bnd_lo[d] : 0;
+        c.bnd_hi[d] = d < h->g.n ? h->bnd_hi[d] : 0;
+    }
+}
+
+// Reads the bounds block the table build leaves after the tables: the host
+// copy sizes the per-run kernel's box and goes to it as launch parameters.
+amy_status read_bounds(amy_handle_s *h) {
+    h->bounds_known = 0;
+    if (h->tmode != AMY_T_STORED_SEPARABLE) return AMY_OK;
+    int32_t b[2 * MAXD + 4];
+    AMY_CUDA(cudaMemcpyAsync(b, h->d_tab + h->g.boff, sizeof b, cudaMemcpyDeviceToHost, h->stream), "bounds read");
+    AMY_CUDA(cudaStreamSynchronize(h->stream), "bounds read");
+    const int all = (1 << h->g.n) - 1;
+    if ((b[2 * MAXD] & all) != all) return AMY_OK;
+    for (int d = 0; d < h->g.n; ++d) {
+        h->bnd_lo[d] = b[d];
+        h->bnd_hi[d] = b[MAXD + d];
+    }
+    h->bounds_known = 1;
+    return AMY_OK;
+}
+
 // One backup V_{k+1} (Vn) -> V_k (Vo) with the handle's precision: the
 // register-resident kernel when the window fits it, the generic one otherwise.
+// Arguments of the register-resident / staged backups for this handle's
+// problem, tables and launch shape.
+FastCall fast_call(const amy_handle_s *h, int spec_kind, const void *Vn, void *Vo, void *Vfinal, uint16_t *pi) {
+    FastCall c;
+    c.Vn = Vn;
+    c.Vo = Vo;
+    c.Vfinal = (float *)Vfinal;
+    c.pi = pi;
+    c.mask = h->d_mask;
+    c.spec_kind = spec_kind;
+    c.kahan = h->prec == AMY_PREC_FP32_KAHAN;
+    c.T = (const float *)h->d_T;
+    c.O = h->d_O;
+    c.npairs = h->npairs;
+    c.tab = h->d_tab;
+    c.ulanes = h->ulanes;
+    c.rows = h->rows;
+    c.grouped = h->grouped;
+    c.runs = h->runs;
+    set_bounds(h, c);
+    c.tilex = h->tilex;
+    c.box_floats = h->box_floats;
+    return c;
+}
+
+// The persistent horizon kernel's arguments (V_N in d_V[0]).
+SynthCall synth_call(amy_handle_s *h, int32_t horizon, void *d_Vout, uint16_t *d_pi, int32_t all_steps) {
+    SynthCall sc;
+    sc.V0 = h->d_V[0];
+    sc.V1 = h->d_V[1];
+    sc.Vfinal = (float *)d_Vout;
+    sc.pi = d_pi;
+    sc.all_steps = all_steps;
+    sc.horizon = horizon;
+    sc.bar = h->d_bar;
+    sc.err = reinterpret_cast<int32_t *>(h->d_bar + 2);
+    sc.spin_limit = h->spin_limit;
+    return sc;
+}
+
+// Whether the persistent horizon kernel applies with the handle's current
+// tables, bounds and launch shape (all blocks resident at once).
+void update_synth_ok(amy_handle_s *h) {
+    h->synth_ok = 0;
+    if (!h->d_bar || !fast_path(h)) return;
+    const FastCall c = fast_call(h, SPEC_SAFETY, h->d_V[0], h->d_V[1], nullptr, nullptr);
+    const SynthCall sc = synth_call(h, 1, nullptr, nullptr, 0);
+    h->synth_ok = launch_synth_fast(h->g, tm_kind_of(h), h->v_store, c, sc, h->sm_count, h->stream, true) == AMY_OK;
+    cudaGetLastError();
+}
+
 amy_status launch_backup(amy_handle_s *h, int spec_kind, const void *Vn, void *Vo, void *Vfinal, uint16_t *pi) {
     KernelTimer tm(h, &h->ev_backup);
     amy_status st;
     if (fast_path(h)) {
-        FastCall c;
-        c.Vn = Vn;
-        c.Vo = Vo;
-        c.Vfinal = (float *)Vfinal;
-        c.pi = pi;
-        c.mask = h->d_mask;
-        c.spec_kind = spec_kind;
-        c.kahan = h->prec == AMY_PREC_FP32_KAHAN;
-        c.T = (const float *)h->d_T;
-        c.O = h->d_O;
-        c.npairs = h->npairs;
-        c.tab = h->d_tab;
-        c.ulanes = h->ulanes;
-        c.rows = h->rows;
-        c.grouped = h->grouped;
-        c.runs = h->runs;
-        c.tilex = h->tilex;
-        c.box_floats = h->box_floats;
+        const FastCall c = fast_call(h, spec_kind, Vn, Vo, Vfinal, pi);
         st = launch_backup_fast(h->g, tm_kind_of(h), h->v_store, c, h->sm_count, h->stream);
     } else {
         st = launch_backup_generic(h, spec_kind, Vn, Vo, Vfinal, pi);
@@ -603,6 +728,7 @@ amy_status autotune_shape(amy_handle_s *h) {
     c.tab = h->d_tab;
     c.grouped = h->grouped;
     c.runs = h->runs;
+    set_bounds(h, c);
     const bool staged = fast_shape(h->g, tm_kind_of(h), c, h->sm_count).staged;
     // candidates: power-of-two input lanes, plus one lane per input run; the
     // staged variant also varies the states per block and the tile mapping
@@ -713,6 +839,8 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     h->rows = 1;
     h->grouped = 0;
     h->runs = 0;
+    h->bounds_known = 0;
+    h->in_stride_b = INT_MIN;
     h->tilex = 0;
     h->box_floats = 0;
     {
@@ -756,6 +884,7 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
         TRY(plan_sep_tables(h->g, params, h->tab_words, &upart));
         h->grouped = input_runs_share_outer(h->g, upart);
         h->runs = input_outer_runs(h->g, upart);
+        input_run_layout(h->g, upart, h->run_starts, h->in_stride_b);
         TRY(dev_alloc(h, (void **)&h->d_tab, (size_t)h->tab_words * 4, "separable tables"));
         e = cudaMemcpy(h->d_tab + h->g.uoff, upart.data(), upart.size() * 4, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
@@ -786,7 +915,20 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
         free_handle(h);
         return cuda_error(e, "build");
     }
+    TRY(read_bounds(h));
     if (opts->autotune) TRY(autotune_shape(h));
+    h->spin_limit = 1 << 20;
+    h->synth_ok = 0;
+    if (fast_path(h) && h->tmode == AMY_T_STORED_SEPARABLE && h->grouped) {
+        TRY(dev_alloc(h, (void **)&h->d_bar, 4 * sizeof(unsigned), "barrier words"));
+        e = cudaMemsetAsync(h->d_bar, 0, 4 * sizeof(unsigned), h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            free_handle(h);
+            return cuda_error(e, "barrier words");
+        }
+        update_synth_ok(h);
+    }
 #undef TRY
     amy_info_t &inf = h->info;
     memset(&inf, 0, sizeof inf);
@@ -808,6 +950,7 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
         c.rows = h->rows;
         c.grouped = h->grouped;
         c.runs = h->runs;
+        set_bounds(h, c);
         c.tilex = h->tilex;
         c.box_floats = h->box_floats;
         const FastShape sh = fast_shape(h->g, tm_kind_of(h), c, h->sm_count);
@@ -832,6 +975,7 @@ amy_status amy_info(amy_handle h, amy_info_t *out) {
         c.rows = h->rows;
         c.grouped = h->grouped;
         c.runs = h->runs;
+        set_bounds(h, c);
         c.tilex = h->tilex;
         const FastShape sh = fast_shape(h->g, tm_kind_of(h), c, h->sm_count);
         out->backup_kernel = sh.staged ? 2 : 1;
@@ -846,12 +990,15 @@ amy_status amy_info(amy_handle h, amy_info_t *out) {
             const int32_t K = b[MAXD + L] - b[L] + wm;
             const bool all = (b[2 * MAXD] & ((1 << h->g.n) - 1)) == ((1 << h->g.n) - 1);
             if (all && K >= wm && K <= wm + 3 && K <= h->g.N[L]) {
-                out->backup_kernel = 3;
+                out->backup_kernel = h->synth_ok ? 5 : sh.runs ? 4 : 3;
                 out->inner_span = K;
             }
         }
     }
     out->input_runs = h->runs;
+    out->build_kernels = h->tmode == AMY_T_ON_THE_FLY ? 0
+                         : h->tmode != AMY_T_STORED_SEPARABLE ? 1
+                         : (h->g.shoff > 0 && h->g.tsx[h->g.n - 1][h->g.n - 1] != 0) ? 3 : 2;
     return AMY_OK;
 }
 
@@ -880,8 +1027,14 @@ amy_status amy_rebuild(amy_handle h, const double *params, int64_t n_params) {
                                  cudaMemcpyHostToDevice, h->stream), "params upload");
     }
     if (h->tmode == AMY_T_ON_THE_FLY) return AMY_OK;
-    if (h->prec == AMY_PREC_FP64) return launch_build<double>(h);
-    return launch_build<float>(h);
+    amy_status st = h->prec == AMY_PREC_FP64 ? launch_build<double>(h) : launch_build<float>(h);
+    // new parameters may move the window origins: refresh the host copy of the bounds
+    if (st == AMY_OK && params) {
+        st = read_bounds(h);
+        if (st == AMY_OK) update_synth_ok(h);
+        h->graph_valid = false;
+    }
+    return st;
 }
 
 amy_status amy_set_profiling(amy_handle h, int32_t on) {
@@ -890,9 +1043,15 @@ amy_status amy_set_profiling(amy_handle h, int32_t on) {
     return AMY_OK;
 }
 
-amy_status amy_kernel_times(amy_handle h, double *backup_ms, int64_t *backup_launches, double *build_ms,
-                            int64_t *build_launches) {
+amy_status amy_kernel_times(amy_handle h, double *backup_ms, int64_t *backup_launches, int64_t *backup_steps,
+                            double *build_ms, int64_t *build_launches) {
     if (!h) return set_error(AMY_E_INVALID_ARG, "null handle");
+    if (backup_steps) {
+        int64_t n = 0;
+        for (int32_t k : h->ev_backup_steps) n += k;
+        *backup_steps = n;
+    }
+    h->ev_backup_steps.clear();
     auto drain = [&](std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &l, double *ms, int64_t *cnt) -> amy_status {
         double tot = 0.0;
         for (auto &p : l) {
@@ -909,8 +1068,9 @@ amy_status amy_kernel_times(amy_handle h, double *backup_ms, int64_t *backup_lau
         return AMY_OK;
     };
     amy_status st = drain(h->ev_backup, backup_ms, backup_launches);
-    if (st != AMY_OK) return st;
-    return drain(h->ev_build, build_ms, build_launches);
+    if (st == AMY_OK) st = drain(h->ev_build, build_ms, build_launches);
+    if (st == AMY_OK) st = check_synth_error(h);
+    return st;
 }
 
 }  // extern "C"
@@ -925,6 +1085,16 @@ amy_status enqueue_synthesis(amy_handle_s *h, const SpecDev &s, int32_t horizon,
     const int64_t nx = h->g.nx;
     amy_status st = launch_mask_any(h, s, h->d_V[0]);
     if (st != AMY_OK) return st;
+    if (h->synth_ok && horizon > 0) {
+        // the whole horizon in one persistent launch
+        AMY_CUDA(cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream), "barrier reset");
+        const FastCall c = fast_call(h, s.kind, h->d_V[0], h->d_V[1], nullptr, nullptr);
+        const SynthCall sc = synth_call(h, horizon, d_Vout, d_pi, all_steps);
+        KernelTimer tm(h, &h->ev_backup, horizon);
+        st = launch_synth_fast(h->g, tm_kind_of(h), h->v_store, c, sc, h->sm_count, h->stream, false);
+        tm.done();
+        return st;
+    }
     int cur = 0;
     for (int32_t k = horizon - 1; k >= 0; --k) {
         uint16_t *pk = nullptr;
@@ -1024,7 +1194,7 @@ amy_status amy_synthesize(amy_handle h, const amy_spec *spec, int32_t horizon, v
         if (own_out) cudaFreeAsync(d_Vout, h->stream);
         if (own_pi) cudaFreeAsync(d_pi, h->stream);
     };
-    if (outputs_on_device && h->use_graphs && !h->profiling) {
+    if (outputs_on_device && h->use_graphs && !h->profiling && !(h->synth_ok && horizon > 0)) {
         st = synthesize_graph(h, s, horizon, d_Vout, d_pi, policy_all_steps);
     } else {
         st = enqueue_synthesis(h, s, horizon, d_Vout, d_pi, policy_all_steps);
@@ -1041,6 +1211,10 @@ amy_status amy_synthesize(amy_handle h, const amy_spec *spec, int32_t horizon, v
         cleanup();
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_error(e, "copy out");
+        if (h->synth_ok && horizon > 0) {
+            st = check_synth_error(h);
+            if (st != AMY_OK) return st;
+        }
         if (policy_out && horizon == 0) {
             // no backup: no policy entries to report
         }

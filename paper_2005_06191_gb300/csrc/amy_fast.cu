@@ -15,6 +15,15 @@ extern template amy_status launch_fast_vt<unorm16>(const Geom &, int, int, int, 
                                                    cudaStream_t);
 extern template amy_status launch_fast_vt<__nv_bfloat16>(const Geom &, int, int, int, const FastCall &, int,
                                                          cudaStream_t);
+template <class VT>
+amy_status launch_synth_vt(const Geom &g, int wm, int var, int tmode, const FastCall &c, const SynthCall &sc,
+                           int sm_count, cudaStream_t st, bool dry_run);
+extern template amy_status launch_synth_vt<float>(const Geom &, int, int, int, const FastCall &, const SynthCall &,
+                                                  int, cudaStream_t, bool);
+extern template amy_status launch_synth_vt<unorm16>(const Geom &, int, int, int, const FastCall &,
+                                                    const SynthCall &, int, cudaStream_t, bool);
+extern template amy_status launch_synth_vt<__nv_bfloat16>(const Geom &, int, int, int, const FastCall &,
+                                                          const SynthCall &, int, cudaStream_t, bool);
 
 int fast_wm(const Geom &g, int prec) {
     if (prec == AMY_PREC_FP64) return 0;
@@ -46,6 +55,7 @@ FastShape fast_shape(const Geom &g, int tmode, const FastCall &c, int sm_count) 
         sh.tilex = FAST_THREADS / sh.ulanes;
     }
     sh.rowtile = sh.staged ? staged_rowtile(g, sh.tilex, c.rows) : 0;
+    sh.runs = sh.staged && c.grouped && sh.rowtile > 0 && g.n >= 2 && runs_kernel_applies(g, wm);
     return sh;
 }
 
@@ -59,12 +69,24 @@ amy_status launch_backup_fast(const Geom &g, int tmode, int v_store, const FastC
     return launch_fast_vt<float>(g, wm, var, tmode, c, sm_count, st);
 }
 
+amy_status launch_synth_fast(const Geom &g, int tmode, int v_store, const FastCall &c, const SynthCall &sc,
+                             int sm_count, cudaStream_t st, bool dry_run) {
+    const int wm = fast_wm(g, AMY_PREC_FP32);
+    if (wm == 0 || tmode == TM_FULL) return AMY_E_UNSUPPORTED;
+    const int var = fast_variant(g, wm, tmode);
+    if (v_store == AMY_V_BF16) return launch_synth_vt<__nv_bfloat16>(g, wm, var, tmode, c, sc, sm_count, st, dry_run);
+    if (v_store == AMY_V_UNORM16) return launch_synth_vt<unorm16>(g, wm, var, tmode, c, sc, sm_count, st, dry_run);
+    return launch_synth_vt<float>(g, wm, var, tmode, c, sc, sm_count, st, dry_run);
+}
+
 amy_status launch_build_sep(const Geom &g, uint32_t *tab, int sm_count, cudaStream_t st) {
     int64_t total = 0;
     for (int d = 0; d < g.n; ++d) total += g.tent[d];
     const int blocks = (int)std::min<int64_t>((total + 127) / 128, (int64_t)sm_count * 16);
     k_build_sep_bounds_init<<<1, 32, 0, st>>>(g, tab);
     k_build_sep<<<std::max(blocks, 1), 128, 0, st>>>(g, tab, total);
+    if (g.shoff > 0 && g.tsx[g.n - 1][g.n - 1] != 0)
+        k_build_shift<<<(g.tent[g.n - 1] + 127) / 128, 128, 0, st>>>(g, tab);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? AMY_OK : cuda_error(e, "table build launch");
 }

@@ -35,6 +35,17 @@ template <class VT> struct FastArgs {
     int32_t grouped;     // staged kernel: inputs come in runs sharing their outer-dim records
     int32_t box_floats;  // staged kernel: shared-memory box budget (floats)
     int32_t stage_tab;   // staged kernel: words of the innermost dim's table to stage (0 = none)
+    int32_t stage_recs;  // per-run kernel: records of the innermost dim's table (staged as weights)
+    int32_t runs_planes; // per-run kernel: 16-byte planes allocated per sliding entry (1 or 2)
+    uint32_t tx_magic;   // per-run kernel: ceil(2^32 / tileX), so tid / tileX = umulhi(tid, tx_magic)
+    int32_t chu_shift;   // per-run kernel: log2 of the 32-lane chunks per innermost row
+    // per-run kernel, from the host when known (else read or derived on the device):
+    int32_t bnd_known;   // 1: bnd_lo / bnd_hi hold the tables' (origin - own coordinate) bounds
+    int32_t bnd_lo[3], bnd_hi[3];
+    int32_t nrs;         // > 0: the input runs (at most 64) start at rs[0 .. nrs - 1], rs[nrs] = inputs
+    int32_t in_stride_b; // byte step between the inner records of consecutive inputs of a run
+                         // (INT_MIN: not constant)
+    uint16_t rs[66];
     int32_t kahan;       // compensated accumulation over window rows
     const float *T;      // per-pair masses [sum W][pairs] (stored factored)
     const int16_t *O;    // per-pair origins [n][pairs]
@@ -497,6 +508,29 @@ static __global__ void k_build_sep(const __grid_constant__ Geom g, uint32_t *__r
             atomicMax(b + MAXD + d, o - xd);
         }
     }
+}
+
+// Shifted-weight copy of the innermost dim's table (Geom::shoff), once the
+// table and its bounds are built: record e gets its masses at the slots they
+// occupy among the K = W + (largest - smallest origin offset) slots that
+// start at own coordinate + smallest offset.
+static __global__ void k_build_shift(const __grid_constant__ Geom g, uint32_t *__restrict__ tab) {
+    const int L = g.n - 1;
+    const int32_t e = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= g.tent[L]) return;
+    const int32_t *b = reinterpret_cast<const int32_t *>(tab + g.boff);
+    const uint32_t *rec = tab + g.toff[L] + (int64_t)e * g.trw[L];
+    const int32_t own = (e / g.tsx[L][L]) % g.N[L];
+    const int32_t sh = (int32_t)rec[0] - own - b[L];
+    const int Wd = g.W[L];
+    float w[8];
+    for (int k = 0; k < 8; ++k) {
+        const int32_t j = k - sh;
+        w[k] = (sh >= 0 && sh + Wd <= 8 && j >= 0 && j < Wd) ? __uint_as_float(rec[1 + j]) : 0.0f;
+    }
+    float4 *out = reinterpret_cast<float4 *>(tab + g.shoff);
+    out[e] = make_float4(w[0], w[1], w[2], w[3]);
+    out[g.tent[L] + e] = make_float4(w[4], w[5], w[6], w[7]);
 }
 
 static __global__ void k_build_sep_bounds_init(const __grid_constant__ Geom g, uint32_t *__restrict__ tab) {

@@ -8,6 +8,7 @@
 
 #include "amy_fast.cuh"
 #include "amy_internal.h"
+#include "amy_runs.cuh"
 #include "amy_staged.cuh"
 
 namespace amy {
@@ -15,6 +16,9 @@ namespace amy {
 template <class VT>
 amy_status launch_fast_vt(const Geom &g, int wm, int var, int tmode, const FastCall &c, int sm_count,
                           cudaStream_t st);
+template <class VT>
+amy_status launch_synth_vt(const Geom &g, int wm, int var, int tmode, const FastCall &c, const SynthCall &sc,
+                           int sm_count, cudaStream_t st, bool dry_run);
 
 namespace fastimpl {
 
@@ -36,6 +40,13 @@ amy_status launch_t(const Geom &g, const FastCall &c, int sm_count, cudaStream_t
     a.grouped = 0;
     a.box_floats = 0;
     a.stage_tab = 0;
+    a.stage_recs = 0;
+    a.runs_planes = 0;
+    a.tx_magic = 0;
+    a.chu_shift = 0;
+    a.bnd_known = 0;
+    a.nrs = 0;
+    a.in_stride_b = INT_MIN;
     // Input lanes per state: one when the grid alone fills the GPU several
     // times over, otherwise up to 8 (power of two) to expose parallelism.
     a.ulanes = (c.ulanes > 0 && FAST_THREADS % c.ulanes == 0) ? c.ulanes : fast_default_ulanes(g, sm_count);
@@ -54,6 +65,138 @@ amy_status launch_t(const Geom &g, const FastCall &c, int sm_count, cudaStream_t
     kern<<<(unsigned)blocks, FAST_THREADS, smem, st>>>(g, a);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? AMY_OK : cuda_error(e, "fast backup launch");
+}
+
+// Per-run variant (row tiles, inputs in runs sharing their outer records,
+// innermost dim's table staged in shared memory as shifted weights).  The
+// box budget is the tile's exact sliding box when the tables' origin bounds
+// are known on the host (c.bounds_known), else a default; a caller-given
+// budget (c.box_floats) caps it.
+template <class VT, int WM, int NS>
+void fill_runs_args(const Geom &g, const FastCall &c, int ul, int tx, int rowtile, bool kahan, FastArgs<VT> &a) {
+    a.Vn = (const VT *)c.Vn;
+    a.Vo = (VT *)c.Vo;
+    a.Vfinal = c.Vfinal;
+    a.pi = c.pi;
+    a.mask = c.mask;
+    a.spec_kind = c.spec_kind;
+    a.kahan = kahan ? 1 : 0;
+    a.T = c.T;
+    a.O = c.O;
+    a.npairs = c.npairs;
+    a.tab = c.tab;
+    a.ulanes = ul;
+    a.tileX = tx;
+    a.rowtile = rowtile;
+    a.grouped = 1;
+    a.stage_tab = 0;
+    a.stage_recs = g.tent[g.n - 1];
+    const int L = g.n - 1;
+    int box;
+    if (c.bounds_known) {
+        const int K = WM + (c.bnd_hi[L] - c.bnd_lo[L]);
+        a.runs_planes = runs_planes(std::min(std::max(K, WM), WM + 3));
+        int64_t nrows = (int64_t)rowtile - 1 + (c.bnd_hi[L - 1] - c.bnd_lo[L - 1]) + WM;
+        if (NS == 3) nrows *= (int64_t)(c.bnd_hi[0] - c.bnd_lo[0]) + WM;
+        box = (int)std::min<int64_t>(runs_box_floats(nrows, g.N[L], K), 48 * 1024);
+    } else {
+        a.runs_planes = runs_planes(WM + 3);
+        box = RUNS_BOX_DEFAULT;
+    }
+    if (c.box_floats > 0) box = std::min(box, c.box_floats);
+    a.box_floats = (std::max(box, 4) + 3) & ~3;
+    a.bnd_known = c.bounds_known;
+    for (int d = 0; d < 3; ++d) {
+        a.bnd_lo[d] = c.bnd_lo[d];
+        a.bnd_hi[d] = c.bnd_hi[d];
+    }
+    a.nrs = (c.run_starts && c.n_runs >= 1 && c.n_runs <= 64) ? c.n_runs : 0;
+    for (int i = 0; i <= a.nrs && a.nrs > 0; ++i) a.rs[i] = (uint16_t)c.run_starts[i];
+    a.in_stride_b = a.nrs > 0 ? c.in_stride_b : INT_MIN;
+    a.tx_magic = (uint32_t)(((1ULL << 32) + (uint64_t)tx - 1) / (uint64_t)tx);
+    int chu = tx / (32 * rowtile), sh = 0;
+    while ((1 << sh) < chu) ++sh;
+    a.chu_shift = sh;
+}
+
+// grid of the per-run kernels: (row tiles of dim n-2, dim 0) for 3-D problems,
+// row tiles of dim 0 for 2-D
+inline dim3 runs_grid(const Geom &g, int rowtile) {
+    return g.n == 3 ? dim3((unsigned)((g.N[1] + rowtile - 1) / rowtile), (unsigned)g.N[0])
+                    : dim3((unsigned)((g.N[0] + rowtile - 1) / rowtile));
+}
+
+// Per-run variant (row tiles, inputs in runs sharing their outer records,
+// innermost dim's table staged in shared memory as shifted weights).  The
+// box budget is the tile's exact sliding box when the tables' origin bounds
+// are known on the host (c.bounds_known), else a default; a caller-given
+// budget (c.box_floats) caps it.
+template <class VT, int WM, int NS, bool KAHAN>
+amy_status launch_runs_k(const Geom &g, const FastCall &c, int ul, int tx, int rowtile, cudaStream_t st) {
+    FastArgs<VT> a;
+    fill_runs_args<VT, WM, NS>(g, c, ul, tx, rowtile, KAHAN, a);
+    const dim3 grid = runs_grid(g, rowtile);
+    if (NS == 3 && g.N[0] > 65535) return set_error(AMY_E_UNSUPPORTED, "per-run backup: dim 0 above 65535");
+    const size_t smem = runs_smem_bytes(NS, WM, a.box_floats, g.nu, a.stage_recs, a.runs_planes, a.tileX * a.ulanes);
+    auto kern = k_backup_runs<VT, WM, NS, KAHAN>;
+    static bool raised = false;
+    if (!raised) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return cuda_error(e, "per-run backup smem attribute");
+        raised = true;
+    }
+    if (smem > 200 * 1024) return set_error(AMY_E_UNSUPPORTED, "per-run backup needs %zu bytes of shared memory", smem);
+    kern<<<grid, (unsigned)(a.tileX * a.ulanes), smem, st>>>(g, a);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AMY_OK : cuda_error(e, "per-run backup launch");
+}
+
+// The persistent horizon kernel: needs the host copies of the bounds (and an
+// inner span of at most WM + 3 slots), at most 64 runs, a box that fits, and
+// every block of the grid resident at once.
+template <class VT, int WM, int NS, bool KAHAN>
+amy_status launch_synth_k(const Geom &g, const FastCall &c, const SynthCall &sc, int ul, int tx, int rowtile,
+                          int sm_count, cudaStream_t st, bool dry_run) {
+    if (!c.bounds_known || !c.run_starts || c.n_runs < 1 || c.n_runs > 64 || g.shoff == 0)
+        return AMY_E_UNSUPPORTED;
+    const int L = g.n - 1;
+    const int KX = c.bnd_hi[L] - c.bnd_lo[L];
+    if (KX < 0 || KX > 3 || WM + KX > g.N[L] || (NS == 3 && g.N[0] > 65535)) return AMY_E_UNSUPPORTED;
+    FastArgs<VT> a;
+    fill_runs_args<VT, WM, NS>(g, c, ul, tx, rowtile, KAHAN, a);
+    int64_t nrows = (int64_t)rowtile - 1 + (c.bnd_hi[L - 1] - c.bnd_lo[L - 1]) + WM;
+    if (NS == 3) nrows *= (int64_t)(c.bnd_hi[0] - c.bnd_lo[0]) + WM;
+    if (runs_box_floats(nrows, g.N[L], WM + KX) > a.box_floats) return AMY_E_UNSUPPORTED;
+    const dim3 grid = runs_grid(g, rowtile);
+    const int threads = a.tileX * a.ulanes;
+    const size_t smem = runs_smem_bytes(NS, WM, a.box_floats, g.nu, a.stage_recs, a.runs_planes, threads);
+    if (smem > 200 * 1024) return AMY_E_UNSUPPORTED;
+    auto kern = k_synth_runs<VT, WM, NS, KAHAN>;
+    static bool raised = false;
+    if (!raised) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return cuda_error(e, "persistent backup smem attribute");
+        raised = true;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return cuda_error(e, "persistent backup occupancy");
+    if ((int64_t)per_sm * sm_count < (int64_t)grid.x * grid.y) return AMY_E_UNSUPPORTED;
+    if (dry_run) return AMY_OK;
+    RunsHorizon hz;
+    hz.V0 = sc.V0;
+    hz.V1 = sc.V1;
+    hz.Vfinal = sc.Vfinal;
+    hz.pi = sc.pi;
+    hz.all_steps = sc.all_steps;
+    hz.horizon = sc.horizon;
+    hz.bar = sc.bar;
+    hz.err = sc.err;
+    hz.spin_limit = sc.spin_limit;
+    Geom gg = g;
+    void *args[] = {(void *)&gg, (void *)&a, (void *)&hz};
+    e = cudaLaunchCooperativeKernel((const void *)kern, grid, dim3((unsigned)threads), args, smem, st);
+    return e == cudaSuccess ? AMY_OK : cuda_error(e, "persistent backup launch");
 }
 
 // Staged variant (low-dimensional problems, exact widths): window boxes in
@@ -79,10 +222,23 @@ amy_status launch_staged_ns(const Geom &g, const FastCall &c, int sm_count, cuda
     a.ulanes = ul;
     a.tileX = tx;
     a.rowtile = staged_rowtile(g, a.tileX, c.rows);
+    if constexpr (NS >= 2 && TM == TM_SEPARABLE) {
+        if (c.grouped && a.rowtile > 0 && runs_kernel_applies(g, WM)) {
+            if (c.kahan) return launch_runs_k<VT, WM, NS, true>(g, c, ul, tx, a.rowtile, st);
+            return launch_runs_k<VT, WM, NS, false>(g, c, ul, tx, a.rowtile, st);
+        }
+    }
     a.grouped = c.grouped;
     a.box_floats = c.box_floats > 0 ? std::min(std::max(c.box_floats, 256), STAGE_BOX_FLOATS) : STAGE_BOX_FLOATS;
     const int64_t tabw = (int64_t)g.tent[g.n - 1] * g.trw[g.n - 1];
     a.stage_tab = (c.grouped && tabw <= STAGE_TAB_WORDS) ? (int32_t)tabw : 0;
+    a.stage_recs = 0;
+    a.runs_planes = 0;
+    a.tx_magic = 0;
+    a.chu_shift = 0;
+    a.bnd_known = 0;
+    a.nrs = 0;
+    a.in_stride_b = INT_MIN;
     const int64_t blocks = staged_blocks(g, a.tileX, a.rowtile);
     const size_t smem = staged_smem_bytes(g.n, WM, a.box_floats, g.nu, a.stage_tab, a.tileX * a.ulanes);
     auto kern = k_backup_staged<VT, WM, TM, NS>;
@@ -121,6 +277,27 @@ amy_status launch_tm(const Geom &g, int var, int tmode, const FastCall &c, int s
 }
 
 }  // namespace fastimpl
+
+template <class VT>
+amy_status launch_synth_vt(const Geom &g, int wm, int var, int tmode, const FastCall &c, const SynthCall &sc,
+                           int sm_count, cudaStream_t st, bool dry_run) {
+    if (tmode != TM_SEPARABLE || var < VAR_EXACT || (wm != 3 && wm != 5) || g.n < 2 || g.n > 3 || c.no_stage ||
+        !c.grouped || !runs_kernel_applies(g, wm))
+        return AMY_E_UNSUPPORTED;
+    int ul = 0, tx = 0;
+    staged_default_shape(g, c, sm_count, ul, tx);
+    if (ul < 1 || tx < 32 || tx % 32 != 0 || tx * ul > STAGE_MAX_THREADS) return AMY_E_UNSUPPORTED;
+    const int rowtile = staged_rowtile(g, tx, c.rows);
+    if (rowtile <= 0) return AMY_E_UNSUPPORTED;
+#define AMY_SYNTH_DISPATCH(WMV, NSV)                                                                              \
+    return c.kahan ? fastimpl::launch_synth_k<VT, WMV, NSV, true>(g, c, sc, ul, tx, rowtile, sm_count, st, dry_run)  \
+                   : fastimpl::launch_synth_k<VT, WMV, NSV, false>(g, c, sc, ul, tx, rowtile, sm_count, st, dry_run);
+    if (wm == 3 && g.n == 3) AMY_SYNTH_DISPATCH(3, 3)
+    if (wm == 3) AMY_SYNTH_DISPATCH(3, 2)
+    if (g.n == 3) AMY_SYNTH_DISPATCH(5, 3)
+    AMY_SYNTH_DISPATCH(5, 2)
+#undef AMY_SYNTH_DISPATCH
+}
 
 template <class VT>
 amy_status launch_fast_vt(const Geom &g, int wm, int var, int tmode, const FastCall &c, int sm_count,

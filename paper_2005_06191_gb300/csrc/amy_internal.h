@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <climits>
 #include <cstdint>
 #include <vector>
 
@@ -40,6 +41,12 @@ struct FastCall {
     int32_t grouped = 0;   // staged variant: inputs come in runs that share every
                            // outer dim's table record (see input_runs_share_outer)
     int32_t runs = 0;      // number of such runs (0 = not grouped)
+    const int32_t *run_starts = nullptr;  // host copy of the input runs' starts (n_runs + 1
+    int32_t n_runs = 0;                   // entries, the last = inputs), or null
+    int32_t in_stride_b = INT_MIN;        // constant byte step of the inner records within a run
+    int32_t bounds_known = 0;  // 1: bnd_lo / bnd_hi hold the tables' bounds on (window
+    int32_t bnd_lo[3] = {0, 0, 0};  // origin - own coordinate) per dim (n <= 3), read
+    int32_t bnd_hi[3] = {0, 0, 0};  // back after the table build; sizes the per-run box
     int32_t tilex = 0;     // staged variant: lane columns (states) per block, a
                            // multiple of 32 with tilex * ulanes <= 512; 0 = default
     int32_t box_floats = 0;  // staged variant: box budget in floats (0 = 6144)
@@ -50,8 +57,15 @@ struct FastCall {
 // that the staged backup may contract the outer dims once per run.  upart
 // holds each input's table-index part per dim (urw words per input).
 bool input_runs_share_outer(const Geom &g, const std::vector<int32_t> &upart);
+// Starts of the runs of consecutive inputs sharing their outer records
+// (with the input count appended), and the byte step between the 16-byte
+// shifted inner records of consecutive inputs of a run when it is the same
+// everywhere (else INT_MIN).
+void input_run_layout(const Geom &g, const std::vector<int32_t> &upart, std::vector<int32_t> &starts,
+                      int32_t &stride_b);
 // Number of runs of consecutive inputs with equal outer-dim table records.
 int32_t input_outer_runs(const Geom &g, const std::vector<int32_t> &upart);
+
 
 // Input lanes per state: one when the grid alone fills the GPU several times
 // over, otherwise up to 8 (power of two) to expose parallelism.
@@ -89,6 +103,7 @@ struct FastShape {
     int tilex;    // lane columns (states) per block
     int rowtile;  // staged variant's rows per tile (0 = consecutive states)
     int staged;   // 1 = shared-memory staged variant
+    int runs;     // 1 = its per-run kernel (grouped inputs on row tiles)
 };
 // Default input lanes and lane columns of the staged variant: with input runs
 // (grouped), one lane per run when there are at most 8 runs, so that every
@@ -106,6 +121,16 @@ inline void staged_default_shape(const Geom &g, const FastCall &c, int sm_count,
         tilex = std::min(256, 32 * std::max(1, 16 / ulanes));
 }
 FastShape fast_shape(const Geom &g, int tmode, const FastCall &c, int sm_count);
+// Whether the per-run kernel (amy_runs.cuh) serves a grouped staged launch
+// with row tiles: 2-D or 3-D, at most 512 inputs, every mean component
+// depending on its own coordinate (so each dim has origin bounds), 4-word
+// input parts and records, and an innermost-dim table of at most 4096 records.
+inline bool runs_kernel_applies(const Geom &g, int wm) {
+    if (g.n < 2 || g.n > 3 || g.nu > 512 || g.urw != 4) return false;
+    for (int d = 0; d < g.n; ++d)
+        if (g.tsx[d][d] == 0 || g.trw[d] != 4 * ((wm + 1 + 3) / 4)) return false;
+    return g.tent[g.n - 1] <= 4096 && g.shoff > 0;
+}
 
 // Width bound (3, 5, 8) of the fast backup for this geometry, 0 if it does not apply.
 int fast_wm(const Geom &g, int prec);
@@ -119,6 +144,26 @@ int fast_variant(const Geom &g, int wm, int tmode);
 constexpr int64_t kVGuard = 32;
 amy_status launch_backup_fast(const Geom &g, int tmode, int v_store, const FastCall &c, int sm_count,
                               cudaStream_t st);
+// The whole horizon in one cooperative launch of the per-run kernel
+// (k_synth_runs): V0 holds V_N, V1 is the other resident vector; policies and
+// the FP32 copy of V_0 as in the per-step path.  bar (two words, zeroed by the
+// caller before each launch) is the grid barrier, *err its error flag.
+struct SynthCall {
+    const void *V0;
+    void *V1;
+    float *Vfinal;
+    uint16_t *pi;
+    int32_t all_steps;
+    int32_t horizon;
+    unsigned *bar;
+    int32_t *err;
+    int32_t spin_limit;
+};
+// Launches it, or with dry_run only checks that it applies to this problem and
+// launch shape and that every block can be resident at once.  Returns
+// AMY_E_UNSUPPORTED (and launches nothing) when it does not apply.
+amy_status launch_synth_fast(const Geom &g, int tmode, int v_store, const FastCall &c, const SynthCall &sc,
+                             int sm_count, cudaStream_t st, bool dry_run);
 amy_status launch_build_sep(const Geom &g, uint32_t *tab, int sm_count, cudaStream_t st);
 // Fills the separable-table fields of g (dependency sets, strides, offsets);
 // returns the table size in 32-bit words.
