@@ -137,13 +137,16 @@ typedef struct {
                                    and keeps the fastest; results do not depend on
                                    the choice.  Skipped (heuristic shapes) when one
                                    backup exceeds 4e9 window slots.  0: heuristic. */
-    int32_t launch_shape[4];    /* fixed backup launch shape, each entry 0 = automatic:
+    int32_t launch_shape[5];    /* fixed backup launch shape, each entry 0 = automatic:
                                    [0] input lanes per state (1..8), [1] states per
                                    block of the staged variant (multiple of 32,
                                    [0]*[1] <= 512), [2] 1 = row tiles, 2 = tiles of
                                    consecutive states, [3] staged box budget in floats
-                                   (256..6144).  Entries that do not apply are ignored;
-                                   the autotuner, when on, overrides them. */
+                                   (256..6144), [4] values of dim 0 per row tile of a
+                                   3-D problem in the per-run kernels (1..8; the
+                                   tile's rows of dim 1 = its rows / this).  Entries
+                                   that do not apply are ignored; the autotuner, when
+                                   on, overrides them. */
 } amy_opts;
 
 /* Closed box tested on representative points: lb[d] <= centre_d <= ub[d]. */
@@ -193,6 +196,7 @@ typedef struct {
     int32_t input_runs;         /* runs of consecutive inputs sharing outer records */
     int32_t inner_span;         /* inner slots K one outer contraction covers (kernels 3, 4) */
     int32_t build_kernels;      /* kernels one table build (amy_build / amy_rebuild) launches */
+    int32_t tile_outer_rows;    /* per-run kernels: values of dim 0 per row tile (3-D) */
 } amy_info_t;
 
 /* Points per dim of [lb, ub] with step eta: floor((ub-lb)/eta + 1e-9) + 1

@@ -177,7 +177,7 @@ def amy_build(problem, tmode: str = "otf", prec: str = "fp32", v_store: str = "n
     `stream` is a cudaStream_t as int; None uses torch's current stream.
     `autotune` times the backup's launch shapes at build and keeps the fastest;
     `launch_shape` = (input lanes, states per block, row tiles 1 / consecutive 2,
-    box floats) fixes them instead (0 entries = automatic)."""
+    box floats, dim-0 values per row tile) fixes them instead (0 entries = automatic)."""
     k = _Keep()
     sysd, states, inputs, sigma, cut = _problem_structs(k, problem)
     o = _abi.amy_opts()
@@ -209,7 +209,7 @@ def amy_info(h: AmyHandle) -> dict:
         "v_store": int(info.v_store), "input_lanes": int(info.input_lanes), "row_tiles": int(info.row_tiles), "block_states": int(info.block_states),
         "grouped_inputs": int(info.grouped_inputs), "backup_kernel": int(info.backup_kernel),
         "input_runs": int(info.input_runs), "inner_span": int(info.inner_span),
-        "build_kernels": int(info.build_kernels),
+        "build_kernels": int(info.build_kernels), "tile_outer_rows": int(info.tile_outer_rows),
     }
 
 

@@ -36,7 +36,7 @@ class amy_cut(C.Structure):
 class amy_opts(C.Structure):
     _fields_ = [("tmode", C.c_int32), ("prec", C.c_int32), ("v_store", C.c_int32),
                 ("device_mem_budget", C.c_int64), ("cuda_stream", C.c_void_p), ("use_graphs", C.c_int32),
-                ("autotune", C.c_int32), ("launch_shape", C.c_int32 * 4)]
+                ("autotune", C.c_int32), ("launch_shape", C.c_int32 * 5)]
 
 
 class amy_box(C.Structure):
@@ -55,7 +55,8 @@ class amy_info_t(C.Structure):
                 ("device_bytes", C.c_int64), ("tmode", C.c_int32), ("prec", C.c_int32),
                 ("v_store", C.c_int32), ("input_lanes", C.c_int32), ("row_tiles", C.c_int32), ("block_states", C.c_int32),
                 ("grouped_inputs", C.c_int32), ("backup_kernel", C.c_int32), ("input_runs", C.c_int32),
-                ("inner_span", C.c_int32), ("build_kernels", C.c_int32)]
+                ("inner_span", C.c_int32), ("build_kernels", C.c_int32),
+                ("tile_outer_rows", C.c_int32)]
 
 
 class amy_server_opts(C.Structure):

@@ -80,16 +80,9 @@ __global__ void __launch_bounds__(FAST_THREADS) k_step_group(const BatchEntry *_
         a.stage_tab = 0;
         a.stage_recs = 0;
         a.runs_planes = 0;
-    a.tx_magic = 0;
-    a.chu_shift = 0;
-    a.bnd_known = 0;
-    a.nrs = 0;
-    a.in_stride_b = INT_MIN;
         a.tx_magic = 0;
         a.chu_shift = 0;
-    a.bnd_known = 0;
-    a.nrs = 0;
-    a.in_stride_b = INT_MIN;
+        a.outer = 1;
         a.bnd_known = 0;
         a.nrs = 0;
         a.in_stride_b = INT_MIN;

@@ -146,6 +146,32 @@ __device__ __forceinline__ void mean_of(const Geom &g, int32_t x, int32_t u, dou
     }
 }
 
+// Component d of the mean, with the same FP64 operations in the same order
+// as mean_of (for the per-dimension tables, which need one component).
+__device__ __forceinline__ double mean_component(const Geom &g, int32_t x, int32_t u, int d) {
+    int32_t xi[MAXD];
+    decode_state(g, x, xi);
+    if (g.sys == SYS_AFFINE) {
+        const int n = g.n;
+        const double *A = g.params + (int64_t)u * (n * n + n);
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < MAXD; ++j)
+            if (j < n) acc = dadd(acc, dmul(__ldg(A + d * n + j), state_centre(g, j, xi[j])));
+        return dadd(acc, __ldg(A + n * n + d));
+    }
+    const int32_t uw = u % g.ucount[1];
+    const int32_t uv = u / g.ucount[1];
+    const double v = dadd(g.ulb[0], dmul((double)uv, g.ueta[0]));
+    const double w = dadd(g.ulb[1], dmul((double)uw, g.ueta[1]));
+    const double tau = __ldg(g.params);
+    const double th = state_centre(g, 2, xi[2]);
+    if (d == 2) return dadd(th, dmul(tau, w));
+    const double tv = dmul(tau, v);
+    if (d == 0) return dadd(state_centre(g, 0, xi[0]), dmul(tv, cos(th)));
+    return dadd(state_centre(g, 1, xi[1]), dmul(tv, sin(th)));
+}
+
 // Window origin of one dimension (first slot index, unwrapped), in the FP64
 // expression order fixed by the ABI.  Far-away origins are clamped where every
 // slot is off the grid anyway.

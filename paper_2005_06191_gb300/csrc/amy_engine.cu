@@ -381,6 +381,7 @@ struct amy_handle_s {
     int32_t bnd_lo[MAXD], bnd_hi[MAXD];
     int tilex;            // staged variant: lane columns per block (0 = default)
     int box_floats;       // staged variant: box budget (0 = default)
+    int outer;            // per-run kernels: values of dim 0 per row tile (0 = 1)
     std::vector<double> host_params;
     // kernel timing: CUDA events around every backup / build kernel when profiling
     bool profiling;
@@ -596,6 +597,7 @@ FastCall fast_call(const amy_handle_s *h, int spec_kind, const void *Vn, void *V
     set_bounds(h, c);
     c.tilex = h->tilex;
     c.box_floats = h->box_floats;
+    c.outer = h->outer;
     return c;
 }
 
@@ -736,37 +738,87 @@ amy_status autotune_shape(amy_handle_s *h) {
     if (staged && h->grouped && h->runs >= 2)  // lanes take whole runs: any count up to the runs
         for (int ul = 3; ul <= std::min(h->runs, 8); ++ul)
             if ((ul & (ul - 1)) != 0) uls.push_back(ul);
-    float best = 3.4e38f;
-    int best_ul = h->ulanes, best_tx = h->tilex, best_rows = h->rows, best_box = h->box_floats;
-    amy_status st = AMY_OK;
+    // candidate shapes: (input lanes, states per block, row tiles, box budget,
+    // dim-0 values per tile).  Staged: powers of two states per block with
+    // either tile mapping and two box budgets; where the per-run kernels take
+    // row tiles also any multiple of 32 states per block split over 1..4
+    // values of dim 0 (exact boxes).  Register-resident: 256 threads.
+    struct Cand {
+        int ul, tx, rows, box, outer;
+    };
+    std::vector<Cand> cands;
     for (int ul : uls) {
         if (ul > 1 && ul > h->g.nu) continue;
-        for (int tx = 32; tx <= 512 && st == AMY_OK; tx <<= 1) {
-            if (tx * ul > (staged ? 512 : 256)) break;
-            if (!staged && tx * ul != 256) continue;
-            for (int cand = 0; cand < (staged ? 4 : 1) && st == AMY_OK; ++cand) {
-                const int rows = cand & 1;
+        if (!staged) {
+            if (256 % ul == 0) cands.push_back({ul, 0, 1, 0, 0});
+            continue;
+        }
+        for (int tx = 32; tx * ul <= 512; tx <<= 1)
+            for (int cand = 0; cand < 4; ++cand) cands.push_back({ul, tx, cand & 1, (cand >> 1) ? 3072 : 0, 0});
+        FastCall q = c;
+        q.ulanes = ul;
+        q.rows = 1;
+        for (int tx = 32; tx * ul <= 512; tx += 32) {
+            q.tilex = tx;
+            for (int outer = 1; outer <= (h->g.n == 3 ? 4 : 1); ++outer) {
+                q.outer = outer;
+                const FastShape sh = fast_shape(h->g, tm_kind_of(h), q, h->sm_count);
+                if (!sh.runs || sh.outer != outer) continue;
+                if ((tx & (tx - 1)) == 0 && outer == 1) continue;  // already listed
+                cands.push_back({ul, tx, 1, 0, outer});
+            }
+        }
+    }
+    float best = 3.4e38f;
+    int best_ul = h->ulanes, best_tx = h->tilex, best_rows = h->rows, best_box = h->box_floats,
+        best_outer = h->outer;
+    amy_status st = AMY_OK;
+    for (const Cand &cd : cands) {
+        if (st != AMY_OK) break;
+        {
+            {
+                const int ul = cd.ul, rows = cd.rows;
                 c.ulanes = ul;
-                c.tilex = staged ? tx : 0;
+                c.tilex = cd.tx;
                 c.rows = rows;
-                c.box_floats = (cand >> 1) ? 3072 : 0;
-                if (rows == 1 && fast_shape(h->g, tm_kind_of(h), c, h->sm_count).rowtile == 0) continue;
-                st = launch_backup_fast(h->g, tm_kind_of(h), h->v_store, c, h->sm_count, h->stream);
+                c.box_floats = cd.box;
+                c.outer = cd.outer;
+                if (rows == 1 && staged && fast_shape(h->g, tm_kind_of(h), c, h->sm_count).rowtile == 0) continue;
+                // per backup: the persistent horizon kernel over 8 backups where
+                // it applies with this shape (synthesis then uses it), else 3
+                // launches of the per-step kernel after a warm-up launch
+                const SynthCall sc = synth_call(h, 8, nullptr, nullptr, 0);
+                const bool persist =
+                    h->d_bar &&
+                    launch_synth_fast(h->g, tm_kind_of(h), h->v_store, c, sc, h->sm_count, h->stream, true) == AMY_OK;
+                cudaGetLastError();
+                const int reps = persist ? 8 : 3;
                 cudaError_t e = cudaSuccess;
-                if (st == AMY_OK) e = cudaEventRecord(ea, h->stream);
-                for (int rep = 0; rep < 3 && st == AMY_OK && e == cudaSuccess; ++rep)
+                if (persist) {
+                    e = cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream);
+                    if (e == cudaSuccess) e = cudaEventRecord(ea, h->stream);
+                    if (e == cudaSuccess)
+                        st = launch_synth_fast(h->g, tm_kind_of(h), h->v_store, c, sc, h->sm_count, h->stream, false);
+                } else {
                     st = launch_backup_fast(h->g, tm_kind_of(h), h->v_store, c, h->sm_count, h->stream);
+                    if (st == AMY_OK) e = cudaEventRecord(ea, h->stream);
+                    for (int rep = 0; rep < reps && st == AMY_OK && e == cudaSuccess; ++rep)
+                        st = launch_backup_fast(h->g, tm_kind_of(h), h->v_store, c, h->sm_count, h->stream);
+                }
                 if (st == AMY_OK && e == cudaSuccess) e = cudaEventRecord(eb, h->stream);
                 if (st == AMY_OK && e == cudaSuccess) e = cudaEventSynchronize(eb);
                 float ms = 0.0f;
                 if (st == AMY_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, ea, eb);
                 if (st == AMY_OK && e != cudaSuccess) st = cuda_error(e, "autotune timing");
+                if (st == AMY_OK && persist) st = check_synth_error(h);
+                ms /= (float)reps;
                 if (st == AMY_OK && ms < best) {
                     best = ms;
                     best_ul = ul;
                     best_tx = c.tilex;
                     best_rows = rows;
                     best_box = c.box_floats;
+                    best_outer = c.outer;
                 }
             }
         }
@@ -778,6 +830,7 @@ amy_status autotune_shape(amy_handle_s *h) {
     h->tilex = best_tx;
     h->rows = best_rows;
     h->box_floats = best_box;
+    h->outer = best_outer;
     return AMY_OK;
 }
 
@@ -847,7 +900,7 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
         const int32_t *ls = opts->launch_shape;
         if (ls[0] < 0 || ls[0] > 8 || ls[1] < 0 || ls[1] > 512 || ls[1] % 32 != 0 ||
             (ls[0] > 0 && ls[1] > 0 && ls[0] * ls[1] > 512) || ls[2] < 0 || ls[2] > 2 ||
-            (ls[3] != 0 && (ls[3] < 256 || ls[3] > 6144))) {
+            (ls[3] != 0 && (ls[3] < 256 || ls[3] > 6144)) || ls[4] < 0 || ls[4] > 8) {
             free_handle(h);
             return set_error(AMY_E_INVALID_ARG, "bad launch shape");
         }
@@ -855,6 +908,7 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
         h->tilex = ls[1];
         h->rows = ls[2] == 2 ? 0 : 1;
         h->box_floats = ls[3];
+        h->outer = ls[4];
     }
     h->use_graphs = opts->use_graphs;
     h->host_params = params;
@@ -916,7 +970,6 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
         return cuda_error(e, "build");
     }
     TRY(read_bounds(h));
-    if (opts->autotune) TRY(autotune_shape(h));
     h->spin_limit = 1 << 20;
     h->synth_ok = 0;
     if (fast_path(h) && h->tmode == AMY_T_STORED_SEPARABLE && h->grouped) {
@@ -927,8 +980,9 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
             free_handle(h);
             return cuda_error(e, "barrier words");
         }
-        update_synth_ok(h);
     }
+    if (opts->autotune) TRY(autotune_shape(h));
+    update_synth_ok(h);
 #undef TRY
     amy_info_t &inf = h->info;
     memset(&inf, 0, sizeof inf);
@@ -945,19 +999,13 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     inf.prec = h->prec;
     inf.v_store = h->v_store;
     if (fast_path(h)) {
-        FastCall c;
-        c.ulanes = h->ulanes;
-        c.rows = h->rows;
-        c.grouped = h->grouped;
-        c.runs = h->runs;
-        set_bounds(h, c);
-        c.tilex = h->tilex;
-        c.box_floats = h->box_floats;
+        const FastCall c = fast_call(h, SPEC_SAFETY, nullptr, nullptr, nullptr, nullptr);
         const FastShape sh = fast_shape(h->g, tm_kind_of(h), c, h->sm_count);
         inf.input_lanes = sh.ulanes;
         inf.row_tiles = sh.rowtile > 0;
         inf.block_states = sh.tilex;
         inf.grouped_inputs = sh.staged && h->grouped;
+        inf.tile_outer_rows = sh.runs ? sh.outer : 1;
     }
     *out = h;
     return AMY_OK;
@@ -970,13 +1018,7 @@ amy_status amy_info(amy_handle h, amy_info_t *out) {
     out->backup_kernel = 0;
     out->inner_span = 0;
     if (fast_path(h)) {
-        FastCall c;
-        c.ulanes = h->ulanes;
-        c.rows = h->rows;
-        c.grouped = h->grouped;
-        c.runs = h->runs;
-        set_bounds(h, c);
-        c.tilex = h->tilex;
+        const FastCall c = fast_call(h, SPEC_SAFETY, nullptr, nullptr, nullptr, nullptr);
         const FastShape sh = fast_shape(h->g, tm_kind_of(h), c, h->sm_count);
         out->backup_kernel = sh.staged ? 2 : 1;
         if (sh.staged && h->grouped && h->tmode == AMY_T_STORED_SEPARABLE) {

@@ -55,7 +55,10 @@ FastShape fast_shape(const Geom &g, int tmode, const FastCall &c, int sm_count) 
         sh.tilex = FAST_THREADS / sh.ulanes;
     }
     sh.rowtile = sh.staged ? staged_rowtile(g, sh.tilex, c.rows) : 0;
-    sh.runs = sh.staged && c.grouped && sh.rowtile > 0 && g.n >= 2 && runs_kernel_applies(g, wm);
+    int rt = 0, outer = 1;
+    sh.runs = sh.staged && c.grouped && sh.rowtile > 0 && g.n >= 2 && runs_kernel_applies(g, wm) &&
+              runs_tile_split(g, sh.rowtile, c.outer, rt, outer);
+    sh.outer = sh.runs ? outer : 1;
     return sh;
 }
 

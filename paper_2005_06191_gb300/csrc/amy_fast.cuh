@@ -39,6 +39,7 @@ template <class VT> struct FastArgs {
     int32_t runs_planes; // per-run kernel: 16-byte planes allocated per sliding entry (1 or 2)
     uint32_t tx_magic;   // per-run kernel: ceil(2^32 / tileX), so tid / tileX = umulhi(tid, tx_magic)
     int32_t chu_shift;   // per-run kernel: log2 of the 32-lane chunks per innermost row
+    int32_t outer;       // per-run kernel, 3-D: values of dim 0 per row tile (rowtile rows of dim 1 each)
     // per-run kernel, from the host when known (else read or derived on the device):
     int32_t bnd_known;   // 1: bnd_lo / bnd_hi hold the tables' (origin - own coordinate) bounds
     int32_t bnd_lo[3], bnd_hi[3];
@@ -467,6 +468,14 @@ __global__ void __launch_bounds__(FAST_THREADS) k_backup_fast(const __grid_const
 static __global__ void k_build_sep(const __grid_constant__ Geom g, uint32_t *__restrict__ tab, int64_t total) {
     float fac[MAXWS];
     int32_t off[MAXWS];
+    // origin bounds gathered per block in shared memory, then one global
+    // atomic per dim and block
+    __shared__ int32_t s_lo[MAXD], s_hi[MAXD];
+    if (threadIdx.x < MAXD) {
+        s_lo[threadIdx.x] = INT_MAX;
+        s_hi[threadIdx.x] = INT_MIN;
+    }
+    __syncthreads();
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         int d = 0;
         int64_t e = t;
@@ -491,10 +500,9 @@ static __global__ void k_build_sep(const __grid_constant__ Geom g, uint32_t *__r
             const int32_t xj = (int32_t)((r / g.tsx[d][j]) % g.N[j]);
             x += xj * g.stride[j];
         }
-        double mu[MAXD];
-        mean_of(g, x, u, mu);
-        const int32_t o = origin_of(g, d, mu[d]);
-        dim_masses_f32(g, d, mu[d], o, fac, off);
+        const double mud = mean_component(g, x, u, d);
+        const int32_t o = origin_of(g, d, mud);
+        dim_masses_f32(g, d, mud, o, fac, off);
         uint32_t *rec = tab + g.toff[d] + e * g.trw[d];
         const int Wd = g.W[d];
         rec[0] = (uint32_t)o;
@@ -503,10 +511,15 @@ static __global__ void k_build_sep(const __grid_constant__ Geom g, uint32_t *__r
         // origin bounds relative to the state's own coordinate d
         if (g.tsx[d][d] != 0) {
             const int32_t xd = (int32_t)((e / g.tsx[d][d]) % g.N[d]);
-            int32_t *b = reinterpret_cast<int32_t *>(tab + g.boff);
-            atomicMin(b + d, o - xd);
-            atomicMax(b + MAXD + d, o - xd);
+            atomicMin(&s_lo[d], o - xd);
+            atomicMax(&s_hi[d], o - xd);
         }
+    }
+    __syncthreads();
+    if (threadIdx.x < MAXD && s_lo[threadIdx.x] != INT_MAX) {
+        int32_t *b = reinterpret_cast<int32_t *>(tab + g.boff);
+        atomicMin(b + threadIdx.x, s_lo[threadIdx.x]);
+        atomicMax(b + MAXD + threadIdx.x, s_hi[threadIdx.x]);
     }
 }
 

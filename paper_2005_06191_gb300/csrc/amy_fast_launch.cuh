@@ -44,6 +44,7 @@ amy_status launch_t(const Geom &g, const FastCall &c, int sm_count, cudaStream_t
     a.runs_planes = 0;
     a.tx_magic = 0;
     a.chu_shift = 0;
+    a.outer = 1;
     a.bnd_known = 0;
     a.nrs = 0;
     a.in_stride_b = INT_MIN;
@@ -72,8 +73,10 @@ amy_status launch_t(const Geom &g, const FastCall &c, int sm_count, cudaStream_t
 // box budget is the tile's exact sliding box when the tables' origin bounds
 // are known on the host (c.bounds_known), else a default; a caller-given
 // budget (c.box_floats) caps it.
+// rowtile: rows of dim n-2 per tile; outer: values of dim 0 per tile (3-D, else 1)
 template <class VT, int WM, int NS>
-void fill_runs_args(const Geom &g, const FastCall &c, int ul, int tx, int rowtile, bool kahan, FastArgs<VT> &a) {
+void fill_runs_args(const Geom &g, const FastCall &c, int ul, int tx, int rowtile, int outer, bool kahan,
+                    FastArgs<VT> &a) {
     a.Vn = (const VT *)c.Vn;
     a.Vo = (VT *)c.Vo;
     a.Vfinal = c.Vfinal;
@@ -97,7 +100,7 @@ void fill_runs_args(const Geom &g, const FastCall &c, int ul, int tx, int rowtil
         const int K = WM + (c.bnd_hi[L] - c.bnd_lo[L]);
         a.runs_planes = runs_planes(std::min(std::max(K, WM), WM + 3));
         int64_t nrows = (int64_t)rowtile - 1 + (c.bnd_hi[L - 1] - c.bnd_lo[L - 1]) + WM;
-        if (NS == 3) nrows *= (int64_t)(c.bnd_hi[0] - c.bnd_lo[0]) + WM;
+        if (NS == 3) nrows *= (int64_t)outer - 1 + (c.bnd_hi[0] - c.bnd_lo[0]) + WM;
         box = (int)std::min<int64_t>(runs_box_floats(nrows, g.N[L], K), 48 * 1024);
     } else {
         a.runs_planes = runs_planes(WM + 3);
@@ -114,17 +117,19 @@ void fill_runs_args(const Geom &g, const FastCall &c, int ul, int tx, int rowtil
     for (int i = 0; i <= a.nrs && a.nrs > 0; ++i) a.rs[i] = (uint16_t)c.run_starts[i];
     a.in_stride_b = a.nrs > 0 ? c.in_stride_b : INT_MIN;
     a.tx_magic = (uint32_t)(((1ULL << 32) + (uint64_t)tx - 1) / (uint64_t)tx);
-    int chu = tx / (32 * rowtile), sh = 0;
+    int chu = tx / (32 * rowtile * outer), sh = 0;
     while ((1 << sh) < chu) ++sh;
     a.chu_shift = sh;
+    a.outer = outer;
 }
 
 // grid of the per-run kernels: (row tiles of dim n-2, dim 0) for 3-D problems,
 // row tiles of dim 0 for 2-D
-inline dim3 runs_grid(const Geom &g, int rowtile) {
-    return g.n == 3 ? dim3((unsigned)((g.N[1] + rowtile - 1) / rowtile), (unsigned)g.N[0])
+inline dim3 runs_grid(const Geom &g, int rowtile, int outer) {
+    return g.n == 3 ? dim3((unsigned)((g.N[1] + rowtile - 1) / rowtile), (unsigned)((g.N[0] + outer - 1) / outer))
                     : dim3((unsigned)((g.N[0] + rowtile - 1) / rowtile));
 }
+
 
 // Per-run variant (row tiles, inputs in runs sharing their outer records,
 // innermost dim's table staged in shared memory as shifted weights).  The
@@ -132,11 +137,11 @@ inline dim3 runs_grid(const Geom &g, int rowtile) {
 // are known on the host (c.bounds_known), else a default; a caller-given
 // budget (c.box_floats) caps it.
 template <class VT, int WM, int NS, bool KAHAN>
-amy_status launch_runs_k(const Geom &g, const FastCall &c, int ul, int tx, int rowtile, cudaStream_t st) {
+amy_status launch_runs_k(const Geom &g, const FastCall &c, int ul, int tx, int rowtile, int outer, cudaStream_t st) {
     FastArgs<VT> a;
-    fill_runs_args<VT, WM, NS>(g, c, ul, tx, rowtile, KAHAN, a);
-    const dim3 grid = runs_grid(g, rowtile);
-    if (NS == 3 && g.N[0] > 65535) return set_error(AMY_E_UNSUPPORTED, "per-run backup: dim 0 above 65535");
+    fill_runs_args<VT, WM, NS>(g, c, ul, tx, rowtile, outer, KAHAN, a);
+    const dim3 grid = runs_grid(g, rowtile, outer);
+    if (grid.y > 65535) return set_error(AMY_E_UNSUPPORTED, "per-run backup: dim 0 above 65535 tiles");
     const size_t smem = runs_smem_bytes(NS, WM, a.box_floats, g.nu, a.stage_recs, a.runs_planes, a.tileX * a.ulanes);
     auto kern = k_backup_runs<VT, WM, NS, KAHAN>;
     static bool raised = false;
@@ -156,18 +161,19 @@ amy_status launch_runs_k(const Geom &g, const FastCall &c, int ul, int tx, int r
 // every block of the grid resident at once.
 template <class VT, int WM, int NS, bool KAHAN>
 amy_status launch_synth_k(const Geom &g, const FastCall &c, const SynthCall &sc, int ul, int tx, int rowtile,
-                          int sm_count, cudaStream_t st, bool dry_run) {
+                          int outer, int sm_count, cudaStream_t st, bool dry_run) {
     if (!c.bounds_known || !c.run_starts || c.n_runs < 1 || c.n_runs > 64 || g.shoff == 0)
         return AMY_E_UNSUPPORTED;
     const int L = g.n - 1;
     const int KX = c.bnd_hi[L] - c.bnd_lo[L];
-    if (KX < 0 || KX > 3 || WM + KX > g.N[L] || (NS == 3 && g.N[0] > 65535)) return AMY_E_UNSUPPORTED;
+    if (KX < 0 || KX > 3 || WM + KX > g.N[L]) return AMY_E_UNSUPPORTED;
     FastArgs<VT> a;
-    fill_runs_args<VT, WM, NS>(g, c, ul, tx, rowtile, KAHAN, a);
+    fill_runs_args<VT, WM, NS>(g, c, ul, tx, rowtile, outer, KAHAN, a);
     int64_t nrows = (int64_t)rowtile - 1 + (c.bnd_hi[L - 1] - c.bnd_lo[L - 1]) + WM;
-    if (NS == 3) nrows *= (int64_t)(c.bnd_hi[0] - c.bnd_lo[0]) + WM;
+    if (NS == 3) nrows *= (int64_t)outer - 1 + (c.bnd_hi[0] - c.bnd_lo[0]) + WM;
     if (runs_box_floats(nrows, g.N[L], WM + KX) > a.box_floats) return AMY_E_UNSUPPORTED;
-    const dim3 grid = runs_grid(g, rowtile);
+    const dim3 grid = runs_grid(g, rowtile, outer);
+    if (grid.y > 65535) return AMY_E_UNSUPPORTED;
     const int threads = a.tileX * a.ulanes;
     const size_t smem = runs_smem_bytes(NS, WM, a.box_floats, g.nu, a.stage_recs, a.runs_planes, threads);
     if (smem > 200 * 1024) return AMY_E_UNSUPPORTED;
@@ -223,9 +229,10 @@ amy_status launch_staged_ns(const Geom &g, const FastCall &c, int sm_count, cuda
     a.tileX = tx;
     a.rowtile = staged_rowtile(g, a.tileX, c.rows);
     if constexpr (NS >= 2 && TM == TM_SEPARABLE) {
-        if (c.grouped && a.rowtile > 0 && runs_kernel_applies(g, WM)) {
-            if (c.kahan) return launch_runs_k<VT, WM, NS, true>(g, c, ul, tx, a.rowtile, st);
-            return launch_runs_k<VT, WM, NS, false>(g, c, ul, tx, a.rowtile, st);
+        int rt = 0, outer = 1;
+        if (c.grouped && a.rowtile > 0 && runs_kernel_applies(g, WM) && runs_tile_split(g, a.rowtile, c.outer, rt, outer)) {
+            if (c.kahan) return launch_runs_k<VT, WM, NS, true>(g, c, ul, tx, rt, outer, st);
+            return launch_runs_k<VT, WM, NS, false>(g, c, ul, tx, rt, outer, st);
         }
     }
     a.grouped = c.grouped;
@@ -236,6 +243,7 @@ amy_status launch_staged_ns(const Geom &g, const FastCall &c, int sm_count, cuda
     a.runs_planes = 0;
     a.tx_magic = 0;
     a.chu_shift = 0;
+    a.outer = 1;
     a.bnd_known = 0;
     a.nrs = 0;
     a.in_stride_b = INT_MIN;
@@ -287,11 +295,13 @@ amy_status launch_synth_vt(const Geom &g, int wm, int var, int tmode, const Fast
     int ul = 0, tx = 0;
     staged_default_shape(g, c, sm_count, ul, tx);
     if (ul < 1 || tx < 32 || tx % 32 != 0 || tx * ul > STAGE_MAX_THREADS) return AMY_E_UNSUPPORTED;
-    const int rowtile = staged_rowtile(g, tx, c.rows);
-    if (rowtile <= 0) return AMY_E_UNSUPPORTED;
-#define AMY_SYNTH_DISPATCH(WMV, NSV)                                                                              \
-    return c.kahan ? fastimpl::launch_synth_k<VT, WMV, NSV, true>(g, c, sc, ul, tx, rowtile, sm_count, st, dry_run)  \
-                   : fastimpl::launch_synth_k<VT, WMV, NSV, false>(g, c, sc, ul, tx, rowtile, sm_count, st, dry_run);
+    int rowtile = 0, outer = 1;
+    if (!runs_tile_split(g, staged_rowtile(g, tx, c.rows), c.outer, rowtile, outer)) return AMY_E_UNSUPPORTED;
+#define AMY_SYNTH_DISPATCH(WMV, NSV)                                                                               \
+    return c.kahan ? fastimpl::launch_synth_k<VT, WMV, NSV, true>(g, c, sc, ul, tx, rowtile, outer, sm_count, st,  \
+                                                                  dry_run)                                         \
+                   : fastimpl::launch_synth_k<VT, WMV, NSV, false>(g, c, sc, ul, tx, rowtile, outer, sm_count, st, \
+                                                                   dry_run);
     if (wm == 3 && g.n == 3) AMY_SYNTH_DISPATCH(3, 3)
     if (wm == 3) AMY_SYNTH_DISPATCH(3, 2)
     if (g.n == 3) AMY_SYNTH_DISPATCH(5, 3)

@@ -50,6 +50,7 @@ struct FastCall {
     int32_t tilex = 0;     // staged variant: lane columns (states) per block, a
                            // multiple of 32 with tilex * ulanes <= 512; 0 = default
     int32_t box_floats = 0;  // staged variant: box budget in floats (0 = 6144)
+    int32_t outer = 0;       // per-run kernels, 3-D: values of dim 0 per row tile (0 = 1)
 };
 
 // Whether consecutive inputs form runs (at least two inputs per run on
@@ -90,6 +91,15 @@ inline int staged_rowtile(const Geom &g, int tileX, int rows) {
     const int rw = tileX / (32 * ch);
     return (rw >= 1 && 4 * R >= 3 * 32 * ch) ? rw : 0;
 }
+// Rows of dim n-2 and values of dim 0 per tile of the per-run kernels from
+// the staged row tiling (rows per tile, all dims): the tile's rows split as
+// outer x rows when `outer` divides them (3-D), else false.
+inline bool runs_tile_split(const Geom &g, int rows_total, int want_outer, int &rowtile, int &outer) {
+    outer = (g.n == 3 && want_outer > 1) ? want_outer : 1;
+    if (rows_total < 1 || rows_total % outer != 0) return false;
+    rowtile = rows_total / outer;
+    return true;
+}
 // Grid of the staged backup: row tiles (within one outermost index when n = 3)
 // or tiles of tileX consecutive states.
 inline int64_t staged_blocks(const Geom &g, int tileX, int rowtile) {
@@ -104,6 +114,7 @@ struct FastShape {
     int rowtile;  // staged variant's rows per tile (0 = consecutive states)
     int staged;   // 1 = shared-memory staged variant
     int runs;     // 1 = its per-run kernel (grouped inputs on row tiles)
+    int outer;    // the per-run kernel's values of dim 0 per tile
 };
 // Default input lanes and lane columns of the staged variant: with input runs
 // (grouped), one lane per run when there are at most 8 runs, so that every

@@ -4,7 +4,8 @@
 // table record (the unicycle: a speed fixes the x and y rows of the window,
 // the turn rates of that speed move only the heading row).
 //
-// A block owns RW whole innermost-dim rows and all inputs; lane p of a warp
+// A block owns a tile of whole innermost-dim rows (for 3-D problems, `outer`
+// values of dim 0 by RW rows of dim 1; for 2-D, RW rows) and all inputs; lane p of a warp
 // holds innermost coordinate p (plus 32 per chunk of longer rows), and lane
 // group c of a state takes the runs c, c + UL, c + 2 UL, ...  The state's
 // coordinates come from the tile mapping, without divisions.  Per (state,
@@ -398,14 +399,19 @@ __global__ void __launch_bounds__(RUNS_MAX_THREADS) k_backup_runs(const __grid_c
     const int32_t k_in = (((xl >> 5) & ((1 << a.chu_shift) - 1)) << 5) + (xl & 31);
     int32_t xi[3] = {0, 0, 0};
     int32_t rowlo, rowhi;  // first and last row index (dim L - 1) of the tile
+    int32_t x0lo = 0, x0hi = 0;  // first and last value of dim 0 (3-D)
     bool ok;
     if (NS == 3) {
-        // grid (row tiles of dim 1, dim 0)
-        xi[0] = (int32_t)blockIdx.y;
+        // grid (row tiles of dim 1, tiles of `outer` values of dim 0); tile
+        // row r = (value r / RW of dim 0, row r % RW of dim 1)
+        const int rx = r / RW, ry = r - rx * RW;
+        x0lo = (int32_t)blockIdx.y * a.outer;
+        x0hi = min(x0lo + a.outer, g.N[0]) - 1;
+        xi[0] = x0lo + rx;
         rowlo = (int32_t)blockIdx.x * RW;
         rowhi = min(rowlo + RW, g.N[1]) - 1;
-        xi[1] = rowlo + r;
-        ok = xi[1] < g.N[1];
+        xi[1] = rowlo + ry;
+        ok = xi[0] < g.N[0] && xi[1] < g.N[1];
     } else {
         rowlo = (int32_t)blockIdx.x * RW;
         rowhi = min(rowlo + RW, g.N[0]) - 1;
@@ -450,8 +456,8 @@ __global__ void __launch_bounds__(RUNS_MAX_THREADS) k_backup_runs(const __grid_c
     // the inner coordinates 0 .. Rn - 1 (padded to 8)
     int32_t blo[2] = {0, 0}, bn[2] = {1, 1};
     if (NS == 3) {
-        blo[0] = xi[0] + dmin[0];
-        bn[0] = dmax[0] - dmin[0] + WM;
+        blo[0] = x0lo + dmin[0];
+        bn[0] = x0hi - x0lo + dmax[0] - dmin[0] + WM;
         blo[1] = rowlo + dmin[1];
         bn[1] = rowhi - rowlo + dmax[1] - dmin[1] + WM;
     } else {
@@ -686,13 +692,17 @@ __global__ void __launch_bounds__(RUNS_MAX_THREADS) k_synth_runs(const __grid_co
     const int32_t k_in = (((xl >> 5) & ((1 << a.chu_shift) - 1)) << 5) + (xl & 31);
     int32_t xi[3] = {0, 0, 0};
     int32_t rowlo, rowhi;
+    int32_t x0lo = 0, x0hi = 0;
     bool ok;
     if (NS == 3) {
-        xi[0] = (int32_t)blockIdx.y;
+        const int rx = r / RW, ry = r - rx * RW;
+        x0lo = (int32_t)blockIdx.y * a.outer;
+        x0hi = min(x0lo + a.outer, g.N[0]) - 1;
+        xi[0] = x0lo + rx;
         rowlo = (int32_t)blockIdx.x * RW;
         rowhi = min(rowlo + RW, g.N[1]) - 1;
-        xi[1] = rowlo + r;
-        ok = xi[1] < g.N[1];
+        xi[1] = rowlo + ry;
+        ok = xi[0] < g.N[0] && xi[1] < g.N[1];
     } else {
         rowlo = (int32_t)blockIdx.x * RW;
         rowhi = min(rowlo + RW, g.N[0]) - 1;
@@ -716,8 +726,8 @@ __global__ void __launch_bounds__(RUNS_MAX_THREADS) k_synth_runs(const __grid_co
     const int NPK = runs_planes(WM + KX);
     int32_t blo[2] = {0, 0}, bn[2] = {1, 1};
     if (NS == 3) {
-        blo[0] = xi[0] + dmin[0];
-        bn[0] = dmax[0] - dmin[0] + WM;
+        blo[0] = x0lo + dmin[0];
+        bn[0] = x0hi - x0lo + dmax[0] - dmin[0] + WM;
         blo[1] = rowlo + dmin[1];
         bn[1] = rowhi - rowlo + dmax[1] - dmin[1] + WM;
     } else {

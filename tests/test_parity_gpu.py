@@ -263,8 +263,11 @@ def test_launch_shapes_agree_bitwise(amy):
     ]
     # fixed shapes: (input lanes, states per block, rows 1 / consecutive 2, box floats);
     # a 256-float box overflows for most tiles and takes the global-memory path
+    # (5th entry: values of dim 0 per row tile of the per-run kernels; 3 does
+    # not divide the 5 rows of (1, 160, 1, 0, 3), which then take the staged kernel)
     fixed = [(1, 256, 2, 0), (5, 32, 1, 0), (2, 64, 1, 256), (3, 64, 2, 0), (8, 32, 0, 1024), (5, 96, 1, 0),
-             (1, 512, 2, 0), (4, 128, 1, 0)]
+             (1, 512, 2, 0), (4, 128, 1, 0), (1, 288, 1, 0, 3), (2, 192, 1, 0, 2), (1, 160, 1, 0, 3),
+             (1, 384, 1, 0, 4)]
     for i, w in enumerate(cases):
         out, shapes, kernels = [], [], set()
         runs = [dict(autotune=False), dict(autotune=True)] + [dict(launch_shape=f) for f in fixed]
@@ -283,7 +286,8 @@ def test_launch_shapes_agree_bitwise(amy):
             # persistent horizon kernel all took part, and agree bitwise
             assert {3, 4, 5} <= kernels, kernels
         compare_synthesis(amy, w, "stored_separable", "fp32")
-    for bad in [(9, 0, 0, 0), (0, 48, 0, 0), (4, 256, 0, 0), (0, 544, 0, 0), (0, 0, 3, 0), (0, 0, 0, 100)]:
+    for bad in [(9, 0, 0, 0), (0, 48, 0, 0), (4, 256, 0, 0), (0, 544, 0, 0), (0, 0, 3, 0), (0, 0, 0, 100),
+                (0, 0, 0, 0, 9)]:
         with pytest.raises(amy.AmyError) as e:
             amy.amy_build(cases[0].problem, tmode="stored_separable", prec="fp32", launch_shape=bad)
         assert "INVALID_ARG" in str(e.value)
