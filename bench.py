@@ -40,24 +40,30 @@ METRIC = "Bellman transitions/s (x*u*x' window slots * horizon)"
 UNIT = "transitions/s"
 
 
-# DRAM traffic of the dominant kernel per launch, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum).  A figure holds only for the
-# kernel sources it was captured on, so each entry carries the digest of the
-# csrc/ tree at capture time and is reported as null once the sources change.
-# key: (workload, tmode, prec, v_store) -> (digest, bytes per launch, states in
+# DRAM traffic of the dominant kernel per backup, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of the launch, divided by the
+# backups that launch performed).  A figure holds only for the kernel sources
+# it was captured on, so each entry carries the digest of the csrc/ tree at
+# capture time and is reported as null once the sources change.
+# key: (workload, tmode, prec, v_store) -> (digest, bytes per backup, states in
 # the captured launch, profile summary).  A capture on a reduced grid is scaled
 # to the full launch by the number of states (the traffic is V in/out, pi and
 # the mask per state; the tables are a few hundred KB at most).
 MEASURED_TRAFFIC = {
+    # k_synth_runs<float,3,3,0>, launch shape 1,288,1,0,3: 704,512 B read + 71,680 B written
+    # per launch of 32 backups
+    ("unicycle", "stored_separable", "fp32", "native"):
+        ("8d188ebfc33ac261", 24256, 78030, "profiles/k_synth_runs_unicycle_51x51x30.md"),
 }
 
 
 def csrc_digest() -> str:
+    """Digest of the device code (the .cuh kernel and launch headers)."""
     import hashlib
     d = os.path.join(ROOT, "paper_2005_06191_gb300", "csrc")
     h = hashlib.sha256()
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if f.endswith(".cuh"):
             h.update(f.encode())
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
@@ -256,32 +262,53 @@ def run_amy(args, rank, world):
     # states whose value the spec fixes carry policy 0xFFFF and cost no backup work
     free = int((PI[0] != -1).sum().item())
     roof = roofline(args, w, info, bk_ms, free, lane_peaks)
+    roof["backups_per_launch"] = kt["backup_steps"] / max(kt["backup_launches"], 1)
+    roof["launch_ms"] = launch_ms
 
-    # end to end through the C ABI with host buffers: build (H2D of the
-    # problem), synthesize with host outputs (D2H of V_0 and every pi_k), destroy
-    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 5))
-    h2d = (np.asarray(p.params).nbytes + 8 * 4 * p.n + 8 * 2 * p.m + 4 * (p.n + p.m) + p.n + 8 * 2 * p.n)
+    # end to end through the C ABI with host buffers, per step: the system
+    # parameters from pinned host memory (amy_rebuild: H2D + table build),
+    # then amy_synthesize with host outputs (D2H of V_0 and every pi_k into
+    # pinned host memory).  The handle (its device buffers and launch shape)
+    # is set up once, as a caller solving a stream of problems of one shape
+    # would.  e2e_cold adds amy_build and amy_destroy to every step.
+    e2e_steps = 0 if args.no_e2e else max(3, min(args.steps, 50))
+    pin_params = torch.from_numpy(np.asarray(p.params, dtype=np.float64)).pin_memory().numpy()
+    h2d = pin_params.nbytes
     d2h = p.n_states * 4 + N * p.n_states * 2
-    Ve, e2e = None, None
+    Ve, e2e, e2e_cold = None, None, None
     if e2e_steps:
-        for _ in range(2):
-            with amy.amy_build(p, tmode=args.tmode, prec=args.prec, v_store=args.v_store) as he:
-                amy.amy_synthesize(he, spec, N, policy_all_steps=True)
+        Vh = torch.empty(p.n_states, dtype=torch.float64 if args.prec == "fp64" else torch.float32,
+                         pin_memory=True).numpy()
+        PIh = torch.empty((N, p.n_states), dtype=torch.int16, pin_memory=True).numpy()
+        for _ in range(3):
+            amy.amy_rebuild(h, pin_params)
+            amy.amy_synthesize(h, spec, N, V_out=Vh, policy_out=PIh, policy_all_steps=True)
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            with amy.amy_build(p, tmode=args.tmode, prec=args.prec, v_store=args.v_store) as he:
-                Ve, PIe = amy.amy_synthesize(he, spec, N, policy_all_steps=True)
+            amy.amy_rebuild(h, pin_params)
+            amy.amy_synthesize(h, spec, N, V_out=Vh, policy_out=PIh, policy_all_steps=True)
         e2e_s = barrier_max(time.perf_counter() - t0, world)
+        Ve = Vh.copy()
         e2e = {"value": trans * e2e_steps * world / e2e_s, "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "per_step": "amy_rebuild(params from pinned host memory) + amy_synthesize(host outputs, pinned)"}
+        cold_steps = max(1, min(e2e_steps, 5))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(cold_steps):
+            with amy.amy_build(p, tmode=args.tmode, prec=args.prec, v_store=args.v_store) as he:
+                amy.amy_synthesize(he, spec, N, V_out=Vh, policy_out=PIh, policy_all_steps=True)
+        cold_s = barrier_max(time.perf_counter() - t0, world)
+        e2e_cold = {"value": trans * cold_steps * world / cold_s, "unit": UNIT,
+                    "per_step": "amy_build + amy_synthesize(host outputs, pinned) + amy_destroy"}
     amy.amy_destroy(h)
     clocks = clk.summary()
     return {
         "value": value, "ms_per_step": ms_max / args.steps, "trans": trans, "info": info,
         "backup_ms": bk_ms, "build_ms": build_ms, "launches": launches, "roofline": roof,
-        "e2e": e2e,
+        "e2e": e2e, "e2e_cold": e2e_cold,
         "clocks": clocks, "V": V_host, "V_e2e": Ve,
         "synth_only_value": trans * args.steps * world / ((ms_max - build_ms * args.steps) / 1e3),
     }
@@ -294,13 +321,15 @@ def roofline(args, w, info, backup_ms, free, lane_peaks):
     algorithmic bytes = rows + V in/out + pi + mask.  With per-dimension
     tables or rows on the fly T stays out of HBM and V_{k+1} is L2-resident
     (or streamed once); the kernel is then bound by the rate at which lanes
-    receive V values: the shared-memory path for the staged kernels, the
-    L1 path of global loads for the register-resident ones.  Both ceilings
-    are measured on the device (amy_measure_lane_loads).  Algorithmic
-    lane-loads per launch: one per (free state, input, window slot) for the
-    gather kernels; for the per-run kernel, K x W^(n-1) per (free state,
-    input run) -- its outer contraction -- the inner rows then being
-    register arithmetic."""
+    receive their operands: the shared-memory path for the staged kernels,
+    the L1 path of global loads for the register-resident ones.  Both
+    ceilings are measured on the device (amy_measure_lane_loads).
+    Algorithmic lane-loads per backup: one V value per (free state, input,
+    window slot) for the gather kernels; for the per-run kernels, the outer
+    contraction's K x W^(n-1) V values per (free state, input run) plus the
+    W innermost-dim masses per (free state, input) that each input's sum
+    applies to it.  The persistent kernel performs all backups of the horizon
+    in one launch; the figures are per backup (the same ratio per launch)."""
     pk = peaks()
     p = w.problem
     nx, nu = p.n_states, p.n_inputs
@@ -319,8 +348,10 @@ def roofline(args, w, info, backup_ms, free, lane_peaks):
     gather = free * nu * slots
     if kern in (3, 4, 5):
         wm = max(info["window"])
-        loads = free * info["input_runs"] * info["inner_span"] * wm ** (info["n"] - 1)
-        path, what = "shared", "K x W^(n-1) shared-memory loads per (free state, input run)"
+        loads = (free * info["input_runs"] * info["inner_span"] * wm ** (info["n"] - 1)
+                 + free * nu * info["window"][-1])
+        path, what = ("shared", "K x W^(n-1) V values per (free state, input run) + the W innermost-dim "
+                      "masses per (free state, input), read from shared memory")
     elif kern == 2:
         loads, path, what = gather, "shared", "one shared-memory load per (free state, input, slot)"
     else:
@@ -330,7 +361,7 @@ def roofline(args, w, info, backup_ms, free, lane_peaks):
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G lane-loads/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_source": src,
             "peak_source": f"measured on this GPU by amy_measure_lane_loads ({path} path)",
-            "algorithmic_lane_loads_per_launch": int(loads), "algorithmic_unit": what,
+            "algorithmic_lane_loads_per_backup": int(loads), "algorithmic_unit": what,
             "backup_kernel": kern,
             "window_slot_rate_vs_gather_ceiling": (gather / (backup_ms / 1e3) / 1e9) / peak}
 
@@ -571,11 +602,13 @@ def main():
         "roofline": r["roofline"],
         "cpu_baseline": cpu,
         "e2e": r["e2e"],
+        "e2e_cold": r["e2e_cold"],
         "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],
         "backup_kernel_ms": r["backup_ms"], "build_kernel_ms": r["build_ms"],
         "synth_only_value": r["synth_only_value"],
         "max_abs_dV_vs_oracle": max_dv,
+        "e2e_V_equals_device_V": (None if r["V_e2e"] is None else bool(np.array_equal(r["V_e2e"], r["V"]))),
     }
     print(json.dumps(line), flush=True)
 

@@ -257,6 +257,16 @@ amy_status amy_rebuild(amy_handle h, const double *params, int64_t n_params);
  * AMY_E_TIMEOUT when a persistent synthesis since the previous check gave up
  * waiting at a grid barrier (its outputs are then invalid). */
 amy_status amy_set_profiling(amy_handle h, int32_t on);
+
+/* Polls a grid-barrier wait of the persistent horizon kernel (k_synth_runs,
+ * amy_info backup_kernel 5) makes before it gives up (default 2^20, about a
+ * tenth of a second; a barrier normally completes within microseconds).  A
+ * wait that gives up makes every block leave the kernel; the synthesis then
+ * returns AMY_E_TIMEOUT (host outputs) or the next call that waits on the
+ * handle's stream reports it, and its outputs are invalid.  The handle stays
+ * usable.  polls < 0 restores the default.  The paper has no counterpart:
+ * this bounds the device-wide wait the persistent kernel adds. */
+amy_status amy_set_wait_limit(amy_handle h, int32_t polls);
 amy_status amy_kernel_times(amy_handle h, double *backup_ms, int64_t *backup_launches, int64_t *backup_steps,
                             double *build_ms, int64_t *build_launches);
 

@@ -218,8 +218,9 @@ def amy_synthesize(h: AmyHandle, spec, horizon: int, V_out=None, policy_out=None
     """amy_synthesize: `horizon` backups; returns (V_0, policy).
 
     With torch CUDA tensors for V_out (and policy_out) the outputs stay on the
-    device (work enqueued on the handle's stream); otherwise numpy arrays are
-    returned."""
+    device (work enqueued on the handle's stream).  Otherwise the outputs are
+    host arrays: the given numpy arrays (e.g. views of pinned memory, which
+    the device writes at full copy speed) or new ones."""
     k = _Keep()
     s = _spec_struct(k, spec)
     nx = h.n_states
@@ -228,10 +229,21 @@ def amy_synthesize(h: AmyHandle, spec, horizon: int, V_out=None, policy_out=None
         pp = C.c_void_p(policy_out.data_ptr()) if policy_out is not None else C.c_void_p(0)
         _check(_lib().amy_synthesize(h.ptr, C.byref(s), int(horizon), vp, pp, int(bool(policy_all_steps)), 1))
         return V_out, policy_out
-    V = np.zeros(nx, dtype=h.out_dtype)
+    pshape = (horizon, nx) if policy_all_steps else (nx,)
+    if V_out is not None:
+        V = V_out
+        if not (isinstance(V, np.ndarray) and V.dtype == h.out_dtype and V.size == nx and V.flags.c_contiguous):
+            raise ValueError(f"V_out must be a contiguous {np.dtype(h.out_dtype)} array of {nx} values")
+    else:
+        V = np.zeros(nx, dtype=h.out_dtype)
     pi = None
-    if want_policy and horizon > 0:
-        pi = np.zeros((horizon, nx) if policy_all_steps else nx, dtype=np.uint16)
+    if policy_out is not None and horizon > 0:
+        pi = policy_out
+        if not (isinstance(pi, np.ndarray) and pi.dtype in (np.uint16, np.int16) and pi.size == int(np.prod(pshape))
+                and pi.flags.c_contiguous):
+            raise ValueError(f"policy_out must be a contiguous 16-bit array of shape {pshape}")
+    elif want_policy and horizon > 0:
+        pi = np.zeros(pshape, dtype=np.uint16)
     _check(_lib().amy_synthesize(h.ptr, C.byref(s), int(horizon), C.c_void_p(V.ctypes.data),
                                  C.c_void_p(pi.ctypes.data) if pi is not None else C.c_void_p(0),
                                  int(bool(policy_all_steps)), 0))
@@ -283,6 +295,12 @@ def amy_set_profiling(h: AmyHandle, on: bool = True) -> None:
     _check(_lib().amy_set_profiling(h.ptr, int(bool(on))))
 
 
+def amy_set_wait_limit(h: AmyHandle, polls: int = -1) -> None:
+    """amy_set_wait_limit: polls before a grid-barrier wait of the persistent
+    kernel gives up (AMY_E_TIMEOUT); -1 restores the default."""
+    _check(_lib().amy_set_wait_limit(h.ptr, int(polls)))
+
+
 def amy_kernel_times(h: AmyHandle) -> dict:
     """Summed CUDA-event durations (ms) and counts of backup / build kernels since
     the last call; backup_steps counts the backups those launches performed."""
@@ -328,7 +346,7 @@ from .serving import (AmyServer, amy_cancel, amy_poll, amy_result_free,  # noqa:
 __all__ = [
     "AmyError", "AmyHandle", "AmyServer", "amy_build", "amy_synthesize", "amy_backup_step",
     "amy_query_rows", "amy_info", "amy_destroy", "amy_grid_count", "amy_last_error",
-    "amy_rebuild", "amy_set_profiling", "amy_kernel_times", "amy_synthesize_noalloc", "amy_measure_lane_loads",
+    "amy_rebuild", "amy_set_profiling", "amy_set_wait_limit", "amy_kernel_times", "amy_synthesize_noalloc", "amy_measure_lane_loads",
     "amy_server_create", "amy_submit", "amy_poll", "amy_wait", "amy_cancel", "amy_server_stats",
     "amy_server_destroy", "amy_result_free", "TMODES", "PRECS", "VSTORES", "POLICY_NONE",
 ]

@@ -89,6 +89,7 @@ PROTOTYPES = {
     "amy_info": (C.c_int32, [C.c_void_p, C.POINTER(amy_info_t)]),
     "amy_rebuild": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64]),
     "amy_set_profiling": (C.c_int32, [C.c_void_p, C.c_int32]),
+    "amy_set_wait_limit": (C.c_int32, [C.c_void_p, C.c_int32]),
     "amy_kernel_times": (C.c_int32, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "amy_destroy": (None, [C.c_void_p]),

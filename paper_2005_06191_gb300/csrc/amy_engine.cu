@@ -794,11 +794,21 @@ amy_status autotune_shape(amy_handle_s *h) {
                 cudaGetLastError();
                 const int reps = persist ? 8 : 3;
                 cudaError_t e = cudaSuccess;
+                float ms_first = 3.4e38f;
                 if (persist) {
-                    e = cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream);
-                    if (e == cudaSuccess) e = cudaEventRecord(ea, h->stream);
-                    if (e == cudaSuccess)
-                        st = launch_synth_fast(h->g, tm_kind_of(h), h->v_store, c, sc, h->sm_count, h->stream, false);
+                    // the better of two launches (the first one also warms up)
+                    for (int t = 0; t < 2 && st == AMY_OK && e == cudaSuccess; ++t) {
+                        e = cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream);
+                        if (e == cudaSuccess) e = cudaEventRecord(ea, h->stream);
+                        if (e == cudaSuccess)
+                            st = launch_synth_fast(h->g, tm_kind_of(h), h->v_store, c, sc, h->sm_count, h->stream,
+                                                   false);
+                        if (t == 0 && st == AMY_OK && e == cudaSuccess) {
+                            e = cudaEventRecord(eb, h->stream);
+                            if (e == cudaSuccess) e = cudaEventSynchronize(eb);
+                            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_first, ea, eb);
+                        }
+                    }
                 } else {
                     st = launch_backup_fast(h->g, tm_kind_of(h), h->v_store, c, h->sm_count, h->stream);
                     if (st == AMY_OK) e = cudaEventRecord(ea, h->stream);
@@ -811,7 +821,7 @@ amy_status autotune_shape(amy_handle_s *h) {
                 if (st == AMY_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, ea, eb);
                 if (st == AMY_OK && e != cudaSuccess) st = cuda_error(e, "autotune timing");
                 if (st == AMY_OK && persist) st = check_synth_error(h);
-                ms /= (float)reps;
+                ms = std::min(ms, ms_first) / (float)reps;
                 if (st == AMY_OK && ms < best) {
                     best = ms;
                     best_ul = ul;
@@ -1079,6 +1089,13 @@ amy_status amy_rebuild(amy_handle h, const double *params, int64_t n_params) {
     return st;
 }
 
+amy_status amy_set_wait_limit(amy_handle h, int32_t polls) {
+    if (!h) return set_error(AMY_E_INVALID_ARG, "null handle");
+    h->spin_limit = polls < 0 ? (1 << 20) : polls;
+    h->graph_valid = false;
+    return AMY_OK;
+}
+
 amy_status amy_set_profiling(amy_handle h, int32_t on) {
     if (!h) return set_error(AMY_E_INVALID_ARG, "null handle");
     h->profiling = on != 0;
@@ -1250,12 +1267,18 @@ amy_status amy_synthesize(amy_handle h, const amy_spec *spec, int32_t horizon, v
         if (e == cudaSuccess && policy_out && horizon > 0)
             e = cudaMemcpyAsync(policy_out, d_pi, (size_t)nx * sizeof(uint16_t) * (policy_all_steps ? horizon : 1),
                                 cudaMemcpyDeviceToHost, h->stream);
+        // the persistent kernel's error flag rides on the same wait
+        int32_t err = 0;
+        const bool persist = h->synth_ok && horizon > 0 && h->d_bar;
+        if (e == cudaSuccess && persist)
+            e = cudaMemcpyAsync(&err, h->d_bar + 2, sizeof err, cudaMemcpyDeviceToHost, h->stream);
         cleanup();
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_error(e, "copy out");
-        if (h->synth_ok && horizon > 0) {
-            st = check_synth_error(h);
-            if (st != AMY_OK) return st;
+        if (err != 0) {
+            AMY_CUDA(cudaMemsetAsync(h->d_bar + 2, 0, sizeof(int32_t), h->stream), "barrier flag reset");
+            if (err == 1) return set_error(AMY_E_TIMEOUT, "persistent backup: a grid barrier wait gave up");
+            return set_error(AMY_E_CUDA, "persistent backup: launch shape rejected on the device");
         }
         if (policy_out && horizon == 0) {
             // no backup: no policy entries to report

@@ -208,6 +208,28 @@ __device__ __forceinline__ void run_contract(const Geom &g, const FastArgs<VT> &
     for (int k = 0; k < K; ++k) R[k] = acc[k];
 }
 
+// One input's window sum from its shifted inner weights at shared address pw
+// and the run's outer contraction R; keeps the max and the lowest maximiser.
+template <int K, int NP>
+__device__ __forceinline__ void input_sum(uint32_t pw, int32_t tt_planeb, const float (&R)[K], int32_t u, float &best,
+                                          int32_t &arg) {
+    float w[NP * 4];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const float4 e = lds_f4(pw + (uint32_t)(p * tt_planeb));
+        w[4 * p + 0] = e.x;
+        w[4 * p + 1] = e.y;
+        w[4 * p + 2] = e.z;
+        w[4 * p + 3] = e.w;
+    }
+    float sum = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) sum = fmaf(w[k], R[k], sum);
+    const bool gt = sum > best;
+    best = gt ? sum : best;
+    arg = gt ? u : arg;
+}
+
 // Window sums of one state for its runs rr = c, c + UL, ... (inputs
 // [rs[rr], rs[rr + 1])); max and lowest maximiser kept in (best, arg).  The
 // next run's outer records are loaded while the current run is summed.
@@ -236,27 +258,18 @@ __device__ __forceinline__ void runs_sums(const Geom &g, const FastArgs<VT> &a, 
         run_contract<VT, WM, NS, K, KAHAN, BOX>(g, a, cur, r0, sbase, offij, bs0b, bs1b, planeb, R);
         // each input's shifted inner weights: s_in[u] holds its record's byte
         // offset; within a run they advance by `stride` bytes when
-        // stride != INT_MIN, so only the run's first offset is looked up
-        uint32_t pw = ttL + (uint32_t)lds_i32(s_in + 4u * (uint32_t)u0);
+        // stride != INT_MIN (a uniform choice, made outside the loop)
+        if (stride != INT_MIN) {
+            uint32_t pw = ttL + (uint32_t)lds_i32(s_in + 4u * (uint32_t)u0);
 #pragma unroll 3
-        for (int32_t u = u0; u < u1; ++u) {
-            if (stride == INT_MIN) pw = ttL + (uint32_t)lds_i32(s_in + 4u * (uint32_t)u);
-            float w[NP * 4];
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const float4 e = lds_f4(pw + (uint32_t)(p * tt_planeb));
-                w[4 * p + 0] = e.x;
-                w[4 * p + 1] = e.y;
-                w[4 * p + 2] = e.z;
-                w[4 * p + 3] = e.w;
+            for (int32_t u = u0; u < u1; ++u) {
+                input_sum<K, NP>(pw, tt_planeb, R, u, best, arg);
+                pw += (uint32_t)stride;
             }
-            float sum = 0.0f;
-#pragma unroll
-            for (int k = 0; k < K; ++k) sum = fmaf(w[k], R[k], sum);
-            const bool gt = sum > best;
-            best = gt ? sum : best;
-            arg = gt ? u : arg;
-            pw += (uint32_t)stride;
+        } else {
+#pragma unroll 3
+            for (int32_t u = u0; u < u1; ++u)
+                input_sum<K, NP>(ttL + (uint32_t)lds_i32(s_in + 4u * (uint32_t)u), tt_planeb, R, u, best, arg);
         }
     }
 }

@@ -352,6 +352,26 @@ def test_graph_replay_matches_direct_launches(amy):
         assert np.array_equal(V.cpu().numpy(), V2h)
 
 
+def test_persistent_barrier_wait_is_bounded(amy):
+    """The persistent horizon kernel's grid-barrier waits have a poll limit:
+    with a limit of zero polls the blocks give up at the first barrier, leave
+    the kernel and the synthesis reports AMY_E_TIMEOUT (no fault, no hang);
+    with the default limit restored the same handle gives the same values and
+    policies as before."""
+    w = W.unicycle(nxy=31, horizon=6, target=(3.0, 5.0))
+    with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32", launch_shape=(4, 128, 1, 0)) as h:
+        assert amy.amy_info(h)["backup_kernel"] == 5
+        ref = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
+        amy.amy_set_wait_limit(h, 0)
+        with pytest.raises(amy.AmyError) as e:
+            amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
+        assert "TIMEOUT" in str(e.value)
+        amy.amy_set_wait_limit(h, -1)
+        again = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
+        assert np.array_equal(ref[0], again[0]) and np.array_equal(ref[1], again[1])
+    compare_synthesis(amy, w, "stored_separable", "fp32")
+
+
 def test_profiling_counts_kernels(amy):
     w = W.unicycle(nxy=21, horizon=5, target=(2.0, 3.0))
     with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32") as h:
