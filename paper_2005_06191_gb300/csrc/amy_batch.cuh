@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(FAST_THREADS) k_step_group(const BatchEntry *_
             s_tile = t;
             s_prob = p;
         }
+        __syncwarp();  // lane 0 searched alone: reconverge warp 0 before the block barrier
         __syncthreads();
         const int64_t t = s_tile;
         if (t >= total_tiles) break;

@@ -594,6 +594,7 @@ __global__ void __launch_bounds__(RUNS_MAX_THREADS) k_backup_runs(const __grid_c
     if (UL > 1) {
         cBest[tid] = best;
         cArg[tid] = arg;
+        __syncwarp();
         __syncthreads();
     }
     if (c == 0 && ok) {
@@ -651,6 +652,7 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
 // wait ends.
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *err, unsigned nblocks, int32_t spin_limit) {
     __shared__ int s_ok;
+    __syncwarp();
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
@@ -675,6 +677,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *err, unsign
         if (ok && ld_acquire_gpu(reinterpret_cast<const unsigned *>(err)) != 0) ok = 0;
         s_ok = ok;
     }
+    // lane 0 spun alone: reconverge warp 0 before the block barrier (an
+    // aligned barrier must be reached by whole warps)
+    __syncwarp();
     __syncthreads();
     return s_ok != 0;
 }
@@ -796,6 +801,7 @@ __global__ void __launch_bounds__(RUNS_MAX_THREADS) k_synth_runs(const __grid_co
             stage_box<VT, NS, 1, true>(g, Vn, sbox4, nrows, bn, blo, bs0, bs1, plane, dmin[L], Rn);
         else
             stage_box<VT, NS, 2, true>(g, Vn, sbox4, nrows, bn, blo, bs0, bs1, plane, dmin[L], Rn);
+        __syncwarp();
         __syncthreads();
         float best = -1.0f;
         int32_t arg = 0x7fffffff;
@@ -818,6 +824,7 @@ __global__ void __launch_bounds__(RUNS_MAX_THREADS) k_synth_runs(const __grid_co
         if (UL > 1) {
             cBest[tid] = best;
             cArg[tid] = arg;
+            __syncwarp();
             __syncthreads();
         }
         if (c == 0 && ok) {
