@@ -50,10 +50,10 @@ UNIT = "transitions/s"
 # to the full launch by the number of states (the traffic is V in/out, pi and
 # the mask per state; the tables are a few hundred KB at most).
 MEASURED_TRAFFIC = {
-    # k_synth_runs<float,3,3,0>, launch shape 1,288,1,0,3: 704,512 B read + 71,680 B written
-    # per launch of 32 backups
+    # k_synth_runs<float,3,3,0>, launch shape 1,288,1,0,3, grid barrier: 702,976 B read +
+    # 79,872 B written per launch of 32 backups
     ("unicycle", "stored_separable", "fp32", "native"):
-        ("8d188ebfc33ac261", 24256, 78030, "profiles/k_synth_runs_unicycle_51x51x30.md"),
+        ("7379c37ee62a5e17", 24464, 78030, "profiles/k_synth_runs_unicycle_51x51x30.md"),
 }
 
 
@@ -219,6 +219,8 @@ def run_amy(args, rank, world):
     shape = [int(v) for v in args.shape.split(",")] if args.shape else None
     h = amy.amy_build(p, tmode=args.tmode, prec=args.prec, v_store=args.v_store, autotune=shape is None,
                       launch_shape=shape)
+    if args.step_wait is not None:
+        amy.amy_set_step_wait(h, args.step_wait)
     info = amy.amy_info(h)
     trans = transitions_per_step(w, info["window_slots"])
     V = torch.empty(p.n_states, dtype=torch.float64 if args.prec == "fp64" else torch.float32, device="cuda")
@@ -547,6 +549,9 @@ def main():
     ap.add_argument("--prec", default=None, choices=["fp64", "fp32", "fp32_kahan"])
     ap.add_argument("--served-n", dest="served_n", type=int, default=256)
     ap.add_argument("--v-store", dest="v_store", default="native", choices=["native", "u16", "bf16"])
+    ap.add_argument("--step-wait", dest="step_wait", type=int, default=None, choices=[0, 1],
+                    help="persistent kernel between backups: 0 = neighbour tiles, 1 = grid barrier "
+                         "(default: the handle's choice, autotuned)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", dest="no_e2e", action="store_true",
                     help="skip the end-to-end (host buffer) measurement, e.g. under a profiler")
@@ -597,6 +602,8 @@ def main():
                                     "row_tiles": r["info"]["row_tiles"], "grouped_inputs": r["info"]["grouped_inputs"],
                                     "chosen_by": ("fixed: " + args.shape) if args.shape else
                                     "amy_build autotune (timed at build, outside the timed region)"},
+                   "step_wait": ("grid barrier" if r["info"]["step_wait"] else "neighbour tiles")
+                   if r["info"]["backup_kernel"] == 5 else None,
                    "l2": "flushed (256 MB write) between timed iterations",
                    "step": f"rebuild stored rows + spec mask + {w.horizon} fused backups (all pi_k written)"},
         "roofline": r["roofline"],

@@ -197,6 +197,9 @@ typedef struct {
     int32_t inner_span;         /* inner slots K one outer contraction covers (kernels 3, 4) */
     int32_t build_kernels;      /* kernels one table build (amy_build / amy_rebuild) launches */
     int32_t tile_outer_rows;    /* per-run kernels: values of dim 0 per row tile (3-D) */
+    int32_t step_wait;          /* persistent kernel (5): what a block waits for between
+                                   backups, 0 neighbour tiles, 1 every block
+                                   (amy_set_step_wait; picked by the autotuner) */
 } amy_info_t;
 
 /* Points per dim of [lb, ub] with step eta: floor((ub-lb)/eta + 1e-9) + 1
@@ -258,15 +261,27 @@ amy_status amy_rebuild(amy_handle h, const double *params, int64_t n_params);
  * waiting at a grid barrier (its outputs are then invalid). */
 amy_status amy_set_profiling(amy_handle h, int32_t on);
 
-/* Polls a grid-barrier wait of the persistent horizon kernel (k_synth_runs,
- * amy_info backup_kernel 5) makes before it gives up (default 2^20, about a
- * tenth of a second; a barrier normally completes within microseconds).  A
- * wait that gives up makes every block leave the kernel; the synthesis then
- * returns AMY_E_TIMEOUT (host outputs) or the next call that waits on the
- * handle's stream reports it, and its outputs are invalid.  The handle stays
- * usable.  polls < 0 restores the default.  The paper has no counterpart:
- * this bounds the device-wide wait the persistent kernel adds. */
+/* Polls a wait between backups of the persistent horizon kernel
+ * (k_synth_runs, amy_info backup_kernel 5) makes before it gives up (default
+ * 2^20, about a tenth of a second; a wait normally completes within
+ * microseconds); 0 makes every wait give up at once.  A wait that gives up
+ * makes every block leave the kernel; the synthesis then returns
+ * AMY_E_TIMEOUT (host outputs) or the next call that waits on the handle's
+ * stream reports it, and its outputs are invalid.  The handle stays usable.
+ * polls < 0 restores the default.  The paper has no counterpart: this bounds
+ * the device-wide wait the persistent kernel adds. */
 amy_status amy_set_wait_limit(amy_handle h, int32_t polls);
+
+/* What a block of the persistent horizon kernel waits for between backups
+ * (Algorithm 4's backup k reads all of V_{k+1}, but one block's window box
+ * reads only the V cells of nearby tiles): mode 0 = only the tiles its box
+ * reads and the tiles whose boxes read it, through per-tile backup counters;
+ * mode 1 = every block (a grid-wide barrier).  The default is mode 1, or the
+ * faster of the two when amy_build autotunes; this call overrides it.
+ * Values and policies are the same in both modes.  Other modes return
+ * AMY_E_INVALID_ARG.  The paper has no counterpart (it launches one backup
+ * after another). */
+amy_status amy_set_step_wait(amy_handle h, int32_t mode);
 amy_status amy_kernel_times(amy_handle h, double *backup_ms, int64_t *backup_launches, int64_t *backup_steps,
                             double *build_ms, int64_t *build_launches);
 

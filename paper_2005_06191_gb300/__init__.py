@@ -210,6 +210,7 @@ def amy_info(h: AmyHandle) -> dict:
         "grouped_inputs": int(info.grouped_inputs), "backup_kernel": int(info.backup_kernel),
         "input_runs": int(info.input_runs), "inner_span": int(info.inner_span),
         "build_kernels": int(info.build_kernels), "tile_outer_rows": int(info.tile_outer_rows),
+        "step_wait": int(info.step_wait),
     }
 
 
@@ -296,9 +297,16 @@ def amy_set_profiling(h: AmyHandle, on: bool = True) -> None:
 
 
 def amy_set_wait_limit(h: AmyHandle, polls: int = -1) -> None:
-    """amy_set_wait_limit: polls before a grid-barrier wait of the persistent
-    kernel gives up (AMY_E_TIMEOUT); -1 restores the default."""
+    """amy_set_wait_limit: polls before a wait between backups of the
+    persistent kernel gives up (AMY_E_TIMEOUT); 0 gives up at once; -1
+    restores the default."""
     _check(_lib().amy_set_wait_limit(h.ptr, int(polls)))
+
+
+def amy_set_step_wait(h: AmyHandle, mode: int = 0) -> None:
+    """amy_set_step_wait: 0 = the persistent kernel's blocks wait only for
+    their neighbour tiles between backups, 1 = for every block."""
+    _check(_lib().amy_set_step_wait(h.ptr, int(mode)))
 
 
 def amy_kernel_times(h: AmyHandle) -> dict:
@@ -346,7 +354,7 @@ from .serving import (AmyServer, amy_cancel, amy_poll, amy_result_free,  # noqa:
 __all__ = [
     "AmyError", "AmyHandle", "AmyServer", "amy_build", "amy_synthesize", "amy_backup_step",
     "amy_query_rows", "amy_info", "amy_destroy", "amy_grid_count", "amy_last_error",
-    "amy_rebuild", "amy_set_profiling", "amy_set_wait_limit", "amy_kernel_times", "amy_synthesize_noalloc", "amy_measure_lane_loads",
+    "amy_rebuild", "amy_set_profiling", "amy_set_wait_limit", "amy_set_step_wait", "amy_kernel_times", "amy_synthesize_noalloc", "amy_measure_lane_loads",
     "amy_server_create", "amy_submit", "amy_poll", "amy_wait", "amy_cancel", "amy_server_stats",
     "amy_server_destroy", "amy_result_free", "TMODES", "PRECS", "VSTORES", "POLICY_NONE",
 ]

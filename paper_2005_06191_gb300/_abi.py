@@ -56,7 +56,7 @@ class amy_info_t(C.Structure):
                 ("v_store", C.c_int32), ("input_lanes", C.c_int32), ("row_tiles", C.c_int32), ("block_states", C.c_int32),
                 ("grouped_inputs", C.c_int32), ("backup_kernel", C.c_int32), ("input_runs", C.c_int32),
                 ("inner_span", C.c_int32), ("build_kernels", C.c_int32),
-                ("tile_outer_rows", C.c_int32)]
+                ("tile_outer_rows", C.c_int32), ("step_wait", C.c_int32)]
 
 
 class amy_server_opts(C.Structure):
@@ -90,6 +90,7 @@ PROTOTYPES = {
     "amy_rebuild": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64]),
     "amy_set_profiling": (C.c_int32, [C.c_void_p, C.c_int32]),
     "amy_set_wait_limit": (C.c_int32, [C.c_void_p, C.c_int32]),
+    "amy_set_step_wait": (C.c_int32, [C.c_void_p, C.c_int32]),
     "amy_kernel_times": (C.c_int32, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "amy_destroy": (None, [C.c_void_p]),

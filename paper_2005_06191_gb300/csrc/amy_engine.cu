@@ -399,12 +399,14 @@ struct amy_handle_s {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_backup, ev_build;
     std::vector<int32_t> ev_backup_steps;  // backups performed by each timed backup launch
     // persistent horizon kernel: applies to this handle's problem and shape
-    // (checked after the shape is fixed), its grid barrier words (arrivals,
-    // generation, error flag) and the polls a barrier wait makes before it
-    // gives up
+    // (checked after the shape is fixed), its barrier block (kBarWords:
+    // grid-barrier words, per-tile backup counters, error flag), the polls a
+    // wait makes before it gives up, and whether blocks wait for every block
+    // (grid barrier) or only for their neighbour tiles between backups
     int synth_ok;
     unsigned *d_bar;
     int32_t spin_limit;
+    int32_t grid_barrier;
     amy_info_t info;
 };
 
@@ -529,10 +531,10 @@ amy_status launch_backup_generic(amy_handle_s *h, int spec_kind, const void *Vn,
 amy_status check_synth_error(amy_handle_s *h) {
     if (!h->d_bar) return AMY_OK;
     int32_t err = 0;
-    AMY_CUDA(cudaMemcpyAsync(&err, h->d_bar + 2, sizeof err, cudaMemcpyDeviceToHost, h->stream), "barrier flag read");
+    AMY_CUDA(cudaMemcpyAsync(&err, h->d_bar + kBarErrWord, sizeof err, cudaMemcpyDeviceToHost, h->stream), "barrier flag read");
     AMY_CUDA(cudaStreamSynchronize(h->stream), "barrier flag read");
     if (err == 0) return AMY_OK;
-    AMY_CUDA(cudaMemsetAsync(h->d_bar + 2, 0, sizeof(int32_t), h->stream), "barrier flag reset");
+    AMY_CUDA(cudaMemsetAsync(h->d_bar + kBarErrWord, 0, sizeof(int32_t), h->stream), "barrier flag reset");
     if (err == 1) return set_error(AMY_E_TIMEOUT, "persistent backup: a grid barrier wait gave up");
     return set_error(AMY_E_CUDA, "persistent backup: launch shape rejected on the device");
 }
@@ -611,7 +613,8 @@ SynthCall synth_call(amy_handle_s *h, int32_t horizon, void *d_Vout, uint16_t *d
     sc.all_steps = all_steps;
     sc.horizon = horizon;
     sc.bar = h->d_bar;
-    sc.err = reinterpret_cast<int32_t *>(h->d_bar + 2);
+    sc.err = reinterpret_cast<int32_t *>(h->d_bar + kBarErrWord);
+    sc.grid_barrier = h->grid_barrier;
     sc.spin_limit = h->spin_limit;
     return sc;
 }
@@ -771,7 +774,7 @@ amy_status autotune_shape(amy_handle_s *h) {
     }
     float best = 3.4e38f;
     int best_ul = h->ulanes, best_tx = h->tilex, best_rows = h->rows, best_box = h->box_floats,
-        best_outer = h->outer;
+        best_outer = h->outer, best_wait = h->grid_barrier;
     amy_status st = AMY_OK;
     for (const Cand &cd : cands) {
         if (st != AMY_OK) break;
@@ -793,42 +796,49 @@ amy_status autotune_shape(amy_handle_s *h) {
                     launch_synth_fast(h->g, tm_kind_of(h), h->v_store, c, sc, h->sm_count, h->stream, true) == AMY_OK;
                 cudaGetLastError();
                 const int reps = persist ? 8 : 3;
-                cudaError_t e = cudaSuccess;
-                float ms_first = 3.4e38f;
-                if (persist) {
-                    // the better of two launches (the first one also warms up)
-                    for (int t = 0; t < 2 && st == AMY_OK && e == cudaSuccess; ++t) {
-                        e = cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream);
-                        if (e == cudaSuccess) e = cudaEventRecord(ea, h->stream);
-                        if (e == cudaSuccess)
-                            st = launch_synth_fast(h->g, tm_kind_of(h), h->v_store, c, sc, h->sm_count, h->stream,
-                                                   false);
-                        if (t == 0 && st == AMY_OK && e == cudaSuccess) {
-                            e = cudaEventRecord(eb, h->stream);
-                            if (e == cudaSuccess) e = cudaEventSynchronize(eb);
-                            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_first, ea, eb);
+                // the persistent kernel is timed with either wait between
+                // backups (grid barrier first)
+                for (int wait = 1; wait >= (persist ? 0 : 1) && st == AMY_OK; --wait) {
+                    h->grid_barrier = wait;
+                    const SynthCall scw = synth_call(h, 8, nullptr, nullptr, 0);
+                    cudaError_t e = cudaSuccess;
+                    float ms_first = 3.4e38f;
+                    if (persist) {
+                        // the better of two launches (the first one also warms up)
+                        for (int t = 0; t < 2 && st == AMY_OK && e == cudaSuccess; ++t) {
+                            e = cudaMemsetAsync(h->d_bar, 0, kBarResetBytes, h->stream);
+                            if (e == cudaSuccess) e = cudaEventRecord(ea, h->stream);
+                            if (e == cudaSuccess)
+                                st = launch_synth_fast(h->g, tm_kind_of(h), h->v_store, c, scw, h->sm_count, h->stream,
+                                                       false);
+                            if (t == 0 && st == AMY_OK && e == cudaSuccess) {
+                                e = cudaEventRecord(eb, h->stream);
+                                if (e == cudaSuccess) e = cudaEventSynchronize(eb);
+                                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_first, ea, eb);
+                            }
                         }
-                    }
-                } else {
-                    st = launch_backup_fast(h->g, tm_kind_of(h), h->v_store, c, h->sm_count, h->stream);
-                    if (st == AMY_OK) e = cudaEventRecord(ea, h->stream);
-                    for (int rep = 0; rep < reps && st == AMY_OK && e == cudaSuccess; ++rep)
+                    } else {
                         st = launch_backup_fast(h->g, tm_kind_of(h), h->v_store, c, h->sm_count, h->stream);
-                }
-                if (st == AMY_OK && e == cudaSuccess) e = cudaEventRecord(eb, h->stream);
-                if (st == AMY_OK && e == cudaSuccess) e = cudaEventSynchronize(eb);
-                float ms = 0.0f;
-                if (st == AMY_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, ea, eb);
-                if (st == AMY_OK && e != cudaSuccess) st = cuda_error(e, "autotune timing");
-                if (st == AMY_OK && persist) st = check_synth_error(h);
-                ms = std::min(ms, ms_first) / (float)reps;
-                if (st == AMY_OK && ms < best) {
-                    best = ms;
-                    best_ul = ul;
-                    best_tx = c.tilex;
-                    best_rows = rows;
-                    best_box = c.box_floats;
-                    best_outer = c.outer;
+                        if (st == AMY_OK) e = cudaEventRecord(ea, h->stream);
+                        for (int rep = 0; rep < reps && st == AMY_OK && e == cudaSuccess; ++rep)
+                            st = launch_backup_fast(h->g, tm_kind_of(h), h->v_store, c, h->sm_count, h->stream);
+                    }
+                    if (st == AMY_OK && e == cudaSuccess) e = cudaEventRecord(eb, h->stream);
+                    if (st == AMY_OK && e == cudaSuccess) e = cudaEventSynchronize(eb);
+                    float ms = 0.0f;
+                    if (st == AMY_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, ea, eb);
+                    if (st == AMY_OK && e != cudaSuccess) st = cuda_error(e, "autotune timing");
+                    if (st == AMY_OK && persist) st = check_synth_error(h);
+                    ms = std::min(ms, ms_first) / (float)reps;
+                    if (st == AMY_OK && ms < best) {
+                        best = ms;
+                        best_ul = ul;
+                        best_tx = c.tilex;
+                        best_rows = rows;
+                        best_box = c.box_floats;
+                        best_outer = c.outer;
+                        best_wait = wait;
+                    }
                 }
             }
         }
@@ -841,6 +851,7 @@ amy_status autotune_shape(amy_handle_s *h) {
     h->rows = best_rows;
     h->box_floats = best_box;
     h->outer = best_outer;
+    h->grid_barrier = best_wait;
     return AMY_OK;
 }
 
@@ -981,10 +992,11 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     }
     TRY(read_bounds(h));
     h->spin_limit = 1 << 20;
+    h->grid_barrier = 1;
     h->synth_ok = 0;
     if (fast_path(h) && h->tmode == AMY_T_STORED_SEPARABLE && h->grouped) {
-        TRY(dev_alloc(h, (void **)&h->d_bar, 4 * sizeof(unsigned), "barrier words"));
-        e = cudaMemsetAsync(h->d_bar, 0, 4 * sizeof(unsigned), h->stream);
+        TRY(dev_alloc(h, (void **)&h->d_bar, kBarWords * sizeof(unsigned), "barrier words"));
+        e = cudaMemsetAsync(h->d_bar, 0, kBarWords * sizeof(unsigned), h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) {
             free_handle(h);
@@ -1025,6 +1037,7 @@ amy_status amy_info(amy_handle h, amy_info_t *out) {
     if (!h || !out) return set_error(AMY_E_INVALID_ARG, "null argument");
     *out = h->info;
     out->device_bytes = h->bytes;
+    out->step_wait = h->grid_barrier;
     out->backup_kernel = 0;
     out->inner_span = 0;
     if (fast_path(h)) {
@@ -1096,6 +1109,14 @@ amy_status amy_set_wait_limit(amy_handle h, int32_t polls) {
     return AMY_OK;
 }
 
+amy_status amy_set_step_wait(amy_handle h, int32_t mode) {
+    if (!h) return set_error(AMY_E_INVALID_ARG, "null handle");
+    if (mode != 0 && mode != 1) return set_error(AMY_E_INVALID_ARG, "step wait mode %d (0 or 1)", (int)mode);
+    h->grid_barrier = mode;
+    h->graph_valid = false;
+    return AMY_OK;
+}
+
 amy_status amy_set_profiling(amy_handle h, int32_t on) {
     if (!h) return set_error(AMY_E_INVALID_ARG, "null handle");
     h->profiling = on != 0;
@@ -1146,7 +1167,7 @@ amy_status enqueue_synthesis(amy_handle_s *h, const SpecDev &s, int32_t horizon,
     if (st != AMY_OK) return st;
     if (h->synth_ok && horizon > 0) {
         // the whole horizon in one persistent launch
-        AMY_CUDA(cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream), "barrier reset");
+        AMY_CUDA(cudaMemsetAsync(h->d_bar, 0, kBarResetBytes, h->stream), "barrier reset");
         const FastCall c = fast_call(h, s.kind, h->d_V[0], h->d_V[1], nullptr, nullptr);
         const SynthCall sc = synth_call(h, horizon, d_Vout, d_pi, all_steps);
         KernelTimer tm(h, &h->ev_backup, horizon);
@@ -1271,12 +1292,12 @@ amy_status amy_synthesize(amy_handle h, const amy_spec *spec, int32_t horizon, v
         int32_t err = 0;
         const bool persist = h->synth_ok && horizon > 0 && h->d_bar;
         if (e == cudaSuccess && persist)
-            e = cudaMemcpyAsync(&err, h->d_bar + 2, sizeof err, cudaMemcpyDeviceToHost, h->stream);
+            e = cudaMemcpyAsync(&err, h->d_bar + kBarErrWord, sizeof err, cudaMemcpyDeviceToHost, h->stream);
         cleanup();
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_error(e, "copy out");
         if (err != 0) {
-            AMY_CUDA(cudaMemsetAsync(h->d_bar + 2, 0, sizeof(int32_t), h->stream), "barrier flag reset");
+            AMY_CUDA(cudaMemsetAsync(h->d_bar + kBarErrWord, 0, sizeof(int32_t), h->stream), "barrier flag reset");
             if (err == 1) return set_error(AMY_E_TIMEOUT, "persistent backup: a grid barrier wait gave up");
             return set_error(AMY_E_CUDA, "persistent backup: launch shape rejected on the device");
         }

@@ -125,6 +125,26 @@ void fill_runs_args(const Geom &g, const FastCall &c, int ul, int tx, int rowtil
 
 // grid of the per-run kernels: (row tiles of dim n-2, dim 0) for 3-D problems,
 // row tiles of dim 0 for 2-D
+// Neighbour radius (in tiles) of the persistent kernel's wait along one grid
+// extent of G tiles of S points of a dim with N points.  The box of the tile
+// [t, t + S) spans the cells [t + lo, t + S - 1 + hi + wm - 1] (lo, hi: the
+// bounds of origin minus own coordinate), so the tiles it reads lie within
+// max(ceil(-lo / S), ceil((hi + wm - 1) / S)) of it, and by the same bound
+// every tile that reads it lies within that radius too.  A periodic dim wraps
+// by whole tiles when S divides N (sets `bit` in wrap); otherwise it waits for
+// the whole extent.
+inline int nbr_radius(int lo, int hi, int wm, int S, int N, int G, bool periodic, uint32_t &wrap, uint32_t bit) {
+    const int below = std::max(0, -lo), above = std::max(0, hi + wm - 1);
+    int r = std::max((below + S - 1) / S, (above + S - 1) / S);
+    if (periodic) {
+        if (N % S == 0)
+            wrap |= bit;
+        else
+            r = G;
+    }
+    return std::min(r, G);
+}
+
 inline dim3 runs_grid(const Geom &g, int rowtile, int outer) {
     return g.n == 3 ? dim3((unsigned)((g.N[1] + rowtile - 1) / rowtile), (unsigned)((g.N[0] + outer - 1) / outer))
                     : dim3((unsigned)((g.N[0] + rowtile - 1) / rowtile));
@@ -199,6 +219,20 @@ amy_status launch_synth_k(const Geom &g, const FastCall &c, const SynthCall &sc,
     hz.bar = sc.bar;
     hz.err = sc.err;
     hz.spin_limit = sc.spin_limit;
+    hz.flags = nullptr;
+    hz.nr_y = hz.nr_x = 0;
+    hz.wrap = 0;
+    if (!sc.grid_barrier && (int64_t)grid.x * grid.y <= kBarTiles) {
+        // neighbour radius per grid extent: blockIdx.x tiles dim n-2 by
+        // rowtile points, blockIdx.y (3-D) tiles dim 0 by outer points
+        const int dx = g.n - 2;
+        hz.nr_x = nbr_radius(c.bnd_lo[dx], c.bnd_hi[dx], WM, rowtile, g.N[dx], (int)grid.x,
+                             (g.periodic >> dx) & 1u, hz.wrap, 2u);
+        if (NS == 3)
+            hz.nr_y = nbr_radius(c.bnd_lo[0], c.bnd_hi[0], WM, outer, g.N[0], (int)grid.y, g.periodic & 1u,
+                                 hz.wrap, 1u);
+        hz.flags = sc.bar + 2;
+    }
     Geom gg = g;
     void *args[] = {(void *)&gg, (void *)&a, (void *)&hz};
     e = cudaLaunchCooperativeKernel((const void *)kern, grid, dim3((unsigned)threads), args, smem, st);

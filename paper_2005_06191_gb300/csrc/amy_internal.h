@@ -157,8 +157,14 @@ amy_status launch_backup_fast(const Geom &g, int tmode, int v_store, const FastC
                               cudaStream_t st);
 // The whole horizon in one cooperative launch of the per-run kernel
 // (k_synth_runs): V0 holds V_N, V1 is the other resident vector; policies and
-// the FP32 copy of V_0 as in the per-step path.  bar (two words, zeroed by the
-// caller before each launch) is the grid barrier, *err its error flag.
+// the FP32 copy of V_0 as in the per-step path.  bar is the handle's barrier
+// block (kBarWords words): the grid barrier's arrival count and generation,
+// one backup counter per tile for the neighbour wait, then the error flag
+// *err.  The caller zeroes its first kBarResetBytes before each launch.
+constexpr int kBarTiles = 4096;
+constexpr int kBarErrWord = 2 + kBarTiles;
+constexpr int kBarWords = kBarErrWord + 2;
+constexpr size_t kBarResetBytes = (size_t)kBarErrWord * sizeof(unsigned);
 struct SynthCall {
     const void *V0;
     void *V1;
@@ -169,6 +175,7 @@ struct SynthCall {
     unsigned *bar;
     int32_t *err;
     int32_t spin_limit;
+    int32_t grid_barrier;  // 1: wait for every block between backups (no neighbour wait)
 };
 // Launches it, or with dry_run only checks that it applies to this problem and
 // launch shape and that every block can be resident at once.  Returns

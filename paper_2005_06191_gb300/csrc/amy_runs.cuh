@@ -282,6 +282,19 @@ __device__ __forceinline__ void runs_sums(const Geom &g, const FastArgs<VT> &a, 
 // inner cell dmin + p + k, wrapped when periodic, zero beyond a bounded edge
 // (those slots carry zero mass).  Source offsets and copy sizes are set once
 // per lane; a row off the grid is written as zeros.
+// Inner cell c of a box row: wrapped into [0, Rn) when the dim is periodic,
+// else flagged off (ok = false: its slots carry zero mass and hold 0).
+__device__ __forceinline__ void inner_cell(int32_t &c, bool &ok, int32_t Rn, bool periodic) {
+    if ((uint32_t)c < (uint32_t)Rn) return;
+    if (periodic) {
+        c %= Rn;
+        c = c < 0 ? c + Rn : c;
+    } else {
+        ok = false;
+        c = 0;
+    }
+}
+
 template <class VT, int NS, int NP, bool L2ONLY>
 __device__ __forceinline__ void stage_box(const Geom &g, const VT *Vn, float4 *sbox4, int32_t nrows,
                                           const int32_t (&bn)[2], const int32_t (&blo)[2], int32_t bs0, int32_t bs1,
@@ -338,6 +351,57 @@ __device__ __forceinline__ void stage_box(const Geom &g, const VT *Vn, float4 *s
                 srcb[k] = okc ? cc : 0;
                 nb[k] = okc ? 4u : 0u;
             }
+            if constexpr (L2ONLY) {
+                // Loads that bypass L1 (V was written by other SMs since this
+                // SM last read it).  Slot k of entry p is inner cell
+                // dminL + p + k, so a row needs only the cells dminL + p0 + 0
+                // ... + 31 + NC - 1: lane l loads cells l and 32 + l (l < NC - 1)
+                // of that range, and slot k of lane l's entry is taken by a
+                // shuffle from lane (l + k) mod 32, which offers its first
+                // cell when l + k < 32, i.e. when its own lane index is >= k,
+                // else its second.  RB rows at a time: their loads are all
+                // issued before the first store, sharing one L2 round trip.
+                int32_t ca = dminL + p0 + lane, cb = ca + 32;
+                bool oka = true, okb = lane < NC - 1;
+                inner_cell(ca, oka, Rn, per_in);
+                inner_cell(cb, okb, Rn, per_in);
+                constexpr int RB = 4;
+                for (int32_t j0 = 0; j0 < cnt; j0 += RB) {
+                    int32_t lin[RB], sidx[RB];
+                    float va[RB], vb[RB];
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) {
+                        const int32_t jj = min(j0 + r, cnt - 1);
+                        lin[r] = __shfl_sync(0xffffffffu, mlin, jj);
+                        sidx[r] = __shfl_sync(0xffffffffu, msidx, jj);
+                        if (j0 + r >= cnt) lin[r] = -1;
+                    }
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) {
+                        va[r] = (lin[r] >= 0 && oka) ? ld_cg(Vn + lin[r] + ca) : 0.0f;
+                        vb[r] = (lin[r] >= 0 && okb) ? ld_cg(Vn + lin[r] + cb) : 0.0f;
+                    }
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) {
+                        if (j0 + r < cnt) {
+                            float v[NC];
+#pragma unroll
+                            for (int k = 0; k < NC; ++k)
+                                v[k] = __shfl_sync(0xffffffffu, lane >= k ? va[r] : vb[r], (lane + k) & 31);
+                            if (p < Rn) {
+                                const uint32_t dst = sb + 16u * (uint32_t)(sidx[r] + p);
+#pragma unroll
+                                for (int q = 0; q < NP; ++q)
+                                    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(
+                                                     dst + 16u * (uint32_t)(q * plane)),
+                                                 "f"(v[4 * q]), "f"(v[4 * q + 1]), "f"(v[4 * q + 2]), "f"(v[4 * q + 3])
+                                                 : "memory");
+                            }
+                        }
+                    }
+                }
+                continue;
+            }
             for (int32_t j = 0; j < cnt; ++j) {
                 const int32_t lin = __shfl_sync(0xffffffffu, mlin, j);
                 const int32_t sidx = __shfl_sync(0xffffffffu, msidx, j);
@@ -349,20 +413,6 @@ __device__ __forceinline__ void stage_box(const Geom &g, const VT *Vn, float4 *s
                             asm volatile("st.shared.v4.f32 [%0], {%1, %1, %1, %1};\n" ::"r"(dst + 16u * (uint32_t)(q * plane)),
                                          "f"(0.0f)
                                          : "memory");
-                    } else if constexpr (L2ONLY) {
-                        // loads that bypass L1: V was written by other SMs since
-                        // this SM last read it
-                        const VT *row = Vn + lin;
-#pragma unroll
-                        for (int q = 0; q < NP; ++q) {
-                            float v[4];
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) v[k] = nb[4 * q + k] ? ld_cg(row + srcb[4 * q + k]) : 0.0f;
-                            asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(
-                                             dst + 16u * (uint32_t)(q * plane)),
-                                         "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
-                                         : "memory");
-                        }
                     } else if constexpr (std::is_same<VT, float>::value) {
                         const float *row = Vn + lin;
 #pragma unroll
@@ -622,10 +672,12 @@ __global__ void __launch_bounds__(RUNS_MAX_THREADS) k_backup_runs(const __grid_c
 // ---------------------------------------------------------------------------
 // The whole horizon in one launch (Algorithm 4's N backups): every block owns
 // one row tile for all steps, stages its tables, run starts and per-state
-// data once, and per step stages only its window box from V_{k+1}; steps are
-// separated by a grid-wide barrier.  All blocks must be resident at once (a
-// cooperative launch checks this).  Values and policies are those of N
-// launches of k_backup_runs with the same shape.
+// data once, and per step stages only its window box from V_{k+1}.  Between
+// backups a block waits only for the tiles its box reads and the tiles whose
+// boxes read it (a neighbour wait on per-tile backup counters), or, when the
+// host asks for it, for every block (grid barrier).  All blocks must be
+// resident at once (a cooperative launch checks this).  Values and policies
+// are those of N launches of k_backup_runs with the same shape.
 // ---------------------------------------------------------------------------
 struct RunsHorizon {
     const void *V0;      // V_N (read by the first backup)
@@ -635,14 +687,93 @@ struct RunsHorizon {
     int32_t all_steps;
     int32_t horizon;
     unsigned *bar;       // grid barrier: arrivals, generation (zero at launch)
-    int32_t *err;        // set to 1 when a barrier wait gives up, 2 on a bad launch shape
-    int32_t spin_limit;  // polls before a barrier wait gives up
+    unsigned *flags;     // per-tile backup counters (zero at launch), or null: grid barrier
+    int32_t *err;        // set to 1 when a wait gives up, 2 on a bad launch shape
+    int32_t spin_limit;  // polls before a wait gives up (0: every wait gives up at once)
+    // neighbour radius in tiles along blockIdx.y and blockIdx.x (a radius
+    // with 2r + 1 >= the grid's extent means the whole extent), and bit 0 / 1:
+    // that extent wraps (a periodic dim whose points fill whole tiles)
+    int32_t nr_y, nr_x;
+    uint32_t wrap;
 };
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;\n" : : "l"(p), "r"(v) : "memory");
+}
+
+// Tile index along one grid extent for neighbour i of 2r + 1 (or of the
+// whole extent), or -1 when that neighbour lies off a non-wrapping edge.
+__device__ __forceinline__ int nbr_tile(int self, int i, int r, int G, bool wrap) {
+    if (2 * r + 1 >= G) return i;
+    int t = self - r + i;
+    if (wrap) {
+        t = t < 0 ? t + G : (t >= G ? t - G : t);
+    } else if (t < 0 || t >= G) {
+        return -1;
+    }
+    return t;
+}
+
+// Neighbour wait after backup number `done` (1-based) of this launch: the
+// block publishes its counter (after all of its V and policy writes), then
+// the lanes of warp 0 poll the counters of the neighbour tiles until each
+// reaches `done`.  The neighbours are the tiles within the host's radius: they
+// include every tile whose V cells this block's next box reads (read after
+// write) and every tile whose box reads this block's cells (their reads of
+// the buffer this block overwrites next must be over: write after read).
+// Each poll loop stops after spin_limit polls, or sooner once another block
+// reported an error; a block that gives up sets the error flag.  Returns
+// false when the kernel has to stop.
+__device__ __forceinline__ bool neighbour_wait(const RunsHorizon &hz, unsigned done) {
+    __shared__ int s_ok;
+    __syncwarp();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const int Gx = (int)gridDim.x, Gy = (int)gridDim.y;
+        const int bx = (int)blockIdx.x, by = (int)blockIdx.y;
+        if (lane == 0) {
+            __threadfence();  // the block's V and policy writes before its counter
+            st_release_gpu(hz.flags + by * Gx + bx, done);
+        }
+        __syncwarp();
+        const int cy = min(2 * hz.nr_y + 1, Gy), cx = min(2 * hz.nr_x + 1, Gx);
+        int ok = hz.spin_limit > 0;
+        for (int i = lane; ok && i < cy * cx; i += 32) {
+            const int iy = i / cx, ix = i - iy * cx;
+            const int ty = nbr_tile(by, iy, hz.nr_y, Gy, hz.wrap & 1u);
+            const int tx = nbr_tile(bx, ix, hz.nr_x, Gx, hz.wrap & 2u);
+            if (ty < 0 || tx < 0 || (ty == by && tx == bx)) continue;
+            const unsigned *fl = hz.flags + ty * Gx + tx;
+            int32_t it = 0;
+            while (ld_acquire_gpu(fl) < done) {
+                if (++it > hz.spin_limit ||
+                    ((it & 31) == 0 && ld_acquire_gpu(reinterpret_cast<const unsigned *>(hz.err)) != 0)) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (lane == 0) {
+            if (!ok)
+                atomicExch(hz.err, 1);
+            else if (ld_acquire_gpu(reinterpret_cast<const unsigned *>(hz.err)) != 0)
+                ok = 0;
+            s_ok = ok;
+        }
+    }
+    // warp 0 polled alone: reconverge it before the block barrier
+    __syncwarp();
+    __syncthreads();
+    return s_ok != 0;
 }
 
 // Grid-wide barrier: the last block to arrive resets the arrival count and
@@ -667,14 +798,18 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *err, unsign
             int32_t it = 0;
             while (ld_acquire_gpu(bar + 1) == gen) {
                 if (++it > spin_limit) {
-                    atomicExch(err, 1);
                     ok = 0;
                     break;
                 }
                 __nanosleep(64);
             }
         }
-        if (ok && ld_acquire_gpu(reinterpret_cast<const unsigned *>(err)) != 0) ok = 0;
+        // a limit of zero: every wait gives up at once
+        if (spin_limit <= 0) ok = 0;
+        if (!ok)
+            atomicExch(err, 1);
+        else if (ld_acquire_gpu(reinterpret_cast<const unsigned *>(err)) != 0)
+            ok = 0;
         s_ok = ok;
     }
     // lane 0 spun alone: reconverge warp 0 before the block barrier (an
@@ -847,7 +982,11 @@ __global__ void __launch_bounds__(RUNS_MAX_THREADS) k_synth_runs(const __grid_co
             if (k == 0 && hz.Vfinal) hz.Vfinal[x] = best;
             if (hz.pi && (hz.all_steps || k == 0)) hz.pi[(hz.all_steps ? (int64_t)k * nx : 0) + x] = pol;
         }
-        if (j + 1 < hz.horizon && !grid_barrier(hz.bar, hz.err, nblocks, hz.spin_limit)) return;
+        if (j + 1 < hz.horizon) {
+            const bool go = hz.flags ? neighbour_wait(hz, (unsigned)(j + 1))
+                                     : grid_barrier(hz.bar, hz.err, nblocks, hz.spin_limit);
+            if (!go) return;
+        }
         const VT *t = Vn;
         Vn = Vo;
         Vo = const_cast<VT *>(t);

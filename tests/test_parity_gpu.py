@@ -352,15 +352,17 @@ def test_graph_replay_matches_direct_launches(amy):
         assert np.array_equal(V.cpu().numpy(), V2h)
 
 
-def test_persistent_barrier_wait_is_bounded(amy):
-    """The persistent horizon kernel's grid-barrier waits have a poll limit:
-    with a limit of zero polls the blocks give up at the first barrier, leave
-    the kernel and the synthesis reports AMY_E_TIMEOUT (no fault, no hang);
-    with the default limit restored the same handle gives the same values and
-    policies as before."""
+@pytest.mark.parametrize("step_wait", [0, 1])
+def test_persistent_barrier_wait_is_bounded(amy, step_wait):
+    """The persistent horizon kernel's waits between backups (neighbour tiles,
+    or the grid barrier) have a poll limit: with a limit of zero every wait
+    gives up at once, the blocks leave the kernel and the synthesis reports
+    AMY_E_TIMEOUT (no fault, no hang); with the default limit restored the
+    same handle gives the same values and policies as before."""
     w = W.unicycle(nxy=31, horizon=6, target=(3.0, 5.0))
     with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32", launch_shape=(4, 128, 1, 0)) as h:
         assert amy.amy_info(h)["backup_kernel"] == 5
+        amy.amy_set_step_wait(h, step_wait)
         ref = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
         amy.amy_set_wait_limit(h, 0)
         with pytest.raises(amy.AmyError) as e:
@@ -369,7 +371,51 @@ def test_persistent_barrier_wait_is_bounded(amy):
         amy.amy_set_wait_limit(h, -1)
         again = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
         assert np.array_equal(ref[0], again[0]) and np.array_equal(ref[1], again[1])
+        with pytest.raises(amy.AmyError) as e:
+            amy.amy_set_step_wait(h, 2)
+        assert "INVALID_ARG" in str(e.value)
     compare_synthesis(amy, w, "stored_separable", "fp32")
+
+
+def _periodic_x(w, nxy):
+    """The unicycle with its x coordinate periodic as well (a wrapping tile
+    extent for the persistent kernel's neighbour wait)."""
+    import dataclasses
+    p = dataclasses.replace(w.problem, x_periodic=[1, 0, 1], name=f"unicycle_px{nxy}")
+    return W.with_sizes(w, problem=p)
+
+
+def test_persistent_step_waits_agree(amy):
+    """Waiting between backups only for the neighbour tiles (the tiles a
+    block's window box reads, and those whose boxes read it) gives the same
+    values and policies, bit for bit, as the grid-wide barrier: on plain
+    tiles, on tiles that wrap around a periodic dim in whole tiles (27 x
+    values in tiles of 3), on a periodic dim the tiles do not divide (28 x
+    values: the whole extent is waited for), and with one x value per tile.
+    Both agree with the oracle."""
+    cases = [
+        (W.unicycle(nxy=31, horizon=7, target=(3.0, 5.0)), (1, 288, 1, 0, 3)),
+        (_periodic_x(W.unicycle(nxy=27, horizon=7, target=(3.0, 5.0)), 27), (1, 288, 1, 0, 3)),
+        (_periodic_x(W.unicycle(nxy=28, horizon=7, target=(3.0, 5.0)), 28), (1, 288, 1, 0, 3)),
+        (_periodic_x(W.unicycle(nxy=27, horizon=7, target=(3.0, 5.0)), 27), (2, 96, 1, 0, 1)),
+    ]
+    for w, shape in cases:
+        out = []
+        with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32", launch_shape=shape) as h:
+            assert amy.amy_info(h)["backup_kernel"] == 5, w.problem.name
+            assert amy.amy_info(h)["step_wait"] == 1   # the default without autotuning
+            for mode in (0, 1, 0):
+                amy.amy_set_step_wait(h, mode)
+                assert amy.amy_info(h)["step_wait"] == mode
+                out.append(amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True))
+        for k in (1, 2):
+            assert np.array_equal(out[0][0], out[k][0]), (w.problem.name, shape, k)
+            assert np.array_equal(out[0][1], out[k][1]), (w.problem.name, shape, k)
+        ref = oracle.synthesize(w.problem, w.spec, w.horizon, want_all=True)
+        dV = float(np.max(np.abs(out[0][0].astype(np.float64) - ref["V"])))
+        assert dV <= TOL["fp32"], (w.problem.name, dV)
+        sure = ref["gap"] > GAP["fp32"]
+        assert not ((out[0][1] != ref["pi"]) & sure).any(), w.problem.name
 
 
 def test_profiling_counts_kernels(amy):
