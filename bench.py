@@ -379,17 +379,27 @@ def time_oracle(w, horizon: int):
     return time.perf_counter() - t0, r
 
 
-def time_oracle_sample(w, n_states: int, seed: int = W.SEED):
+def time_oracle_sample(w, n_states: int, seed: int = W.SEED, nthreads: int = 0):
     """One backup of the oracle at n_states seeded states (rows computed in
-    full); returns (seconds, transitions)."""
+    full) on nthreads host threads (0: all cores); returns (seconds,
+    transitions)."""
     import oracle
     oracle.build_oracle()
     rng = np.random.default_rng(seed)
     st = rng.choice(w.problem.n_states, size=min(n_states, w.problem.n_states), replace=False)
     Vn = rng.uniform(0.0, 1.0, size=w.problem.n_states)
     t0 = time.perf_counter()
-    oracle.backup_states(w.problem, w.spec, Vn, st)
+    oracle.backup_states(w.problem, w.spec, Vn, st, nthreads=nthreads)
     return time.perf_counter() - t0, len(st) * w.problem.n_inputs * window_slots_of(w)
+
+
+def one_core_oracle(w, workload: str) -> dict:
+    """The oracle on one host thread: one backup at a bounded sample of seeded
+    states (a few seconds of work)."""
+    n_s = {"unicycle": 20000, "robot": 400, "rooms7": 200}.get(workload, 10)
+    dt, tr = time_oracle_sample(w, n_s, nthreads=1)
+    return {"value": tr / dt, "unit": UNIT, "cores": 1,
+            "sample": f"one backup at {n_s} seeded states (full rows), FP64, one thread"}
 
 
 def window_slots_of(w) -> int:
@@ -591,6 +601,7 @@ def main():
             dt, tr = time_oracle_sample(w, n_s)
             cpu = {"value": tr / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"one backup at {n_s} seeded states (full rows), FP64"}
+        cpu["one_core"] = one_core_oracle(w, args.workload)
     line = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,

@@ -158,7 +158,7 @@ amy_status launch_backup_fast(const Geom &g, int tmode, int v_store, const FastC
 // The whole horizon in one cooperative launch of the per-run kernel
 // (k_synth_runs): V0 holds V_N, V1 is the other resident vector; policies and
 // the FP32 copy of V_0 as in the per-step path.  bar is the handle's barrier
-// block (kBarWords words): the grid barrier's arrival count and generation,
+// block (kBarWords words): the grid barrier's arrival count and a spare word,
 // one backup counter per tile for the neighbour wait, then the error flag
 // *err.  The caller zeroes its first kBarResetBytes before each launch.
 constexpr int kBarTiles = 4096;

@@ -686,7 +686,7 @@ struct RunsHorizon {
     uint16_t *pi;        // policies: [horizon][n_x] when all_steps, else pi_0 only; or null
     int32_t all_steps;
     int32_t horizon;
-    unsigned *bar;       // grid barrier: arrivals, generation (zero at launch)
+    unsigned *bar;       // grid barrier: monotonic arrival count (zero at launch)
     unsigned *flags;     // per-tile backup counters (zero at launch), or null: grid barrier
     int32_t *err;        // set to 1 when a wait gives up, 2 on a bad launch shape
     int32_t spin_limit;  // polls before a wait gives up (0: every wait gives up at once)
@@ -738,10 +738,9 @@ __device__ __forceinline__ bool neighbour_wait(const RunsHorizon &hz, unsigned d
         const int lane = threadIdx.x;
         const int Gx = (int)gridDim.x, Gy = (int)gridDim.y;
         const int bx = (int)blockIdx.x, by = (int)blockIdx.y;
-        if (lane == 0) {
-            __threadfence();  // the block's V and policy writes before its counter
-            st_release_gpu(hz.flags + by * Gx + bx, done);
-        }
+        // the block's V and policy writes (ordered before this lane by the
+        // block barrier) before its counter: a release store
+        if (lane == 0) st_release_gpu(hz.flags + by * Gx + bx, done);
         __syncwarp();
         const int cy = min(2 * hz.nr_y + 1, Gy), cx = min(2 * hz.nr_x + 1, Gx);
         int ok = hz.spin_limit > 0;
@@ -763,10 +762,7 @@ __device__ __forceinline__ bool neighbour_wait(const RunsHorizon &hz, unsigned d
         }
         ok = __all_sync(0xffffffffu, ok);
         if (lane == 0) {
-            if (!ok)
-                atomicExch(hz.err, 1);
-            else if (ld_acquire_gpu(reinterpret_cast<const unsigned *>(hz.err)) != 0)
-                ok = 0;
+            if (!ok) atomicExch(hz.err, 1);
             s_ok = ok;
         }
     }
@@ -776,40 +772,35 @@ __device__ __forceinline__ bool neighbour_wait(const RunsHorizon &hz, unsigned d
     return s_ok != 0;
 }
 
-// Grid-wide barrier: the last block to arrive resets the arrival count and
-// opens the next generation; the others poll the generation (acquire), at
-// most spin_limit times.  Returns false when this block gave up or another
-// block reported an error; the kernel then leaves its step loop, so every
-// wait ends.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *err, unsigned nblocks, int32_t spin_limit) {
+// Grid-wide barrier number `done` (1-based) of this launch on a monotonic
+// arrival count (zero at launch): after the block's V and policy writes,
+// thread 0 adds one with release semantics (a fence, then a reduction that
+// returns nothing) and polls the count with acquire loads until every block
+// has arrived `done` times.  No block resets anything, so no arrival waits on
+// another block's second round trip.  Each wait stops after spin_limit polls
+// (0: at once), or sooner once another block reported an error; a block that
+// gives up sets the error flag.  Returns false when the kernel has to stop.
+__device__ __forceinline__ bool grid_barrier(unsigned *count, int32_t *err, unsigned nblocks, unsigned done,
+                                             int32_t spin_limit) {
     __shared__ int s_ok;
     __syncwarp();
     __syncthreads();
     if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned gen = ld_acquire_gpu(bar + 1);
-        __threadfence();  // this block's V and policy writes before its arrival
-        const unsigned prev = atomicAdd(bar, 1u);
-        if (prev == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            int32_t it = 0;
-            while (ld_acquire_gpu(bar + 1) == gen) {
-                if (++it > spin_limit) {
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
+        asm volatile("fence.acq_rel.gpu;\n"
+                     "red.relaxed.gpu.global.add.u32 [%0], 1;\n" ::"l"(count)
+                     : "memory");
+        const unsigned target = nblocks * done;
+        int ok = spin_limit > 0;
+        int32_t it = 0;
+        while (ok && ld_acquire_gpu(count) < target) {
+            if (++it > spin_limit ||
+                ((it & 31) == 0 && ld_acquire_gpu(reinterpret_cast<const unsigned *>(err)) != 0)) {
+                ok = 0;
+                break;
             }
+            __nanosleep(32);
         }
-        // a limit of zero: every wait gives up at once
-        if (spin_limit <= 0) ok = 0;
-        if (!ok)
-            atomicExch(err, 1);
-        else if (ld_acquire_gpu(reinterpret_cast<const unsigned *>(err)) != 0)
-            ok = 0;
+        if (!ok) atomicExch(err, 1);
         s_ok = ok;
     }
     // lane 0 spun alone: reconverge warp 0 before the block barrier (an
@@ -820,7 +811,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *err, unsign
 }
 
 template <class VT, int WM, int NS, bool KAHAN>
-__global__ void __launch_bounds__(RUNS_MAX_THREADS) k_synth_runs(const __grid_constant__ Geom g,
+__global__ void __launch_bounds__(RUNS_MAX_THREADS, 2) k_synth_runs(const __grid_constant__ Geom g,
                                                                 const __grid_constant__ FastArgs<VT> a,
                                                                 const RunsHorizon hz) {
     static_assert(NS == 2 || NS == 3, "row tiles of 2-D or 3-D problems");
@@ -984,7 +975,7 @@ __global__ void __launch_bounds__(RUNS_MAX_THREADS) k_synth_runs(const __grid_co
         }
         if (j + 1 < hz.horizon) {
             const bool go = hz.flags ? neighbour_wait(hz, (unsigned)(j + 1))
-                                     : grid_barrier(hz.bar, hz.err, nblocks, hz.spin_limit);
+                                     : grid_barrier(hz.bar, hz.err, nblocks, (unsigned)(j + 1), hz.spin_limit);
             if (!go) return;
         }
         const VT *t = Vn;
