@@ -789,10 +789,12 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, int32_t *err, unsi
         asm volatile("fence.acq_rel.gpu;\n"
                      "red.relaxed.gpu.global.add.u32 [%0], 1;\n" ::"l"(count)
                      : "memory");
+        // modulo 2^32: the count stays within nblocks of the target, so the
+        // signed difference decides even after the product wraps (long horizons)
         const unsigned target = nblocks * done;
         int ok = spin_limit > 0;
         int32_t it = 0;
-        while (ok && ld_acquire_gpu(count) < target) {
+        while (ok && (int32_t)(ld_acquire_gpu(count) - target) < 0) {
             if (++it > spin_limit ||
                 ((it & 31) == 0 && ld_acquire_gpu(reinterpret_cast<const unsigned *>(err)) != 0)) {
                 ok = 0;
