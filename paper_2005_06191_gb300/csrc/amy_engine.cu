@@ -407,6 +407,13 @@ struct amy_handle_s {
     unsigned *d_bar;
     int32_t spin_limit;
     int32_t grid_barrier;
+    // host outputs: a device staging buffer kept across calls (grown on
+    // demand; a per-call stream-ordered allocation went back to the driver at
+    // every synchronisation and cost more than the synthesis), and a
+    // page-locked word the barrier error flag is read into
+    void *d_stage;
+    size_t stage_cap;
+    int32_t *h_err;
     amy_info_t info;
 };
 
@@ -435,6 +442,8 @@ void free_handle(amy_handle_s *h) {
     cudaFree(h->d_mask);
     cudaFree(h->d_tab);
     cudaFree(h->d_bar);
+    cudaFree(h->d_stage);
+    if (h->h_err) cudaFreeHost(h->h_err);
     for (auto &p : h->ev_backup) h->ev_pool.push_back(p.first), h->ev_pool.push_back(p.second);
     for (auto &p : h->ev_build) h->ev_pool.push_back(p.first), h->ev_pool.push_back(p.second);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -442,6 +451,25 @@ void free_handle(amy_handle_s *h) {
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
+}
+
+// The host-output staging buffer, at least `bytes` long.  Grown with the
+// stream idle (the previous call's copies out of it have completed).  It is
+// outside the device-memory budget (a call with host outputs must not fail
+// where one with device outputs succeeds) and reported in device_bytes.
+amy_status stage_buffer(amy_handle_s *h, size_t bytes, void **out) {
+    if (bytes > h->stage_cap) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_error(e, "output staging");
+        cudaFree(h->d_stage);
+        h->d_stage = nullptr;
+        h->stage_cap = 0;
+        e = cudaMalloc(&h->d_stage, bytes);
+        if (e != cudaSuccess) return cuda_error(e, "output staging");
+        h->stage_cap = bytes;
+    }
+    *out = h->d_stage;
+    return AMY_OK;
 }
 
 #define AMY_CUDA(call, what)                          \
@@ -529,10 +557,12 @@ amy_status launch_backup_generic(amy_handle_s *h, int spec_kind, const void *Vn,
 // Reads and clears the persistent kernel's error flag (synchronises the
 // handle's stream).
 amy_status check_synth_error(amy_handle_s *h) {
-    if (!h->d_bar) return AMY_OK;
-    int32_t err = 0;
-    AMY_CUDA(cudaMemcpyAsync(&err, h->d_bar + kBarErrWord, sizeof err, cudaMemcpyDeviceToHost, h->stream), "barrier flag read");
+    if (!h->d_bar || !h->h_err) return AMY_OK;
+    *h->h_err = 0;
+    AMY_CUDA(cudaMemcpyAsync(h->h_err, h->d_bar + kBarErrWord, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream),
+             "barrier flag read");
     AMY_CUDA(cudaStreamSynchronize(h->stream), "barrier flag read");
+    const int32_t err = *h->h_err;
     if (err == 0) return AMY_OK;
     AMY_CUDA(cudaMemsetAsync(h->d_bar + kBarErrWord, 0, sizeof(int32_t), h->stream), "barrier flag reset");
     if (err == 1) return set_error(AMY_E_TIMEOUT, "persistent backup: a grid barrier wait gave up");
@@ -996,6 +1026,11 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     h->synth_ok = 0;
     if (fast_path(h) && h->tmode == AMY_T_STORED_SEPARABLE && h->grouped) {
         TRY(dev_alloc(h, (void **)&h->d_bar, kBarWords * sizeof(unsigned), "barrier words"));
+        e = cudaHostAlloc((void **)&h->h_err, sizeof(int32_t), cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            free_handle(h);
+            return cuda_error(e, "barrier flag host word");
+        }
         e = cudaMemsetAsync(h->d_bar, 0, kBarWords * sizeof(unsigned), h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) {
@@ -1036,7 +1071,7 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
 amy_status amy_info(amy_handle h, amy_info_t *out) {
     if (!h || !out) return set_error(AMY_E_INVALID_ARG, "null argument");
     *out = h->info;
-    out->device_bytes = h->bytes;
+    out->device_bytes = h->bytes + (int64_t)h->stage_cap;
     out->step_wait = h->grid_barrier;
     out->backup_kernel = 0;
     out->inner_span = 0;
@@ -1253,27 +1288,21 @@ amy_status amy_synthesize(amy_handle h, const amy_spec *spec, int32_t horizon, v
     // buffer (device) or a staging buffer (host).
     void *d_Vout = nullptr;
     uint16_t *d_pi = nullptr;
-    bool own_out = false, own_pi = false;
     if (outputs_on_device) {
         d_Vout = V_out;
         d_pi = policy_out;
     } else {
-        AMY_CUDA(cudaMallocAsync(&d_Vout, (size_t)nx * osz, h->stream), "output staging");
-        own_out = true;
-        if (policy_out && horizon > 0) {
-            const size_t pbytes = (size_t)nx * sizeof(uint16_t) * (policy_all_steps ? horizon : 1);
-            cudaError_t e = cudaMallocAsync((void **)&d_pi, pbytes, h->stream);
-            if (e != cudaSuccess) {
-                cudaFreeAsync(d_Vout, h->stream);
-                return cuda_error(e, "policy staging");
-            }
-            own_pi = true;
-        }
+        // V_0 then the policies in the handle's staging buffer
+        const size_t vbytes = ((size_t)nx * osz + 255) & ~(size_t)255;
+        const size_t pbytes =
+            policy_out && horizon > 0 ? (size_t)nx * sizeof(uint16_t) * (policy_all_steps ? horizon : 1) : 0;
+        void *buf = nullptr;
+        st = stage_buffer(h, vbytes + pbytes, &buf);
+        if (st != AMY_OK) return st;
+        d_Vout = buf;
+        if (pbytes) d_pi = reinterpret_cast<uint16_t *>(static_cast<unsigned char *>(buf) + vbytes);
     }
-    auto cleanup = [&]() {
-        if (own_out) cudaFreeAsync(d_Vout, h->stream);
-        if (own_pi) cudaFreeAsync(d_pi, h->stream);
-    };
+    auto cleanup = [&]() {};
     if (outputs_on_device && h->use_graphs && !h->profiling && !(h->synth_ok && horizon > 0)) {
         st = synthesize_graph(h, s, horizon, d_Vout, d_pi, policy_all_steps);
     } else {
@@ -1289,13 +1318,15 @@ amy_status amy_synthesize(amy_handle h, const amy_spec *spec, int32_t horizon, v
             e = cudaMemcpyAsync(policy_out, d_pi, (size_t)nx * sizeof(uint16_t) * (policy_all_steps ? horizon : 1),
                                 cudaMemcpyDeviceToHost, h->stream);
         // the persistent kernel's error flag rides on the same wait
-        int32_t err = 0;
-        const bool persist = h->synth_ok && horizon > 0 && h->d_bar;
+        const bool persist = h->synth_ok && horizon > 0 && h->d_bar && h->h_err;
+        if (persist) *h->h_err = 0;
         if (e == cudaSuccess && persist)
-            e = cudaMemcpyAsync(&err, h->d_bar + kBarErrWord, sizeof err, cudaMemcpyDeviceToHost, h->stream);
+            e = cudaMemcpyAsync(h->h_err, h->d_bar + kBarErrWord, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                h->stream);
         cleanup();
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_error(e, "copy out");
+        const int32_t err = persist ? *h->h_err : 0;
         if (err != 0) {
             AMY_CUDA(cudaMemsetAsync(h->d_bar + kBarErrWord, 0, sizeof(int32_t), h->stream), "barrier flag reset");
             if (err == 1) return set_error(AMY_E_TIMEOUT, "persistent backup: a grid barrier wait gave up");
@@ -1324,39 +1355,28 @@ amy_status amy_backup_step(amy_handle h, const amy_spec *spec, const void *V_nex
     st = launch_mask_any(h, s, h->d_V[1]);
     if (st != AMY_OK) return st;
     const void *src = V_next;
-    void *staging = nullptr;
+    // host buffers: V_next, then V_k and pi_k, in the handle's staging buffer
+    const size_t vbytes = ((size_t)nx * osz + 255) & ~(size_t)255;
+    unsigned char *stage = nullptr;
     if (!on_device) {
-        AMY_CUDA(cudaMallocAsync(&staging, (size_t)nx * osz, h->stream), "staging");
-        cudaError_t e = cudaMemcpyAsync(staging, V_next, (size_t)nx * osz, cudaMemcpyHostToDevice, h->stream);
-        if (e != cudaSuccess) {
-            cudaFreeAsync(staging, h->stream);
-            return cuda_error(e, "V_next upload");
-        }
-        src = staging;
+        void *buf = nullptr;
+        st = stage_buffer(h, 2 * vbytes + (size_t)nx * 2, &buf);
+        if (st != AMY_OK) return st;
+        stage = static_cast<unsigned char *>(buf);
+        AMY_CUDA(cudaMemcpyAsync(stage, V_next, (size_t)nx * osz, cudaMemcpyHostToDevice, h->stream), "V_next upload");
+        src = stage;
     }
     cudaError_t e = cudaSuccess;
     if (h->prec == AMY_PREC_FP64 || h->v_store == AMY_V_NATIVE)
         e = cudaMemcpyAsync(h->d_V[0], src, (size_t)nx * osz, cudaMemcpyDeviceToDevice, h->stream);
     else
         st = launch_f32_to_v16((const float *)src, h->d_V[0], h->v_store, nx, h->stream);
-    if (e != cudaSuccess || st != AMY_OK) {
-        if (staging) cudaFreeAsync(staging, h->stream);
-        return e != cudaSuccess ? cuda_error(e, "V_next copy") : st;
-    }
+    if (e != cudaSuccess || st != AMY_OK) return e != cudaSuccess ? cuda_error(e, "V_next copy") : st;
     void *d_out = V_out;
     uint16_t *d_pi = policy_out;
-    void *own_out = nullptr;
-    uint16_t *own_pi = nullptr;
     if (!on_device) {
-        e = cudaMallocAsync(&own_out, (size_t)nx * osz, h->stream);
-        if (e == cudaSuccess && policy_out) e = cudaMallocAsync((void **)&own_pi, (size_t)nx * 2, h->stream);
-        if (e != cudaSuccess) {
-            if (staging) cudaFreeAsync(staging, h->stream);
-            if (own_out) cudaFreeAsync(own_out, h->stream);
-            return cuda_error(e, "output staging");
-        }
-        d_out = own_out;
-        d_pi = own_pi;
+        d_out = stage + vbytes;
+        d_pi = policy_out ? reinterpret_cast<uint16_t *>(stage + 2 * vbytes) : nullptr;
     }
     st = launch_backup(h, s.kind, h->d_V[0], h->d_V[1], d_out, d_pi);
     if (st == AMY_OK && !on_device) {
@@ -1364,9 +1384,6 @@ amy_status amy_backup_step(amy_handle h, const amy_spec *spec, const void *V_nex
         if (e == cudaSuccess && policy_out)
             e = cudaMemcpyAsync(policy_out, d_pi, (size_t)nx * 2, cudaMemcpyDeviceToHost, h->stream);
     }
-    if (staging) cudaFreeAsync(staging, h->stream);
-    if (own_out) cudaFreeAsync(own_out, h->stream);
-    if (own_pi) cudaFreeAsync(own_pi, h->stream);
     if (st != AMY_OK) return st;
     if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_error(e, "backup step");

@@ -204,8 +204,14 @@ amy_status launch_synth_k(const Geom &g, const FastCall &c, const SynthCall &sc,
         if (e != cudaSuccess) return cuda_error(e, "persistent backup smem attribute");
         raised = true;
     }
+    // the occupancy query does not reject a block above the kernel's launch
+    // bound (the launch would fail): check it first
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return cuda_error(e, "persistent backup attributes");
+    if (threads > fa.maxThreadsPerBlock) return AMY_E_UNSUPPORTED;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e != cudaSuccess) return cuda_error(e, "persistent backup occupancy");
     if ((int64_t)per_sm * sm_count < (int64_t)grid.x * grid.y) return AMY_E_UNSUPPORTED;
     if (dry_run) return AMY_OK;
