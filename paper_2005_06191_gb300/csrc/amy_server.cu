@@ -166,6 +166,11 @@ struct amy_server_s {
     amy_status init_status = AMY_OK;
     std::string init_err;
     cudaStream_t stream = nullptr;
+    // the requests' device memory: a pool of the server's own that keeps
+    // freed memory mapped up to the budget (the device's default pool hands
+    // it back to the driver at every synchronisation, and the next admission
+    // pays for mapping it again)
+    cudaMemPool_t pool = nullptr;
     int sm_count = 0;
     TickSlot ring[kTickRing];
     int64_t tick_no = 0;
@@ -324,7 +329,7 @@ void carve(Req *r) {
 // shape class waits (autotuning).
 amy_status admit(amy_server_s *s, Req *r) {
     r->dbytes = device_bytes(r);
-    cudaError_t e = cudaMallocAsync(&r->dmem, r->dbytes, s->stream);
+    cudaError_t e = cudaMallocFromPoolAsync(&r->dmem, r->dbytes, s->pool, s->stream);
     if (e != cudaSuccess) return cuda_error(e, "request memory");
     carve(r);
     // finite guard cells around both V buffers (read with zero mass)
@@ -541,6 +546,17 @@ void scheduler(amy_server_s *s) {
     cudaError_t e = cudaSetDevice(s->opts.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->opts.device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        cudaMemPoolProps pp;
+        std::memset(&pp, 0, sizeof pp);
+        pp.allocType = cudaMemAllocationTypePinned;
+        pp.handleTypes = cudaMemHandleTypeNone;
+        pp.location.type = cudaMemLocationTypeDevice;
+        pp.location.id = s->opts.device;
+        e = cudaMemPoolCreate(&s->pool, &pp);
+        uint64_t keep = s->opts.device_mem_budget > 0 ? (uint64_t)s->opts.device_mem_budget : ~0ull;
+        if (e == cudaSuccess) e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     for (int i = 0; i < kTickRing && e == cudaSuccess; ++i) {
         TickSlot &t = s->ring[i];
         e = cudaMallocHost(&t.h, sizeof(BatchEntry) * s->opts.max_slots);
@@ -834,6 +850,8 @@ void amy_server_destroy(amy_server s) {
     }
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     s->pinned.release_all();
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->pool) cudaMemPoolDestroy(s->pool);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }
