@@ -225,7 +225,12 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
  * [horizon][n_states]; it may be NULL.  outputs_on_device != 0: V_out and
  * policy_out are device pointers and the call returns once the work is
  * enqueued on the handle's stream; otherwise they are host pointers and the
- * call returns after the copy. */
+ * call returns after the copy.  Host buffers in page-locked memory the
+ * device can address (cudaHostAlloc, cudaHostRegister) are written by the
+ * kernels in place, so their copy-out overlaps the backups; after an error
+ * reported once the kernels ran (AMY_E_TIMEOUT, AMY_E_CUDA) their contents
+ * are unspecified.  Other host buffers are filled from a device staging
+ * buffer the handle keeps between calls, only on AMY_OK. */
 amy_status amy_synthesize(amy_handle h, const amy_spec *spec, int32_t horizon, void *V_out,
                           uint16_t *policy_out, int32_t policy_all_steps,
                           int32_t outputs_on_device);

@@ -472,6 +472,18 @@ amy_status stage_buffer(amy_handle_s *h, size_t bytes, void **out) {
     return AMY_OK;
 }
 
+// The device address of page-locked host memory the device can write
+// (cudaHostAlloc / cudaHostRegister'ed, mapped), or null for any other
+// pointer (pageable memory goes through the staging buffer).
+void *mapped_host(void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 #define AMY_CUDA(call, what)                          \
     do {                                              \
         cudaError_t e__ = (call);                     \
@@ -1288,19 +1300,33 @@ amy_status amy_synthesize(amy_handle h, const amy_spec *spec, int32_t horizon, v
     // buffer (device) or a staging buffer (host).
     void *d_Vout = nullptr;
     uint16_t *d_pi = nullptr;
+    // host outputs the kernels write in place (page-locked, device-mapped):
+    // their copy-out then overlaps the backups
+    bool v_direct = false, pi_direct = false;
     if (outputs_on_device) {
         d_Vout = V_out;
         d_pi = policy_out;
     } else {
-        // V_0 then the policies in the handle's staging buffer
-        const size_t vbytes = ((size_t)nx * osz + 255) & ~(size_t)255;
-        const size_t pbytes =
-            policy_out && horizon > 0 ? (size_t)nx * sizeof(uint16_t) * (policy_all_steps ? horizon : 1) : 0;
-        void *buf = nullptr;
-        st = stage_buffer(h, vbytes + pbytes, &buf);
-        if (st != AMY_OK) return st;
-        d_Vout = buf;
-        if (pbytes) d_pi = reinterpret_cast<uint16_t *>(static_cast<unsigned char *>(buf) + vbytes);
+        if (horizon > 0) {
+            d_Vout = mapped_host(V_out);
+            v_direct = d_Vout != nullptr;
+            if (policy_out) {
+                d_pi = static_cast<uint16_t *>(mapped_host(policy_out));
+                pi_direct = d_pi != nullptr;
+            }
+        }
+        // the others in the handle's staging buffer: V_0, then the policies
+        const size_t vbytes = v_direct ? 0 : ((size_t)nx * osz + 255) & ~(size_t)255;
+        const size_t pbytes = policy_out && horizon > 0 && !pi_direct
+                                  ? (size_t)nx * sizeof(uint16_t) * (policy_all_steps ? horizon : 1)
+                                  : 0;
+        if (vbytes + pbytes > 0) {
+            void *buf = nullptr;
+            st = stage_buffer(h, vbytes + pbytes, &buf);
+            if (st != AMY_OK) return st;
+            if (!v_direct) d_Vout = buf;
+            if (pbytes) d_pi = reinterpret_cast<uint16_t *>(static_cast<unsigned char *>(buf) + vbytes);
+        }
     }
     auto cleanup = [&]() {};
     if (outputs_on_device && h->use_graphs && !h->profiling && !(h->synth_ok && horizon > 0)) {
@@ -1313,8 +1339,9 @@ amy_status amy_synthesize(amy_handle h, const amy_spec *spec, int32_t horizon, v
         return st;
     }
     if (!outputs_on_device) {
-        cudaError_t e = cudaMemcpyAsync(V_out, d_Vout, (size_t)nx * osz, cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess && policy_out && horizon > 0)
+        cudaError_t e = cudaSuccess;
+        if (!v_direct) e = cudaMemcpyAsync(V_out, d_Vout, (size_t)nx * osz, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && policy_out && horizon > 0 && !pi_direct)
             e = cudaMemcpyAsync(policy_out, d_pi, (size_t)nx * sizeof(uint16_t) * (policy_all_steps ? horizon : 1),
                                 cudaMemcpyDeviceToHost, h->stream);
         // the persistent kernel's error flag rides on the same wait

@@ -183,6 +183,35 @@ def test_device_outputs(amy):
     assert np.max(np.abs(V.cpu().numpy() - ref["V"])) <= TOL["fp32"]
 
 
+@pytest.mark.parametrize("tmode,prec", [("stored_separable", "fp32"), ("otf", "fp32_kahan"), ("stored_full", "fp64")])
+def test_host_outputs_pinned_pageable_device_agree(amy, tmode, prec):
+    """Host outputs in page-locked memory are written by the kernels in place,
+    pageable ones go through the handle's staging buffer, device outputs stay
+    on the device: all three give the same V_0 and policies, bit for bit, on
+    repeated calls (the staging buffer is reused) and for horizon 0."""
+    import torch
+    w = W.unicycle(nxy=21, horizon=6, target=(2.0, 3.0))
+    n, N = w.problem.n_states, w.horizon
+    fdt = torch.float64 if prec == "fp64" else torch.float32
+    with amy.amy_build(w.problem, tmode=tmode, prec=prec) as h:
+        Vd = torch.empty(n, dtype=fdt, device="cuda")
+        Pd = torch.empty((N, n), dtype=torch.int16, device="cuda")
+        amy.amy_synthesize(h, w.spec, N, V_out=Vd, policy_out=Pd, policy_all_steps=True)
+        torch.cuda.synchronize()
+        Vd, Pd = Vd.cpu().numpy(), Pd.cpu().numpy().view(np.uint16)
+        for _ in range(2):
+            Vp = torch.full((n,), -1.0, dtype=fdt, pin_memory=True).numpy()
+            Pp = torch.full((N, n), 7, dtype=torch.int16, pin_memory=True).numpy()
+            amy.amy_synthesize(h, w.spec, N, V_out=Vp, policy_out=Pp, policy_all_steps=True)
+            Vq, Pq = amy.amy_synthesize(h, w.spec, N, policy_all_steps=True)   # pageable
+            assert np.array_equal(Vp, Vd) and np.array_equal(Pp.view(np.uint16), Pd)
+            assert np.array_equal(Vq, Vd) and np.array_equal(Pq, Pd)
+        V0p = torch.full((n,), -1.0, dtype=fdt, pin_memory=True).numpy()
+        amy.amy_synthesize(h, w.spec, 0, V_out=V0p)
+        V0q, _ = amy.amy_synthesize(h, w.spec, 0)
+        assert np.array_equal(V0p, V0q) and set(np.unique(V0q)) <= {0.0, 1.0}
+
+
 def test_memory_budget_rejected(amy):
     w = W.unicycle()
     with pytest.raises(amy.AmyError) as e:
