@@ -255,7 +255,8 @@ def run_amy(args, rank, world):
     # kernel-level roofline of the dominant kernel (the fused backup)
     # kernels per timed step: the backups, one spec-mask kernel, and the build
     # (for the per-dimension tables: bounds reset + tables [+ shifted inner table])
-    launches = kt["backup_launches"] + info["build_kernels"] * kt["build_launches"] + args.steps
+    launches = (info["backup_launch_kernels"] * kt["backup_launches"] + info["build_kernels"] * kt["build_launches"]
+                + args.steps)
     # per backup: the persistent kernel performs the whole horizon in one launch
     bk_ms = kt["backup_ms"] / max(kt["backup_steps"], 1)
     launch_ms = kt["backup_ms"] / max(kt["backup_launches"], 1)

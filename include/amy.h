@@ -192,7 +192,9 @@ typedef struct {
                                    with one outer contraction per input run, 4 the
                                    per-run kernel on row tiles (k_backup_runs), 5 its
                                    persistent form: the whole horizon in one
-                                   cooperative launch (k_synth_runs) */
+                                   cooperative launch (k_synth_runs), 6 stored full
+                                   rows split over window-row groups (k_backup_rows,
+                                   then k_argmax_rows) */
     int32_t input_runs;         /* runs of consecutive inputs sharing outer records */
     int32_t inner_span;         /* inner slots K one outer contraction covers (kernels 3, 4) */
     int32_t build_kernels;      /* kernels one table build (amy_build / amy_rebuild) launches */
@@ -200,6 +202,8 @@ typedef struct {
     int32_t step_wait;          /* persistent kernel (5): what a block waits for between
                                    backups, 0 neighbour tiles, 1 every block
                                    (amy_set_step_wait; picked by the autotuner) */
+    int32_t backup_launch_kernels; /* kernels one backup launch of amy_kernel_times
+                                   runs (2 for kernel 6, else 1) */
 } amy_info_t;
 
 /* Points per dim of [lb, ub] with step eta: floor((ub-lb)/eta + 1e-9) + 1

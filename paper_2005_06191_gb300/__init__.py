@@ -210,7 +210,7 @@ def amy_info(h: AmyHandle) -> dict:
         "grouped_inputs": int(info.grouped_inputs), "backup_kernel": int(info.backup_kernel),
         "input_runs": int(info.input_runs), "inner_span": int(info.inner_span),
         "build_kernels": int(info.build_kernels), "tile_outer_rows": int(info.tile_outer_rows),
-        "step_wait": int(info.step_wait),
+        "step_wait": int(info.step_wait), "backup_launch_kernels": int(info.backup_launch_kernels),
     }
 
 

@@ -56,7 +56,8 @@ class amy_info_t(C.Structure):
                 ("v_store", C.c_int32), ("input_lanes", C.c_int32), ("row_tiles", C.c_int32), ("block_states", C.c_int32),
                 ("grouped_inputs", C.c_int32), ("backup_kernel", C.c_int32), ("input_runs", C.c_int32),
                 ("inner_span", C.c_int32), ("build_kernels", C.c_int32),
-                ("tile_outer_rows", C.c_int32), ("step_wait", C.c_int32)]
+                ("tile_outer_rows", C.c_int32), ("step_wait", C.c_int32),
+                ("backup_launch_kernels", C.c_int32)]
 
 
 class amy_server_opts(C.Structure):

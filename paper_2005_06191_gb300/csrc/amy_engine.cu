@@ -363,6 +363,10 @@ struct amy_handle_s {
     double *d_params;
     void *d_T;
     int16_t *d_O;
+    // stored full rows with wide windows: the backup is split over window
+    // rows (k_backup_rows), its pair sums S[u][x] kept here, or null
+    void *d_split;
+    int32_t split_groups;
     int64_t npairs;
     void *d_V[2];         // V ping-pong (interior start)
     void *d_Vbase[2];     // allocations: kVGuard finite guard cells on each side
@@ -437,6 +441,7 @@ void free_handle(amy_handle_s *h) {
     cudaFree(h->d_params);
     cudaFree(h->d_T);
     cudaFree(h->d_O);
+    cudaFree(h->d_split);
     cudaFree(h->d_Vbase[0]);
     cudaFree(h->d_Vbase[1]);
     cudaFree(h->d_mask);
@@ -512,6 +517,19 @@ amy_status launch_backup_t(amy_handle_s *h, int spec_kind, const VT *Vn, VT *Vo,
     a.O = h->d_O;
     a.npairs = h->npairs;
     a.tab = h->d_tab;
+    if constexpr (TM == TM_FULL) {
+        if (h->d_split) {
+            // split over window rows: pair sums, then max / argmax per state
+            const dim3 grid((unsigned)((h->g.nx + 31) / 32), (unsigned)h->g.nu);
+            k_backup_rows<R, VT, KAHAN><<<grid, dim3(32, (unsigned)h->split_groups), 0, h->stream>>>(
+                h->g, a, (R *)h->d_split);
+            AMY_CUDA(cudaGetLastError(), "backup launch");
+            const int blocks = (int)std::min<int64_t>((h->g.nx + 255) / 256, 65535);
+            k_argmax_rows<R, VT><<<blocks, 256, 0, h->stream>>>(h->g, a, (const R *)h->d_split);
+            AMY_CUDA(cudaGetLastError(), "argmax launch");
+            return AMY_OK;
+        }
+    }
     const int blocks = (h->g.nx + h->tileX - 1) / h->tileX;
     const size_t smem = (size_t)h->tileX * h->g.nu * sizeof(R);
     k_backup<R, VT, TM, KAHAN><<<blocks, 256, smem, h->stream>>>(h->g, a);
@@ -1012,6 +1030,15 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
         const int64_t per_pair = (h->tmode == AMY_T_STORED_FULL) ? g.wtot : g.wsum;
         TRY(dev_alloc(h, &h->d_T, (size_t)(h->npairs * per_pair) * rsize(h), "stored T"));
         TRY(dev_alloc(h, (void **)&h->d_O, (size_t)(h->npairs * g.n) * sizeof(int16_t), "stored origins"));
+        // wide stored full rows: split each pair's window over up to 8 groups
+        // of rows when the pair sums fit the budget (else one thread per pair)
+        const int rows = g.wtot / g.W[g.n - 1];
+        const size_t sbytes = (size_t)h->npairs * rsize(h);
+        if (h->tmode == AMY_T_STORED_FULL && g.wtot >= 256 && rows >= 2 &&
+            (h->budget <= 0 || h->bytes + (int64_t)sbytes <= h->budget)) {
+            TRY(dev_alloc(h, &h->d_split, sbytes, "pair sums"));
+            h->split_groups = std::min(rows, ROWS_MAX_GROUPS);
+        }
     }
     e = cudaMemcpyAsync(h->d_params, params.data(), params.size() * sizeof(double), cudaMemcpyHostToDevice,
                         h->stream);
@@ -1085,7 +1112,8 @@ amy_status amy_info(amy_handle h, amy_info_t *out) {
     *out = h->info;
     out->device_bytes = h->bytes + (int64_t)h->stage_cap;
     out->step_wait = h->grid_barrier;
-    out->backup_kernel = 0;
+    out->backup_kernel = h->d_split ? 6 : 0;
+    out->backup_launch_kernels = h->d_split ? 2 : 1;
     out->inner_span = 0;
     if (fast_path(h)) {
         const FastCall c = fast_call(h, SPEC_SAFETY, nullptr, nullptr, nullptr, nullptr);

@@ -325,6 +325,111 @@ __global__ void __launch_bounds__(256) k_backup(const __grid_constant__ Geom g, 
 }
 
 // ---------------------------------------------------------------------------
+// Stored-full backup split over window rows (dense or wide windows with few
+// pairs: one thread per pair leaves the GPU short of loads in flight).  A
+// block takes 32 consecutive states of one input (T read coalesced across
+// the 32 pairs) and blockDim.y groups; group q sums the window rows (runs of
+// the innermost dim, C order) [q*rows/G, (q+1)*rows/G) with the same per-row
+// arithmetic as window_sum_full, the group partials are added in group
+// order, and the pair's sum s(x, u) goes to S[u][x] (-1 for masked states).
+// k_argmax_rows then takes the max over u and the lowest maximiser.
+// ---------------------------------------------------------------------------
+template <class R, class VT, bool KAHAN>
+__device__ __forceinline__ R window_rows_full(const Geom &g, const R *__restrict__ Trow, int64_t npairs,
+                                              const int32_t *off, const VT *__restrict__ V, int r0, int r1) {
+    const int n = g.n;
+    const int WL = g.W[n - 1];
+    const int bL = g.wsum - WL;
+    int k[MAXD], fb[MAXD];
+    int acc_fb = 0;
+    for (int d = 0; d < n; ++d) {
+        fb[d] = acc_fb;
+        acc_fb += g.W[d];
+        k[d] = 0;
+    }
+    // multi-index of row r0 over dims 0..n-2 (C order)
+    int rem = r0;
+    for (int d = n - 2; d >= 0; --d) {
+        k[d] = rem % g.W[d];
+        rem /= g.W[d];
+    }
+    R acc = R(0), comp = R(0);
+    for (int r = r0; r < r1; ++r) {
+        int32_t base = 0;
+        for (int d = 0; d < n - 1; ++d) base += off[fb[d] + k[d]];
+        const R *Tr = Trow + (int64_t)r * WL * npairs;
+        R inner = R(0);
+        for (int j = 0; j < WL; ++j)
+            inner = fma_r(__ldg(Tr + (int64_t)j * npairs), vload<R, VT>(V + base + off[bL + j]), inner);
+        accum<R, KAHAN>(acc, comp, inner);
+        for (int d = n - 2; d >= 0; --d) {
+            if (++k[d] < g.W[d]) break;
+            k[d] = 0;
+        }
+    }
+    return acc;
+}
+
+constexpr int ROWS_MAX_GROUPS = 8;
+
+template <class R, class VT, bool KAHAN>
+__global__ void __launch_bounds__(32 * ROWS_MAX_GROUPS) k_backup_rows(const __grid_constant__ Geom g,
+                                                                      const BackupArgs<R, VT> a,
+                                                                      R *__restrict__ S) {
+    __shared__ R part[ROWS_MAX_GROUPS][32];
+    const int lane = threadIdx.x, q = threadIdx.y, G = blockDim.y;
+    const int32_t x = (int32_t)blockIdx.x * 32 + lane;
+    const int32_t u = (int32_t)blockIdx.y;
+    const bool live = x < g.nx && !state_masked(a.spec_kind, a.mask[x]);
+    R s = R(0);
+    if (live) {
+        const int rows = g.wtot / g.W[g.n - 1];
+        const int r0 = (int)((int64_t)rows * q / G), r1 = (int)((int64_t)rows * (q + 1) / G);
+        const int64_t pair = (int64_t)u * g.nx + x;
+        int32_t off[MAXWS];
+        row_setup_stored<R>(g, a.T, a.O, a.npairs, pair, false, nullptr, off, nullptr);
+        s = window_rows_full<R, VT, KAHAN>(g, a.T + pair, a.npairs, off, a.Vn, r0, r1);
+    }
+    part[q][lane] = s;
+    __syncthreads();
+    if (q == 0 && x < g.nx) {
+        R acc = R(0), comp = R(0);
+        for (int i = 0; i < G; ++i) accum<R, KAHAN>(acc, comp, part[i][lane]);
+        S[(int64_t)u * g.nx + x] = live ? acc : R(-1);
+    }
+}
+
+// Max over inputs of S[u][x] per state, lowest maximiser, spec values on
+// masked states (the collect step of k_backup).
+template <class R, class VT>
+__global__ void __launch_bounds__(256) k_argmax_rows(const __grid_constant__ Geom g, const BackupArgs<R, VT> a,
+                                                     const R *__restrict__ S) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.nx; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = (int32_t)i;
+        const uint8_t f = a.mask[x];
+        R best;
+        uint16_t arg;
+        if (state_masked(a.spec_kind, f)) {
+            best = (a.spec_kind != SPEC_SAFETY && (f & F_TARGET)) ? R(1) : R(0);
+            arg = 0xFFFF;
+        } else {
+            best = R(-1);
+            arg = 0;
+            for (int u = 0; u < g.nu; ++u) {
+                const R s = S[(int64_t)u * g.nx + x];
+                if (s > best) {
+                    best = s;
+                    arg = (uint16_t)u;
+                }
+            }
+        }
+        a.Vo[x] = vstore_cast<VT, R>(best);
+        if (a.Vfinal) a.Vfinal[x] = best;
+        if (a.pi) a.pi[x] = arg;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Stored T construction (Algorithm 2): one thread per (x, u) pair.
 // ---------------------------------------------------------------------------
 template <class R, int TM>

@@ -36,6 +36,37 @@ def test_robot_lin_fp32(amy, robot_ref, tmode, prec):
     compare_synthesis(amy, w, tmode, prec, ref=ref)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_kahan"])
+def test_stored_full_row_split(amy, robot_ref, prec):
+    """Wide stored full rows (the robot's dense 41 x 41 windows) are summed by
+    groups of window rows, their pair sums reduced per state by a second
+    kernel (backup kernel 6); without room in the budget for the pair sums
+    one thread takes each pair (kernel 0).  Both match the oracle; they
+    agree with each other to rounding (the row groups only reassociate the
+    sum) and their policies agree wherever the top-two gap is clear."""
+    w, ref = robot_ref
+    out, kernels = [], []
+    with amy.amy_build(w.problem, tmode="stored_full", prec=prec) as h:
+        info = amy.amy_info(h)
+        kernels.append(info["backup_kernel"])
+        assert info["backup_launch_kernels"] == 2
+        full_bytes = info["device_bytes"]
+        out.append(amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True))
+    with amy.amy_build(w.problem, tmode="stored_full", prec=prec, device_mem_budget=full_bytes - 1) as h:
+        info = amy.amy_info(h)
+        kernels.append(info["backup_kernel"])
+        assert info["backup_launch_kernels"] == 1
+        out.append(amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True))
+    assert kernels == [6, 0]
+    tol = TOL[prec]
+    for V, pi in out:
+        assert float(np.max(np.abs(V.astype(np.float64) - ref["V"]))) <= tol
+        sure = ref["gap"] > GAP[prec]
+        assert not ((pi != ref["pi"]) & sure).any()
+    assert float(np.max(np.abs(out[0][0].astype(np.float64) - out[1][0]))) <= (1e-14 if prec == "fp64" else 2e-6)
+    compare_synthesis(amy, w, "stored_full", prec, ref=ref)
+
+
 def test_robot_lin_rows(amy):
     w = W.robot_lin()
     for tmode, prec, tol in [("stored_full", "fp64", 1e-14), ("otf", "fp32", 2e-6)]:
@@ -475,7 +506,8 @@ def test_auto_mode_picks_and_matches(amy):
 def test_backup_kernel_reported_and_lane_load_ceilings(amy):
     expect = [(W.rooms7(n_per_dim=4, horizon=1), "stored_separable", 1),   # 7-D: register-resident
               (W.random_affine(np.random.default_rng(3), 2, [37, 30], 6, window=[3, 3]), "stored_separable", 2),
-              (W.robot_lin(), "stored_full", 0)]                              # dense 41-wide rows: generic
+              (W.robot_lin(), "stored_full", 6),     # dense 41-wide stored rows: split over window rows
+              (W.robot_lin(), "otf", 0)]             # 41-wide rows on the fly: generic
     for w, tmode, kern in expect:
         with amy.amy_build(w.problem, tmode=tmode, prec="fp32") as h:
             assert amy.amy_info(h)["backup_kernel"] == kern, (w.problem.name, tmode)
