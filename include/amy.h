@@ -192,9 +192,9 @@ typedef struct {
                                    with one outer contraction per input run, 4 the
                                    per-run kernel on row tiles (k_backup_runs), 5 its
                                    persistent form: the whole horizon in one
-                                   cooperative launch (k_synth_runs), 6 stored full
-                                   rows split over window-row groups (k_backup_rows,
-                                   then k_argmax_rows) */
+                                   cooperative launch (k_synth_runs), 6 stored rows
+                                   (full or factored) split over window-row groups
+                                   (k_backup_rows, then k_argmax_rows) */
     int32_t input_runs;         /* runs of consecutive inputs sharing outer records */
     int32_t inner_span;         /* inner slots K one outer contraction covers (kernels 3, 4) */
     int32_t build_kernels;      /* kernels one table build (amy_build / amy_rebuild) launches */
@@ -341,6 +341,13 @@ amy_status amy_synthesize_noalloc(const amy_system *sys, const amy_grid *states,
  * current device.  Takes a few milliseconds; allocates 16 MiB temporarily.
  * Errors: INVALID_ARG (null pointer), CUDA. */
 amy_status amy_measure_lane_loads(double *shared_per_s, double *global_per_s);
+
+/* Measured fused multiply-add rates of the current device, FP32 and FP64, in
+ * FMAs per second summed over all threads (independent chains, every SM
+ * full): the ceiling of a backup bound by its FMAs (the FP64 paths; GB300
+ * issues FP64 far slower than FP32).  Takes a few milliseconds.  Errors:
+ * INVALID_ARG (null pointer), CUDA. */
+amy_status amy_measure_fma(double *fp32_per_s, double *fp64_per_s);
 
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of independent synthesis requests.

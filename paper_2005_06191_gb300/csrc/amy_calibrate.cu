@@ -1,5 +1,6 @@
-// amy_calibrate.cu -- measured ceilings of the two load paths the fused
-// backup kernels gather V through, used as roofline denominators:
+// amy_calibrate.cu -- measured ceilings used as roofline denominators: the
+// FP32 and FP64 fused multiply-add issue rates, and the two load paths the
+// fused backup kernels gather V through:
 //   - shared memory: 32-bit loads, every warp reading 32 consecutive words
 //     (one wavefront per instruction, no bank conflict);
 //   - global memory hitting L1: 32-bit loads, every warp reading 32
@@ -49,10 +50,76 @@ __global__ void __launch_bounds__(CAL_THREADS) k_cal_global(const float *__restr
     out[blockIdx.x * blockDim.x + threadIdx.x] = (s0 + s1) + (s2 + s3);
 }
 
+// Fused multiply-add issue: every thread runs FMA_CHAINS independent chains
+// a = a * b + c (b, c runtime values, so nothing folds), FMA_ITERS steps
+// each; the chains keep the pipe busy rather than waiting on one result.
+constexpr int FMA_THREADS = 256;
+constexpr int FMA_CHAINS = 8;
+
+template <class R>
+__global__ void __launch_bounds__(FMA_THREADS) k_cal_fma(R b, R c, int iters, R *__restrict__ out) {
+    R acc[FMA_CHAINS];
+#pragma unroll
+    for (int i = 0; i < FMA_CHAINS; ++i) acc[i] = (R)(threadIdx.x + i);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < FMA_CHAINS; ++i) acc[i] = fma(acc[i], b, c);
+    }
+    R s = 0;
+#pragma unroll
+    for (int i = 0; i < FMA_CHAINS; ++i) s += acc[i];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
 }  // namespace amy
 
 using namespace amy;
+
+extern "C" amy_status amy_measure_fma(double *fp32_per_s, double *fp64_per_s) {
+    if (!fp32_per_s || !fp64_per_s) return set_error(AMY_E_INVALID_ARG, "null argument");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_error(e, "device query");
+    const int blocks = sms * 8;  // 2048 threads per SM
+    double *out = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&out, (size_t)blocks * FMA_THREADS * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    double rate[2] = {0.0, 0.0};
+    for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
+        const int iters = which == 0 ? 4096 : 256;  // FP64 issues far slower on this part
+        float best = 3.4e38f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // first pass warms up
+            e = cudaEventRecord(a, st);
+            if (which == 0)
+                k_cal_fma<float><<<blocks, FMA_THREADS, 0, st>>>(0.999f, 1e-3f, iters, reinterpret_cast<float *>(out));
+            else
+                k_cal_fma<double><<<blocks, FMA_THREADS, 0, st>>>(0.999, 1e-3, iters, out);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(b, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+            if (e == cudaSuccess && rep > 0 && ms < best) best = ms;
+        }
+        const double fmas = (double)blocks * FMA_THREADS * FMA_CHAINS * iters;
+        rate[which] = fmas / (best * 1e-3);
+    }
+    if (out) cudaFreeAsync(out, st);
+    if (st) cudaStreamSynchronize(st);
+    if (st) cudaStreamDestroy(st);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_error(e, "FMA calibration");
+    *fp32_per_s = rate[0];
+    *fp64_per_s = rate[1];
+    return AMY_OK;
+}
 
 extern "C" amy_status amy_measure_lane_loads(double *shared_per_s, double *global_per_s) {
     if (!shared_per_s || !global_per_s) return set_error(AMY_E_INVALID_ARG, "null argument");

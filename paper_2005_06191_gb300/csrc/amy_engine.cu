@@ -363,8 +363,8 @@ struct amy_handle_s {
     double *d_params;
     void *d_T;
     int16_t *d_O;
-    // stored full rows with wide windows: the backup is split over window
-    // rows (k_backup_rows), its pair sums S[u][x] kept here, or null
+    // stored rows (full or factored) with wide windows: the backup is split
+    // over window rows (k_backup_rows), its pair sums S[u][x] kept here, or null
     void *d_split;
     int32_t split_groups;
     int64_t npairs;
@@ -517,11 +517,11 @@ amy_status launch_backup_t(amy_handle_s *h, int spec_kind, const VT *Vn, VT *Vo,
     a.O = h->d_O;
     a.npairs = h->npairs;
     a.tab = h->d_tab;
-    if constexpr (TM == TM_FULL) {
+    if constexpr (TM == TM_FULL || TM == TM_FACTORED) {
         if (h->d_split) {
             // split over window rows: pair sums, then max / argmax per state
             const dim3 grid((unsigned)((h->g.nx + 31) / 32), (unsigned)h->g.nu);
-            k_backup_rows<R, VT, KAHAN><<<grid, dim3(32, (unsigned)h->split_groups), 0, h->stream>>>(
+            k_backup_rows<R, VT, TM, KAHAN><<<grid, dim3(32, (unsigned)h->split_groups), 0, h->stream>>>(
                 h->g, a, (R *)h->d_split);
             AMY_CUDA(cudaGetLastError(), "backup launch");
             const int blocks = (int)std::min<int64_t>((h->g.nx + 255) / 256, 65535);
@@ -1030,11 +1030,11 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
         const int64_t per_pair = (h->tmode == AMY_T_STORED_FULL) ? g.wtot : g.wsum;
         TRY(dev_alloc(h, &h->d_T, (size_t)(h->npairs * per_pair) * rsize(h), "stored T"));
         TRY(dev_alloc(h, (void **)&h->d_O, (size_t)(h->npairs * g.n) * sizeof(int16_t), "stored origins"));
-        // wide stored full rows: split each pair's window over up to 8 groups
-        // of rows when the pair sums fit the budget (else one thread per pair)
+        // wide stored rows: split each pair's window over up to 8 groups of
+        // rows when the pair sums fit the budget (else one thread per pair)
         const int rows = g.wtot / g.W[g.n - 1];
         const size_t sbytes = (size_t)h->npairs * rsize(h);
-        if (h->tmode == AMY_T_STORED_FULL && g.wtot >= 256 && rows >= 2 &&
+        if (g.wtot >= 256 && rows >= 2 &&
             (h->budget <= 0 || h->bytes + (int64_t)sbytes <= h->budget)) {
             TRY(dev_alloc(h, &h->d_split, sbytes, "pair sums"));
             h->split_groups = std::min(rows, ROWS_MAX_GROUPS);

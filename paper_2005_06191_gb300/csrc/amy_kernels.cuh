@@ -325,13 +325,14 @@ __global__ void __launch_bounds__(256) k_backup(const __grid_constant__ Geom g, 
 }
 
 // ---------------------------------------------------------------------------
-// Stored-full backup split over window rows (dense or wide windows with few
+// Stored-row backup split over window rows (dense or wide windows with few
 // pairs: one thread per pair leaves the GPU short of loads in flight).  A
 // block takes 32 consecutive states of one input (T read coalesced across
 // the 32 pairs) and blockDim.y groups; group q sums the window rows (runs of
 // the innermost dim, C order) [q*rows/G, (q+1)*rows/G) with the same per-row
-// arithmetic as window_sum_full, the group partials are added in group
-// order, and the pair's sum s(x, u) goes to S[u][x] (-1 for masked states).
+// arithmetic as window_sum_full / window_sum_factored, the group partials are
+// added in group order, and the pair's sum s(x, u) goes to S[u][x] (-1 for
+// masked states).
 // k_argmax_rows then takes the max over u and the lowest maximiser.
 // ---------------------------------------------------------------------------
 template <class R, class VT, bool KAHAN>
@@ -370,12 +371,55 @@ __device__ __forceinline__ R window_rows_full(const Geom &g, const R *__restrict
     return acc;
 }
 
+// The same for a factored row: row r's weight is the product of its outer
+// dims' masses taken left to right (the prefix product window_sum_factored
+// carries), rows of weight zero are skipped.
+template <class R, class VT, bool KAHAN>
+__device__ __forceinline__ R window_rows_factored(const Geom &g, const R *fac, const int32_t *off,
+                                                  const VT *__restrict__ V, int r0, int r1) {
+    const int n = g.n;
+    const int WL = g.W[n - 1];
+    const int bL = g.wsum - WL;
+    int k[MAXD], fb[MAXD];
+    int acc_fb = 0;
+    for (int d = 0; d < n; ++d) {
+        fb[d] = acc_fb;
+        acc_fb += g.W[d];
+        k[d] = 0;
+    }
+    int rem = r0;
+    for (int d = n - 2; d >= 0; --d) {
+        k[d] = rem % g.W[d];
+        rem /= g.W[d];
+    }
+    R acc = R(0), comp = R(0);
+    for (int r = r0; r < r1; ++r) {
+        R w = R(1);
+        int32_t base = 0;
+        for (int d = 0; d < n - 1; ++d) {
+            w *= fac[fb[d] + k[d]];
+            base += off[fb[d] + k[d]];
+        }
+        if (w != R(0)) {
+            R inner = R(0);
+            for (int j = 0; j < WL; ++j) inner = fma_r(fac[bL + j], vload<R, VT>(V + base + off[bL + j]), inner);
+            accum<R, KAHAN>(acc, comp, w * inner);
+        }
+        for (int d = n - 2; d >= 0; --d) {
+            if (++k[d] < g.W[d]) break;
+            k[d] = 0;
+        }
+    }
+    return acc;
+}
+
 constexpr int ROWS_MAX_GROUPS = 8;
 
-template <class R, class VT, bool KAHAN>
+template <class R, class VT, int TM, bool KAHAN>
 __global__ void __launch_bounds__(32 * ROWS_MAX_GROUPS) k_backup_rows(const __grid_constant__ Geom g,
                                                                       const BackupArgs<R, VT> a,
                                                                       R *__restrict__ S) {
+    static_assert(TM == TM_FULL || TM == TM_FACTORED, "stored rows");
     __shared__ R part[ROWS_MAX_GROUPS][32];
     const int lane = threadIdx.x, q = threadIdx.y, G = blockDim.y;
     const int32_t x = (int32_t)blockIdx.x * 32 + lane;
@@ -387,8 +431,14 @@ __global__ void __launch_bounds__(32 * ROWS_MAX_GROUPS) k_backup_rows(const __gr
         const int r0 = (int)((int64_t)rows * q / G), r1 = (int)((int64_t)rows * (q + 1) / G);
         const int64_t pair = (int64_t)u * g.nx + x;
         int32_t off[MAXWS];
-        row_setup_stored<R>(g, a.T, a.O, a.npairs, pair, false, nullptr, off, nullptr);
-        s = window_rows_full<R, VT, KAHAN>(g, a.T + pair, a.npairs, off, a.Vn, r0, r1);
+        if constexpr (TM == TM_FULL) {
+            row_setup_stored<R>(g, a.T, a.O, a.npairs, pair, false, nullptr, off, nullptr);
+            s = window_rows_full<R, VT, KAHAN>(g, a.T + pair, a.npairs, off, a.Vn, r0, r1);
+        } else {
+            R fac[MAXWS];
+            row_setup_stored<R>(g, a.T, a.O, a.npairs, pair, true, fac, off, nullptr);
+            s = window_rows_factored<R, VT, KAHAN>(g, fac, off, a.Vn, r0, r1);
+        }
     }
     part[q][lane] = s;
     __syncthreads();

@@ -36,9 +36,10 @@ def test_robot_lin_fp32(amy, robot_ref, tmode, prec):
     compare_synthesis(amy, w, tmode, prec, ref=ref)
 
 
+@pytest.mark.parametrize("tmode", ["stored_full", "stored_factored"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32_kahan"])
-def test_stored_full_row_split(amy, robot_ref, prec):
-    """Wide stored full rows (the robot's dense 41 x 41 windows) are summed by
+def test_stored_row_split(amy, robot_ref, tmode, prec):
+    """Wide stored rows (the robot's dense 41 x 41 windows) are summed by
     groups of window rows, their pair sums reduced per state by a second
     kernel (backup kernel 6); without room in the budget for the pair sums
     one thread takes each pair (kernel 0).  Both match the oracle; they
@@ -46,13 +47,13 @@ def test_stored_full_row_split(amy, robot_ref, prec):
     sum) and their policies agree wherever the top-two gap is clear."""
     w, ref = robot_ref
     out, kernels = [], []
-    with amy.amy_build(w.problem, tmode="stored_full", prec=prec) as h:
+    with amy.amy_build(w.problem, tmode=tmode, prec=prec) as h:
         info = amy.amy_info(h)
         kernels.append(info["backup_kernel"])
         assert info["backup_launch_kernels"] == 2
         full_bytes = info["device_bytes"]
         out.append(amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True))
-    with amy.amy_build(w.problem, tmode="stored_full", prec=prec, device_mem_budget=full_bytes - 1) as h:
+    with amy.amy_build(w.problem, tmode=tmode, prec=prec, device_mem_budget=full_bytes - 1) as h:
         info = amy.amy_info(h)
         kernels.append(info["backup_kernel"])
         assert info["backup_launch_kernels"] == 1
@@ -64,7 +65,7 @@ def test_stored_full_row_split(amy, robot_ref, prec):
         sure = ref["gap"] > GAP[prec]
         assert not ((pi != ref["pi"]) & sure).any()
     assert float(np.max(np.abs(out[0][0].astype(np.float64) - out[1][0]))) <= (1e-14 if prec == "fp64" else 2e-6)
-    compare_synthesis(amy, w, "stored_full", prec, ref=ref)
+    compare_synthesis(amy, w, tmode, prec, ref=ref)
 
 
 def test_robot_lin_rows(amy):
@@ -515,3 +516,6 @@ def test_backup_kernel_reported_and_lane_load_ceilings(amy):
     # 152 SMs x 32 lanes x ~2 GHz is about 1e13 lane-loads/s for either path
     for k in ("shared", "global_l1"):
         assert 1e12 < peaks[k] < 3e13, peaks
+    # FP32: 152 SMs x 128 lanes x ~2 GHz is about 4e13 FMA/s; FP64 far below it
+    fma = amy.amy_measure_fma()
+    assert 1e13 < fma["fp32"] < 1e14 and 1e10 < fma["fp64"] < fma["fp32"], fma
