@@ -192,9 +192,10 @@ typedef struct {
                                    with one outer contraction per input run, 4 the
                                    per-run kernel on row tiles (k_backup_runs), 5 its
                                    persistent form: the whole horizon in one
-                                   cooperative launch (k_synth_runs), 6 stored rows
-                                   (full or factored) split over window-row groups
-                                   (k_backup_rows, then k_argmax_rows) */
+                                   cooperative launch (k_synth_runs), 6 wide rows
+                                   (stored full, stored factored or on the fly)
+                                   split over window-row groups (k_backup_rows or
+                                   k_backup_rows_otf, then k_argmax_rows) */
     int32_t input_runs;         /* runs of consecutive inputs sharing outer records */
     int32_t inner_span;         /* inner slots K one outer contraction covers (kernels 3, 4) */
     int32_t build_kernels;      /* kernels one table build (amy_build / amy_rebuild) launches */

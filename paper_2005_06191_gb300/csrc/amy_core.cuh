@@ -254,27 +254,66 @@ __device__ __forceinline__ void dim_masses_f32(const Geom &g, int d, double mu, 
 }
 
 // FP64 path: each cell's mass from its own two edges, as in Algorithm 1.
+// Slot k of dim d's window (origin o, kmax slots kept): its mass and V offset.
+__device__ __forceinline__ void slot_mass_f64(const Geom &g, int d, double mu, int32_t o, int kmax, int k,
+                                              double &fac, int32_t &off) {
+    const double k2 = g.k2[d];
+    const double h = dmul(0.5, g.eta[d]);
+    const double c = state_centre(g, d, o + k);
+    const double elo = dsub(c, h), ehi = dadd(c, h);
+    double mass;
+    if (elo >= mu)
+        mass = 0.5 * erfc(ddiv(dsub(elo, mu), k2)) - 0.5 * erfc(ddiv(dsub(ehi, mu), k2));
+    else if (ehi <= mu)
+        mass = 0.5 * erfc(ddiv(dsub(mu, ehi), k2)) - 0.5 * erfc(ddiv(dsub(mu, elo), k2));
+    else
+        mass = 1.0 - 0.5 * erfc(ddiv(dsub(mu, elo), k2)) - 0.5 * erfc(ddiv(dsub(ehi, mu), k2));
+    bool on;
+    const int32_t cell = cell_of(g, d, o + k, on);
+    fac = (on && k < kmax) ? mass : 0.0;
+    off = cell * g.stride[d];
+}
+
 __device__ __forceinline__ void dim_masses_f64(const Geom &g, int d, double mu, int32_t o,
                                                double *fac, int32_t *off) {
     const int W = g.W[d];
     const int kmax = kept_upper(g, d, mu, o);
-    const double k2 = g.k2[d];
-    const double h = dmul(0.5, g.eta[d]);
-    for (int k = 0; k < W; ++k) {
-        const double c = state_centre(g, d, o + k);
-        const double elo = dsub(c, h), ehi = dadd(c, h);
-        double mass;
-        if (elo >= mu)
-            mass = 0.5 * erfc(ddiv(dsub(elo, mu), k2)) - 0.5 * erfc(ddiv(dsub(ehi, mu), k2));
-        else if (ehi <= mu)
-            mass = 0.5 * erfc(ddiv(dsub(mu, ehi), k2)) - 0.5 * erfc(ddiv(dsub(mu, elo), k2));
-        else
-            mass = 1.0 - 0.5 * erfc(ddiv(dsub(mu, elo), k2)) - 0.5 * erfc(ddiv(dsub(ehi, mu), k2));
-        bool on;
-        const int32_t cell = cell_of(g, d, o + k, on);
-        fac[k] = (on && k < kmax) ? mass : 0.0;
-        off[k] = cell * g.stride[d];
-    }
+    for (int k = 0; k < W; ++k) slot_mass_f64(g, d, mu, o, kmax, k, fac[k], off[k]);
+}
+
+// One slot of dim_masses_f32 on its own: the same edge values (edge k is
+// fmaf(k, eta, e0), edge 0 is e0) and the same arithmetic, so the mass is
+// bit for bit the one the incremental loop gives.
+__device__ __forceinline__ void slot_mass_f32(const Geom &g, int d, double mu, int32_t o, int kmax, int k,
+                                              float &fac, int32_t &off) {
+    const double c0 = state_centre(g, d, o);
+    const float e0 = (float)dsub(dsub(c0, dmul(0.5, g.eta[d])), mu);
+    const float etaf = (float)g.eta[d];
+    const float r = g.rk2f[d];
+    const float dlo = k == 0 ? e0 : fmaf((float)k, etaf, e0);
+    const float dhi = fmaf((float)(k + 1), etaf, e0);
+    const float tlo = 0.5f * erfcf(fabsf(dlo) * r);
+    const float thi = 0.5f * erfcf(fabsf(dhi) * r);
+    float mass;
+    if (dlo >= 0.0f)
+        mass = tlo - thi;
+    else if (dhi <= 0.0f)
+        mass = thi - tlo;
+    else
+        mass = 1.0f - tlo - thi;
+    bool on;
+    const int32_t cell = cell_of(g, d, o + k, on);
+    fac = (on && k < kmax) ? fmaxf(mass, 0.0f) : 0.0f;
+    off = cell * g.stride[d];
+}
+
+__device__ __forceinline__ void slot_mass(const Geom &g, int d, double mu, int32_t o, int kmax, int k, double &fac,
+                                          int32_t &off) {
+    slot_mass_f64(g, d, mu, o, kmax, k, fac, off);
+}
+__device__ __forceinline__ void slot_mass(const Geom &g, int d, double mu, int32_t o, int kmax, int k, float &fac,
+                                          int32_t &off) {
+    slot_mass_f32(g, d, mu, o, kmax, k, fac, off);
 }
 
 template <class R>

@@ -517,12 +517,24 @@ amy_status launch_backup_t(amy_handle_s *h, int spec_kind, const VT *Vn, VT *Vo,
     a.O = h->d_O;
     a.npairs = h->npairs;
     a.tab = h->d_tab;
-    if constexpr (TM == TM_FULL || TM == TM_FACTORED) {
+    if constexpr (TM == TM_FULL || TM == TM_FACTORED || TM == TM_OTF) {
         if (h->d_split) {
             // split over window rows: pair sums, then max / argmax per state
             const dim3 grid((unsigned)((h->g.nx + 31) / 32), (unsigned)h->g.nu);
-            k_backup_rows<R, VT, TM, KAHAN><<<grid, dim3(32, (unsigned)h->split_groups), 0, h->stream>>>(
-                h->g, a, (R *)h->d_split);
+            const dim3 block(32, (unsigned)h->split_groups);
+            if constexpr (TM == TM_OTF) {
+                const size_t smem = (size_t)h->g.wsum * 32 * (sizeof(R) + sizeof(int32_t));
+                auto kern = k_backup_rows_otf<R, VT, KAHAN>;
+                static bool raised = false;
+                if (!raised) {
+                    AMY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024),
+                             "row-split smem attribute");
+                    raised = true;
+                }
+                kern<<<grid, block, smem, h->stream>>>(h->g, a, (R *)h->d_split);
+            } else {
+                k_backup_rows<R, VT, TM, KAHAN><<<grid, block, 0, h->stream>>>(h->g, a, (R *)h->d_split);
+            }
             AMY_CUDA(cudaGetLastError(), "backup launch");
             const int blocks = (int)std::min<int64_t>((h->g.nx + 255) / 256, 65535);
             k_argmax_rows<R, VT><<<blocks, 256, 0, h->stream>>>(h->g, a, (const R *)h->d_split);
@@ -1026,7 +1038,18 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
             free_handle(h);
             return cuda_error(e, "table index upload");
         }
-    } else if (h->tmode != AMY_T_ON_THE_FLY) {
+    } else if (h->tmode == AMY_T_ON_THE_FLY) {
+        // wide windows on the fly: split each pair's window over up to 8
+        // groups of rows, its masses shared in shared memory (at most 96 KiB)
+        const int rows = g.wtot / g.W[g.n - 1];
+        const size_t sbytes = (size_t)h->npairs * rsize(h);
+        const size_t smem = (size_t)g.wsum * 32 * (rsize(h) + sizeof(int32_t));
+        if (!fast_path(h) && g.wtot >= 256 && rows >= 2 && smem <= 96 * 1024 &&
+            (h->budget <= 0 || h->bytes + (int64_t)sbytes <= h->budget)) {
+            TRY(dev_alloc(h, &h->d_split, sbytes, "pair sums"));
+            h->split_groups = std::min(rows, ROWS_MAX_GROUPS);
+        }
+    } else {
         const int64_t per_pair = (h->tmode == AMY_T_STORED_FULL) ? g.wtot : g.wsum;
         TRY(dev_alloc(h, &h->d_T, (size_t)(h->npairs * per_pair) * rsize(h), "stored T"));
         TRY(dev_alloc(h, (void **)&h->d_O, (size_t)(h->npairs * g.n) * sizeof(int16_t), "stored origins"));

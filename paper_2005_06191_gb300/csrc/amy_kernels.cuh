@@ -374,7 +374,7 @@ __device__ __forceinline__ R window_rows_full(const Geom &g, const R *__restrict
 // The same for a factored row: row r's weight is the product of its outer
 // dims' masses taken left to right (the prefix product window_sum_factored
 // carries), rows of weight zero are skipped.
-template <class R, class VT, bool KAHAN>
+template <class R, class VT, bool KAHAN, int ST = 1>
 __device__ __forceinline__ R window_rows_factored(const Geom &g, const R *fac, const int32_t *off,
                                                   const VT *__restrict__ V, int r0, int r1) {
     const int n = g.n;
@@ -397,12 +397,13 @@ __device__ __forceinline__ R window_rows_factored(const Geom &g, const R *fac, c
         R w = R(1);
         int32_t base = 0;
         for (int d = 0; d < n - 1; ++d) {
-            w *= fac[fb[d] + k[d]];
-            base += off[fb[d] + k[d]];
+            w *= fac[(fb[d] + k[d]) * ST];
+            base += off[(fb[d] + k[d]) * ST];
         }
         if (w != R(0)) {
             R inner = R(0);
-            for (int j = 0; j < WL; ++j) inner = fma_r(fac[bL + j], vload<R, VT>(V + base + off[bL + j]), inner);
+            for (int j = 0; j < WL; ++j)
+                inner = fma_r(fac[(bL + j) * ST], vload<R, VT>(V + base + off[(bL + j) * ST]), inner);
             accum<R, KAHAN>(acc, comp, w * inner);
         }
         for (int d = n - 2; d >= 0; --d) {
@@ -439,6 +440,56 @@ __global__ void __launch_bounds__(32 * ROWS_MAX_GROUPS) k_backup_rows(const __gr
             row_setup_stored<R>(g, a.T, a.O, a.npairs, pair, true, fac, off, nullptr);
             s = window_rows_factored<R, VT, KAHAN>(g, fac, off, a.Vn, r0, r1);
         }
+    }
+    part[q][lane] = s;
+    __syncthreads();
+    if (q == 0 && x < g.nx) {
+        R acc = R(0), comp = R(0);
+        for (int i = 0; i < G; ++i) accum<R, KAHAN>(acc, comp, part[i][lane]);
+        S[(int64_t)u * g.nx + x] = live ? acc : R(-1);
+    }
+}
+
+// The same split for rows on the fly.  The pair's masses are computed once
+// per block and shared: group q evaluates the slots q, q + G, ... of the
+// concatenated per-dim windows (the mean and origins in FP64, each slot's
+// mass as dim_masses computes it) into shared memory, laid out [slot][lane]
+// so that the row sums read them without bank conflicts; then every group
+// sums its window rows from there.
+template <class R, class VT, bool KAHAN>
+__global__ void __launch_bounds__(32 * ROWS_MAX_GROUPS) k_backup_rows_otf(const __grid_constant__ Geom g,
+                                                                          const BackupArgs<R, VT> a,
+                                                                          R *__restrict__ S) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sfac = reinterpret_cast<R *>(smem_raw);                            // [wsum][32]
+    int32_t *soff = reinterpret_cast<int32_t *>(sfac + (size_t)g.wsum * 32);  // [wsum][32]
+    __shared__ R part[ROWS_MAX_GROUPS][32];
+    const int lane = threadIdx.x, q = threadIdx.y, G = blockDim.y;
+    const int32_t x = (int32_t)blockIdx.x * 32 + lane;
+    const int32_t u = (int32_t)blockIdx.y;
+    const bool live = x < g.nx && !state_masked(a.spec_kind, a.mask[x]);
+    if (live) {
+        double mu[MAXD];
+        mean_of(g, x, u, mu);
+        int d = 0, b = 0;
+        int32_t o = origin_of(g, 0, mu[0]);
+        int kmax = kept_upper(g, 0, mu[0], o);
+        for (int sl = q; sl < g.wsum; sl += G) {
+            while (sl >= b + g.W[d]) {
+                b += g.W[d];
+                ++d;
+                o = origin_of(g, d, mu[d]);
+                kmax = kept_upper(g, d, mu[d], o);
+            }
+            slot_mass(g, d, mu[d], o, kmax, sl - b, sfac[sl * 32 + lane], soff[sl * 32 + lane]);
+        }
+    }
+    __syncthreads();
+    R s = R(0);
+    if (live) {
+        const int rows = g.wtot / g.W[g.n - 1];
+        const int r0 = (int)((int64_t)rows * q / G), r1 = (int)((int64_t)rows * (q + 1) / G);
+        s = window_rows_factored<R, VT, KAHAN, 32>(g, sfac + lane, soff + lane, a.Vn, r0, r1);
     }
     part[q][lane] = s;
     __syncthreads();

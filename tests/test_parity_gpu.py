@@ -36,10 +36,11 @@ def test_robot_lin_fp32(amy, robot_ref, tmode, prec):
     compare_synthesis(amy, w, tmode, prec, ref=ref)
 
 
-@pytest.mark.parametrize("tmode", ["stored_full", "stored_factored"])
+@pytest.mark.parametrize("tmode", ["stored_full", "stored_factored", "otf"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32_kahan"])
-def test_stored_row_split(amy, robot_ref, tmode, prec):
-    """Wide stored rows (the robot's dense 41 x 41 windows) are summed by
+def test_wide_row_split(amy, robot_ref, tmode, prec):
+    """Wide rows (the robot's dense 41 x 41 windows; stored, or on the fly with
+    each pair's masses computed once per block into shared memory) are summed by
     groups of window rows, their pair sums reduced per state by a second
     kernel (backup kernel 6); without room in the budget for the pair sums
     one thread takes each pair (kernel 0).  Both match the oracle; they
@@ -508,7 +509,7 @@ def test_backup_kernel_reported_and_lane_load_ceilings(amy):
     expect = [(W.rooms7(n_per_dim=4, horizon=1), "stored_separable", 1),   # 7-D: register-resident
               (W.random_affine(np.random.default_rng(3), 2, [37, 30], 6, window=[3, 3]), "stored_separable", 2),
               (W.robot_lin(), "stored_full", 6),     # dense 41-wide stored rows: split over window rows
-              (W.robot_lin(), "otf", 0)]             # 41-wide rows on the fly: generic
+              (W.robot_lin(), "otf", 6)]             # 41-wide rows on the fly: the same split
     for w, tmode, kern in expect:
         with amy.amy_build(w.problem, tmode=tmode, prec="fp32") as h:
             assert amy.amy_info(h)["backup_kernel"] == kern, (w.problem.name, tmode)
