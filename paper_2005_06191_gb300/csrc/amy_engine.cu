@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <utility>
@@ -435,6 +436,37 @@ amy_status dev_alloc(amy_handle_s *h, void **p, size_t bytes, const char *what) 
     return AMY_OK;
 }
 
+// Page-locked words the handles read their barrier error flag into, handed
+// out from 4 KiB pages that stay allocated until the process exits: one
+// page-locked allocation (and its release, which synchronises the device) per
+// handle cost a large share of building and destroying a small problem.
+struct PinnedWords {
+    std::mutex mu;
+    std::vector<int32_t *> free_words;
+    int32_t *take() {
+        std::lock_guard<std::mutex> lk(mu);
+        if (free_words.empty()) {
+            int32_t *page = nullptr;
+            if (cudaHostAlloc((void **)&page, 4096, cudaHostAllocPortable) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            for (int i = 0; i < 4096 / (int)sizeof(int32_t); ++i) free_words.push_back(page + i);
+        }
+        int32_t *w = free_words.back();
+        free_words.pop_back();
+        return w;
+    }
+    void give(int32_t *w) {
+        std::lock_guard<std::mutex> lk(mu);
+        free_words.push_back(w);
+    }
+};
+PinnedWords &pinned_words() {
+    static PinnedWords *p = new PinnedWords();  // never destroyed: handles may outlive static destructors
+    return *p;
+}
+
 void free_handle(amy_handle_s *h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
@@ -448,7 +480,7 @@ void free_handle(amy_handle_s *h) {
     cudaFree(h->d_tab);
     cudaFree(h->d_bar);
     cudaFree(h->d_stage);
-    if (h->h_err) cudaFreeHost(h->h_err);
+    if (h->h_err) pinned_words().give(h->h_err);
     for (auto &p : h->ev_backup) h->ev_pool.push_back(p.first), h->ev_pool.push_back(p.second);
     for (auto &p : h->ev_build) h->ev_pool.push_back(p.first), h->ev_pool.push_back(p.second);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -1088,10 +1120,10 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     h->synth_ok = 0;
     if (fast_path(h) && h->tmode == AMY_T_STORED_SEPARABLE && h->grouped) {
         TRY(dev_alloc(h, (void **)&h->d_bar, kBarWords * sizeof(unsigned), "barrier words"));
-        e = cudaHostAlloc((void **)&h->h_err, sizeof(int32_t), cudaHostAllocDefault);
-        if (e != cudaSuccess) {
+        h->h_err = pinned_words().take();
+        if (!h->h_err) {
             free_handle(h);
-            return cuda_error(e, "barrier flag host word");
+            return set_error(AMY_E_CUDA, "barrier flag host word: page-locked allocation failed");
         }
         e = cudaMemsetAsync(h->d_bar, 0, kBarWords * sizeof(unsigned), h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
