@@ -490,6 +490,12 @@ void free_handle(amy_handle_s *h) {
     delete h;
 }
 
+// Whether splitting each pair's window rows over thread groups can help:
+// only when one thread per pair leaves the GPU's thread slots (2048 per SM)
+// unfilled; with more pairs than that the generic kernel already keeps every
+// SM busy and the split would only add the pair sums' round trip.
+bool split_pays(const amy_handle_s *h) { return h->npairs < (int64_t)h->sm_count * 2048; }
+
 // The host-output staging buffer, at least `bytes` long.  Grown with the
 // stream idle (the previous call's copies out of it have completed).  It is
 // outside the device-memory budget (a call with host outputs must not fail
@@ -1076,7 +1082,7 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
         const int rows = g.wtot / g.W[g.n - 1];
         const size_t sbytes = (size_t)h->npairs * rsize(h);
         const size_t smem = (size_t)g.wsum * 32 * (rsize(h) + sizeof(int32_t));
-        if (!fast_path(h) && g.wtot >= 256 && rows >= 2 && smem <= 96 * 1024 &&
+        if (!fast_path(h) && g.wtot >= 256 && rows >= 2 && smem <= 96 * 1024 && split_pays(h) &&
             (h->budget <= 0 || h->bytes + (int64_t)sbytes <= h->budget)) {
             TRY(dev_alloc(h, &h->d_split, sbytes, "pair sums"));
             h->split_groups = std::min(rows, ROWS_MAX_GROUPS);
@@ -1089,7 +1095,7 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
         // rows when the pair sums fit the budget (else one thread per pair)
         const int rows = g.wtot / g.W[g.n - 1];
         const size_t sbytes = (size_t)h->npairs * rsize(h);
-        if (g.wtot >= 256 && rows >= 2 &&
+        if (g.wtot >= 256 && rows >= 2 && split_pays(h) &&
             (h->budget <= 0 || h->bytes + (int64_t)sbytes <= h->budget)) {
             TRY(dev_alloc(h, &h->d_split, sbytes, "pair sums"));
             h->split_groups = std::min(rows, ROWS_MAX_GROUPS);
