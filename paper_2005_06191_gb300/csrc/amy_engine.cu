@@ -563,12 +563,11 @@ amy_status launch_backup_t(amy_handle_s *h, int spec_kind, const VT *Vn, VT *Vo,
             if constexpr (TM == TM_OTF) {
                 const size_t smem = (size_t)h->g.wsum * 32 * (sizeof(R) + sizeof(int32_t));
                 auto kern = k_backup_rows_otf<R, VT, KAHAN>;
-                static bool raised = false;
-                if (!raised) {
-                    AMY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024),
+                // above the default 48 KiB the kernel needs the opt-in (set on
+                // every such launch: the attribute is per device)
+                if (smem > 48 * 1024)
+                    AMY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                              "row-split smem attribute");
-                    raised = true;
-                }
                 kern<<<grid, block, smem, h->stream>>>(h->g, a, (R *)h->d_split);
             } else {
                 k_backup_rows<R, VT, TM, KAHAN><<<grid, block, 0, h->stream>>>(h->g, a, (R *)h->d_split);
