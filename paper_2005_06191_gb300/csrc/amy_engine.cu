@@ -368,6 +368,11 @@ struct amy_handle_s {
     // over window rows (k_backup_rows), its pair sums S[u][x] kept here, or null
     void *d_split;
     int32_t split_groups;
+    // wide stored rows: the build runs one thread per (slot, pair)
+    // (k_build_slots); stored full rows take their per-slot masses from
+    // d_bfac (wsum x pairs) and expand them (k_build_expand)
+    int32_t slot_build;
+    void *d_bfac;
     int64_t npairs;
     void *d_V[2];         // V ping-pong (interior start)
     void *d_Vbase[2];     // allocations: kVGuard finite guard cells on each side
@@ -474,6 +479,7 @@ void free_handle(amy_handle_s *h) {
     cudaFree(h->d_T);
     cudaFree(h->d_O);
     cudaFree(h->d_split);
+    cudaFree(h->d_bfac);
     cudaFree(h->d_Vbase[0]);
     cudaFree(h->d_Vbase[1]);
     cudaFree(h->d_mask);
@@ -792,6 +798,20 @@ amy_status launch_build(amy_handle_s *h) {
         tm.done();
         return st;
     }
+    if (h->slot_build) {
+        const int64_t items = (int64_t)h->g.wsum * h->npairs;
+        const int bs = (int)std::min<int64_t>((items + 255) / 256, (int64_t)h->sm_count * 64);
+        R *F = h->tmode == AMY_T_STORED_FULL ? (R *)h->d_bfac : (R *)h->d_T;
+        k_build_slots<R><<<bs, 256, 0, h->stream>>>(h->g, F, h->d_O, h->npairs);
+        if (h->tmode == AMY_T_STORED_FULL) {
+            const int64_t entries = (int64_t)h->g.wtot * h->npairs;
+            const int be = (int)std::min<int64_t>((entries + 255) / 256, (int64_t)h->sm_count * 64);
+            k_build_expand<R><<<be, 256, 0, h->stream>>>(h->g, F, (R *)h->d_T, h->npairs);
+        }
+        tm.done();
+        AMY_CUDA(cudaGetLastError(), "build launch");
+        return AMY_OK;
+    }
     const int blocks = (int)std::min<int64_t>((h->npairs + 127) / 128, (int64_t)h->sm_count * 32);
     if (h->tmode == AMY_T_STORED_FULL)
         k_build<R, TM_FULL><<<blocks, 128, 0, h->stream>>>(h->g, (R *)h->d_T, h->d_O, h->npairs);
@@ -1090,9 +1110,23 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
         const int64_t per_pair = (h->tmode == AMY_T_STORED_FULL) ? g.wtot : g.wsum;
         TRY(dev_alloc(h, &h->d_T, (size_t)(h->npairs * per_pair) * rsize(h), "stored T"));
         TRY(dev_alloc(h, (void **)&h->d_O, (size_t)(h->npairs * g.n) * sizeof(int16_t), "stored origins"));
-        // wide stored rows: split each pair's window over up to 8 groups of
-        // rows when the pair sums fit the budget (else one thread per pair)
+        // wide stored rows with few pairs: the build runs per (slot, pair)
+        // (full rows need the per-slot masses in a buffer of their own, when
+        // it fits the budget), and the backup splits each pair's window over
+        // up to 8 groups of rows when the pair sums fit (else one thread per
+        // pair does each)
         const int rows = g.wtot / g.W[g.n - 1];
+        if (g.wtot >= 256 && split_pays(h)) {
+            if (h->tmode == AMY_T_STORED_FACTORED) {
+                h->slot_build = 1;
+            } else {
+                const size_t fbytes = (size_t)h->npairs * g.wsum * rsize(h);
+                if (h->budget <= 0 || h->bytes + (int64_t)fbytes <= h->budget) {
+                    TRY(dev_alloc(h, &h->d_bfac, fbytes, "per-slot masses"));
+                    h->slot_build = 1;
+                }
+            }
+        }
         const size_t sbytes = (size_t)h->npairs * rsize(h);
         if (g.wtot >= 256 && rows >= 2 && split_pays(h) &&
             (h->budget <= 0 || h->bytes + (int64_t)sbytes <= h->budget)) {
@@ -1197,7 +1231,7 @@ amy_status amy_info(amy_handle h, amy_info_t *out) {
     }
     out->input_runs = h->runs;
     out->build_kernels = h->tmode == AMY_T_ON_THE_FLY ? 0
-                         : h->tmode != AMY_T_STORED_SEPARABLE ? 1
+                         : h->tmode != AMY_T_STORED_SEPARABLE ? (h->slot_build && h->tmode == AMY_T_STORED_FULL ? 2 : 1)
                          : (h->g.shoff > 0 && h->g.tsx[h->g.n - 1][h->g.n - 1] != 0) ? 3 : 2;
     return AMY_OK;
 }
