@@ -569,67 +569,6 @@ __global__ void __launch_bounds__(128) k_build(const __grid_constant__ Geom g, R
 }
 
 // ---------------------------------------------------------------------------
-// Stored-row construction for wide windows with few pairs (where one thread
-// per pair leaves the GPU idle): one thread per (window slot, pair) computes
-// that slot's mass (the mean and origin in FP64, the mass as dim_masses does)
-// into F[slot][pair] -- the factored layout -- and the first slot of each dim
-// writes the pair's origin; k_build_expand then forms each full-row entry as
-// the product of its dims' masses in the order k_build multiplies them.
-// ---------------------------------------------------------------------------
-template <class R>
-__global__ void __launch_bounds__(256) k_build_slots(const __grid_constant__ Geom g, R *__restrict__ F,
-                                                     int16_t *__restrict__ O, int64_t npairs) {
-    const int64_t total = (int64_t)g.wsum * npairs;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t sl = (int32_t)(i / npairs);
-        const int64_t pair = i - (int64_t)sl * npairs;
-        const int32_t u = (int32_t)(pair / g.nx);
-        const int32_t x = (int32_t)(pair - (int64_t)u * g.nx);
-        int d = 0, b = 0;
-        while (sl >= b + g.W[d]) {
-            b += g.W[d];
-            ++d;
-        }
-        double mu[MAXD];
-        mean_of(g, x, u, mu);
-        const int32_t o = origin_of(g, d, mu[d]);
-        const int kmax = kept_upper(g, d, mu[d], o);
-        R m;
-        int32_t off;
-        slot_mass(g, d, mu[d], o, kmax, sl - b, m, off);
-        F[i] = m;
-        if (sl == b) O[(int64_t)d * npairs + pair] = (int16_t)o;
-    }
-}
-
-template <class R>
-__global__ void __launch_bounds__(256) k_build_expand(const __grid_constant__ Geom g, const R *__restrict__ F,
-                                                      R *__restrict__ T, int64_t npairs) {
-    int fb[MAXD];
-    int acc = 0;
-    for (int d = 0; d < g.n; ++d) {
-        fb[d] = acc;
-        acc += g.W[d];
-    }
-    const int64_t total = (int64_t)g.wtot * npairs;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t t = (int32_t)(i / npairs);
-        const int64_t pair = i - (int64_t)t * npairs;
-        int k[MAXD];
-        int32_t rem = t;
-        for (int d = g.n - 1; d >= 0; --d) {
-            k[d] = rem % g.W[d];
-            rem /= g.W[d];
-        }
-        R v = R(1);
-        for (int d = 0; d < g.n; ++d) v = v * F[(int64_t)(fb[d] + k[d]) * npairs + pair];
-        T[i] = v;
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Row query: origin and window probabilities (double) of listed pairs.
 // ---------------------------------------------------------------------------
 template <class R>
