@@ -266,9 +266,10 @@ amy_status amy_rebuild(amy_handle h, const double *params, int64_t n_params);
  * for the recorded events, returns the summed durations (ms), the launch
  * counts and the number of backups those launches performed (one per launch,
  * or the whole horizon for the persistent kernel) since the previous call,
- * and resets them.  Any argument may be NULL.  It also reports
- * AMY_E_TIMEOUT when a persistent synthesis since the previous check gave up
- * waiting at a grid barrier (its outputs are then invalid). */
+ * and resets them (a backup launch of backup kernel 6 runs two kernels:
+ * amy_info backup_launch_kernels).  Any argument may be NULL.  It also
+ * reports AMY_E_TIMEOUT when a persistent synthesis since the previous check
+ * gave up waiting between backups (its outputs are then invalid). */
 amy_status amy_set_profiling(amy_handle h, int32_t on);
 
 /* Polls a wait between backups of the persistent horizon kernel
