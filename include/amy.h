@@ -293,11 +293,26 @@ amy_status amy_set_wait_limit(amy_handle h, int32_t polls);
  * AMY_E_INVALID_ARG.  The paper has no counterpart (it launches one backup
  * after another). */
 amy_status amy_set_step_wait(amy_handle h, int32_t mode);
+
+/* The kernel times amy_set_profiling collects (see there): summed backup and
+ * build durations in ms, their launch counts and the backups performed.
+ * Waits for the recorded events.  Errors: INVALID_ARG (null handle),
+ * TIMEOUT (a persistent synthesis gave up), CUDA. */
 amy_status amy_kernel_times(amy_handle h, double *backup_ms, int64_t *backup_launches, int64_t *backup_steps,
                             double *build_ms, int64_t *build_launches);
 
+/* The handle's derived abstraction (Sec. 5.2: window widths and cut half
+ * widths per dim, window slots), its storage and precision, the device bytes
+ * it owns, and the backup kernel and launch shape its synthesis uses (fields
+ * of amy_info_t).  Writes *out; errors: INVALID_ARG (null argument), CUDA. */
 amy_status amy_info(amy_handle h, amy_info_t *out);
+
+/* Releases the handle and everything it owns on the device after its stream
+ * has drained.  NULL is ignored; the handle must not be used afterwards. */
 void amy_destroy(amy_handle h);
+
+/* The message of the calling thread's last failed call (empty if none).  The
+ * pointer stays valid until that thread's next call into the library. */
 const char *amy_last_error(void);
 
 /* ------------------------------------------------------------------------
