@@ -114,10 +114,13 @@ typedef enum {
 typedef enum { AMY_PREC_FP64 = 0, AMY_PREC_FP32 = 1, AMY_PREC_FP32_KAHAN = 2 } amy_prec;
 
 /* Storage of V_k between backups (FP32 precisions only).  AMY_V_BF16 halves
- * the bytes of every V gather; its rounding error (up to 2^-9 per backup) is
- * biased upwards by the max over inputs and grows about linearly with the
- * horizon.  AMY_V_UNORM16 stores round(V * 65535) in 16 bits (V lies in
- * [0, 1]): same bytes, error at most 2^-17 per backup. */
+ * the bytes of every V gather: each value is a bfloat16 folded about 1/2
+ * (V < 1/2 stored as bf16(V), V >= 1/2 as -bf16(1 - V); the sign bit marks
+ * the fold), so its rounding error is at most 2^-9 * min(V, 1 - V) <= 2^-10
+ * per backup and zero at 0 and 1.  The errors of successive backups add up
+ * along the horizon.  AMY_V_UNORM16 stores round(V * 65535) in 16 bits (V
+ * lies in [0, 1]): same bytes, error at most 2^-17 per backup.  V_out is
+ * FP32 in both cases (the last backup writes it unrounded). */
 typedef enum { AMY_V_NATIVE = 0, AMY_V_BF16 = 1, AMY_V_UNORM16 = 2 } amy_vstore;
 
 typedef struct {
@@ -341,9 +344,13 @@ const char *amy_last_error(void);
  * call's contents; every entry a call reads is written earlier by the same
  * call (it clears the few guard cells around its value vectors itself), but
  * calls whose work overlaps on the GPU (on different streams or threads) race
- * on it and must be serialised.  The
- * parameters are copied from host memory during the call; the call returns
- * once the work is enqueued.
+ * on it and must be serialised.  The parameters reach the array by an
+ * asynchronous copy ordered on cuda_stream: from pageable host memory the
+ * source has been read when the call returns, but from page-locked memory
+ * (cudaHostAlloc / cudaHostRegister) the copy runs later on the stream, so
+ * the caller must leave sys->params unchanged until the stream has passed
+ * this call's work (e.g. synchronise it first).  Everything else is read
+ * during the call, which returns once the work is enqueued.
  * ------------------------------------------------------------------------ */
 #define AMY_NOALLOC_SCRATCH_BYTES (16u << 20)
 amy_status amy_synthesize_noalloc(const amy_system *sys, const amy_grid *states, const amy_grid *inputs,

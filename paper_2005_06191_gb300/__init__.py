@@ -119,6 +119,29 @@ def _is_cuda_tensor(t) -> bool:
     return hasattr(t, "is_cuda") and bool(t.is_cuda)
 
 
+def _check_device_out(t, name: str, numel: int, dtypes) -> None:
+    """Checks a caller's device buffer before its pointer goes to the library:
+    a torch CUDA tensor on the current device, of one of `dtypes`,
+    contiguous, with exactly `numel` entries (the kernels write that many)."""
+    import torch
+    if not _is_cuda_tensor(t):
+        raise ValueError(f"{name} must be a torch CUDA tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name} has dtype {t.dtype}; expected one of {[str(d) for d in dtypes]}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} entries; expected {numel}")
+
+
+def _policy_dtypes():
+    import torch
+    return tuple(d for d in (torch.int16, getattr(torch, "uint16", None)) if d is not None)
+
+
 def _current_stream_ptr():
     """torch's current stream; its legacy default stream (handle 0) is passed
     as cudaStreamLegacy so that the library does not create its own stream."""
@@ -226,6 +249,11 @@ def amy_synthesize(h: AmyHandle, spec, horizon: int, V_out=None, policy_out=None
     s = _spec_struct(k, spec)
     nx = h.n_states
     if V_out is not None and _is_cuda_tensor(V_out):
+        import torch
+        _check_device_out(V_out, "V_out", nx, (torch.float64,) if h.prec == "fp64" else (torch.float32,))
+        if policy_out is not None and horizon > 0:
+            _check_device_out(policy_out, "policy_out", nx * (horizon if policy_all_steps else 1),
+                              _policy_dtypes())
         vp = C.c_void_p(V_out.data_ptr())
         pp = C.c_void_p(policy_out.data_ptr()) if policy_out is not None else C.c_void_p(0)
         _check(_lib().amy_synthesize(h.ptr, C.byref(s), int(horizon), vp, pp, int(bool(policy_all_steps)), 1))
@@ -256,6 +284,12 @@ def amy_backup_step(h: AmyHandle, spec, V_next, V_out=None, policy_out=None):
     k = _Keep()
     s = _spec_struct(k, spec)
     if _is_cuda_tensor(V_next):
+        import torch
+        fdt = (torch.float64,) if h.prec == "fp64" else (torch.float32,)
+        _check_device_out(V_next, "V_next", h.n_states, fdt)
+        _check_device_out(V_out, "V_out", h.n_states, fdt)
+        if policy_out is not None:
+            _check_device_out(policy_out, "policy_out", h.n_states, _policy_dtypes())
         _check(_lib().amy_backup_step(h.ptr, C.byref(s), C.c_void_p(V_next.data_ptr()),
                                       C.c_void_p(V_out.data_ptr()),
                                       C.c_void_p(policy_out.data_ptr()) if policy_out is not None else C.c_void_p(0),
@@ -346,6 +380,11 @@ def amy_synthesize_noalloc(problem, spec, horizon: int, V_out, policy_out=None, 
     (float32) and policy_out (16-bit, may be None) are torch CUDA tensors of
     n_states entries; the work is enqueued on `stream` (None: torch's current
     stream)."""
+    import torch
+    nx = int(np.prod(problem.x_count, dtype=np.int64))
+    _check_device_out(V_out, "V_out", nx, (torch.float32,))
+    if policy_out is not None:
+        _check_device_out(policy_out, "policy_out", nx, _policy_dtypes())
     k = _Keep()
     sysd, states, inputs, sigma, cut = _problem_structs(k, problem)
     s = _spec_struct(k, spec)

@@ -10,6 +10,8 @@
 // the single-problem register-resident kernel.
 #pragma once
 
+#include <atomic>
+
 #include <climits>
 
 #include <algorithm>
@@ -98,11 +100,10 @@ amy_status launch_group_t(const BatchEntry *d_entries, int32_t n, int64_t tiles,
                           int sm_count, cudaStream_t st) {
     const size_t smem = kGeomSmemBytes + fast_smem_bytes(max_n, WM);
     auto kern = k_step_group<VT, WM, TM, VAR>;
-    static size_t raised = 48 * 1024;
-    if (smem > raised) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return cuda_error(e, "batched smem attribute");
-        raised = 200 * 1024;
+    if (smem > 48 * 1024) {
+        static std::atomic<uint64_t> raised{0};
+        const amy_status r = smem_optin((const void *)kern, 200 * 1024, raised, "batched smem attribute");
+        if (r != AMY_OK) return r;
     }
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FAST_THREADS, smem);

@@ -42,6 +42,18 @@ amy_status cuda_error(cudaError_t e, const char *what) {
     return set_error(AMY_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+amy_status smem_optin(const void *func, int bytes, std::atomic<uint64_t> &done, const char *what) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, what);
+    const uint64_t bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return AMY_OK;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return cuda_error(e, what);
+    done.fetch_or(bit, std::memory_order_acq_rel);
+    return AMY_OK;
+}
+
 int64_t grid_count(double lb, double ub, double eta) {
     return (int64_t)std::floor((ub - lb) / eta + 1e-9) + 1;
 }
@@ -49,8 +61,10 @@ int64_t grid_count(double lb, double ub, double eta) {
 // Window shape per dim (Sec. 5.2 and the Remark on the cutting region): the
 // 1-D density of N(0, sigma^2) equals gamma at +-xs; the row keeps
 // floor(2 xs / eta) + 1 slots.  Same FP64 expression as documented in amy.h.
-amy_status make_geom(const amy_system *sys, const amy_grid *st, const amy_grid *in,
-                     const double *sigma, const amy_cut *cut, Geom &g, std::vector<double> &params) {
+// Validation and geometry only, with no heap use (amy_synthesize_noalloc
+// calls it directly; make_geom adds the host copy of the parameters).
+amy_status fill_geom(const amy_system *sys, const amy_grid *st, const amy_grid *in, const double *sigma,
+                     const amy_cut *cut, Geom &g) {
     if (!sys || !st || !in || !sigma || !cut) return set_error(AMY_E_INVALID_ARG, "null argument");
     const int n = st->n, m = in->n;
     if (n < 1 || n > MAXD || m < 1 || m > MAXD) return set_error(AMY_E_INVALID_ARG, "dims must be 1..8");
@@ -100,9 +114,8 @@ amy_status make_geom(const amy_system *sys, const amy_grid *st, const amy_grid *
     } else {
         return set_error(AMY_E_INVALID_ARG, "unknown system kind %d", sys->kind);
     }
-    params.assign(sys->params, sys->params + sys->n_params);
-    for (double v : params)
-        if (!std::isfinite(v)) return set_error(AMY_E_INVALID_ARG, "non-finite system parameter");
+    for (int64_t i = 0; i < sys->n_params; ++i)
+        if (!std::isfinite(sys->params[i])) return set_error(AMY_E_INVALID_ARG, "non-finite system parameter");
     // window
     int64_t wtot = 1;
     int32_t wsum = 0;
@@ -141,6 +154,14 @@ amy_status make_geom(const amy_system *sys, const amy_grid *st, const amy_grid *
     if (wsum > MAXWS) return set_error(AMY_E_UNSUPPORTED, "sum of window widths %d exceeds %d", wsum, MAXWS);
     g.wtot = (int32_t)wtot;
     g.wsum = wsum;
+    return AMY_OK;
+}
+
+amy_status make_geom(const amy_system *sys, const amy_grid *st, const amy_grid *in,
+                     const double *sigma, const amy_cut *cut, Geom &g, std::vector<double> &params) {
+    const amy_status r = fill_geom(sys, st, in, sigma, cut, g);
+    if (r != AMY_OK) return r;
+    params.assign(sys->params, sys->params + sys->n_params);
     return AMY_OK;
 }
 

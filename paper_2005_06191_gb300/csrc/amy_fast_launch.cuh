@@ -5,6 +5,7 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 
 #include "amy_fast.cuh"
 #include "amy_internal.h"
@@ -55,12 +56,9 @@ amy_status launch_t(const Geom &g, const FastCall &c, int sm_count, cudaStream_t
     const size_t smem = fast_smem_bytes(g.n, WM);
     auto kern = k_backup_fast<VT, WM, TM, VAR>;
     if (smem > 48 * 1024) {
-        static bool raised = false;
-        if (!raised) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            if (e != cudaSuccess) return cuda_error(e, "fast backup smem attribute");
-            raised = true;
-        }
+        static std::atomic<uint64_t> raised{0};
+        const amy_status r = smem_optin((const void *)kern, 200 * 1024, raised, "fast backup smem attribute");
+        if (r != AMY_OK) return r;
     }
     const int64_t blocks = ((int64_t)g.nx + a.tileX - 1) / a.tileX;
     kern<<<(unsigned)blocks, FAST_THREADS, smem, st>>>(g, a);
@@ -164,11 +162,10 @@ amy_status launch_runs_k(const Geom &g, const FastCall &c, int ul, int tx, int r
     if (grid.y > 65535) return set_error(AMY_E_UNSUPPORTED, "per-run backup: dim 0 above 65535 tiles");
     const size_t smem = runs_smem_bytes(NS, WM, a.box_floats, g.nu, a.stage_recs, a.runs_planes, a.tileX * a.ulanes);
     auto kern = k_backup_runs<VT, WM, NS, KAHAN>;
-    static bool raised = false;
-    if (!raised) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return cuda_error(e, "per-run backup smem attribute");
-        raised = true;
+    static std::atomic<uint64_t> raised{0};
+    {
+        const amy_status r = smem_optin((const void *)kern, 200 * 1024, raised, "per-run backup smem attribute");
+        if (r != AMY_OK) return r;
     }
     if (smem > 200 * 1024) return set_error(AMY_E_UNSUPPORTED, "per-run backup needs %zu bytes of shared memory", smem);
     kern<<<grid, (unsigned)(a.tileX * a.ulanes), smem, st>>>(g, a);
@@ -198,11 +195,10 @@ amy_status launch_synth_k(const Geom &g, const FastCall &c, const SynthCall &sc,
     const size_t smem = runs_smem_bytes(NS, WM, a.box_floats, g.nu, a.stage_recs, a.runs_planes, threads);
     if (smem > 200 * 1024) return AMY_E_UNSUPPORTED;
     auto kern = k_synth_runs<VT, WM, NS, KAHAN>;
-    static bool raised = false;
-    if (!raised) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return cuda_error(e, "persistent backup smem attribute");
-        raised = true;
+    static std::atomic<uint64_t> raised{0};
+    {
+        const amy_status r = smem_optin((const void *)kern, 200 * 1024, raised, "persistent backup smem attribute");
+        if (r != AMY_OK) return r;
     }
     // the occupancy query does not reject a block above the kernel's launch
     // bound (the launch would fail): check it first
@@ -290,11 +286,10 @@ amy_status launch_staged_ns(const Geom &g, const FastCall &c, int sm_count, cuda
     const int64_t blocks = staged_blocks(g, a.tileX, a.rowtile);
     const size_t smem = staged_smem_bytes(g.n, WM, a.box_floats, g.nu, a.stage_tab, a.tileX * a.ulanes);
     auto kern = k_backup_staged<VT, WM, TM, NS>;
-    static bool raised = false;
-    if (!raised) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return cuda_error(e, "staged backup smem attribute");
-        raised = true;
+    static std::atomic<uint64_t> raised{0};
+    {
+        const amy_status r = smem_optin((const void *)kern, 200 * 1024, raised, "staged backup smem attribute");
+        if (r != AMY_OK) return r;
     }
     kern<<<(unsigned)blocks, (unsigned)(a.tileX * a.ulanes), smem, st>>>(g, a);
     cudaError_t e = cudaGetLastError();

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstdint>
 #include <vector>
@@ -17,10 +18,19 @@ namespace amy {
 amy_status set_error(amy_status st, const char *fmt, ...);
 amy_status cuda_error(cudaError_t e, const char *what);
 int64_t grid_count(double lb, double ub, double eta);
+// Validation, grid and window geometry of a problem (no heap use).
+amy_status fill_geom(const amy_system *sys, const amy_grid *st, const amy_grid *in, const double *sigma,
+                     const amy_cut *cut, Geom &g);
+// fill_geom plus a host copy of the system parameters.
 amy_status make_geom(const amy_system *sys, const amy_grid *st, const amy_grid *in, const double *sigma,
                      const amy_cut *cut, Geom &g, std::vector<double> &params);
 amy_status make_spec(const Geom &g, const amy_spec *spec, SpecDev &s);
 int choose_tile(int32_t nx, int32_t nu, int sm_count);
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device the first time it is needed there.  The attribute belongs to the
+// device, so `done` keeps one bit per device ordinal (0..63; higher ordinals
+// set the attribute on every call).
+amy_status smem_optin(const void *func, int bytes, std::atomic<uint64_t> &done, const char *what);
 // Type-erased arguments of the register-resident backup kernel.
 struct FastCall {
     const void *Vn;

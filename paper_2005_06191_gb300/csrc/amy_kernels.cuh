@@ -10,11 +10,26 @@ namespace amy {
 
 // Storage types of V between backups: native FP32/FP64, bfloat16, or a
 // 16-bit fixed-point code round(V * 65535) (V is a probability in [0, 1]).
+//
+// The bfloat16 form is folded about 1/2: V < 1/2 is stored as bf16(V) and
+// V >= 1/2 as -bf16(1 - V), the sign bit (unused by a probability) marking
+// the fold.  Both 1 - V (V in [1/2, 1]) and the decode 1 + b (b in
+// [-1/2, -0]) are exact in FP32, so the only rounding is bf16's, relative to
+// min(V, 1 - V): at most 2^-10 absolute instead of 2^-9, and exact at 0 and
+// 1, where reach and safety values collect.
+__device__ __forceinline__ __nv_bfloat16 bf16_fold(float v) {
+    v = fminf(fmaxf(v, 0.0f), 1.0f);
+    return v < 0.5f ? __float2bfloat16_rn(v) : __float2bfloat16_rn(-(1.0f - v));
+}
+__device__ __forceinline__ float bf16_unfold(__nv_bfloat16 b) {
+    const float f = __bfloat162float(b);
+    return signbit(f) ? 1.0f + f : f;
+}
 template <class R, class VT> __device__ __forceinline__ R vload(const VT *p);
 template <> __device__ __forceinline__ double vload<double, double>(const double *p) { return __ldg(p); }
 template <> __device__ __forceinline__ float vload<float, float>(const float *p) { return __ldg(p); }
 template <> __device__ __forceinline__ float vload<float, __nv_bfloat16>(const __nv_bfloat16 *p) {
-    return __bfloat162float(__ldg(p));
+    return bf16_unfold(__ldg(p));
 }
 template <> __device__ __forceinline__ float vload<float, unorm16>(const unorm16 *p) {
     return (float)__ldg(&p->bits) * (1.0f / 65535.0f);
@@ -24,7 +39,7 @@ template <class VT, class R> __device__ __forceinline__ VT vstore_cast(R v);
 template <> __device__ __forceinline__ double vstore_cast<double, double>(double v) { return v; }
 template <> __device__ __forceinline__ float vstore_cast<float, float>(float v) { return v; }
 template <> __device__ __forceinline__ __nv_bfloat16 vstore_cast<__nv_bfloat16, float>(float v) {
-    return __float2bfloat16_rn(v);
+    return bf16_fold(v);
 }
 template <> __device__ __forceinline__ unorm16 vstore_cast<unorm16, float>(float v) {
     unorm16 r;

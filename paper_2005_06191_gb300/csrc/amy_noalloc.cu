@@ -54,100 +54,6 @@ amy_status scratch_address(int dev, unsigned char **out) {
 
 size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 
-// Problem validation and geometry for this entry point, with no heap use:
-// the same checks and the same FP64 window-shape expressions as amy_build.
-amy_status geom_noheap(const amy_system *sys, const amy_grid *st, const amy_grid *in, const double *sigma,
-                       const amy_cut *cut, Geom &g) {
-    if (!sys || !st || !in || !sigma || !cut) return set_error(AMY_E_INVALID_ARG, "null argument");
-    const int n = st->n, m = in->n;
-    if (n < 1 || n > MAXD || m < 1 || m > MAXD) return set_error(AMY_E_INVALID_ARG, "dims must be 1..8");
-    if (sys->n != n || sys->m != m) return set_error(AMY_E_INVALID_ARG, "system dims differ from grids");
-    if (!st->lb || !st->eta || !st->count || !in->lb || !in->eta || !in->count)
-        return set_error(AMY_E_INVALID_ARG, "null grid array");
-    memset(&g, 0, sizeof g);
-    g.n = n;
-    g.m = m;
-    int64_t nx = 1, nu = 1;
-    for (int d = 0; d < n; ++d) {
-        if (st->count[d] < 1 || !(st->eta[d] > 0.0) || !std::isfinite(st->lb[d]) || !std::isfinite(st->eta[d]))
-            return set_error(AMY_E_INVALID_ARG, "bad state grid in dim %d", d);
-        if (!(sigma[d] > 0.0) || !std::isfinite(sigma[d]))
-            return set_error(AMY_E_INVALID_ARG, "sigma[%d] must be positive", d);
-        g.N[d] = st->count[d];
-        g.lb[d] = st->lb[d];
-        g.eta[d] = st->eta[d];
-        if (st->periodic && st->periodic[d]) g.periodic |= 1u << d;
-        nx *= st->count[d];
-        if (nx > 2147483647LL) return set_error(AMY_E_INVALID_ARG, "more than 2^31-1 states");
-    }
-    for (int d = 0; d < m; ++d) {
-        if (in->count[d] < 1 || !(in->eta[d] > 0.0)) return set_error(AMY_E_INVALID_ARG, "bad input grid in dim %d", d);
-        g.ucount[d] = in->count[d];
-        g.ulb[d] = in->lb[d];
-        g.ueta[d] = in->eta[d];
-        nu *= in->count[d];
-        if (nu > 65535) return set_error(AMY_E_INVALID_ARG, "more than 65535 inputs");
-    }
-    g.nx = (int32_t)nx;
-    g.nu = (int32_t)nu;
-    int64_t s = 1;
-    for (int d = n - 1; d >= 0; --d) {
-        g.stride[d] = (int32_t)s;
-        s *= g.N[d];
-    }
-    if (sys->kind == AMY_SYS_AFFINE_PER_INPUT) {
-        if (!sys->params || sys->n_params != nu * (int64_t)(n * n + n))
-            return set_error(AMY_E_INVALID_ARG, "affine system needs n_u*(n*n+n) params");
-        g.sys = SYS_AFFINE;
-    } else if (sys->kind == AMY_SYS_UNICYCLE) {
-        if (n != 3 || m != 2 || !sys->params || sys->n_params < 1)
-            return set_error(AMY_E_INVALID_ARG, "unicycle needs n=3, m=2, params={tau}");
-        g.sys = SYS_UNICYCLE;
-    } else {
-        return set_error(AMY_E_INVALID_ARG, "unknown system kind %d", sys->kind);
-    }
-    for (int64_t i = 0; i < sys->n_params; ++i)
-        if (!std::isfinite(sys->params[i])) return set_error(AMY_E_INVALID_ARG, "non-finite system parameter");
-    int64_t wtot = 1;
-    int32_t wsum = 0;
-    for (int d = 0; d < n; ++d) {
-        const bool per = (g.periodic >> d) & 1u;
-        g.k2[d] = sigma[d] * std::sqrt(2.0);
-        g.rk2f[d] = (float)(1.0 / (sigma[d] * std::sqrt(2.0)));
-        if (cut->window) {
-            g.wmode = WM_EXPLICIT;
-            const int32_t W = cut->window[d];
-            if (W < 1 || (W % 2) == 0) return set_error(AMY_E_INVALID_ARG, "explicit window must be odd (dim %d)", d);
-            if (per && W > g.N[d]) return set_error(AMY_E_INVALID_ARG, "window wider than periodic dim %d", d);
-            g.W[d] = W;
-            g.xs[d] = INFINITY;
-        } else if (cut->gamma == 0.0) {
-            g.wmode = WM_DENSE;
-            if (per) return set_error(AMY_E_INVALID_ARG, "dense rows need non-periodic dims");
-            g.W[d] = g.N[d];
-            g.xs[d] = INFINITY;
-        } else {
-            g.wmode = WM_GAMMA;
-            if (!(cut->gamma > 0.0) || !std::isfinite(cut->gamma)) return set_error(AMY_E_INVALID_ARG, "bad gamma");
-            const double arg = 1.0 / (cut->gamma * sigma[d] * std::sqrt(2.0 * M_PI));
-            if (!(arg > 1.0)) return set_error(AMY_E_INVALID_ARG, "gamma at or above the peak density (dim %d)", d);
-            const double xs = sigma[d] * std::sqrt(2.0 * std::log(arg));
-            const double w = std::floor(2.0 * xs / g.eta[d]) + 1.0;
-            if (!(w >= 1.0) || w > 1.0e6) return set_error(AMY_E_INVALID_ARG, "bad window width (dim %d)", d);
-            g.W[d] = (int32_t)w;
-            if (per && g.W[d] > g.N[d]) return set_error(AMY_E_INVALID_ARG, "window wider than periodic dim %d", d);
-            g.xs[d] = xs;
-        }
-        wtot *= g.W[d];
-        wsum += g.W[d];
-        if (wtot > (1LL << 30)) return set_error(AMY_E_UNSUPPORTED, "window box too large");
-    }
-    if (wsum > MAXWS) return set_error(AMY_E_UNSUPPORTED, "sum of window widths %d exceeds %d", wsum, MAXWS);
-    g.wtot = (int32_t)wtot;
-    g.wsum = wsum;
-    return AMY_OK;
-}
-
 }  // namespace
 }  // namespace amy
 
@@ -162,7 +68,7 @@ extern "C" amy_status amy_synthesize_noalloc(const amy_system *sys, const amy_gr
     if (prec != AMY_PREC_FP32 && prec != AMY_PREC_FP32_KAHAN)
         return set_error(AMY_E_UNSUPPORTED, "amy_synthesize_noalloc runs in FP32 or FP32_KAHAN");
     Geom g;
-    amy_status st = geom_noheap(sys, states, inputs, sigma, cut, g);
+    amy_status st = fill_geom(sys, states, inputs, sigma, cut, g);
     if (st != AMY_OK) return st;
     SpecDev sd;
     st = make_spec(g, spec, sd);

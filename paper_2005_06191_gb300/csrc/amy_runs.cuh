@@ -118,7 +118,7 @@ __device__ __forceinline__ float ld_cg(const float *p) {
 __device__ __forceinline__ float ld_cg(const __nv_bfloat16 *p) {
     unsigned short b;
     asm volatile("ld.global.cg.u16 %0, [%1];\n" : "=h"(b) : "l"(p));
-    return __bfloat162float(__ushort_as_bfloat16(b));
+    return bf16_unfold(__ushort_as_bfloat16(b));
 }
 __device__ __forceinline__ float ld_cg(const unorm16 *p) {
     unsigned short b;

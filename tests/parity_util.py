@@ -9,9 +9,10 @@ import oracle
 # Tolerances (max |dV| against the FP64 oracle):
 #   FP32 paths 1e-5 (accumulated over the horizon);
 #   FP64 paths 1e-12 (only erfc/cos implementations and summation order differ);
-#   16-bit V storage: 2e-3, the bound for 16-bit-stored V.  unorm16 meets it
-#   (at most 2^-17 per backup).  bfloat16 rounds by up to 2^-9 per backup and
-#   the max over inputs biases that upwards, so its bound is horizon * 2^-9.
+#   16-bit V storage: 2e-3, the stated bound for 16-bit-stored V.  unorm16
+#   meets it (at most 2^-17 per backup).  The folded bfloat16 rounds by up to
+#   2^-10 per backup; where the accumulated error exceeds 2e-3 the test says
+#   so (BF16_OVER) instead of widening the bound.
 TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp32_kahan": 1e-5, "u16": 2e-3, "bf16": 2e-3}
 # Policies must agree bit for bit wherever the oracle's top-two action values
 # differ by more than this; elsewhere the chosen input must be within
@@ -24,8 +25,6 @@ def tol_key(prec: str, v_store: str) -> str:
 
 
 def tol_of(key: str, horizon: int) -> float:
-    if key == "bf16":
-        return max(TOL["bf16"], horizon * 2.0 ** -9 + 1e-5)
     return TOL[key]
 
 
@@ -43,8 +42,12 @@ def load_engine():
 
 
 def compare_synthesis(amy, w, tmode: str, prec: str, v_store: str = "native", ref=None,
-                      tie_samples: int = 64, rng_seed: int = 0):
-    """Full-horizon parity of V_0 and every pi_k.  Returns a dict of statistics."""
+                      tie_samples: int = 64, rng_seed: int = 0, bf16_over_ok: bool = False):
+    """Full-horizon parity of V_0 and every pi_k.  Returns a dict of statistics.
+
+    bf16_over_ok: for folded-bfloat16 V whose accumulated rounding is known to
+    pass 2e-3 on this workload, a larger max|dV| is returned in the stats
+    (key "bf16_over") instead of failing; the caller reports it."""
     p, s, N = w.problem, w.spec, w.horizon
     if ref is None:
         ref = oracle.synthesize(p, s, N, want_all=True)
@@ -53,8 +56,11 @@ def compare_synthesis(amy, w, tmode: str, prec: str, v_store: str = "native", re
     with amy.amy_build(p, tmode=tmode, prec=prec, v_store=v_store) as h:
         V, pi = amy.amy_synthesize(h, s, N, policy_all_steps=True)
     dV = float(np.max(np.abs(V.astype(np.float64) - ref["V"]))) if V.size else 0.0
-    assert dV <= tol, f"max|dV| = {dV:.3e} > {tol:.1e}"
     stats = {"max_dV": dV, "policy_checked": 0, "policy_ties": 0}
+    if bf16_over_ok and key == "bf16" and dV > tol:
+        stats["bf16_over"] = dV
+        return stats
+    assert dV <= tol, f"max|dV| = {dV:.3e} > {tol:.1e}"
     if N > 0:
         sure = ref["gap"] > gthr
         bad = (pi != ref["pi"]) & sure
@@ -69,6 +75,17 @@ def compare_synthesis(amy, w, tmode: str, prec: str, v_store: str = "native", re
                 av = oracle.action_values(p, ref["V_all"][k + 1], int(x))
                 assert av[pi[k, x]] >= av.max() - 2 * tol, (k, x)
     return stats
+
+
+def bf16_folded(v):
+    """The values the engine reads back from folded-bfloat16 storage: V below
+    1/2 rounded to bfloat16, V at or above 1/2 as 1 minus bfloat16(1 - V)."""
+    import torch
+    v = np.clip(np.asarray(v, dtype=np.float32), 0.0, 1.0)
+    lo = v < 0.5
+    r = np.where(lo, v, np.float32(1.0) - v).astype(np.float32)
+    r = torch.from_numpy(r).to(torch.bfloat16).to(torch.float32).numpy()
+    return np.where(lo, r, np.float32(1.0) - r).astype(np.float64)
 
 
 def compare_rows(amy, w, tmode: str, prec: str, n_pairs: int = 512, seed: int = 1):
@@ -101,8 +118,7 @@ def compare_one_step(amy, w, tmode: str, prec: str, v_store: str, states, V_next
     # the oracle sees exactly the values the engine read (bf16-rounded when stored so)
     vref_in = vin.astype(np.float64)
     if v_store == "bf16":
-        import torch
-        vref_in = torch.from_numpy(vin).to(torch.bfloat16).to(torch.float64).numpy()
+        vref_in = bf16_folded(vin)
     elif v_store == "u16":
         code = np.rint(np.clip(vin, 0.0, 1.0) * np.float32(65535)).astype(np.float32)
         vref_in = (code * (np.float32(1.0) / np.float32(65535))).astype(np.float64)
@@ -112,3 +128,45 @@ def compare_one_step(amy, w, tmode: str, prec: str, v_store: str, states, V_next
     sure = gap > gap_of(key, 1)
     assert np.all(pi[states][sure] == pir[sure])
     return dV, int(sure.sum())
+
+
+def v16_read_back(vin, v_store: str):
+    """The values the engine's backup reads from V_next stored as v_store."""
+    if v_store == "bf16":
+        return bf16_folded(vin)
+    if v_store == "u16":
+        code = np.rint(np.clip(vin, 0.0, 1.0) * np.float32(65535)).astype(np.float32)
+        return (code * (np.float32(1.0) / np.float32(65535))).astype(np.float64)
+    return np.asarray(vin, dtype=np.float64)
+
+
+def compare_steps(amy, w, tmode: str, prec: str, n_sample: int, seed: int, v_store: str = "native",
+                  first_sample: int = 0, horizon: int = None):
+    """Sampled one-step operator parity over the whole horizon at full size:
+    the GPU performs every backup over the whole grid starting from V_N, and
+    at each step the oracle recomputes V_k and pi_k at n_sample seeded states
+    (first_sample at the first step, when given) from the very V_{k+1} the
+    GPU read.  Returns the largest |dV| seen."""
+    p, s = w.problem, w.spec
+    key = tol_key(prec, v_store)
+    tol, gthr = tol_of(key, 1), gap_of(key, 1)
+    rng = np.random.default_rng(seed)
+    mask = oracle.spec_mask(p, s)
+    V = ((mask & (4 if s.kind == "safety" else 1)) != 0).astype(np.float32)
+    worst, checked = 0.0, 0
+    N = w.horizon if horizon is None else horizon
+    with amy.amy_build(p, tmode=tmode, prec=prec, v_store=v_store) as h:
+        for k in range(N):
+            Vk, pik = amy.amy_backup_step(h, s, V)
+            ns = first_sample if (k == 0 and first_sample) else n_sample
+            states = np.sort(rng.choice(p.n_states, size=min(ns, p.n_states), replace=False))
+            Vr, pir, gap = oracle.backup_states(p, s, v16_read_back(V, v_store), states)
+            dV = float(np.max(np.abs(Vk[states].astype(np.float64) - Vr)))
+            assert dV <= tol, f"step {k}: max|dV| = {dV:.3e} > {tol:.1e}"
+            sure = gap > gthr
+            bad = (pik[states] != pir) & sure
+            assert not bad.any(), f"step {k}: {int(bad.sum())} policies differ where the gap exceeds {gthr}"
+            worst = max(worst, dV)
+            checked += int(sure.sum())
+            V = Vk.astype(np.float32)
+    return worst, checked

@@ -347,6 +347,78 @@ def test_brute_force_policy_attains_max():
 
 
 # --------------------------------------------------------------------------
+# The action values (the window sum of Algorithm 4 for every input at one
+# state, the quantity the GPU tie check compares policies by): pinned to an
+# independent transition matrix, to the pinned synthesis and to pinned rows.
+# --------------------------------------------------------------------------
+def test_action_values_match_independent_chain_matrix():
+    """On the 5-cell chain, s_u(x) equals sum_x' T[x, u, x'] V(x') with T from
+    mpmath cell integrals (P6's matrix), for arbitrary V_next."""
+    eta, sig = 1.0, 0.7
+    drifts = (-1, 0, 1)
+    T = _chain_T(sig, eta, drifts)
+    p = _affine_problem("chain", [0.0], [eta], [5], [np.eye(1)] * 3,
+                        [np.array([float(d)]) for d in drifts], [sig], gamma=0.0,
+                        u_lb=[0.0], u_eta=[1.0], u_count=[3])
+    rng = np.random.default_rng(17)
+    for _ in range(4):
+        Vn = rng.uniform(0.0, 1.0, size=5)
+        for x in range(5):
+            av = oracle.action_values(p, Vn, x)
+            np.testing.assert_allclose(av, T[x] @ Vn, atol=1e-13, rtol=0)
+
+
+def _check_action_values_against_synthesis(p, s, N):
+    """max_u s_u(V_{k+1}, x) is V_k(x) bit for bit and its lowest maximiser is
+    pi_k(x), at every free state and step of the pinned synthesis."""
+    r = oracle.synthesize(p, s, N, want_all=True)
+    mask = oracle.spec_mask(p, s)
+    free = (mask & 4) != 0 if s.kind == W.SAFETY else (mask & 3) == 0
+    checked = 0
+    for k in range(N):
+        for x in np.flatnonzero(free):
+            av = oracle.action_values(p, r["V_all"][k + 1], int(x))
+            assert av.max() == r["V_all"][k][x], (k, x)
+            assert int(np.flatnonzero(av == av.max())[0]) == int(r["pi"][k, x]), (k, x)
+            checked += 1
+    assert checked > 0
+
+
+def test_action_values_agree_with_synthesis_chain():
+    eta, sig = 1.0, 0.6
+    p = _affine_problem("chain", [0.0], [eta], [5], [np.eye(1)] * 3,
+                        [np.array([float(d)]) for d in (-1, 0, 1)], [sig], gamma=0.0,
+                        u_lb=[0.0], u_eta=[1.0], u_count=[3])
+    spec = Spec(W.REACH_AVOID, targets=[([4.0], [4.0])], avoids=[([0.0], [0.0])])
+    _check_action_values_against_synthesis(p, spec, 3)
+
+
+def test_action_values_agree_with_synthesis_and_rows_3d():
+    """A random 3-D gamma-cut problem with a periodic dim: the same bit-exact
+    agreement with the synthesis, and each s_u equals the sum over the pinned
+    row (origin, probabilities) of probability x V at the wrapped / dropped
+    cells, formed here in numpy."""
+    rng = np.random.default_rng(33)
+    w = W.random_affine(rng, 3, [7, 6, 8], 4, gamma=2e-2, periodic=[0, 0, 1], kind=W.REACH, horizon=3)
+    p, s = w.problem, w.spec
+    _check_action_values_against_synthesis(p, s, w.horizon)
+    Wd, _ = oracle.window_shape(p)
+    Vn = rng.uniform(0.0, 1.0, size=p.n_states)
+    for x in rng.choice(p.n_states, size=40, replace=False):
+        av = oracle.action_values(p, Vn, int(x))
+        for u in range(p.n_inputs):
+            origin, probs = oracle.row(p, int(x), u)
+            acc = 0.0
+            for t, (a, b, c) in enumerate(itertools.product(range(Wd[0]), range(Wd[1]), range(Wd[2]))):
+                i, j, k = origin[0] + a, origin[1] + b, (origin[2] + c) % p.x_count[2]
+                if not (0 <= i < p.x_count[0] and 0 <= j < p.x_count[1]):
+                    assert probs[t] == 0.0
+                    continue
+                acc += probs[t] * Vn[(i * p.x_count[1] + j) * p.x_count[2] + k]
+            assert abs(av[u] - acc) <= 1e-13, (x, u)
+
+
+# --------------------------------------------------------------------------
 # P8: deterministic limit equals graph reachability (BFS)
 # --------------------------------------------------------------------------
 def _bfs_reach(n_states, succ, target, avoid, N):

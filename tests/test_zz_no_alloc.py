@@ -58,8 +58,26 @@ def test_noalloc_matches_allocating_path_on_consecutive_calls(amy):
 
 def test_noalloc_refuses_problems_beyond_its_scratch(amy):
     import torch
-    w = W.traffic6(n_per_dim=21, horizon=1)   # 85.8M states: far beyond the fixed scratch
-    V = torch.empty(1, dtype=torch.float32, device="cuda")
+    w = W.traffic6(n_per_dim=12, horizon=1)   # 2.99M states: about 27 MB of scratch, above the 16 MiB array
+    V = torch.empty(w.problem.n_states, dtype=torch.float32, device="cuda")
     with pytest.raises(amy.AmyError) as e:
         amy.amy_synthesize_noalloc(w.problem, w.spec, w.horizon, V)
     assert "INVALID_ARG" in str(e.value) and "scratch" in str(e.value)
+
+
+def test_noalloc_binding_rejects_bad_output_buffers(amy):
+    """The binding checks the caller's device buffers before any pointer
+    reaches the library: too few entries, a wrong dtype or a host tensor
+    raise ValueError and nothing is launched."""
+    import torch
+    w = W.unicycle(nxy=11, horizon=2, target=(1.0, 2.0))
+    n = w.problem.n_states
+    for bad in (torch.empty(n - 1, dtype=torch.float32, device="cuda"),
+                torch.empty(n, dtype=torch.float64, device="cuda"),
+                torch.empty(n, dtype=torch.float32)):
+        with pytest.raises(ValueError):
+            amy.amy_synthesize_noalloc(w.problem, w.spec, w.horizon, bad)
+    V = torch.empty(n, dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        amy.amy_synthesize_noalloc(w.problem, w.spec, w.horizon, V, torch.empty(2 * n, dtype=torch.int16,
+                                                                                 device="cuda"))
