@@ -1,16 +1,20 @@
 #!/usr/bin/env python
-"""Benchmark: Bellman transitions/s of the GB300 engine on the unicycle workload.
+"""Benchmark: Bellman transitions/s of the GB300 engine.
 
-Workload (the configuration the metric is quoted on): 3-D nonlinear unicycle,
-51 x 51 x 30 states (theta periodic), 45 inputs, sigma 0.05, gamma 1e-6
-(3 x 3 x 3 window), reach [8,10]^2 x all headings, horizon 32, FP32.
+Default workload: the largest configuration that fits one GPU, the 6-D linear
+traffic ring -- 21^6 = 85.8 M states, 4 inputs (two binary on-ramp lights),
+sigma 0.5, explicit 5^6 windows (15,625 slots), safety [0,18]^6, horizon 8,
+FP32 with Kahan-compensated window sums, per-dimension tables.  The other
+workloads (unicycle 51x51x30, robot 41x41, rooms 9^7, the served stream) run
+with --workload.
 
-One step = one pass of the whole hot path over the workload: the stored rows
-are rebuilt on the GPU (amy_rebuild), the spec mask and V_N are formed, and
-32 fused backups + max/argmax run, every pi_k written.  Transitions per step
-= n_states * n_inputs * prod(W) * horizon (every allocated window slot).
+One step = one pass of the whole hot path over the workload: the tables are
+rebuilt on the GPU (amy_rebuild), the spec mask and V_N are formed, and
+`horizon` fused backups + max/argmax run, every pi_k written.  Transitions
+per step = n_states * n_inputs * prod(W) * horizon (every allocated window
+slot).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl amy|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl amy|reference] [--workload ...]
 
 N > 1 runs one independent replica per GPU (weak scaling, no collective).
 --impl reference times the FP64 CPU oracle on the same workload.
@@ -36,6 +40,9 @@ import workloads as W  # noqa: E402
 
 WORKLOAD_NAME = ("unicycle 51x51x30 states (theta periodic), 45 inputs, sigma 0.05, gamma 1e-6 "
                  "(3x3x3 window), reach [8,10]^2, horizon 32")
+TRAFFIC_NAME = ("6-D traffic ring 21^6 states (85.8 M), 4 inputs, sigma 0.5, window 5^6, safety [0,18]^6, "
+                "horizon 8, FP32 + Kahan")
+DEFAULT_WORKLOAD = "traffic6"
 METRIC = "Bellman transitions/s (x*u*x' window slots * horizon)"
 UNIT = "transitions/s"
 
@@ -175,8 +182,7 @@ WORKLOADS = {
               "2-D linear robot 41x41 states, 25 inputs, sigma 0.2, dense rows, reach-avoid, horizon 8"),
     "rooms7": (lambda s: W.rooms7(n_per_dim=s or 9), "stored_separable", "fp32_kahan",
                "7-room temperature ring 9^7 states, 5 inputs, sigma 0.02, window 3^7, safety, horizon 10"),
-    "traffic6": (lambda s: W.traffic6(n_per_dim=s or 21), "stored_separable", "fp32_kahan",
-                 "6-D traffic ring 21^6 states, 4 inputs, sigma 0.5, window 5^6, safety [0,18]^6, horizon 8"),
+    "traffic6": (lambda s: W.traffic6(n_per_dim=s or 21), "stored_separable", "fp32_kahan", TRAFFIC_NAME),
 }
 
 
@@ -221,6 +227,8 @@ def run_amy(args, rank, world):
                       launch_shape=shape)
     if args.step_wait is not None:
         amy.amy_set_step_wait(h, args.step_wait)
+    if args.plane is not None or args.plane_smem:
+        amy.amy_set_plane(h, args.plane if args.plane is not None else 1, args.plane_smem)
     info = amy.amy_info(h)
     trans = transitions_per_step(w, info["window_slots"])
     V = torch.empty(p.n_states, dtype=torch.float64 if args.prec == "fp64" else torch.float32, device="cuda")
@@ -235,8 +243,12 @@ def run_amy(args, rank, world):
         step()
     torch.cuda.synchronize()
     lane_peaks = amy.amy_measure_lane_loads()  # roofline denominators (outside the timed region)
-    if args.prec == "fp64":
+    if args.prec == "fp64" or info["backup_kernel"] == 7:
         lane_peaks.update({"fma_" + k: v for k, v in amy.amy_measure_fma().items()})
+    if info["backup_kernel"] == 7:
+        lane_peaks["l2_bytes"] = amy.amy_measure_l2()
+    # the plane kernel's own work in one backup (counted in an untimed run)
+    work = amy.amy_backup_work(h, spec) if info["backup_kernel"] == 7 else None
     barrier(world)
     amy.amy_kernel_times(h)  # reset
     amy.amy_set_profiling(h, True)
@@ -259,6 +271,8 @@ def run_amy(args, rank, world):
     # (for the per-dimension tables: bounds reset + tables [+ shifted inner table])
     launches = (info["backup_launch_kernels"] * kt["backup_launches"] + info["build_kernels"] * kt["build_launches"]
                 + args.steps)
+    if info["backup_kernel"] == 7:
+        launches += args.steps  # the padded copy of V_N the plane kernel reads, once per synthesis
     # per backup: the persistent kernel performs the whole horizon in one launch
     bk_ms = kt["backup_ms"] / max(kt["backup_steps"], 1)
     launch_ms = kt["backup_ms"] / max(kt["backup_launches"], 1)
@@ -266,7 +280,7 @@ def run_amy(args, rank, world):
     V_host = V.cpu().numpy()
     # states whose value the spec fixes carry policy 0xFFFF and cost no backup work
     free = int((PI[0] != -1).sum().item())
-    roof = roofline(args, w, info, bk_ms, free, lane_peaks)
+    roof = roofline(args, w, info, bk_ms, free, lane_peaks, work)
     roof["backups_per_launch"] = kt["backup_steps"] / max(kt["backup_launches"], 1)
     roof["launch_ms"] = launch_ms
 
@@ -276,7 +290,8 @@ def run_amy(args, rank, world):
     # pinned host memory).  The handle (its device buffers and launch shape)
     # is set up once, as a caller solving a stream of problems of one shape
     # would.  e2e_cold adds amy_build and amy_destroy to every step.
-    e2e_steps = 0 if args.no_e2e else max(3, min(args.steps, 50))
+    heavy = trans > 1e12   # e.g. the 21^6 traffic ring: about a second per step
+    e2e_steps = 0 if args.no_e2e else (min(3, max(args.steps, 1)) if heavy else max(3, min(args.steps, 50)))
     pin_params = torch.from_numpy(np.asarray(p.params, dtype=np.float64)).pin_memory().numpy()
     h2d = pin_params.nbytes
     d2h = p.n_states * 4 + N * p.n_states * 2
@@ -299,7 +314,7 @@ def run_amy(args, rank, world):
         e2e = {"value": trans * e2e_steps * world / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "per_step": "amy_rebuild(params from pinned host memory) + amy_synthesize(host outputs, pinned)"}
-        cold_steps = max(1, min(e2e_steps, 5))
+        cold_steps = 1 if heavy else max(1, min(e2e_steps, 5))
         barrier(world)
         t0 = time.perf_counter()
         for _ in range(cold_steps):
@@ -319,7 +334,44 @@ def run_amy(args, rank, world):
     }
 
 
-def roofline(args, w, info, backup_ms, free, lane_peaks):
+def roofline_plane(args, w, info, backup_ms, work, lane_peaks):
+    """Roofline of the plane kernel (backup kernel 7) from the work it counts
+    in one backup (amy_backup_work): stage 1 streams V_{k+1} through L2 (each
+    staged row reads K values, coalesced across a plane), stage 2 reads the
+    partial box from shared memory, and both issue FP32 fused multiply-adds
+    (one per value read, plus W[n-2] + 1 per second-stage row).  Three
+    ceilings, each measured on this GPU (amy_measure_l2,
+    amy_measure_lane_loads, amy_measure_fma); the closest one is reported as
+    the bound and the others beside it."""
+    bk_s = backup_ms / 1e3
+    vbytes = 2 if args.v_store != "native" else 4
+    l2_bytes = work["v_loads"] * vbytes
+    fmas = work["v_loads"] + work["box_loads"] + work["box_rows"] * (info["window"][-2] + 1)
+    c_l2 = {"bound": "l2", "achieved": l2_bytes / bk_s / 1e9, "peak": lane_peaks["l2_bytes"] / 1e9,
+            "unit": "GB/s", "peak_source": "measured on this GPU by amy_measure_l2 (32 MiB L2-resident read)",
+            "algorithmic_bytes_per_backup": int(l2_bytes)}
+    c_sh = {"bound": "alu", "achieved": work["box_loads"] / bk_s / 1e9, "peak": lane_peaks["shared"] / 1e9,
+            "unit": "G shared lane-loads/s",
+            "peak_source": "measured on this GPU by amy_measure_lane_loads (shared path)",
+            "algorithmic_lane_loads_per_backup": int(work["box_loads"])}
+    c_fma = {"bound": "alu", "achieved": fmas / bk_s / 1e12, "peak": lane_peaks["fma_fp32"] / 1e12,
+             "unit": "T FMA/s (FP32)", "peak_source": "measured on this GPU by amy_measure_fma (FP32)",
+             "algorithmic_fmas_per_backup": int(fmas)}
+    cs = [c_l2, c_sh, c_fma]
+    for c in cs:
+        c["frac"] = c["achieved"] / c["peak"]
+    cs.sort(key=lambda c: -c["frac"])
+    first = dict(cs[0])
+    first["other_ceilings"] = [{k: c[k] for k in ("bound", "achieved", "peak", "unit", "frac")} for c in cs[1:]]
+    traffic, src = measured_traffic(args, w.problem.n_states)
+    first.update({"traffic": traffic, "traffic_source": src, "backup_kernel": 7,
+                  "work_per_backup": work,
+                  "nominal_window_slots_per_backup": int(w.problem.n_states * w.problem.n_inputs *
+                                                         info["window_slots"])})
+    return first
+
+
+def roofline(args, w, info, backup_ms, free, lane_peaks, work=None):
     """Roofline of the fused backup kernel.
 
     Stored full / factored rows are streamed from HBM: bound = hbm,
@@ -335,6 +387,8 @@ def roofline(args, w, info, backup_ms, free, lane_peaks):
     W innermost-dim masses per (free state, input) that each input's sum
     applies to it.  The persistent kernel performs all backups of the horizon
     in one launch; the figures are per backup (the same ratio per launch)."""
+    if work is not None:
+        return roofline_plane(args, w, info, backup_ms, work, lane_peaks)
     pk = peaks()
     p = w.problem
     nx, nu = p.n_states, p.n_inputs
@@ -423,10 +477,19 @@ def time_oracle_sample(w, n_states: int, seed: int = W.SEED, nthreads: int = 0):
     return time.perf_counter() - t0, len(st) * w.problem.n_inputs * window_slots_of(w)
 
 
+# seeded states per oracle backup sample (full rows): all cores for the CPU
+# baseline (about 10 s), one thread (a few seconds), one step of the
+# reference arm (a few seconds, so that its warm-up and timed steps end
+# within a few minutes)
+ORACLE_SAMPLE = {"rooms7": 2000, "traffic6": 200_000}
+ONE_CORE_SAMPLE = {"unicycle": 20000, "robot": 400, "rooms7": 200, "traffic6": 2000}
+REFERENCE_SAMPLE = {"rooms7": 2000, "traffic6": 50_000}
+
+
 def one_core_oracle(w, workload: str) -> dict:
     """The oracle on one host thread: one backup at a bounded sample of seeded
     states (a few seconds of work)."""
-    n_s = {"unicycle": 20000, "robot": 400, "rooms7": 200}.get(workload, 10)
+    n_s = ONE_CORE_SAMPLE.get(workload, 10)
     dt, tr = time_oracle_sample(w, n_s, nthreads=1)
     return {"value": tr / dt, "unit": UNIT, "cores": 1,
             "sample": f"one backup at {n_s} seeded states (full rows), FP64, one thread"}
@@ -447,7 +510,7 @@ def oracle_step(args, w):
         trans = w.problem.n_states * w.problem.n_inputs * slots * w.horizon
         return (lambda: time_oracle(w, w.horizon)[0], trans,
                 f"the whole workload per step (full grid, {w.horizon} backups), FP64")
-    n_s = 2000 if args.workload == "rooms7" else 100
+    n_s = REFERENCE_SAMPLE.get(args.workload, 100)
 
     def run():
         return time_oracle_sample(w, n_s)[0]
@@ -581,10 +644,11 @@ def run_served(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 10 for the traffic ring, 400 for the unicycle, 50 otherwise)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="amy", choices=["amy", "reference"])
-    ap.add_argument("--workload", default="unicycle", choices=list(WORKLOADS) + ["served"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(WORKLOADS) + ["served"])
     ap.add_argument("--tmode", default=None, choices=["otf", "stored_full", "stored_factored", "stored_separable"])
     ap.add_argument("--prec", default=None, choices=["fp64", "fp32", "fp32_kahan"])
     ap.add_argument("--served-n", dest="served_n", type=int, default=256)
@@ -592,6 +656,11 @@ def main():
     ap.add_argument("--step-wait", dest="step_wait", type=int, default=None, choices=[0, 1],
                     help="persistent kernel between backups: 0 = neighbour tiles, 1 = grid barrier "
                          "(default: the handle's choice, autotuned)")
+    ap.add_argument("--plane", type=int, default=None, choices=[0, 1],
+                    help="banded problems with tables: 1 = the plane kernel (default where it applies), "
+                         "0 = the per-state kernel")
+    ap.add_argument("--plane-smem", dest="plane_smem", type=int, default=0,
+                    help="shared memory per block of the plane kernel in bytes (0 = default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", dest="no_e2e", action="store_true",
                     help="skip the end-to-end (host buffer) measurement, e.g. under a profiler")
@@ -604,6 +673,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.steps is None:
+        args.steps = {"traffic6": 10, "unicycle": 400}.get(args.workload, 50)
     if args.workload != "served":
         args.tmode = args.tmode or WORKLOADS[args.workload][1]
         args.prec = args.prec or WORKLOADS[args.workload][2]
@@ -627,7 +698,7 @@ def main():
                    "sample": f"the whole workload once (full grid, {w.horizon} backups), FP64"}
             max_dv = float(np.max(np.abs(r["V"].astype(np.float64) - ref["V"])))
         else:
-            n_s = 2000 if args.workload == "rooms7" else 100
+            n_s = ORACLE_SAMPLE.get(args.workload, 100)
             dt, tr = time_oracle_sample(w, n_s)
             cpu = {"value": tr / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"one backup at {n_s} seeded states (full rows), FP64"}

@@ -198,7 +198,9 @@ typedef struct {
                                    cooperative launch (k_synth_runs), 6 wide rows
                                    (stored full, stored factored or on the fly)
                                    split over window-row groups (k_backup_rows or
-                                   k_backup_rows_otf, then k_argmax_rows) */
+                                   k_backup_rows_otf, then k_argmax_rows), 7 the
+                                   plane kernel of banded problems with tables
+                                   (k_backup_plane, see amy_set_plane) */
     int32_t input_runs;         /* runs of consecutive inputs sharing outer records */
     int32_t inner_span;         /* inner slots K one outer contraction covers (kernels 3, 4) */
     int32_t build_kernels;      /* kernels one table build (amy_build / amy_rebuild) launches */
@@ -296,6 +298,41 @@ amy_status amy_set_wait_limit(amy_handle h, int32_t polls);
  * AMY_E_INVALID_ARG.  The paper has no counterpart (it launches one backup
  * after another). */
 amy_status amy_set_step_wait(amy_handle h, int32_t mode);
+
+/* Backup kernel of problems with per-dimension tables whose mean components
+ * each depend on a few coordinates (banded coupling, as in the room and road
+ * rings of Sec. 8.2 / 8.3; four or more state dims, no periodic dim, planes
+ * of at most 512 states).  Algorithm 4's window sum is reassociated per
+ * plane of the two innermost dims: the dims whose masses the whole plane
+ * shares are contracted first, once per plane, into a partial box held in
+ * shared memory, from which each state sums its remaining dims (amy_info
+ * backup_kernel 7).  The same terms are summed, in another FP32 order, so
+ * values agree with the per-state kernels to rounding.
+ * on = 1 (the default) uses it wherever it applies, on = 0 the per-state
+ * register-resident kernel.  smem_bytes caps one block's shared memory
+ * (16 KiB .. 200 KiB; 0 = 100 KiB, two blocks per SM); the partial box is
+ * staged in chunks when it does not fit, which does not change the result.
+ * Errors: INVALID_ARG (null handle, bad mode or size). */
+amy_status amy_set_plane(amy_handle h, int32_t on, int32_t smem_bytes);
+
+/* Work the plane kernel performs in one backup (roofline numerators), for
+ * the handle's problem and this spec: one backup from V_N with counters on,
+ * on the handle's own buffers and stream (synchronised; not for a timed
+ * region).  v_loads: values of V_{k+1} read from global memory in the first
+ * stage (each S combination of each staged row); box_loads: values read from
+ * the shared-memory partial box in the second stage; box_rows: second-stage
+ * rows summed (one FP32 FMA per box load plus W[n-2] + 1 per row).  The
+ * paper has no counterpart.  Errors: INVALID_ARG, UNSUPPORTED (the handle
+ * does not run backup kernel 7), CUDA. */
+amy_status amy_backup_work(amy_handle h, const amy_spec *spec, int64_t *v_loads, int64_t *box_loads,
+                           int64_t *box_rows);
+
+/* Measured read bandwidth of the L2 cache: 16-byte loads that bypass L1
+ * (ld.global.cg) streaming a 32 MiB buffer that stays in L2, every SM busy,
+ * in bytes per second on the current device (roofline denominator of
+ * kernels that stream L2-resident data).  Allocates 32 MiB temporarily.
+ * Errors: INVALID_ARG (null pointer), CUDA. */
+amy_status amy_measure_l2(double *bytes_per_s);
 
 /* The kernel times amy_set_profiling collects (see there): summed backup and
  * build durations in ms, their launch counts and the backups performed.

@@ -343,6 +343,31 @@ def amy_set_step_wait(h: AmyHandle, mode: int = 0) -> None:
     _check(_lib().amy_set_step_wait(h.ptr, int(mode)))
 
 
+def amy_set_plane(h: AmyHandle, on: int = 1, smem_bytes: int = 0) -> None:
+    """amy_set_plane: 1 = the plane kernel (banded problems with tables,
+    backup kernel 7) where it applies, 0 = the per-state kernel; smem_bytes
+    caps its shared memory per block (0 = default)."""
+    _check(_lib().amy_set_plane(h.ptr, int(on), int(smem_bytes)))
+
+
+def amy_backup_work(h: AmyHandle, spec) -> dict:
+    """amy_backup_work: the plane kernel's work in one backup for this spec
+    (V values read from global memory, values read from the shared-memory
+    partial box, second-stage rows); runs one untimed backup."""
+    k = _Keep()
+    s = _spec_struct(k, spec)
+    a, b, c = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+    _check(_lib().amy_backup_work(h.ptr, C.byref(s), C.byref(a), C.byref(b), C.byref(c)))
+    return {"v_loads": a.value, "box_loads": b.value, "box_rows": c.value}
+
+
+def amy_measure_l2() -> float:
+    """amy_measure_l2: measured L2 read bandwidth (bytes/s) of the current device."""
+    v = C.c_double(0.0)
+    _check(_lib().amy_measure_l2(C.byref(v)))
+    return v.value
+
+
 def amy_kernel_times(h: AmyHandle) -> dict:
     """Summed CUDA-event durations (ms) and counts of backup / build kernels since
     the last call; backup_steps counts the backups those launches performed."""
@@ -401,7 +426,7 @@ from .serving import (AmyServer, amy_cancel, amy_poll, amy_result_free,  # noqa:
 __all__ = [
     "AmyError", "AmyHandle", "AmyServer", "amy_build", "amy_synthesize", "amy_backup_step",
     "amy_query_rows", "amy_info", "amy_destroy", "amy_grid_count", "amy_last_error",
-    "amy_rebuild", "amy_set_profiling", "amy_set_wait_limit", "amy_set_step_wait", "amy_kernel_times", "amy_synthesize_noalloc", "amy_measure_lane_loads", "amy_measure_fma",
+    "amy_rebuild", "amy_set_profiling", "amy_set_wait_limit", "amy_set_step_wait", "amy_set_plane", "amy_backup_work", "amy_measure_l2", "amy_kernel_times", "amy_synthesize_noalloc", "amy_measure_lane_loads", "amy_measure_fma",
     "amy_server_create", "amy_submit", "amy_poll", "amy_wait", "amy_cancel", "amy_server_stats",
     "amy_server_destroy", "amy_result_free", "TMODES", "PRECS", "VSTORES", "POLICY_NONE",
 ]

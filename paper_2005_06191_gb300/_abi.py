@@ -92,6 +92,10 @@ PROTOTYPES = {
     "amy_set_profiling": (C.c_int32, [C.c_void_p, C.c_int32]),
     "amy_set_wait_limit": (C.c_int32, [C.c_void_p, C.c_int32]),
     "amy_set_step_wait": (C.c_int32, [C.c_void_p, C.c_int32]),
+    "amy_set_plane": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int32]),
+    "amy_backup_work": (C.c_int32, [C.c_void_p, C.POINTER(amy_spec), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int64)]),
+    "amy_measure_l2": (C.c_int32, [DP]),
     "amy_kernel_times": (C.c_int32, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "amy_destroy": (None, [C.c_void_p]),

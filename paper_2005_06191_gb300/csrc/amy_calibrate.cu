@@ -71,10 +71,78 @@ __global__ void __launch_bounds__(FMA_THREADS) k_cal_fma(R b, R c, int iters, R 
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// L2 read bandwidth: 16-byte loads at L2 (not cached in L1) over a buffer
+// that fits in L2, every thread striding through it; four loads in flight per
+// thread per step.
+constexpr int L2_THREADS = 512;
+__global__ void __launch_bounds__(L2_THREADS) k_cal_l2(const float4 *__restrict__ src, int64_t n4, int passes,
+                                                      float *__restrict__ out) {
+    float s = 0.0f;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int ps = 0; ps < passes; ++ps) {
+        const int64_t start = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x + (int64_t)ps * 4096) % step;
+        for (int64_t i = start; i + 3 * step < n4; i += 4 * step) {
+            float4 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                asm volatile("ld.global.cg.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+                             : "=f"(v[q].x), "=f"(v[q].y), "=f"(v[q].z), "=f"(v[q].w)
+                             : "l"(src + i + q * step));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s += (v[q].x + v[q].y) + (v[q].z + v[q].w);
+        }
+    }
+    out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
 }  // namespace amy
 
 using namespace amy;
+
+extern "C" amy_status amy_measure_l2(double *bytes_per_s) {
+    if (!bytes_per_s) return set_error(AMY_E_INVALID_ARG, "null argument");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_error(e, "device query");
+    const int blocks = sms * 4;  // 2048 threads per SM
+    const int64_t n4 = (int64_t)(32 << 20) / 16;
+    const int passes = 64;
+    float4 *src = nullptr;
+    float *out = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&src, (size_t)n4 * 16, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&out, (size_t)blocks * L2_THREADS * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(src, 0, (size_t)n4 * 16, st);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    float best = 3.4e38f;
+    for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep) {  // first pass warms L2 up
+        e = cudaEventRecord(a, st);
+        if (e == cudaSuccess) k_cal_l2<<<blocks, L2_THREADS, 0, st>>>(src, n4, passes, out);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && rep > 0 && ms < best) best = ms;
+    }
+    // bytes actually read: each pass reads the whole groups of 4 * step vectors
+    const int64_t step = (int64_t)blocks * L2_THREADS;
+    const int64_t per_pass = (n4 / (4 * step)) * 4 * step * 16;
+    if (src) cudaFreeAsync(src, st);
+    if (out) cudaFreeAsync(out, st);
+    if (st) cudaStreamSynchronize(st);
+    if (st) cudaStreamDestroy(st);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_error(e, "L2 calibration");
+    *bytes_per_s = (double)per_pass * passes / (best * 1e-3);
+    return AMY_OK;
+}
 
 extern "C" amy_status amy_measure_fma(double *fp32_per_s, double *fp64_per_s) {
     if (!fp32_per_s || !fp64_per_s) return set_error(AMY_E_INVALID_ARG, "null argument");

@@ -67,7 +67,10 @@ struct Geom {
     // After the index parts, at word boff: per dim d the smallest and largest
     // window origin minus the state's own coordinate d over the table
     // (words boff + d and boff + MAXD + d), then a bit mask of the dims for
-    // which that bound exists (component d depends on coordinate d).
+    // which that bound exists (component d depends on coordinate d), three
+    // spare words, and per dim d < n - 2 the largest spread (max - min) of
+    // its window origin over one plane of the two innermost dims (words
+    // boff + 2 * MAXD + 4 + d; 0 when component d ignores those coordinates).
     int64_t boff;
     // After the bounds block, at word shoff (0 = absent; 2-D and 3-D problems
     // whose innermost table has at most 4096 records): that table as shifted

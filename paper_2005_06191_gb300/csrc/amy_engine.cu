@@ -311,7 +311,7 @@ amy_status plan_sep_tables(Geom &g, const std::vector<double> &params, int64_t &
         }
     }
     g.boff = off + (int64_t)g.nu * g.urw;
-    words = g.boff + 2 * MAXD + 4;
+    words = g.boff + 3 * MAXD + 4;
     g.shoff = 0;
     if (n >= 2 && n <= 3 && g.tent[n - 1] <= 4096) {
         g.shoff = (words + 3) / 4 * 4;
@@ -474,6 +474,20 @@ struct amy_handle_s {
     int tilex;            // staged variant: lane columns per block (0 = default)
     int box_floats;       // staged variant: box budget (0 = default)
     int outer;            // per-run kernels: values of dim 0 per row tile (0 = 1)
+    // plane kernel (banded problems with tables): its plan from the tables'
+    // origin spreads, whether it is used where it applies, and its
+    // shared-memory budget per block (0 = default)
+    int32_t spread[MAXD];
+    PlanePlan plane;
+    int use_plane;
+    int plane_smem;
+    // its padded copies of the two V vectors (planes padded to Ppad values;
+    // null when the problem lacks the plane structure) and which V vector
+    // the padded copies currently mirror (null: none, repack first)
+    void *d_Vp[2];
+    int64_t vp_rows;
+    int32_t vp_pad;
+    const void *vp_src;
     std::vector<double> host_params;
     // kernel timing: CUDA events around every backup / build kernel when profiling
     bool profiling;
@@ -564,6 +578,8 @@ void free_handle(amy_handle_s *h) {
     cudaFree(h->d_bfac);
     cudaFree(h->d_Vbase[0]);
     cudaFree(h->d_Vbase[1]);
+    cudaFree(h->d_Vp[0]);
+    cudaFree(h->d_Vp[1]);
     cudaFree(h->d_mask);
     cudaFree(h->d_tab);
     cudaFree(h->d_bar);
@@ -758,10 +774,13 @@ void set_bounds(const amy_handle_s *h, FastCall &c) {
 // copy sizes the per-run kernel's box and goes to it as launch parameters.
 amy_status read_bounds(amy_handle_s *h) {
     h->bounds_known = 0;
+    h->plane = PlanePlan();
     if (h->tmode != AMY_T_STORED_SEPARABLE) return AMY_OK;
-    int32_t b[2 * MAXD + 4];
+    int32_t b[3 * MAXD + 4];
     AMY_CUDA(cudaMemcpyAsync(b, h->d_tab + h->g.boff, sizeof b, cudaMemcpyDeviceToHost, h->stream), "bounds read");
     AMY_CUDA(cudaStreamSynchronize(h->stream), "bounds read");
+    for (int d = 0; d < MAXD; ++d) h->spread[d] = b[2 * MAXD + 4 + d];
+    plan_plane(h->g, TM_SEPARABLE, h->prec, h->spread, h->plane_smem, h->plane);
     const int all = (1 << h->g.n) - 1;
     if ((b[2 * MAXD] & all) != all) return AMY_OK;
     for (int d = 0; d < h->g.n; ++d) {
@@ -797,6 +816,7 @@ FastCall fast_call(const amy_handle_s *h, int spec_kind, const void *Vn, void *V
     c.tilex = h->tilex;
     c.box_floats = h->box_floats;
     c.outer = h->outer;
+    c.plane = (h->use_plane && h->plane.ok && h->d_Vp[0]) ? &h->plane : nullptr;
     return c;
 }
 
@@ -827,15 +847,33 @@ void update_synth_ok(amy_handle_s *h) {
     cudaGetLastError();
 }
 
-amy_status launch_backup(amy_handle_s *h, int spec_kind, const void *Vn, void *Vo, void *Vfinal, uint16_t *pi) {
-    KernelTimer tm(h, &h->ev_backup);
-    amy_status st;
+amy_status launch_backup(amy_handle_s *h, int spec_kind, const void *Vn, void *Vo, void *Vfinal, uint16_t *pi,
+                         unsigned long long *work = nullptr) {
     if (fast_path(h)) {
-        const FastCall c = fast_call(h, spec_kind, Vn, Vo, Vfinal, pi);
-        st = launch_backup_fast(h->g, tm_kind_of(h), h->v_store, c, h->sm_count, h->stream);
-    } else {
-        st = launch_backup_generic(h, spec_kind, Vn, Vo, Vfinal, pi);
+        FastCall c = fast_call(h, spec_kind, Vn, Vo, Vfinal, pi);
+        c.work = work;
+        if (c.plane) {
+            // the plane kernel reads V_{k+1} from its padded copy: make it when
+            // the copies do not mirror Vn (V_N, a caller's V_{k+1})
+            if (Vn != h->d_V[0] && Vn != h->d_V[1])
+                return set_error(AMY_E_INVALID_ARG, "plane backup: V_{k+1} is not one of the handle's vectors");
+            const int in = Vn == h->d_V[1] ? 1 : 0;
+            if (h->vp_src != Vn) {
+                amy_status r = launch_plane_repack(h->v_store, Vn, h->d_Vp[in], h->vp_rows, h->plane.P, h->vp_pad,
+                                                   h->stream);
+                if (r != AMY_OK) return r;
+            }
+            c.Vpn = h->d_Vp[in];
+            c.Vpo = h->d_Vp[in ^ 1];
+        }
+        KernelTimer tm(h, &h->ev_backup);
+        const amy_status st = launch_backup_fast(h->g, tm_kind_of(h), h->v_store, c, h->sm_count, h->stream);
+        tm.done();
+        h->vp_src = (c.plane && st == AMY_OK) ? Vo : nullptr;
+        return st;
     }
+    KernelTimer tm(h, &h->ev_backup);
+    const amy_status st = launch_backup_generic(h, spec_kind, Vn, Vo, Vfinal, pi);
     tm.done();
     return st;
 }
@@ -866,6 +904,7 @@ amy_status launch_backup_generic(amy_handle_s *h, int spec_kind, const void *Vn,
 }
 
 amy_status launch_mask_any(amy_handle_s *h, const SpecDev &s, void *VN) {
+    h->vp_src = nullptr;  // V is rewritten: the plane kernel's padded copies no longer mirror it
     if (h->prec == AMY_PREC_FP64) return launch_mask<double, double>(h, s, (double *)VN);
     if (h->v_store == AMY_V_BF16) return launch_mask<float, __nv_bfloat16>(h, s, (__nv_bfloat16 *)VN);
     if (h->v_store == AMY_V_UNORM16) return launch_mask<float, unorm16>(h, s, (unorm16 *)VN);
@@ -1128,6 +1167,13 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     h->in_stride_b = INT_MIN;
     h->tilex = 0;
     h->box_floats = 0;
+    h->use_plane = 1;
+    h->plane_smem = 0;
+    for (int d = 0; d < MAXD; ++d) h->spread[d] = -1;
+    h->d_Vp[0] = h->d_Vp[1] = nullptr;
+    h->vp_rows = 0;
+    h->vp_pad = 0;
+    h->vp_src = nullptr;
     {
         const int32_t *ls = opts->launch_shape;
         if (ls[0] < 0 || ls[0] > 8 || ls[1] < 0 || ls[1] > 512 || ls[1] % 32 != 0 ||
@@ -1235,6 +1281,24 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
         free_handle(h);
         return cuda_error(e, "build");
     }
+    {
+        int64_t rows = 0;
+        int32_t Ppad = 0;
+        if (plane_structure(h->g, tm_kind_of(h), h->prec, rows, Ppad)) {
+            // the plane kernel's padded V copies (pads stay zero)
+            const size_t vb = (size_t)rows * Ppad * vsize(h);
+            for (int i = 0; i < 2; ++i) {
+                TRY(dev_alloc(h, &h->d_Vp[i], vb, "padded V"));
+                e = cudaMemsetAsync(h->d_Vp[i], 0, vb, h->stream);
+                if (e != cudaSuccess) {
+                    free_handle(h);
+                    return cuda_error(e, "padded V init");
+                }
+            }
+            h->vp_rows = rows;
+            h->vp_pad = Ppad;
+        }
+    }
     TRY(read_bounds(h));
     h->spin_limit = 1 << 20;
     h->grid_barrier = 1;
@@ -1254,6 +1318,7 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
         }
     }
     if (opts->autotune) TRY(autotune_shape(h));
+    h->vp_src = nullptr;
     update_synth_ok(h);
 #undef TRY
     amy_info_t &inf = h->info;
@@ -1291,7 +1356,13 @@ amy_status amy_info(amy_handle h, amy_info_t *out) {
     out->backup_kernel = h->d_split ? 6 : 0;
     out->backup_launch_kernels = h->d_split ? 2 : 1;
     out->inner_span = 0;
-    if (fast_path(h)) {
+    if (fast_path(h) && h->use_plane && h->plane.ok && h->tmode == AMY_T_STORED_SEPARABLE) {
+        out->backup_kernel = 7;
+        out->input_lanes = 1;
+        out->row_tiles = 0;
+        out->block_states = h->plane.G * h->plane.P;
+        out->grouped_inputs = 0;
+    } else if (fast_path(h)) {
         const FastCall c = fast_call(h, SPEC_SAFETY, nullptr, nullptr, nullptr, nullptr);
         const FastShape sh = fast_shape(h->g, tm_kind_of(h), c, h->sm_count);
         out->backup_kernel = sh.staged ? 2 : 1;
@@ -1314,7 +1385,8 @@ amy_status amy_info(amy_handle h, amy_info_t *out) {
     out->input_runs = h->runs;
     out->build_kernels = h->tmode == AMY_T_ON_THE_FLY ? 0
                          : h->tmode != AMY_T_STORED_SEPARABLE ? (h->slot_build && h->tmode == AMY_T_STORED_FULL ? 2 : 1)
-                         : (h->g.shoff > 0 && h->g.tsx[h->g.n - 1][h->g.n - 1] != 0) ? 3 : 2;
+                         : 2 + ((h->g.shoff > 0 && h->g.tsx[h->g.n - 1][h->g.n - 1] != 0) ? 1 : 0) +
+                               (h->g.n >= 4 ? 1 : 0);
     return AMY_OK;
 }
 
@@ -1365,6 +1437,48 @@ amy_status amy_set_step_wait(amy_handle h, int32_t mode) {
     if (mode != 0 && mode != 1) return set_error(AMY_E_INVALID_ARG, "step wait mode %d (0 or 1)", (int)mode);
     h->grid_barrier = mode;
     h->graph_valid = false;
+    return AMY_OK;
+}
+
+amy_status amy_set_plane(amy_handle h, int32_t on, int32_t smem_bytes) {
+    if (!h) return set_error(AMY_E_INVALID_ARG, "null handle");
+    if (on != 0 && on != 1) return set_error(AMY_E_INVALID_ARG, "plane mode %d (0 or 1)", (int)on);
+    if (smem_bytes != 0 && (smem_bytes < 16 * 1024 || smem_bytes > 200 * 1024))
+        return set_error(AMY_E_INVALID_ARG, "plane kernel shared memory %d bytes (0, or 16 KiB..200 KiB)",
+                         (int)smem_bytes);
+    h->use_plane = on;
+    h->plane_smem = smem_bytes;
+    if (h->tmode == AMY_T_STORED_SEPARABLE)
+        plan_plane(h->g, TM_SEPARABLE, h->prec, h->spread, h->plane_smem, h->plane);
+    h->graph_valid = false;
+    return AMY_OK;
+}
+
+amy_status amy_backup_work(amy_handle h, const amy_spec *spec, int64_t *v_loads, int64_t *box_loads,
+                           int64_t *box_rows) {
+    if (!h || !spec || !v_loads || !box_loads || !box_rows) return set_error(AMY_E_INVALID_ARG, "null argument");
+    if (!(fast_path(h) && h->use_plane && h->plane.ok && h->tmode == AMY_T_STORED_SEPARABLE))
+        return set_error(AMY_E_UNSUPPORTED, "work counters exist for the plane kernel (backup kernel 7) only");
+    SpecDev s;
+    amy_status st = make_spec(h->g, spec, s);
+    if (st != AMY_OK) return st;
+    unsigned long long *d_work = nullptr;
+    AMY_CUDA(cudaMallocAsync((void **)&d_work, 4 * sizeof(unsigned long long), h->stream), "work counters");
+    cudaError_t e = cudaMemsetAsync(d_work, 0, 4 * sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) {
+        st = launch_mask_any(h, s, h->d_V[0]);
+        if (st == AMY_OK) st = launch_backup(h, s.kind, h->d_V[0], h->d_V[1], nullptr, nullptr, d_work);
+    }
+    unsigned long long w[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess && st == AMY_OK) e = cudaMemcpyAsync(w, d_work, sizeof w, cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(d_work, h->stream);
+    const cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    if (st != AMY_OK) return st;
+    if (e != cudaSuccess) return cuda_error(e, "work counters");
+    if (e2 != cudaSuccess) return cuda_error(e2, "work counters");
+    *v_loads = (int64_t)w[0];
+    *box_loads = (int64_t)w[1];
+    *box_rows = (int64_t)w[2];
     return AMY_OK;
 }
 

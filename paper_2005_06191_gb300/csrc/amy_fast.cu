@@ -3,6 +3,7 @@
 #include <algorithm>
 
 #include "amy_fast.cuh"
+#include "amy_plane.cuh"
 #include "amy_internal.h"
 
 namespace amy {
@@ -33,6 +34,91 @@ int fast_wm(const Geom &g, int prec) {
     if (wm == 0) return 0;
     if (fast_smem_bytes(g.n, wm) > 200 * 1024) return 0;
     return wm;
+}
+
+bool plane_structure(const Geom &g, int tmode, int prec, int64_t &rows, int32_t &Ppad) {
+    const int n = g.n;
+    if (tmode != TM_SEPARABLE || prec == AMY_PREC_FP64 || n < 4 || g.periodic != 0) return false;
+    if (fast_wm(g, AMY_PREC_FP32) == 0) return false;
+    const int64_t P = (int64_t)g.N[n - 2] * g.N[n - 1];
+    if (P > PLANE_MAX_THREADS) return false;
+    bool shared = false;
+    for (int d = 0; d < n - 2; ++d) shared = shared || (g.tsx[d][n - 2] == 0 && g.tsx[d][n - 1] == 0);
+    if (!shared) return false;
+    rows = (int64_t)g.nx / P;
+    Ppad = (int32_t)((P + 3) / 4 * 4);
+    return rows * Ppad + 64 < 2147483647LL;
+}
+
+amy_status launch_plane_repack(int v_store, const void *V, void *Vp, int64_t rows, int32_t P, int32_t Ppad,
+                               cudaStream_t st) {
+    const int blocks = (int)std::min<int64_t>((rows * Ppad + 255) / 256, 16384);
+    if (v_store == AMY_V_BF16)
+        k_plane_repack<__nv_bfloat16><<<blocks, 256, 0, st>>>((const __nv_bfloat16 *)V, (__nv_bfloat16 *)Vp, rows, P,
+                                                              Ppad);
+    else if (v_store == AMY_V_UNORM16)
+        k_plane_repack<unorm16><<<blocks, 256, 0, st>>>((const unorm16 *)V, (unorm16 *)Vp, rows, P, Ppad);
+    else
+        k_plane_repack<float><<<blocks, 256, 0, st>>>((const float *)V, (float *)Vp, rows, P, Ppad);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AMY_OK : cuda_error(e, "plane repack launch");
+}
+
+void plan_plane(const Geom &g, int tmode, int prec, const int32_t *spread, int smem_budget, PlanePlan &pl) {
+    pl = PlanePlan();
+    const int n = g.n;
+    int64_t rows = 0;
+    int32_t Ppad = 0;
+    if (!spread || !plane_structure(g, tmode, prec, rows, Ppad)) return;
+    const int64_t P = (int64_t)g.N[n - 2] * g.N[n - 1];
+    int64_t ngroups = 1;
+    for (int d = 0; d < n - 2; ++d) {
+        ngroups *= g.N[d];
+        const bool dep = g.tsx[d][n - 2] != 0 || g.tsx[d][n - 1] != 0;
+        if (dep) {
+            if (pl.nB == PLANE_MAXB || spread[d] < 0) return;
+            pl.bdim[pl.nB] = d;
+            pl.brange[pl.nB] = spread[d] + g.W[d];
+            pl.bstrideF[pl.nB] = (int32_t)(g.stride[d] / P);
+            ++pl.nB;
+        } else {
+            if (pl.nS == PLANE_MAXS) return;
+            pl.sdim[pl.nS++] = d;
+        }
+    }
+    if (pl.nS == 0) return;  // nothing is shared by a plane: the per-state kernels do as well
+    int64_t K = 1;
+    for (int s = 0; s < pl.nS; ++s) K *= g.W[pl.sdim[s]];
+    if (K > 4096) return;
+    pl.K = (int32_t)K;
+    pl.P = (int32_t)P;
+    int64_t rs0 = 1;
+    for (int b = 1; b < pl.nB; ++b) rs0 *= pl.brange[b];
+    pl.rs0 = (int32_t)rs0;
+    const int64_t budget = smem_budget > 0 ? smem_budget : kPlaneSmemDefault;
+    const int64_t span0 = pl.nB > 0 ? pl.brange[0] : 1;
+    // the most groups per block that hold their whole staged union, else one
+    // group with the union staged in chunks of the first B dim
+    int64_t G = std::min<int64_t>(std::max<int64_t>(PLANE_MAX_THREADS / P, 1), ngroups);
+    int64_t chunk = span0;
+    while (G > 1 && (int64_t)plane_smem_bytes((int)G, pl.K, (int)(span0 * rs0), Ppad) > budget) --G;
+    if ((int64_t)plane_smem_bytes((int)G, pl.K, (int)(span0 * rs0), Ppad) > budget) {
+        G = 1;
+        chunk = 0;
+        while (chunk < span0 && (int64_t)plane_smem_bytes(1, pl.K, (int)((chunk + 1) * rs0), Ppad) <= budget)
+            ++chunk;
+        if (chunk < 1) return;
+    }
+    pl.G = (int32_t)G;
+    pl.chunk = (int32_t)chunk;
+    pl.rent = (int32_t)(chunk * rs0);
+    pl.threads = (int32_t)((G * P + 31) / 32 * 32);
+    pl.Ppad = Ppad;
+    pl.Q = Ppad / 4;
+    pl.teams = std::max(1, pl.threads / (pl.G * pl.Q));
+    pl.smem = (int64_t)plane_smem_bytes(pl.G, pl.K, pl.rent, Ppad);
+    if (pl.smem > 200 * 1024) return;
+    pl.ok = 1;
 }
 
 int fast_variant(const Geom &g, int wm, int tmode) {
@@ -88,6 +174,12 @@ amy_status launch_build_sep(const Geom &g, uint32_t *tab, int sm_count, cudaStre
     const int blocks = (int)std::min<int64_t>((total + 127) / 128, (int64_t)sm_count * 16);
     k_build_sep_bounds_init<<<1, 32, 0, st>>>(g, tab);
     k_build_sep<<<std::max(blocks, 1), 128, 0, st>>>(g, tab, total);
+    if (g.n >= 4) {
+        int64_t tmax = 1;
+        for (int d = 0; d < g.n - 2; ++d) tmax = std::max<int64_t>(tmax, g.tent[d]);
+        const int sb = (int)std::min<int64_t>((tmax + 127) / 128, (int64_t)sm_count * 8);
+        k_plane_spread<<<std::max(sb, 1), 128, 0, st>>>(g, tab);
+    }
     if (g.shoff > 0 && g.tsx[g.n - 1][g.n - 1] != 0)
         k_build_shift<<<(g.tent[g.n - 1] + 127) / 128, 128, 0, st>>>(g, tab);
     cudaError_t e = cudaGetLastError();

@@ -552,6 +552,7 @@ static __global__ void k_build_sep_bounds_init(const __grid_constant__ Geom g, u
     if (d < MAXD) {
         b[d] = INT_MAX;
         b[MAXD + d] = INT_MIN;
+        b[2 * MAXD + 4 + d] = 0;  // plane spreads (k_plane_spread)
     }
     if (d == 0) {
         int32_t m = 0;

@@ -9,6 +9,7 @@
 
 #include "amy_fast.cuh"
 #include "amy_internal.h"
+#include "amy_plane.cuh"
 #include "amy_runs.cuh"
 #include "amy_staged.cuh"
 
@@ -310,8 +311,59 @@ amy_status launch_var(const Geom &g, int var, const FastCall &c, int sm, cudaStr
     return launch_t<VT, WM, TM, VAR_GENERAL>(g, c, sm, st);
 }
 
+// The plane kernel (amy_plane.cuh) with the handle's plan.
+template <class VT, int WM>
+amy_status launch_plane_t(const Geom &g, const FastCall &c, cudaStream_t st) {
+    const PlanePlan &pl = *c.plane;
+    PlaneArgs<VT> a;
+    a.Vn = (const VT *)c.Vn;
+    a.Vo = (VT *)c.Vo;
+    a.Vfinal = c.Vfinal;
+    a.pi = c.pi;
+    a.mask = c.mask;
+    a.tab = c.tab;
+    a.spec_kind = c.spec_kind;
+    a.kahan = c.kahan;
+    a.P = pl.P;
+    a.N1 = g.N[g.n - 1];
+    a.G = pl.G;
+    int64_t ngroups = 1;
+    for (int d = 0; d < g.n - 2; ++d) ngroups *= g.N[d];
+    a.ngroups = (int32_t)ngroups;
+    a.nS = pl.nS;
+    a.nB = pl.nB;
+    for (int i = 0; i < PLANE_MAXS; ++i) a.sdim[i] = pl.sdim[i];
+    for (int i = 0; i < PLANE_MAXB; ++i) {
+        a.bdim[i] = pl.bdim[i];
+        a.brange[i] = pl.brange[i];
+    }
+    a.chunk = pl.chunk;
+    a.rs0 = pl.rs0;
+    a.rent = pl.rent;
+    a.K = pl.K;
+    a.work = c.work;
+    a.Vpn = (const VT *)c.Vpn;
+    a.Vpo = (VT *)c.Vpo;
+    a.Ppad = pl.Ppad;
+    a.Q = pl.Q;
+    a.teams = pl.teams;
+    for (int i = 0; i < PLANE_MAXB; ++i) a.bstrideF[i] = pl.bstrideF[i];
+    if (!a.Vpn || !a.Vpo) return set_error(AMY_E_INVALID_ARG, "plane backup without its padded V copies");
+    auto kern = k_backup_plane<VT, WM>;
+    static std::atomic<uint64_t> raised{0};
+    {
+        const amy_status r = smem_optin((const void *)kern, 200 * 1024, raised, "plane backup smem attribute");
+        if (r != AMY_OK) return r;
+    }
+    const int64_t blocks = (ngroups + pl.G - 1) / pl.G;
+    kern<<<(unsigned)blocks, (unsigned)pl.threads, (size_t)pl.smem, st>>>(g, a);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AMY_OK : cuda_error(e, "plane backup launch");
+}
+
 template <class VT, int WM>
 amy_status launch_tm(const Geom &g, int var, int tmode, const FastCall &c, int sm, cudaStream_t st) {
+    if (tmode == TM_SEPARABLE && c.plane && c.plane->ok) return launch_plane_t<VT, WM>(g, c, st);
     switch (tmode) {
         case TM_OTF: return launch_var<VT, WM, TM_OTF>(g, var, c, sm, st);
         case TM_FACTORED: return launch_t<VT, WM, TM_FACTORED, VAR_GENERAL>(g, c, sm, st);

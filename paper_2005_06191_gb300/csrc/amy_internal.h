@@ -31,6 +31,38 @@ int choose_tile(int32_t nx, int32_t nu, int sm_count);
 // device, so `done` keeps one bit per device ordinal (0..63; higher ordinals
 // set the attribute on every call).
 amy_status smem_optin(const void *func, int bytes, std::atomic<uint64_t> &done, const char *what);
+// Plan of the plane kernel (amy_plane.cuh, backup kernel 7): the F dims
+// contracted first (S: mean component free of the two innermost coordinates)
+// and those staged as ranges (B), the largest range of a group's windows per
+// B dim, and the launch shape (G groups of P states per block, R staged in
+// chunks of `chunk` values of the first B dim).
+struct PlanePlan {
+    int32_t ok = 0;
+    int32_t nS = 0, nB = 0;
+    int32_t sdim[6] = {0, 0, 0, 0, 0, 0};
+    int32_t bdim[3] = {0, 0, 0};
+    int32_t brange[3] = {1, 1, 1};
+    int32_t K = 0, G = 0, chunk = 1, rs0 = 1, rent = 1, threads = 0, P = 0;
+    int32_t Ppad = 0, Q = 0, teams = 0;  // padded plane, stage-1 team size, teams per group
+    int32_t bstrideF[3] = {0, 0, 0};     // plane-index strides of the B dims
+    int64_t smem = 0;
+};
+// Whether a problem has the plane kernel's structure (independent of the
+// tables' origin spreads): tables, FP32, four or more dims, no periodic dim,
+// planes of at most 448 states, some F dim shared by a plane.  Its padded V
+// copies then take rows * Ppad values each (rows = nx / P).
+bool plane_structure(const Geom &g, int tmode, int prec, int64_t &rows, int32_t &Ppad);
+// Padded copy of V for the plane kernel (k_plane_repack), on `st`.
+amy_status launch_plane_repack(int v_store, const void *V, void *Vp, int64_t rows, int32_t P, int32_t Ppad,
+                               cudaStream_t st);
+// Default shared memory of one plane-kernel block: two blocks per SM.
+constexpr int kPlaneSmemDefault = 100 * 1024;
+// The plan for a problem with per-dimension tables; spread[d] is the tables'
+// largest spread (max - min) of dim d's window origin over one plane of
+// states, read back after the table build (negative: unknown).  smem_budget
+// 0 takes kPlaneSmemDefault.  pl.ok = 0 when the kernel does not apply.
+void plan_plane(const Geom &g, int tmode, int prec, const int32_t *spread, int smem_budget, PlanePlan &pl);
+
 // Type-erased arguments of the register-resident backup kernel.
 struct FastCall {
     const void *Vn;
@@ -61,6 +93,10 @@ struct FastCall {
                            // multiple of 32 with tilex * ulanes <= 512; 0 = default
     int32_t box_floats = 0;  // staged variant: box budget in floats (0 = 6144)
     int32_t outer = 0;       // per-run kernels, 3-D: values of dim 0 per row tile (0 = 1)
+    const PlanePlan *plane = nullptr;  // tables mode: the plane kernel's plan when it runs
+    unsigned long long *work = nullptr;  // plane kernel: work counters (3 words), or null
+    const void *Vpn = nullptr;  // plane kernel: padded copy of V_{k+1}
+    void *Vpo = nullptr;        // plane kernel: padded copy of V_k (written)
 };
 
 // Whether consecutive inputs form runs (at least two inputs per run on

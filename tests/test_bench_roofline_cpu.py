@@ -92,3 +92,27 @@ def test_gather_kernels_use_their_load_path(monkeypatch):
     info2 = _info(2, [3, 3], kernel=2)
     r2 = bench.roofline(_args("unicycle", "stored_separable", "fp32"), w, info2, 1.0, nx, dict(LANES))
     assert "shared" in r2["peak_source"]
+
+
+def test_plane_kernel_roofline_from_counted_work(monkeypatch):
+    """Kernel 7: stage-1 V values (4 bytes each, through L2), stage-2 box loads
+    (shared lane-loads) and FP32 FMAs (one per value read plus W + 1 per
+    second-stage row), each against its measured ceiling; the highest
+    fraction is the bound, the other two are listed beside it."""
+    monkeypatch.setattr(bench, "measured_traffic", lambda args, n: (None, None))
+    w = W.traffic6()
+    info = _info(6, [5] * 6, kernel=7)
+    work = {"v_loads": 4_000_000_000, "box_loads": 30_000_000_000, "box_rows": 1_200_000_000}
+    lanes = dict(LANES, fma_fp32=40e12, l2_bytes=20e12)
+    r = bench.roofline(_args("traffic6", "stored_separable", "fp32_kahan"), w, info, 100.0, 0, lanes, work)
+    l2 = 4e9 * 4 / 0.1 / 1e9 / 20e3
+    sh = 30e9 / 0.1 / 1e9 / 9.6e3
+    fma = (4e9 + 30e9 + 1.2e9 * 6) / 0.1 / 1e12 / 40.0
+    fr = {"l2": l2, "shared": sh, "fma": fma}
+    assert r["frac"] == pytest.approx(max(fr.values()))
+    assert len(r["other_ceilings"]) == 2
+    assert r["frac"] >= max(c["frac"] for c in r["other_ceilings"])
+    assert r["nominal_window_slots_per_backup"] == w.problem.n_states * 4 * 5 ** 6
+    r16 = bench.roofline(_args("traffic6", "stored_separable", "fp32", "bf16"), w, info, 100.0, 0, lanes, work)
+    l2c = [c for c in [r16] + r16["other_ceilings"] if c["bound"] == "l2"][0]
+    assert l2c["achieved"] == pytest.approx(4e9 * 2 / 0.1 / 1e9)

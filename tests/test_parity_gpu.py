@@ -345,17 +345,25 @@ def test_unicycle_separable(amy, unicycle_ref, prec, v_store):
 
 
 def test_separable_tables_match_factored_bitwise(amy):
-    """Tabulating each component over its dependencies changes no value.  (The
-    unicycle's inputs come in runs sharing the x and y rows; there the tables'
-    kernel contracts those rows once per run, a different summation order, so
-    it is compared within the FP32 tolerance instead.)"""
+    """Tabulating each component over its dependencies changes no value: with
+    the per-state kernel the tables give the factored rows' results bit for
+    bit.  (The unicycle's inputs come in runs sharing the x and y rows, where
+    the tables' kernel contracts those rows once per run, and the banded
+    rings run the plane kernel: different summation orders, compared within
+    FP32 rounding instead -- and bit for bit once the plane kernel is off.)"""
     for w in [W.unicycle(nxy=31, horizon=6, target=(3.0, 5.0)), W.rooms7(n_per_dim=4, horizon=3),
               W.traffic6(n_per_dim=5, horizon=2), W.served_stream(3)[2]]:
-        out, grouped = {}, False
+        out, grouped, plane = {}, False, False
         for tmode in ["stored_factored", "stored_separable"]:
             with amy.amy_build(w.problem, tmode=tmode, prec="fp32") as h:
                 grouped = grouped or amy.amy_info(h)["grouped_inputs"] == 1
+                if amy.amy_info(h)["backup_kernel"] == 7:
+                    plane = True
+                    Vp, _ = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
+                    amy.amy_set_plane(h, 0)
                 out[tmode] = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
+        if plane:
+            assert np.max(np.abs(out["stored_factored"][0] - Vp)) <= 2e-6
         if grouped:
             assert w.problem.name.startswith("unicycle")
             assert np.max(np.abs(out["stored_factored"][0] - out["stored_separable"][0])) <= 2e-6
@@ -591,7 +599,8 @@ def test_auto_mode_picks_and_matches(amy):
 
 
 def test_backup_kernel_reported_and_lane_load_ceilings(amy):
-    expect = [(W.rooms7(n_per_dim=4, horizon=1), "stored_separable", 1),   # 7-D: register-resident
+    expect = [(W.rooms7(n_per_dim=4, horizon=1), "stored_separable", 7),   # 7-D ring: the plane kernel
+              (W.rooms7(n_per_dim=4, horizon=1), "stored_factored", 1),    # 7-D: register-resident
               (W.random_affine(np.random.default_rng(3), 2, [37, 30], 6, window=[3, 3]), "stored_separable", 2),
               (W.robot_lin(), "stored_full", 6),     # dense 41-wide stored rows: split over window rows
               (W.robot_lin(), "otf", 6)]             # 41-wide rows on the fly: the same split

@@ -1,0 +1,120 @@
+"""GPU parity of the plane kernel (backup kernel 7): banded problems with
+per-dimension tables, whose window sums are reassociated per plane of the two
+innermost dims (the dims a plane shares contracted first, the partial box
+staged in shared memory).  Checked against the FP64 oracle, against the
+per-state register-resident kernel, and across shared-memory budgets (the
+partial box staged whole or in chunks)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from parity_util import GAP, compare_synthesis, load_engine
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amy():
+    return load_engine()
+
+
+def _cases():
+    ring_rooms8 = W.rooms7(n_per_dim=4, horizon=3, n_rooms=8)
+    rooms_reach = W.rooms7(n_per_dim=5, horizon=4)
+    rooms_reach.spec = W.Spec(W.REACH_AVOID, targets=[([19.5] * 7, [20.5] * 7)],
+                              avoids=[([19.0] * 7, [19.25] * 7)])
+    return [
+        ("traffic6 ring 6^6", W.traffic6(n_per_dim=6, horizon=2)),           # S = {1, 2}, B = {0, 3}
+        ("traffic6 line 6^6", W.traffic6(n_per_dim=6, horizon=2, wrap=False)),  # S = {0, 1, 2}, B = {3}
+        ("rooms7 5^7", W.rooms7(n_per_dim=5, horizon=4)),                    # S = {1, 2, 3}, B = {0, 4}
+        ("rooms7 5^7 reach-avoid", rooms_reach),
+        ("rooms 8-ring 4^8", ring_rooms8),                                   # S = {1..4}, B = {0, 5}
+        ("traffic5 ring 9^5 window 3", W.traffic6(n_per_dim=9, horizon=4, n_cells=5, window=3)),
+    ]
+
+
+@pytest.fixture(scope="module")
+def refs():
+    return {name: (w, oracle.synthesize(w.problem, w.spec, w.horizon, want_all=True)) for name, w in _cases()}
+
+
+@pytest.mark.parametrize("name", [c[0] for c in _cases()])
+def test_plane_kernel_matches_oracle(amy, refs, name):
+    w, ref = refs[name]
+    with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32") as h:
+        assert amy.amy_info(h)["backup_kernel"] == 7, name
+    for prec in ("fp32", "fp32_kahan"):
+        compare_synthesis(amy, w, "stored_separable", prec, ref=ref)
+    compare_synthesis(amy, w, "stored_separable", "fp32", v_store="u16", ref=ref)
+    st = compare_synthesis(amy, w, "stored_separable", "fp32", v_store="bf16", ref=ref, bf16_over_ok=True)
+    assert "bf16_over" not in st, st
+
+
+@pytest.mark.parametrize("name", [c[0] for c in _cases()])
+def test_plane_kernel_agrees_with_per_state_kernel(amy, refs, name):
+    """Kernel 7 against kernel 1 on the same handle: the same terms in another
+    FP32 order, so values agree to rounding and policies agree wherever the
+    oracle's top-two gap is clear."""
+    w, ref = refs[name]
+    with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32_kahan") as h:
+        Va, Pa = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
+        amy.amy_set_plane(h, False)
+        assert amy.amy_info(h)["backup_kernel"] == 1
+        Vb, Pb = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
+        amy.amy_set_plane(h, True)
+        assert amy.amy_info(h)["backup_kernel"] == 7
+        Vc, Pc = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
+    assert np.array_equal(Va, Vc) and np.array_equal(Pa, Pc)
+    assert float(np.max(np.abs(Va - Vb))) <= 2e-6
+    sure = ref["gap"] > GAP["fp32"]
+    assert not ((Pa != Pb) & sure).any()
+
+
+@pytest.mark.parametrize("name", [c[0] for c in _cases()])
+def test_plane_kernel_chunking_is_bitwise_neutral(amy, name):
+    """Staging the partial box whole (several groups per block) or in chunks
+    of the first staged dim (small budgets) sums every state's rows in the
+    same order: identical values and policies."""
+    w = dict(_cases())[name]
+    out = []
+    with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32") as h:
+        for budget in (0, 16 * 1024, 24 * 1024, 48 * 1024, 200 * 1024):
+            amy.amy_set_plane(h, True, budget)
+            out.append(amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True))
+    for k in range(1, len(out)):
+        assert np.array_equal(out[0][0], out[k][0]), (name, k)
+        assert np.array_equal(out[0][1], out[k][1]), (name, k)
+
+
+def test_plane_kernel_settings_rejected(amy):
+    w = W.traffic6(n_per_dim=5, horizon=1)
+    with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32") as h:
+        for on, sm in ((2, 0), (1, 1024), (1, 300 * 1024), (-1, 0)):
+            with pytest.raises(amy.AmyError) as e:
+                amy.amy_set_plane(h, on, sm)
+            assert "INVALID_ARG" in str(e.value)
+
+
+def test_plane_kernel_not_used_where_nothing_is_shared(amy):
+    """A dense random 4-D system: every mean component depends on the plane
+    coordinates, nothing is shared by a plane, and the per-state kernel runs."""
+    for w in W.served_stream(40):
+        if w.problem.n == 4:
+            break
+    with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32") as h:
+        assert amy.amy_info(h)["backup_kernel"] != 7
+        with pytest.raises(amy.AmyError) as e:
+            amy.amy_backup_work(h, w.spec)
+        assert "UNSUPPORTED" in str(e.value)
+
+
+def test_plane_work_counts_traffic6_small(amy):
+    """The work counters of one backup: every staged row reads K values of V
+    (K = 25 for the ring's two shared 5-wide dims) and every second-stage
+    row 25 values of the box; the counts are positive and consistent."""
+    w = W.traffic6(n_per_dim=8, horizon=1)
+    with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32") as h:
+        wk = amy.amy_backup_work(h, w.spec)
+    assert wk["v_loads"] > 0 and wk["v_loads"] % 25 == 0
+    assert wk["box_loads"] == 25 * wk["box_rows"] > 0
