@@ -48,6 +48,8 @@ class _Problem(C.Structure):
         ("sys_kind", C.c_int32), ("params", C.POINTER(C.c_double)), ("n_params", C.c_int64),
         ("sigma", C.POINTER(C.c_double)),
         ("gamma", C.c_double), ("window", C.POINTER(C.c_int32)),
+        ("p", C.c_int32), ("w_lb", C.POINTER(C.c_double)), ("w_eta", C.POINTER(C.c_double)),
+        ("w_count", C.POINTER(C.c_int32)),
     ]
 
 
@@ -124,6 +126,10 @@ def _problem(p, keep: _Keep) -> _Problem:
     s.sigma = keep.f64(p.sigma)
     s.gamma = float(p.gamma)
     s.window = keep.i32(p.window) if p.window is not None else C.POINTER(C.c_int32)()
+    wc = list(getattr(p, "w_count", None) or [])
+    s.p = len(wc)
+    if wc:
+        s.w_lb, s.w_eta, s.w_count = keep.f64(p.w_lb), keep.f64(p.w_eta), keep.i32(wc)
     return s
 
 
@@ -165,13 +171,19 @@ def mean(p, x: int, u: int) -> np.ndarray:
     return mu
 
 
-def row(p, x: int, u: int):
-    """(origin[n], probs[prod W]) of the transition row of (x, u), window C order."""
+def n_disturbances(p) -> int:
+    wc = list(getattr(p, "w_count", None) or [])
+    return int(np.prod(wc, dtype=np.int64)) if wc else 1
+
+
+def row(p, x: int, u: int, w: int = 0):
+    """(origin[n], probs[prod W]) of the transition row of (x, u[, w]), window C order."""
     lib, keep = _load(), _Keep()
     W, _ = window_shape(p)
     origin = np.zeros(p.n, np.int32)
     probs = np.zeros(int(np.prod(W, dtype=np.int64)), np.float64)
-    if lib.orc_row(C.byref(_problem(p, keep)), x, u, origin.ctypes.data, probs.ctypes.data) != 0:
+    pair = int(u) * n_disturbances(p) + int(w)
+    if lib.orc_row(C.byref(_problem(p, keep)), x, pair, origin.ctypes.data, probs.ctypes.data) != 0:
         raise ValueError("orc_row failed")
     return origin, probs
 
@@ -202,7 +214,8 @@ def backup_states(p, sp, V_next, states: Sequence[int], nthreads: int = 0):
 
 
 def action_values(p, V_next, x: int) -> np.ndarray:
-    """Window sums s_u for every input u at state x (no masking)."""
+    """Every input's value at state x (no masking): the window sum s_u, or
+    with a disturbance grid min over w of s_{u,w}."""
     lib, keep = _load(), _Keep()
     Vn = np.ascontiguousarray(np.asarray(V_next, dtype=np.float64))
     out = np.zeros(p.n_inputs, np.float64)

@@ -30,7 +30,9 @@
  *   - gamma == 0: dense, W = N, o = 0;
  *   - reach-avoid via V masking (V = 1 on the target, 0 on the avoid set),
  *     safety as V_k = 1_S * max_u sum;
- *   - argmax ties: lowest input index; masked states carry policy 0xFFFF.
+ *   - argmax ties: lowest input index; masked states carry policy 0xFFFF;
+ *   - with a disturbance grid each input's value is the min over the grid
+ *     (the adversary moves after the input, knowing it; Sec. 3 Remark).
  * The target-jump vector of Algorithm 3 is not formed: with V fixed to 1 on
  * the target and 0 on the avoid set, sum_x' T V equals T0 + T_zeroed V exactly.
  */
@@ -98,15 +100,18 @@ int orc_window_shape(const orc_problem *p, int32_t *W, double *xstar) {
     return 0;
 }
 
-/* Mean of the post state, Algorithm 2 "Set mu = f(x, nu, w)" (no disturbance):
- * the system is evaluated at the representative points of the state and input
- * cells. */
+/* Mean of the post state, Algorithm 2 "Set mu = f(x, nu, w)": the system is
+ * evaluated at the representative points of the state, input and (when
+ * given) disturbance cells.  The affine system carries one (A, c) per
+ * (input, disturbance) pair, so f(x, nu, w) = A x + c needs only the pair's
+ * index; u is that index (u*n_w + w). */
 int orc_mean(const orc_problem *p, int64_t x, int64_t u, double *mu) {
     const int n = p->n, m = p->m;
     int32_t xi[ORC_MAXD], ui[ORC_MAXD];
     double xc[ORC_MAXD], uc[ORC_MAXD];
     decode(x, p->x_count, n, xi);
-    decode(u, p->u_count, m, ui);
+    if (p->sys_kind == ORC_SYS_UNICYCLE) decode(u, p->u_count, m, ui);
+    else for (int d = 0; d < m; ++d) ui[d] = 0;
     for (int d = 0; d < n; ++d) xc[d] = p->x_lb[d] + (double)xi[d] * p->x_eta[d];
     for (int d = 0; d < m; ++d) uc[d] = p->u_lb[d] + (double)ui[d] * p->u_eta[d];
     if (p->sys_kind == ORC_SYS_AFFINE_PER_INPUT) {
@@ -187,26 +192,29 @@ typedef struct {
     int64_t wtot;
     int32_t wsum;
     int64_t stride[ORC_MAXD];
-    int64_t nx, nu;
+    int64_t nx, nu, nw; /* states, inputs, disturbance points (1 without a grid) */
 } orc_shape;
 
 static int shape_of(const orc_problem *p, orc_shape *sh) {
     if (p->n < 1 || p->n > ORC_MAXD || p->m < 1 || p->m > ORC_MAXD) return -1;
+    if (p->p < 0 || p->p > ORC_MAXD) return -1;
     if (orc_window_shape(p, sh->W, sh->xs) != 0) return -1;
     sh->wtot = prod_i32(sh->W, p->n);
     sh->wsum = 0;
     for (int d = 0; d < p->n; ++d) sh->wsum += sh->W[d];
     sh->nx = prod_i32(p->x_count, p->n);
     sh->nu = prod_i32(p->u_count, p->m);
+    sh->nw = p->p > 0 ? prod_i32(p->w_count, p->p) : 1;
+    if (sh->nw < 1) return -1;
     int64_t st = 1;
     for (int d = p->n - 1; d >= 0; --d) {
         sh->stride[d] = st;
         st *= p->x_count[d];
     }
     if (p->sys_kind == ORC_SYS_AFFINE_PER_INPUT &&
-        p->n_params != sh->nu * (int64_t)(p->n * p->n + p->n))
+        p->n_params != sh->nu * sh->nw * (int64_t)(p->n * p->n + p->n))
         return -1;
-    if (p->sys_kind == ORC_SYS_UNICYCLE && (p->n != 3 || p->m != 2 || p->n_params < 1)) return -1;
+    if (p->sys_kind == ORC_SYS_UNICYCLE && (p->n != 3 || p->m != 2 || p->n_params < 1 || p->p != 0)) return -1;
     return 0;
 }
 
@@ -227,7 +235,7 @@ static int pair_factors(const orc_problem *p, const orc_shape *sh, int64_t x, in
 int orc_row(const orc_problem *p, int64_t x, int64_t u, int32_t *origin, double *probs) {
     orc_shape sh;
     if (shape_of(p, &sh) != 0) return -1;
-    if (x < 0 || x >= sh.nx || u < 0 || u >= sh.nu) return -1;
+    if (x < 0 || x >= sh.nx || u < 0 || u >= sh.nu * sh.nw) return -1;
     double *fac = (double *)malloc(sizeof(double) * sh.wsum);
     int64_t *cell = (int64_t *)malloc(sizeof(int64_t) * sh.wsum);
     if (!fac || !cell || pair_factors(p, &sh, x, u, origin, fac, cell) != 0) {
@@ -286,12 +294,56 @@ int orc_spec_mask(const orc_problem *p, const orc_spec *s, uint8_t *mask) {
     return 0;
 }
 
-/* The collect step of Algorithm 4 for one state: V_in by the window sum for
- * every u, then max over u with the lowest maximising index. */
+/* V_in of Algorithm 4 for one state and one (input, disturbance) pair index:
+ * the sum over the cutting window of T(x'|x,u,w) * V_next[x'], in increasing
+ * window (C) order. */
+static double window_sum(const orc_problem *p, const orc_shape *sh, int64_t x, int64_t pair, const double *Vn,
+                         double *fac, int64_t *cell) {
+    const int n = p->n;
+    pair_factors(p, sh, x, pair, NULL, fac, cell);
+    int32_t k[ORC_MAXD] = {0};
+    double acc = 0.0;
+    for (int64_t t = 0; t < sh->wtot; ++t) {
+        double w = 1.0;
+        int64_t lin = 0;
+        int off = 0, drop = 0;
+        for (int d = 0; d < n; ++d) {
+            int64_t cidx = cell[off + k[d]];
+            if (cidx < 0) {
+                drop = 1;
+                break;
+            }
+            w = w * fac[off + k[d]];
+            lin += cidx * sh->stride[d];
+            off += sh->W[d];
+        }
+        if (!drop) acc += w * Vn[lin];
+        for (int d = n - 1; d >= 0; --d) {
+            if (++k[d] < sh->W[d]) break;
+            k[d] = 0;
+        }
+    }
+    return acc;
+}
+
+/* The value the input u secures at x: the worst case over the disturbance
+ * grid, min_w V_in(x, u, w) (Algorithm 3's "minimize with respect to W",
+ * Algorithm 4's inner min); V_in itself without a disturbance grid. */
+static double input_value(const orc_problem *p, const orc_shape *sh, int64_t x, int64_t u, const double *Vn,
+                          double *fac, int64_t *cell) {
+    double mn = INFINITY;
+    for (int64_t w = 0; w < sh->nw; ++w) {
+        const double v = window_sum(p, sh, x, u * sh->nw + w, Vn, fac, cell);
+        if (v < mn) mn = v;
+    }
+    return mn;
+}
+
+/* The collect step of Algorithm 4 for one state: the value of every input,
+ * then the max over inputs with the lowest maximising index. */
 static void backup_one(const orc_problem *p, const orc_shape *sh, const orc_spec *s,
                        uint8_t f, const double *Vn, int64_t x, double *fac, int64_t *cell,
                        double *V, uint16_t *pi, double *gap) {
-    const int n = p->n;
     int masked;
     double mval;
     if (s->kind == ORC_SAFETY) {
@@ -310,29 +362,7 @@ static void backup_one(const orc_problem *p, const orc_shape *sh, const orc_spec
     double best = -INFINITY, best2 = -INFINITY;
     int64_t arg = 0;
     for (int64_t u = 0; u < sh->nu; ++u) {
-        pair_factors(p, sh, x, u, NULL, fac, cell);
-        int32_t k[ORC_MAXD] = {0};
-        double acc = 0.0;
-        for (int64_t t = 0; t < sh->wtot; ++t) {
-            double w = 1.0;
-            int64_t lin = 0;
-            int off = 0, drop = 0;
-            for (int d = 0; d < n; ++d) {
-                int64_t cidx = cell[off + k[d]];
-                if (cidx < 0) {
-                    drop = 1;
-                    break;
-                }
-                w = w * fac[off + k[d]];
-                lin += cidx * sh->stride[d];
-                off += sh->W[d];
-            }
-            if (!drop) acc += w * Vn[lin];
-            for (int d = n - 1; d >= 0; --d) {
-                if (++k[d] < sh->W[d]) break;
-                k[d] = 0;
-            }
-        }
+        const double acc = input_value(p, sh, x, u, Vn, fac, cell);
         if (acc > best) {
             best2 = best;
             best = acc;
@@ -346,7 +376,7 @@ static void backup_one(const orc_problem *p, const orc_shape *sh, const orc_spec
     *gap = (sh->nu > 1) ? best - best2 : INFINITY;
 }
 
-/* The window sum of Algorithm 4 (V_in for one state and every input). */
+/* The action values of Algorithm 4 at one state (every input's value). */
 int orc_action_values(const orc_problem *p, const double *V_next, int64_t x, double *out) {
     orc_shape sh;
     if (shape_of(p, &sh) != 0 || x < 0 || x >= sh.nx) return -1;
@@ -357,33 +387,7 @@ int orc_action_values(const orc_problem *p, const double *V_next, int64_t x, dou
         free(cell);
         return -1;
     }
-    const int n = p->n;
-    for (int64_t u = 0; u < sh.nu; ++u) {
-        pair_factors(p, &sh, x, u, NULL, fac, cell);
-        int32_t k[ORC_MAXD] = {0};
-        double acc = 0.0;
-        for (int64_t t = 0; t < sh.wtot; ++t) {
-            double w = 1.0;
-            int64_t lin = 0;
-            int off = 0, drop = 0;
-            for (int d = 0; d < n; ++d) {
-                int64_t cidx = cell[off + k[d]];
-                if (cidx < 0) {
-                    drop = 1;
-                    break;
-                }
-                w = w * fac[off + k[d]];
-                lin += cidx * sh.stride[d];
-                off += sh.W[d];
-            }
-            if (!drop) acc += w * V_next[lin];
-            for (int d = n - 1; d >= 0; --d) {
-                if (++k[d] < sh.W[d]) break;
-                k[d] = 0;
-            }
-        }
-        out[u] = acc;
-    }
+    for (int64_t u = 0; u < sh.nu; ++u) out[u] = input_value(p, &sh, x, u, V_next, fac, cell);
     free(fac);
     free(cell);
     return 0;

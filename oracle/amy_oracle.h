@@ -17,7 +17,9 @@
  *     covariance;
  *   - Bellman synthesis (Algorithm 3 / Algorithm 4, OFA semantics of Sec. 6.1):
  *     safety, reachability and reach-avoid value functions with the
- *     lowest-index argmax policy.
+ *     lowest-index argmax policy; with a disturbance grid the max over inputs
+ *     of the min over disturbances (the two-and-a-half player game of the
+ *     Remark in Sec. 3, Algorithm 4's collect step).
  *
  * Everything is IEEE FP64; compile with -ffp-contract=off so that no multiply
  * and add are fused (the exact operation order is part of the definition of
@@ -53,6 +55,16 @@ typedef struct {
     const double *sigma;       /* [n] per-dim noise standard deviation */
     double gamma;              /* cutting threshold; 0 = dense */
     const int32_t *window;     /* [n] explicit odd window widths, or NULL */
+    /* Disturbance grid W^ (Sec. 3, the dt-SCS with bounded disturbances; the
+     * max-min game of its Remark): p dims, representative points
+     * w_lb + j*w_eta, j < w_count.  p = 0: no disturbance (W^ a single point).
+     * With p > 0 only the affine system applies and params holds one
+     * (A, c) record per (input, disturbance) pair, disturbance fastest:
+     * pair index u*n_w + w, n_w = prod(w_count). */
+    int32_t p;
+    const double *w_lb;        /* [p] */
+    const double *w_eta;       /* [p] */
+    const int32_t *w_count;    /* [p] */
 } orc_problem;
 
 typedef struct {
@@ -74,12 +86,13 @@ int64_t orc_grid_count(double lb, double ub, double eta);
  * mode).  Returns 0, or -1 when the cut is empty / invalid. */
 int orc_window_shape(const orc_problem *p, int32_t *W, double *xstar);
 
-/* Mean mu[n] = f(centre(x), centre(u)) for linear state index x, input index u. */
+/* Mean mu[n] = f(centre(x), centre(u), centre(w)) for linear state index x
+ * and input index u -- with a disturbance grid, the pair index u*n_w + w. */
 int orc_mean(const orc_problem *p, int64_t x, int64_t u, double *mu);
 
 /* One transition row: origin[n] (first slot index per dim, unwrapped) and the
  * |W| window probabilities in C order over the window box (0 for dropped
- * slots).  Returns 0 or -1. */
+ * slots); u as in orc_mean.  Returns 0 or -1. */
 int orc_row(const orc_problem *p, int64_t x, int64_t u, int32_t *origin, double *probs);
 
 /* Per-state flags: bit0 target, bit1 avoid, bit2 safe. */
@@ -93,8 +106,9 @@ int orc_backup_states(const orc_problem *p, const orc_spec *s, const double *V_n
                       const int64_t *states, int64_t n_states,
                       double *V_out, uint16_t *pi_out, double *gap_out, int nthreads);
 
-/* Action values s_u = sum over the window of T(x'|x,u) * V_next[x'] for every
- * input u at one (unmasked) state x: out[n_u]. */
+/* Action values at one (unmasked) state x for every input u: the window sum
+ * s_{u,w} = sum over the window of T(x'|x,u,w) * V_next[x'], minimised over
+ * the disturbances w (just s_u without a disturbance grid): out[n_u]. */
 int orc_action_values(const orc_problem *p, const double *V_next, int64_t x, double *out);
 
 /* Full synthesis over `horizon` backups.  V_out[n_x] = V_0.

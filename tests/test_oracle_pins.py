@@ -419,6 +419,148 @@ def test_action_values_agree_with_synthesis_and_rows_3d():
 
 
 # --------------------------------------------------------------------------
+# The disturbance player (the max-min game of the Remark in Sec. 3; Algorithm
+# 3's "minimize with respect to W", Algorithm 4's inner min): pinned by brute
+# force over controller and adversary strategies, and by exact reductions.
+# --------------------------------------------------------------------------
+def _chain_Tw(sig, drifts, pushes):
+    """T[x, u, w, x'] of the 5-cell chain with mean x + drift_u + push_w (mpmath)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 30
+    T = np.zeros((5, len(drifts), len(pushes), 5))
+    for x in range(5):
+        for u, dr in enumerate(drifts):
+            for w, pw in enumerate(pushes):
+                mu = mpmath.mpf(x) + mpmath.mpf(dr) + mpmath.mpf(pw)
+                for y in range(5):
+                    T[x, u, w, y] = float(mpmath.ncdf(y + 0.5, mu, sig) - mpmath.ncdf(y - 0.5, mu, sig))
+    return T
+
+
+def _game_brute_force(T, kind, N, target, avoid, safe):
+    """max over controller Markov policies of min over adversary Markov
+    strategies (the adversary sees the state and step, hence the input) of
+    the probability of the spec, by enumerating every path."""
+    nU, nW = T.shape[1], T.shape[2]
+    free = [x for x in range(5) if (x in safe if kind == "safety" else (x not in target and x not in avoid))]
+    slots = [(k, x) for k in range(N) for x in free]
+
+    def value(pol, adv, x0):
+        # probability by forward propagation over the distribution of the state
+        dist = np.zeros(5)
+        dist[x0] = 1.0
+        won = 0.0
+        for k in range(N + 1):
+            nxt = np.zeros(5)
+            for x in range(5):
+                pr = dist[x]
+                if pr == 0.0:
+                    continue
+                if kind == "safety":
+                    if x not in safe:
+                        continue          # left S: lost
+                    if k == N:
+                        won += pr
+                        continue
+                else:
+                    if x in target:
+                        won += pr
+                        continue
+                    if x in avoid or k == N:
+                        continue
+                nxt += pr * T[x, pol[(k, x)], adv[(k, x)]]
+            dist = nxt
+        return won
+
+    best = np.full(5, -1.0)
+    for pf in itertools.product(range(nU), repeat=len(slots)):
+        pol = dict(zip(slots, pf))
+        worst = np.full(5, np.inf)
+        for af in itertools.product(range(nW), repeat=len(slots)):
+            adv = dict(zip(slots, af))
+            for x0 in range(5):
+                worst[x0] = min(worst[x0], value(pol, adv, x0))
+        best = np.maximum(best, worst)
+    return best
+
+
+def _disturbed_chain(drifts, pushes, sig, gamma=0.0):
+    As = [np.eye(1)] * (len(drifts) * len(pushes))
+    cs = [np.array([float(d + pw)]) for d in drifts for pw in pushes]
+    p = _affine_problem("dchain", [0.0], [1.0], [5], As, cs, [sig], gamma=gamma,
+                        u_lb=[0.0], u_eta=[1.0], u_count=[len(drifts)])
+    p.w_lb, p.w_eta, p.w_count = [0.0], [1.0], [len(pushes)]
+    return p
+
+
+@pytest.mark.parametrize("kind,N,safe", [("reach_avoid", 2, {1, 2, 3}), ("safety", 2, {1, 2, 3}),
+                                         ("safety", 3, {1, 2})])
+def test_disturbance_game_brute_force(kind, N, safe):
+    drifts, pushes, sig = (0, 1), (0, -1), 0.7
+    T = _chain_Tw(sig, drifts, pushes)
+    target, avoid = {4}, ({0} if kind == "reach_avoid" else set())
+    bf = _game_brute_force(T, kind, N, target, avoid, safe)
+    p = _disturbed_chain(drifts, pushes, sig)
+    if kind == "safety":
+        lo, hi = min(safe), max(safe)
+        spec = Spec(W.SAFETY, safe=([float(lo)], [float(hi)]))
+    else:
+        spec = Spec(W.REACH_AVOID, targets=[([4.0], [4.0])], avoids=[([0.0], [0.0])])
+    r = oracle.synthesize(p, spec, N)
+    np.testing.assert_allclose(r["V"], bf, atol=1e-12, rtol=0)
+
+
+def test_disturbance_reductions():
+    """A one-point disturbance grid, or disturbances that do not move the
+    mean, give the disturbance-free values bit for bit; a larger disturbance
+    grid can only lower the values (the min runs over a superset)."""
+    rng = np.random.default_rng(71)
+    w = W.random_affine(rng, 2, [11, 9], 3, gamma=5e-3, kind=W.REACH_AVOID, horizon=4)
+    p, s, N = w.problem, w.spec, w.horizon
+    ref = oracle.synthesize(p, s, N)
+    import dataclasses
+    p1 = dataclasses.replace(p, w_lb=[0.0], w_eta=[1.0], w_count=[1])
+    r1 = oracle.synthesize(p1, s, N)
+    assert np.array_equal(r1["V"], ref["V"]) and np.array_equal(r1["pi"], ref["pi"])
+    rec = p.params.reshape(p.n_inputs, -1)
+    p3 = dataclasses.replace(p, w_lb=[-1.0], w_eta=[1.0], w_count=[3], params=np.repeat(rec, 3, axis=0).reshape(-1))
+    r3 = oracle.synthesize(p3, s, N)
+    assert np.array_equal(r3["V"], ref["V"]) and np.array_equal(r3["pi"], ref["pi"])
+    # genuine pushes of the mean: a superset of pushes can only lower V
+    A = rec[:, :4].reshape(-1, 2, 2)
+    c = rec[:, 4:]
+    pushes_small, pushes_big = [0.0, 0.3], [0.0, 0.3, -0.4]
+    vals = []
+    for pushes in (pushes_small, pushes_big):
+        As, cs = [], []
+        for u in range(p.n_inputs):
+            for pw in pushes:
+                As.append(A[u])
+                cs.append(c[u] + pw)
+        q = dataclasses.replace(p, w_lb=[0.0], w_eta=[1.0], w_count=[len(pushes)], params=W.affine_params(As, cs))
+        vals.append(oracle.synthesize(q, s, N)["V"])
+    assert np.all(vals[1] <= vals[0] + 1e-15) and np.all(vals[0] <= ref["V"] + 1e-15)
+    assert np.any(vals[1] < vals[0] - 1e-6)
+
+
+def test_disturbance_action_values_are_min_over_w():
+    """Each input's value is the min over the disturbance points of its window
+    sums, formed here from the pinned rows (row(p, x, u, w))."""
+    p = _disturbed_chain((0, 1, -1), (0, -1, 1), 0.6)
+    rng = np.random.default_rng(5)
+    Vn = rng.uniform(0.0, 1.0, size=5)
+    for x in range(5):
+        av = oracle.action_values(p, Vn, x)
+        for u in range(3):
+            sums = []
+            for wv in range(3):
+                o, pr = oracle.row(p, x, u, wv)
+                sums.append(float(pr @ Vn))      # dense chain: window = the whole grid, origin 0
+                assert o[0] == 0
+            assert abs(av[u] - min(sums)) <= 1e-15
+
+
+# --------------------------------------------------------------------------
 # P8: deterministic limit equals graph reachability (BFS)
 # --------------------------------------------------------------------------
 def _bfs_reach(n_states, succ, target, avoid, N):

@@ -51,6 +51,11 @@ class Problem:
     sigma: List[float]          # per-dim noise standard deviation
     gamma: float = 0.0          # cutting threshold (0 = dense when window is None)
     window: Optional[List[int]] = None
+    # disturbance grid (empty: none); with one, params holds (A, c) per
+    # (input, disturbance) pair, disturbance fastest
+    w_lb: List[float] = field(default_factory=list)
+    w_eta: List[float] = field(default_factory=list)
+    w_count: List[int] = field(default_factory=list)
 
     @property
     def n(self) -> int:
@@ -67,6 +72,10 @@ class Problem:
     @property
     def n_inputs(self) -> int:
         return int(np.prod(self.u_count, dtype=np.int64))
+
+    @property
+    def n_disturbances(self) -> int:
+        return int(np.prod(self.w_count, dtype=np.int64)) if self.w_count else 1
 
 
 @dataclass
@@ -131,6 +140,56 @@ def robot_lin(n_per_dim: int = 41, horizon: int = 8, precision: str = "fp64") ->
     p.params = linear_system_params(np.eye(2), np.eye(2), ucs)
     spec = Spec(REACH_AVOID, targets=[([3.0, 3.0], [5.0, 5.0])], avoids=[([-1.0, -1.0], [1.0, 1.0])])
     return Workload(p, spec, horizon, precision=precision, tmode="stored_full")
+
+
+def disturbed_affine_params(A_of, c_of, ucs: np.ndarray, wcs: np.ndarray) -> np.ndarray:
+    """Pack (A, c) per (input, disturbance) pair, disturbance fastest:
+    A_of(u, w) and c_of(u, w) take the pair's centres."""
+    As, cs = [], []
+    for u in ucs:
+        for w in wcs:
+            As.append(A_of(u, w))
+            cs.append(c_of(u, w))
+    return affine_params(As, cs)
+
+
+def disturbance_centres(p: Problem) -> np.ndarray:
+    """All disturbance points in C order (last dim fastest)."""
+    axes = [p.w_lb[d] + np.arange(p.w_count[d], dtype=np.float64) * p.w_eta[d] for d in range(len(p.w_count))]
+    mesh = np.meshgrid(*axes, indexing="ij")
+    return np.stack([g.reshape(-1) for g in mesh], axis=1)
+
+
+# ---------------------------------------------------------------------------
+# robot_dist: the paper's 2-D robot of Sec. 7 with its bounded disturbance,
+# x1+ = x1 + tau v1 cos(v2) + w, x2+ = x2 + tau v1 sin(v2) + w (the second
+# line read with v1, like the first), tau = 10, X = [-10,10]^2 at 0.5,
+# U = [-1,1]^2, W = [-1,1] at 0.2, Sigma = diag(0.75, 0.75), gamma = 1e-3
+# (13 x 13 windows), safety in X for 8 steps.  Inputs at 0.2 give the
+# 41^2 x 11^2 = 203401 state-input pairs of the paper's safety rows.
+# ---------------------------------------------------------------------------
+def robot_dist(n_per_dim: int = 41, u_step: float = 0.2, w_step: float = 0.2, horizon: int = 8,
+               kind: str = SAFETY) -> Workload:
+    lo, hi = -10.0, 10.0
+    eta = (hi - lo) / (n_per_dim - 1)
+    nu1 = int(round(2.0 / u_step)) + 1
+    nw = int(round(2.0 / w_step)) + 1
+    tau = 10.0
+    p = Problem(
+        name=f"robot_dist_{n_per_dim}",
+        x_lb=[lo, lo], x_eta=[eta, eta], x_count=[n_per_dim, n_per_dim], x_periodic=[0, 0],
+        u_lb=[-1.0, -1.0], u_eta=[u_step, u_step], u_count=[nu1, nu1],
+        sys_kind=AFFINE, params=np.zeros(0), sigma=[math.sqrt(0.75)] * 2, gamma=1e-3, window=None,
+        w_lb=[-1.0], w_eta=[w_step], w_count=[nw])
+    p.params = disturbed_affine_params(
+        lambda u, w: np.eye(2),
+        lambda u, w: np.array([tau * u[0] * math.cos(u[1]) + w[0], tau * u[0] * math.sin(u[1]) + w[0]]),
+        input_centres(p), disturbance_centres(p))
+    if kind == SAFETY:
+        spec = Spec(SAFETY, safe=([lo, lo], [hi, hi]))
+    else:
+        spec = Spec(REACH_AVOID, targets=[([5.0, 5.0], [10.0, 10.0])], avoids=[([-2.0, -2.0], [2.0, 2.0])])
+    return Workload(p, spec, horizon, precision="fp32", tmode="otf")
 
 
 # ---------------------------------------------------------------------------
