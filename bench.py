@@ -183,6 +183,9 @@ WORKLOADS = {
     "rooms7": (lambda s: W.rooms7(n_per_dim=s or 9), "stored_separable", "fp32_kahan",
                "7-room temperature ring 9^7 states, 5 inputs, sigma 0.02, window 3^7, safety, horizon 10"),
     "traffic6": (lambda s: W.traffic6(n_per_dim=s or 21), "stored_separable", "fp32_kahan", TRAFFIC_NAME),
+    "robot_dist": (lambda s: W.robot_dist(n_per_dim=s or 41), "otf", "fp32",
+                   "2-D robot of Sec. 7 with its disturbance: 41^2 states, 121 inputs, 11 disturbance points, "
+                   "Sigma = 0.75 I, gamma 1e-3 (13x13 window), safety in X, horizon 8 (203401 state-input pairs)"),
 }
 
 
@@ -203,7 +206,7 @@ def workload_name(args) -> str:
 
 def transitions_per_step(w, window_slots: int) -> int:
     p = w.problem
-    return p.n_states * p.n_inputs * window_slots * w.horizon
+    return p.n_states * p.n_inputs * p.n_disturbances * window_slots * w.horizon
 
 
 # ---------------------------------------------------------------------------
@@ -474,7 +477,7 @@ def time_oracle_sample(w, n_states: int, seed: int = W.SEED, nthreads: int = 0):
     Vn = rng.uniform(0.0, 1.0, size=w.problem.n_states)
     t0 = time.perf_counter()
     oracle.backup_states(w.problem, w.spec, Vn, st, nthreads=nthreads)
-    return time.perf_counter() - t0, len(st) * w.problem.n_inputs * window_slots_of(w)
+    return time.perf_counter() - t0, len(st) * w.problem.n_inputs * w.problem.n_disturbances * window_slots_of(w)
 
 
 # seeded states per oracle backup sample (full rows): all cores for the CPU
@@ -505,16 +508,16 @@ def oracle_step(args, w):
     """One timed step of the oracle and its description: the whole workload
     where the oracle finishes it in seconds (robot, unicycle), else one
     backup at a bounded set of seeded states with full rows."""
-    if args.workload in ("unicycle", "robot"):
+    if args.workload in ("unicycle", "robot", "robot_dist"):
         slots = window_slots_of(w)
-        trans = w.problem.n_states * w.problem.n_inputs * slots * w.horizon
+        trans = w.problem.n_states * w.problem.n_inputs * w.problem.n_disturbances * slots * w.horizon
         return (lambda: time_oracle(w, w.horizon)[0], trans,
                 f"the whole workload per step (full grid, {w.horizon} backups), FP64")
     n_s = REFERENCE_SAMPLE.get(args.workload, 100)
 
     def run():
         return time_oracle_sample(w, n_s)[0]
-    trans = min(n_s, w.problem.n_states) * w.problem.n_inputs * window_slots_of(w)
+    trans = min(n_s, w.problem.n_states) * w.problem.n_inputs * w.problem.n_disturbances * window_slots_of(w)
     return run, trans, f"one backup at {n_s} seeded states (full rows) per step, FP64"
 
 
@@ -692,7 +695,7 @@ def main():
     cpu = None
     max_dv = None
     if not args.no_cpu_baseline:
-        if args.workload in ("unicycle", "robot"):
+        if args.workload in ("unicycle", "robot", "robot_dist"):
             dt, ref = time_oracle(w, w.horizon)
             cpu = {"value": r["trans"] / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"the whole workload once (full grid, {w.horizon} backups), FP64"}

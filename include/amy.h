@@ -50,7 +50,7 @@ typedef struct amy_server_s *amy_server;
  * lb[d] + j*eta[d] for 0 <= j < count[d]; cell j is [centre - eta/2,
  * centre + eta/2).  periodic[d] != 0 makes dim d wrap modulo count[d]
  * (periodic may be NULL).  n in 1..8. */
-typedef struct {
+typedef struct amy_grid_s {
     int32_t n;
     const double *lb;
     const double *eta;
@@ -58,14 +58,24 @@ typedef struct {
     const uint8_t *periodic;
 } amy_grid;
 
-/* System f of Eq. 4 (no disturbance), evaluated at representative points.
+/* System f of Eq. 4, evaluated at representative points.
  * AMY_SYS_AFFINE_PER_INPUT: for each discrete input u (C order over the input
  *   grid) params holds A_u (n*n, row-major) then c_u (n); the mean is
  *   mu_i = (sum_j A_u[i][j] * x_j, summed j = 0..n-1 from 0.0) + c_u[i],
  *   every product and sum rounded separately in FP64 (no fused multiply-add).
  *   n_params must be n_u * (n*n + n).
  * AMY_SYS_UNICYCLE: n = 3, m = 2, params = {tau}; with state (x, y, th) and
- *   input (v, w): mu = (x + (tau*v)*cos(th), y + (tau*v)*sin(th), th + tau*w). */
+ *   input (v, w): mu = (x + (tau*v)*cos(th), y + (tau*v)*sin(th), th + tau*w).
+ * disturb: the disturbance grid W^ of the dt-SCS with bounded disturbances
+ *   (Sec. 3; the representative points of Sec. 4), or NULL for none (the
+ *   system of Eq. 4).  With a grid of n_w points (C order, p = disturb->n
+ *   dims, m + p <= 8) the synthesis is the max-min game of the Remark in
+ *   Sec. 3: every input's value is the min over the n_w disturbance points
+ *   of its window sums (Algorithm 4's inner min), and the policy is the
+ *   lowest input maximising that value.  Only the affine kind takes a grid:
+ *   params then holds one (A, c) record per (input, disturbance) pair,
+ *   disturbance fastest (record u * n_w + w), n_params = n_u * n_w * (n*n + n);
+ *   disturb->periodic is ignored. */
 typedef enum { AMY_SYS_AFFINE_PER_INPUT = 0, AMY_SYS_UNICYCLE = 1 } amy_sys_kind;
 typedef struct {
     int32_t kind;
@@ -73,6 +83,7 @@ typedef struct {
     int32_t m;
     const double *params;
     int64_t n_params;
+    const struct amy_grid_s *disturb;  /* NULL: no disturbance */
 } amy_system;
 
 /* Cutting region (Sec. 5.2 and its Remark on constructing the region).
@@ -210,6 +221,8 @@ typedef struct {
                                    (amy_set_step_wait; picked by the autotuner) */
     int32_t backup_launch_kernels; /* kernels one backup launch of amy_kernel_times
                                    runs (2 for kernel 6, else 1) */
+    int32_t n_disturbances;     /* disturbance points n_w (1 without a grid); n_inputs
+                                   counts the control inputs */
 } amy_info_t;
 
 /* Points per dim of [lb, ub] with step eta: floor((ub-lb)/eta + 1e-9) + 1

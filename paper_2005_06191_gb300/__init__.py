@@ -84,6 +84,9 @@ def _problem_structs(k: _Keep, p):
     sysd.n, sysd.m = p.n, p.m
     sysd.params = k.f64(p.params)
     sysd.n_params = int(np.asarray(p.params).size)
+    wc = list(getattr(p, "w_count", None) or [])
+    if wc:
+        sysd.disturb = C.pointer(k.obj(_grid(k, p.w_lb, p.w_eta, wc)))
     states = _grid(k, p.x_lb, p.x_eta, p.x_count, p.x_periodic)
     inputs = _grid(k, p.u_lb, p.u_eta, p.u_count)
     cut = _abi.amy_cut()
@@ -234,6 +237,7 @@ def amy_info(h: AmyHandle) -> dict:
         "input_runs": int(info.input_runs), "inner_span": int(info.inner_span),
         "build_kernels": int(info.build_kernels), "tile_outer_rows": int(info.tile_outer_rows),
         "step_wait": int(info.step_wait), "backup_launch_kernels": int(info.backup_launch_kernels),
+        "n_disturbances": int(info.n_disturbances),
     }
 
 

@@ -26,7 +26,7 @@ class amy_grid(C.Structure):
 
 class amy_system(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n", C.c_int32), ("m", C.c_int32), ("params", DP),
-                ("n_params", C.c_int64)]
+                ("n_params", C.c_int64), ("disturb", C.POINTER(amy_grid))]
 
 
 class amy_cut(C.Structure):
@@ -57,7 +57,7 @@ class amy_info_t(C.Structure):
                 ("grouped_inputs", C.c_int32), ("backup_kernel", C.c_int32), ("input_runs", C.c_int32),
                 ("inner_span", C.c_int32), ("build_kernels", C.c_int32),
                 ("tile_outer_rows", C.c_int32), ("step_wait", C.c_int32),
-                ("backup_launch_kernels", C.c_int32)]
+                ("backup_launch_kernels", C.c_int32), ("n_disturbances", C.c_int32)]
 
 
 class amy_server_opts(C.Structure):

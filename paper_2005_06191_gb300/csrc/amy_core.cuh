@@ -34,7 +34,9 @@ constexpr uint8_t F_TARGET = 1, F_AVOID = 2, F_SAFE = 4;
 
 struct Geom {
     int32_t n, m;
-    int32_t nx, nu;              // states (< 2^31) and inputs (<= 65535)
+    int32_t nx, nu;              // states (< 2^31) and inputs: (input, disturbance) pairs
+    int32_t nw;                  // disturbance points per input (1: no disturbance); the
+                                 // pair index is u * nw + w, so nu / nw control inputs
     int32_t N[MAXD];             // points per state dim
     int32_t stride[MAXD];        // C-order strides of the state index
     double lb[MAXD], eta[MAXD];

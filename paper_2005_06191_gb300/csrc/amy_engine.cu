@@ -95,8 +95,30 @@ amy_status fill_geom(const amy_system *sys, const amy_grid *st, const amy_grid *
         nu *= in->count[d];
         if (nu > 65535) return set_error(AMY_E_INVALID_ARG, "more than 65535 inputs");
     }
+    // disturbance grid (Sec. 3): its dims follow the input dims, so that the
+    // (input, disturbance) pairs are enumerated in C order with the
+    // disturbance fastest -- pair index u * nw + w
+    int64_t nw = 1;
+    const amy_grid *dg = sys->disturb;
+    if (dg && dg->n > 0) {
+        if (sys->kind != AMY_SYS_AFFINE_PER_INPUT)
+            return set_error(AMY_E_UNSUPPORTED, "a disturbance grid needs the affine system kind");
+        if (m + dg->n > MAXD) return set_error(AMY_E_INVALID_ARG, "input and disturbance dims must total at most 8");
+        if (!dg->lb || !dg->eta || !dg->count) return set_error(AMY_E_INVALID_ARG, "null disturbance grid array");
+        for (int d = 0; d < dg->n; ++d) {
+            if (dg->count[d] < 1 || !(dg->eta[d] > 0.0) || !std::isfinite(dg->lb[d]))
+                return set_error(AMY_E_INVALID_ARG, "bad disturbance grid in dim %d", d);
+            g.ucount[m + d] = dg->count[d];
+            g.ulb[m + d] = dg->lb[d];
+            g.ueta[m + d] = dg->eta[d];
+            nw *= dg->count[d];
+            if (nu * nw > (1 << 24)) return set_error(AMY_E_INVALID_ARG, "more than 2^24 input-disturbance pairs");
+        }
+        g.m = m + dg->n;
+    }
     g.nx = (int32_t)nx;
-    g.nu = (int32_t)nu;
+    g.nu = (int32_t)(nu * nw);
+    g.nw = (int32_t)nw;
     int64_t s = 1;
     for (int d = n - 1; d >= 0; --d) {
         g.stride[d] = (int32_t)s;
@@ -104,8 +126,8 @@ amy_status fill_geom(const amy_system *sys, const amy_grid *st, const amy_grid *
     }
     // system
     if (sys->kind == AMY_SYS_AFFINE_PER_INPUT) {
-        if (!sys->params || sys->n_params != nu * (int64_t)(n * n + n))
-            return set_error(AMY_E_INVALID_ARG, "affine system needs n_u*(n*n+n) params");
+        if (!sys->params || sys->n_params != nu * nw * (int64_t)(n * n + n))
+            return set_error(AMY_E_INVALID_ARG, "affine system needs n_u*n_w*(n*n+n) params");
         g.sys = SYS_AFFINE;
     } else if (sys->kind == AMY_SYS_UNICYCLE) {
         if (n != 3 || m != 2 || !sys->params || sys->n_params < 1)
@@ -1324,7 +1346,8 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     amy_info_t &inf = h->info;
     memset(&inf, 0, sizeof inf);
     inf.n_states = g.nx;
-    inf.n_inputs = g.nu;
+    inf.n_inputs = g.nu / g.nw;
+    inf.n_disturbances = g.nw;
     inf.n = g.n;
     for (int d = 0; d < g.n; ++d) {
         inf.window[d] = g.W[d];

@@ -38,7 +38,7 @@ int fast_wm(const Geom &g, int prec) {
 
 bool plane_structure(const Geom &g, int tmode, int prec, int64_t &rows, int32_t &Ppad) {
     const int n = g.n;
-    if (tmode != TM_SEPARABLE || prec == AMY_PREC_FP64 || n < 4 || g.periodic != 0) return false;
+    if (tmode != TM_SEPARABLE || prec == AMY_PREC_FP64 || n < 4 || g.periodic != 0 || g.nw != 1) return false;
     if (fast_wm(g, AMY_PREC_FP32) == 0) return false;
     const int64_t P = (int64_t)g.N[n - 2] * g.N[n - 1];
     if (P > PLANE_MAX_THREADS) return false;
@@ -133,7 +133,8 @@ FastShape fast_shape(const Geom &g, int tmode, const FastCall &c, int sm_count) 
     FastShape sh;
     const int wm = fast_wm(g, AMY_PREC_FP32);
     const int var = wm ? fast_variant(g, wm, tmode) : VAR_GENERAL;
-    sh.staged = wm > 0 && wm <= 5 && tmode == TM_SEPARABLE && var >= VAR_EXACT && g.n <= 3 && !c.no_stage;
+    sh.staged = wm > 0 && wm <= 5 && tmode == TM_SEPARABLE && var >= VAR_EXACT && g.n <= 3 && !c.no_stage &&
+                g.nw == 1;
     if (sh.staged) {
         staged_default_shape(g, c, sm_count, sh.ulanes, sh.tilex);
     } else {

@@ -227,7 +227,14 @@ __device__ __forceinline__ void backup_tile(const Geom &g, const FastArgs<VT> &a
             cth = cos(xc[2]);
             sth = sin(xc[2]);
         }
-        for (int u = c; u < g.nu; u += UL) {
+        // Inputs of this lane: u = c, c + UL, ...; with a disturbance grid
+        // (nw points per input, pair index u * nw + w) the lane takes whole
+        // blocks of nw pairs and keeps the min over each block (the
+        // adversary's move of the max-min game) before the max over inputs.
+        const int NW = g.nw;
+        int wk = 0;
+        float mn = 0.0f;
+        for (int u = c * NW; u < g.nu; ++u) {
             float tA[WM], tB[WM], tL[WM];
             int32_t oA[WM], oB[WM], oL[WM];
 #pragma unroll
@@ -422,9 +429,24 @@ __device__ __forceinline__ void backup_tile(const Geom &g, const FastArgs<VT> &a
                 }
                 s = acc;
             }
-            if (s > best) {
-                best = s;
-                arg = u;
+            if (NW == 1) {
+                if (s > best) {
+                    best = s;
+                    arg = u;
+                }
+                u += UL - 1;
+            } else {
+                mn = wk == 0 ? s : fminf(mn, s);
+                if (wk == NW - 1) {
+                    if (mn > best) {
+                        best = mn;
+                        arg = u / NW;
+                    }
+                    wk = 0;
+                    u += (UL - 1) * NW;
+                } else {
+                    ++wk;
+                }
             }
         }
     }

@@ -300,7 +300,7 @@ amy_status launch_staged_ns(const Geom &g, const FastCall &c, int sm_count, cuda
 template <class VT, int WM, int TM>
 amy_status launch_var(const Geom &g, int var, const FastCall &c, int sm, cudaStream_t st) {
     if constexpr (WM <= 5 && TM == TM_SEPARABLE) {
-        if (var >= VAR_EXACT && g.n <= 3 && !c.no_stage) {
+        if (var >= VAR_EXACT && g.n <= 3 && !c.no_stage && g.nw == 1) {
             if (g.n == 1) return launch_staged_ns<VT, WM, TM, 1>(g, c, sm, st);
             if (g.n == 2) return launch_staged_ns<VT, WM, TM, 2>(g, c, sm, st);
             return launch_staged_ns<VT, WM, TM, 3>(g, c, sm, st);

@@ -183,7 +183,7 @@ FastShape fast_shape(const Geom &g, int tmode, const FastCall &c, int sm_count);
 // depending on its own coordinate (so each dim has origin bounds), 4-word
 // input parts and records, and an innermost-dim table of at most 4096 records.
 inline bool runs_kernel_applies(const Geom &g, int wm) {
-    if (g.n < 2 || g.n > 3 || g.nu > 512 || g.urw != 4) return false;
+    if (g.n < 2 || g.n > 3 || g.nu > 512 || g.urw != 4 || g.nw != 1) return false;
     for (int d = 0; d < g.n; ++d)
         if (g.tsx[d][d] == 0 || g.trw[d] != 4 * ((wm + 1 + 3) / 4)) return false;
     return g.tent[g.n - 1] <= 4096 && g.shoff > 0;

@@ -47,6 +47,8 @@ template <> __device__ __forceinline__ unorm16 vstore_cast<unorm16, float>(float
     return r;
 }
 
+__device__ __forceinline__ float min_r(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double min_r(double a, double b) { return fmin(a, b); }
 __device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
 
@@ -325,8 +327,10 @@ __global__ void __launch_bounds__(256) k_backup(const __grid_constant__ Geom g, 
         } else {
             best = R(-1);
             arg = 0;
-            for (int u = 0; u < g.nu; ++u) {
-                const R s = sbuf[u * TX + t];
+            // each input's value: min over its disturbance block (nw = 1: none)
+            for (int u = 0; u < g.nu / g.nw; ++u) {
+                R s = sbuf[(u * g.nw) * TX + t];
+                for (int w = 1; w < g.nw; ++w) s = min_r(s, sbuf[(u * g.nw + w) * TX + t]);
                 if (s > best) {
                     best = s;
                     arg = (uint16_t)u;
@@ -531,8 +535,10 @@ __global__ void __launch_bounds__(256) k_argmax_rows(const __grid_constant__ Geo
         } else {
             best = R(-1);
             arg = 0;
-            for (int u = 0; u < g.nu; ++u) {
-                const R s = S[(int64_t)u * g.nx + x];
+            // each input's value: min over its disturbance block (nw = 1: none)
+            for (int u = 0; u < g.nu / g.nw; ++u) {
+                R s = S[(int64_t)(u * g.nw) * g.nx + x];
+                for (int w = 1; w < g.nw; ++w) s = min_r(s, S[(int64_t)(u * g.nw + w) * g.nx + x]);
                 if (s > best) {
                     best = s;
                     arg = (uint16_t)u;
