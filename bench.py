@@ -575,6 +575,18 @@ def run_served(args, rank, world):
     t_plain = time.perf_counter() - t0
     rate = len(reqs) / t_plain
 
+    # closed loop with directly launched ticks, for comparison with the graphs
+    srv_direct = amy.amy_server_create(batched=True, max_slots=64, use_graphs=False)
+    tk = [amy.amy_submit(srv_direct, w) for w in reqs[:32]]
+    for t in tk:
+        amy.amy_wait(srv_direct, t)
+    t0 = time.perf_counter()
+    tk = [amy.amy_submit(srv_direct, w) for w in reqs]
+    for t in tk:
+        amy.amy_wait(srv_direct, t)
+    t_direct = time.perf_counter() - t0
+    srv_direct.close()
+
     srv = amy.amy_server_create(batched=True, max_slots=64)
     tk = [amy.amy_submit(srv, w) for w in reqs[:32]]  # warm: autotune the shape classes
     for t in tk:
@@ -627,6 +639,7 @@ def run_served(args, rank, world):
             "plain": {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "throughput": total_trans / span_p},
         }
     stats = amy.amy_server_stats(srv)
+    stats.update(amy.amy_server_graph_stats(srv))
     srv.close()
     if rank != 0:
         return
@@ -637,8 +650,9 @@ def run_served(args, rank, world):
         "data": "synthetic",
         "config": {"workload": f"served stream: {len(reqs)} seeded random linear problems (2-4 dims, "
                                "20^2-15^4 states, 4-16 inputs, gamma 1e-3, horizons 5-50), Poisson arrivals"},
-        "closed_loop": {"plain_s": t_plain, "batched_s": t_batched,
-                        "plain_throughput": total_trans / t_plain, "batched_throughput": total_trans / t_batched},
+        "closed_loop": {"plain_s": t_plain, "batched_s": t_batched, "batched_direct_ticks_s": t_direct,
+                        "plain_throughput": total_trans / t_plain, "batched_throughput": total_trans / t_batched,
+                        "batched_direct_ticks_throughput": total_trans / t_direct},
         "open_loop": out, "server_stats": stats, "transitions_total": total_trans,
     }
     print(json.dumps(line), flush=True)

@@ -437,7 +437,8 @@ typedef struct {
     int32_t max_slots;          /* problems resident at once; 0 = 64 */
     int32_t max_queue;          /* queued + running requests; 0 = 4096 */
     int32_t batched;            /* 1: one persistent kernel per tick; 0: per problem */
-    int32_t use_graphs;         /* 1: replay captured CUDA graphs for the tick */
+    int32_t use_graphs;         /* 1: ticks whose layout recurs replay a captured CUDA
+                                   graph (amy_server_graph_stats) */
     int32_t device;             /* CUDA device ordinal */
 } amy_server_opts;
 
@@ -474,9 +475,21 @@ amy_status amy_poll(amy_server s, uint64_t ticket, amy_result *out);
 amy_status amy_wait(amy_server s, uint64_t ticket, int64_t timeout_us, amy_result *out);
 /* Cancel a queued or running request; its result reports AMY_E_CANCELLED. */
 amy_status amy_cancel(amy_server s, uint64_t ticket);
-/* Counters: completed requests, ticks, kernel launches, current resident problems. */
+/* Counters: completed requests, ticks, kernel launches (a replayed tick graph
+ * counts one), current resident problems. */
 amy_status amy_server_stats(amy_server s, int64_t *completed, int64_t *ticks, int64_t *launches,
                             int32_t *resident);
+/* With use_graphs: tick graphs captured and tick graphs replayed so far.  A
+ * tick's launches depend on its layout -- which problems take part, in which
+ * order, reading which of their two V vectors -- and a layout seen a second
+ * time is captured into a CUDA graph (batch tables in device memory the
+ * graph owns) and replayed while it recurs; a stable set of residents
+ * alternates between two layouts.  Graphs of a problem are dropped when it
+ * leaves (at most 32 are kept, least recently used first).  In this mode
+ * every tick writes each problem's V_k and pi_k to its output buffers (the
+ * last tick's are the ones returned), so results equal those without graphs
+ * bit for bit.  The paper has no counterpart. */
+amy_status amy_server_graph_stats(amy_server s, int64_t *captures, int64_t *replays);
 void amy_server_destroy(amy_server s);
 void amy_result_free(amy_result *r);
 

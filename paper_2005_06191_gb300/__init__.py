@@ -425,12 +425,14 @@ def amy_synthesize_noalloc(problem, spec, horizon: int, V_out, policy_out=None, 
 
 
 from .serving import (AmyServer, amy_cancel, amy_poll, amy_result_free,  # noqa: E402
-                      amy_server_create, amy_server_destroy, amy_server_stats, amy_submit, amy_wait)
+                      amy_server_create, amy_server_destroy, amy_server_graph_stats, amy_server_stats, amy_submit,
+                      amy_wait)
 
 __all__ = [
     "AmyError", "AmyHandle", "AmyServer", "amy_build", "amy_synthesize", "amy_backup_step",
     "amy_query_rows", "amy_info", "amy_destroy", "amy_grid_count", "amy_last_error",
     "amy_rebuild", "amy_set_profiling", "amy_set_wait_limit", "amy_set_step_wait", "amy_set_plane", "amy_backup_work", "amy_measure_l2", "amy_kernel_times", "amy_synthesize_noalloc", "amy_measure_lane_loads", "amy_measure_fma",
     "amy_server_create", "amy_submit", "amy_poll", "amy_wait", "amy_cancel", "amy_server_stats",
+    "amy_server_graph_stats",
     "amy_server_destroy", "amy_result_free", "TMODES", "PRECS", "VSTORES", "POLICY_NONE",
 ]

@@ -112,6 +112,7 @@ PROTOTYPES = {
     "amy_cancel": (C.c_int32, [C.c_void_p, C.c_uint64]),
     "amy_server_stats": (C.c_int32, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    "amy_server_graph_stats": (C.c_int32, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "amy_server_destroy": (None, [C.c_void_p]),
     "amy_result_free": (None, [C.POINTER(amy_result)]),
 }

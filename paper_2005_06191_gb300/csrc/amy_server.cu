@@ -180,6 +180,18 @@ struct amy_server_s {
     std::atomic<int32_t> n_resident{0};
     std::map<std::string, int> tune;  // input lanes per shape class
     std::string tune_path;
+    // CUDA graphs of tick layouts (opts.use_graphs): the tick's launches for a
+    // given list of (resident problem, V parity), captured on the second
+    // sighting of the layout and replayed while it repeats; each graph owns
+    // the device copy of its batch tables and tile counters
+    struct TickGraph {
+        cudaGraphExec_t exec = nullptr;
+        void *dmem = nullptr;  // batch tables + tile counters
+        int64_t last_used = 0;
+    };
+    std::map<std::vector<uint64_t>, TickGraph> graphs;
+    std::map<std::vector<uint64_t>, int64_t> layouts_seen;
+    std::atomic<int64_t> graph_replays{0}, graph_captures{0};
 };
 
 namespace {
@@ -397,10 +409,13 @@ void publish(amy_server_s *s, Req *r, amy_status st) {
     s->cv_done.notify_all();
 }
 
+void forget_graphs(amy_server_s *s, const Req *r);
+
 // A resident request leaves the ticks: copy V_0 / pi_0 out (unless
 // cancelled), free its device memory (stream-ordered) and record the event
 // after which its result can be published.
 amy_status retire(amy_server_s *s, Req *r, bool copy_out) {
+    forget_graphs(s, r);
     cudaError_t e = cudaSuccess;
     if (copy_out) {
         r->h_out_bytes = (size_t)r->g.nx * 6;
@@ -453,26 +468,113 @@ void drain(amy_server_s *s, std::unique_lock<std::mutex> &lk, bool block) {
     }
 }
 
+constexpr size_t kMaxTickGraphs = 32;
+
+void drop_graph(amy_server_s *s, amy_server_s::TickGraph &tg) {
+    if (tg.exec) cudaGraphExecDestroy(tg.exec);
+    if (tg.dmem) cudaFreeAsync(tg.dmem, s->stream);
+    tg.exec = nullptr;
+    tg.dmem = nullptr;
+}
+
+// Drops every tick graph (and layout count) whose layout contains r, when r
+// leaves the resident set: its device memory is freed, and a later request
+// may be allocated at the same host address.
+void forget_graphs(amy_server_s *s, const Req *r) {
+    const uint64_t tag = (uint64_t)(uintptr_t)r << 1;
+    auto has = [&](const std::vector<uint64_t> &k) {
+        for (uint64_t v : k)
+            if ((v & ~1ull) == tag) return true;
+        return false;
+    };
+    for (auto it = s->graphs.begin(); it != s->graphs.end();) {
+        if (has(it->first)) {
+            drop_graph(s, it->second);
+            it = s->graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    for (auto it = s->layouts_seen.begin(); it != s->layouts_seen.end();) {
+        if (has(it->first))
+            it = s->layouts_seen.erase(it);
+        else
+            ++it;
+    }
+}
+
+amy_status tick_launches(amy_server_s *s, TickSlot &slot, bool graphs, bool capture,
+                         const std::vector<uint64_t> &key);
+
 // One tick: every resident problem advances one backup -- the batched ones in
 // one persistent launch -- without waiting for the GPU (up to kTickRing ticks
-// run ahead).
+// run ahead).  With opts.use_graphs the tick's launches are a CUDA graph of
+// its layout (which problems take part, in which order, at which V parity),
+// captured the second time the layout occurs and replayed while it repeats
+// (a stable set of residents alternates between two layouts).  In that mode
+// every tick writes V_k and pi_k to the problems' output buffers, so that the
+// layout does not depend on which problems take their last step (the last
+// tick's values are the ones copied out, as without graphs).
 amy_status tick(amy_server_s *s) {
     TickSlot &slot = s->ring[s->tick_no % kTickRing];
     if (slot.used) {
         cudaError_t e = cudaEventSynchronize(slot.ev);
         if (e != cudaSuccess) return cuda_error(e, "tick slot");
     }
+    const bool graphs = s->opts.use_graphs != 0;
+    std::vector<uint64_t> key;
+    amy_server_s::TickGraph *cached = nullptr;
+    bool capture = false;
+    if (graphs) {
+        for (Req *r : s->resident)
+            if (r->k_left > 0 && !r->finishing) key.push_back(((uint64_t)(uintptr_t)r << 1) | (uint64_t)r->cur);
+        auto it = s->graphs.find(key);
+        if (it != s->graphs.end()) {
+            cached = &it->second;
+        } else {
+            capture = ++s->layouts_seen[key] >= 2;
+            if (s->layouts_seen.size() > 4 * kMaxTickGraphs) s->layouts_seen.clear();
+        }
+    }
+    if (cached) {
+        cudaError_t e = cudaGraphLaunch(cached->exec, s->stream);
+        if (e != cudaSuccess) return cuda_error(e, "tick graph launch");
+        cached->last_used = s->tick_no;
+        s->graph_replays += 1;
+        s->launches += 1;
+    } else {
+        amy_status st = tick_launches(s, slot, graphs, capture, key);
+        if (st != AMY_OK) return st;
+    }
+    cudaError_t e = cudaEventRecord(slot.ev, s->stream);
+    if (e != cudaSuccess) return cuda_error(e, "tick event");
+    slot.used = true;
+    s->tick_no += 1;
+    for (Req *r : s->resident) {
+        if (r->k_left <= 0 || r->finishing) continue;
+        r->cur ^= 1;
+        r->k_left -= 1;
+        if (r->k_left == 0) r->finishing = true;
+    }
+    s->ticks += 1;
+    return AMY_OK;
+}
+
+// The launches of one tick, enqueued directly (batch tables uploaded from the
+// tick slot), or -- capture -- as a new graph of this layout: its batch
+// tables are uploaded once into device memory the graph owns, the launches
+// are captured and the graph is launched.
+amy_status tick_launches(amy_server_s *s, TickSlot &slot, bool graphs, bool capture,
+                         const std::vector<uint64_t> &key) {
     // group the batched problems by kernel variant; the rest launch one by one
     struct Group {
         int vt, wm, tm, var;
         std::vector<Req *> rs;
     };
     std::vector<Group> groups;
+    std::vector<Req *> singles;
     for (Req *r : s->resident) {
         if (r->k_left <= 0 || r->finishing) continue;
-        const bool last = r->k_left == 1;
-        const void *Vn = r->d_V[r->cur];
-        void *Vo = r->d_V[r->cur ^ 1];
         if (s->opts.batched && r->batched) {
             Group *gp = nullptr;
             for (Group &gg : groups)
@@ -483,21 +585,38 @@ amy_status tick(amy_server_s *s) {
             }
             gp->rs.push_back(r);
         } else {
-            FastCall c = fast_call(r, Vn, Vo, last ? r->d_Vout : nullptr, last ? r->d_pi : nullptr, r->ulanes);
-            amy_status st = r->wm > 0 ? launch_backup_fast(r->g, r->tm, r->v_store, c, s->sm_count, s->stream)
-                                      : launch_backup_generic_fp32(r->g, r->tm, c, r->v_store, s->sm_count, s->stream);
-            if (st != AMY_OK) return st;
-            s->launches += 1;
+            singles.push_back(r);
         }
     }
+    // batch tables in the tick slot's pinned buffer; with a capture they go to
+    // device memory of the graph's own, uploaded before the capture begins
+    BatchEntry *d_tab = slot.d;
+    int32_t *d_cnt = slot.counter;
+    void *gmem = nullptr;
     int32_t ne = 0;
+    for (size_t gi = 0; gi < groups.size() && gi < (size_t)kMaxGroups; ++gi)
+        for (Req *r : groups[gi].rs) {
+            (void)r;
+            ++ne;
+        }
+    if (capture) {
+        const size_t tb = align256(sizeof(BatchEntry) * (size_t)std::max(ne, 1));
+        cudaError_t e = cudaMallocFromPoolAsync(&gmem, tb + sizeof(int32_t) * kMaxGroups, s->pool, s->stream);
+        if (e != cudaSuccess) return cuda_error(e, "tick graph tables");
+        d_tab = (BatchEntry *)gmem;
+        d_cnt = (int32_t *)((char *)gmem + tb);
+    }
+    ne = 0;
+    std::vector<int32_t> gfirst, gcount;
+    std::vector<int64_t> gtiles;
+    std::vector<int> gmaxn;
     for (size_t gi = 0; gi < groups.size() && gi < (size_t)kMaxGroups; ++gi) {
         Group &gg = groups[gi];
         const int32_t first = ne;
         int64_t tiles = 0;
         int max_n = 1;
         for (Req *r : gg.rs) {
-            const bool last = r->k_left == 1;
+            const bool last = graphs || r->k_left == 1;
             BatchEntry &e = slot.h[ne++];
             e.g = r->d_geom;
             e.Vn = r->d_V[r->cur];
@@ -520,25 +639,70 @@ amy_status tick(amy_server_s *s) {
             tiles += r->ntiles;
             max_n = std::max(max_n, r->g.n);
         }
-        cudaError_t e = cudaMemcpyAsync(slot.d + first, slot.h + first, sizeof(BatchEntry) * (ne - first),
-                                        cudaMemcpyHostToDevice, s->stream);
-        if (e != cudaSuccess) return cuda_error(e, "step table upload");
-        amy_status st = launch_step_group(gg.vt, gg.wm, gg.tm, gg.var, slot.d + first, ne - first, tiles,
-                                          slot.counter + gi, max_n, s->sm_count, s->stream);
-        if (st != AMY_OK) return st;
+        gfirst.push_back(first);
+        gcount.push_back(ne - first);
+        gtiles.push_back(tiles);
+        gmaxn.push_back(max_n);
+    }
+    if (ne > 0) {
+        cudaError_t e = cudaMemcpyAsync(d_tab, slot.h, sizeof(BatchEntry) * ne, cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) {
+            if (gmem) cudaFreeAsync(gmem, s->stream);
+            return cuda_error(e, "step table upload");
+        }
+    }
+    if (capture) {
+        cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(gmem, s->stream);
+            return cuda_error(e, "tick capture");
+        }
+    }
+    amy_status st = AMY_OK;
+    for (size_t gi = 0; gi < gfirst.size() && st == AMY_OK; ++gi) {
+        const Group &gg = groups[gi];
+        st = launch_step_group(gg.vt, gg.wm, gg.tm, gg.var, d_tab + gfirst[gi], gcount[gi], gtiles[gi], d_cnt + gi,
+                               gmaxn[gi], s->sm_count, s->stream);
+    }
+    for (size_t i = 0; i < singles.size() && st == AMY_OK; ++i) {
+        Req *r = singles[i];
+        const bool last = graphs || r->k_left == 1;
+        FastCall c = fast_call(r, r->d_V[r->cur], r->d_V[r->cur ^ 1], last ? r->d_Vout : nullptr,
+                               last ? r->d_pi : nullptr, r->ulanes);
+        st = r->wm > 0 ? launch_backup_fast(r->g, r->tm, r->v_store, c, s->sm_count, s->stream)
+                       : launch_backup_generic_fp32(r->g, r->tm, c, r->v_store, s->sm_count, s->stream);
+    }
+    if (capture) {
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess && st == AMY_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (st == AMY_OK && e == cudaSuccess) e = cudaGraphLaunch(exec, s->stream);
+        if (st != AMY_OK || e != cudaSuccess) {
+            if (exec) cudaGraphExecDestroy(exec);
+            cudaFreeAsync(gmem, s->stream);
+            return st != AMY_OK ? st : cuda_error(e, "tick graph");
+        }
+        // keep at most kMaxTickGraphs graphs: the least recently used goes
+        if (s->graphs.size() >= kMaxTickGraphs) {
+            auto lru = s->graphs.begin();
+            for (auto it = s->graphs.begin(); it != s->graphs.end(); ++it)
+                if (it->second.last_used < lru->second.last_used) lru = it;
+            drop_graph(s, lru->second);
+            s->graphs.erase(lru);
+        }
+        amy_server_s::TickGraph &tg = s->graphs[key];
+        tg.exec = exec;
+        tg.dmem = gmem;
+        tg.last_used = s->tick_no;
+        s->layouts_seen.erase(key);
+        s->graph_captures += 1;
         s->launches += 1;
+        return AMY_OK;
     }
-    cudaError_t e = cudaEventRecord(slot.ev, s->stream);
-    if (e != cudaSuccess) return cuda_error(e, "tick event");
-    slot.used = true;
-    s->tick_no += 1;
-    for (Req *r : s->resident) {
-        if (r->k_left <= 0 || r->finishing) continue;
-        r->cur ^= 1;
-        r->k_left -= 1;
-        if (r->k_left == 0) r->finishing = true;
-    }
-    s->ticks += 1;
+    if (st != AMY_OK) return st;
+    s->launches += (int64_t)gfirst.size() + (int64_t)singles.size();
     return AMY_OK;
 }
 
@@ -579,6 +743,9 @@ void scheduler(amy_server_s *s) {
         lk.unlock();
         cudaStreamSynchronize(s->stream);
         lk.lock();
+        for (auto &kv : s->graphs) drop_graph(s, kv.second);
+        s->graphs.clear();
+        s->layouts_seen.clear();
         for (Req *r : s->resident) {
             if (r->dmem) cudaFreeAsync(r->dmem, s->stream);
             r->dmem = nullptr;
@@ -832,6 +999,13 @@ amy_status amy_server_stats(amy_server s, int64_t *completed, int64_t *ticks, in
     return AMY_OK;
 }
 
+amy_status amy_server_graph_stats(amy_server s, int64_t *captures, int64_t *replays) {
+    if (!s) return set_error(AMY_E_INVALID_ARG, "null argument");
+    if (captures) *captures = s->graph_captures;
+    if (replays) *replays = s->graph_replays;
+    return AMY_OK;
+}
+
 void amy_server_destroy(amy_server s) {
     if (!s) return;
     {
@@ -841,6 +1015,8 @@ void amy_server_destroy(amy_server s) {
     }
     if (s->th.joinable()) s->th.join();
     save_tune(s);
+    for (auto &kv : s->graphs) drop_graph(s, kv.second);
+    s->graphs.clear();
     for (auto &kv : s->reqs) delete kv.second;
     for (TickSlot &t : s->ring) {
         if (t.h) cudaFreeHost(t.h);

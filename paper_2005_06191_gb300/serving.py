@@ -107,6 +107,13 @@ def amy_server_stats(srv: AmyServer) -> dict:
     return {"completed": c.value, "ticks": t.value, "launches": l.value, "resident": r.value}
 
 
+def amy_server_graph_stats(srv: AmyServer) -> dict:
+    """Tick graphs captured and replayed (servers created with use_graphs)."""
+    c, r = C.c_int64(0), C.c_int64(0)
+    _pkg()[0](_abi.load().amy_server_graph_stats(srv.ptr, C.byref(c), C.byref(r)))
+    return {"captures": c.value, "replays": r.value}
+
+
 def amy_result_free(res) -> None:
     _abi.load().amy_result_free(C.byref(res))
 

@@ -143,3 +143,40 @@ def test_invalid_request_rejected_at_submit(amy):
         with pytest.raises(amy.AmyError) as e:
             amy.amy_submit(srv, w)
     assert "INVALID_ARG" in str(e.value)
+
+
+@pytest.mark.parametrize("batched", [True, False])
+def test_tick_graphs_match_direct_launches(amy, batched):
+    """Ticks replayed from captured CUDA graphs (a layout captured at its
+    second occurrence) give the results of directly launched ticks bit for
+    bit, for the same mix of requests; the graphs are actually replayed."""
+    reqs = _stream(20, cap_h=24, seed=W.SEED + 23)
+    out = {}
+    for graphs in (False, True):
+        with amy.amy_server_create(batched=batched, max_slots=6, use_graphs=graphs) as srv:
+            tickets = [amy.amy_submit(srv, w) for w in reqs]
+            out[graphs] = [amy.amy_wait(srv, t, timeout_us=120_000_000) for t in tickets]
+            gs = amy.amy_server_graph_stats(srv)
+        if graphs:
+            assert gs["captures"] > 0 and gs["replays"] > gs["captures"], gs
+        else:
+            assert gs["captures"] == 0 and gs["replays"] == 0
+    for w, a, b in zip(reqs, out[False], out[True]):
+        assert a["status"] == 0 and b["status"] == 0
+        assert np.array_equal(a["V"], b["V"]), w.problem.name
+        assert np.array_equal(a["policy"], b["policy"]), w.problem.name
+
+
+def test_bf16_storage_requests(amy):
+    """Folded-bfloat16 V through the server (batched ticks, graphs on) equals
+    the single-problem path bit for bit, within 2e-3 of the oracle."""
+    reqs = _stream(6, seed=W.SEED + 29)
+    for w in reqs:
+        w.v_store = "bf16"
+    with amy.amy_server_create(batched=True) as srv:
+        results = [amy.amy_wait(srv, amy.amy_submit(srv, w), timeout_us=60_000_000) for w in reqs]
+    for w, r in zip(reqs, results):
+        V, _ = _alone(amy, w)
+        assert np.array_equal(r["V"], V)
+        ref = oracle.synthesize(w.problem, w.spec, w.horizon)
+        assert np.max(np.abs(r["V"] - ref["V"])) <= TOL["bf16"]
