@@ -50,7 +50,12 @@ class _Problem(C.Structure):
         ("gamma", C.c_double), ("window", C.POINTER(C.c_int32)),
         ("p", C.c_int32), ("w_lb", C.POINTER(C.c_double)), ("w_eta", C.POINTER(C.c_double)),
         ("w_count", C.POINTER(C.c_int32)),
+        ("noise", C.c_int32), ("noise_p0", C.POINTER(C.c_double)), ("noise_p1", C.POINTER(C.c_double)),
+        ("noise_p2", C.POINTER(C.c_double)), ("noise_p3", C.POINTER(C.c_double)),
     ]
+
+
+_NOISE = {"gaussian": 0, "uniform": 1, "exponential": 2, "beta": 3, "mult_gaussian": 4}
 
 
 class _Spec(C.Structure):
@@ -130,6 +135,9 @@ def _problem(p, keep: _Keep) -> _Problem:
     s.p = len(wc)
     if wc:
         s.w_lb, s.w_eta, s.w_count = keep.f64(p.w_lb), keep.f64(p.w_eta), keep.i32(wc)
+    s.noise = _NOISE[getattr(p, "noise", "gaussian")]
+    for i, arr in enumerate(list(getattr(p, "noise_params", None) or [])[:4]):
+        setattr(s, f"noise_p{i}", keep.f64(arr))
     return s
 
 

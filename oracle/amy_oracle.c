@@ -32,7 +32,10 @@
  *     safety as V_k = 1_S * max_u sum;
  *   - argmax ties: lowest input index; masked states carry policy 0xFFFF;
  *   - with a disturbance grid each input's value is the min over the grid
- *     (the adversary moves after the input, knowing it; Sec. 3 Remark).
+ *     (the adversary moves after the input, knowing it; Sec. 3 Remark);
+ *   - other noise distributions (Sec. 6.2): cells are kept by their centres
+ *     inside the cut interval [mu + clo, mu + chi] as in the Gaussian case;
+ *     bounded supports are their own cut; multiplicative noise is uncut.
  * The target-jump vector of Algorithm 3 is not formed: with V fixed to 1 on
  * the target and 0 on the avoid set, sum_x' T V equals T0 + T_zeroed V exactly.
  */
@@ -72,9 +75,78 @@ int64_t orc_grid_count(double lb, double ub, double eta) {
     return (int64_t)floor((ub - lb) / eta + 1e-9) + 1;
 }
 
-/* Cutting region size, Sec. 5.2 and its Remark: solve the 1-D density = gamma
- * per dimension, then the fixed number of slots per dimension. */
+/* Cutting region of one dimension in gamma mode (Sec. 5.2 and its Remark):
+ * the noise values t with density >= gamma, as the interval [clo, chi]
+ * around the mean.  Gaussian: the 1-D density equals gamma at +-xs.  For the
+ * other distributions of Sec. 6.2 the region follows their support: the
+ * support itself when it is bounded (uniform: where the flat density reaches
+ * gamma at all; beta), [0, log(rate/gamma)/rate] for the exponential.
+ * Multiplicative noise has no cut.  Returns 0, or -1 when the region is
+ * empty or not defined. */
+static int cut_interval(const orc_problem *p, int d, double *clo, double *chi) {
+    const double g = p->gamma;
+    switch (p->noise) {
+        case ORC_NOISE_GAUSSIAN: {
+            double s = p->sigma[d];
+            double arg = 1.0 / (g * s * sqrt(2.0 * M_PI));
+            if (!(arg > 1.0)) return -1; /* gamma at or above the peak density */
+            double xs = s * sqrt(2.0 * log(arg));
+            *clo = -xs;
+            *chi = xs;
+            return 0;
+        }
+        case ORC_NOISE_UNIFORM: {
+            double a = p->noise_p0[d];
+            if (!(g <= 1.0 / (2.0 * a))) return -1;
+            *clo = -a;
+            *chi = a;
+            return 0;
+        }
+        case ORC_NOISE_EXPONENTIAL: {
+            double rate = p->noise_p0[d];
+            if (!(g < rate)) return -1;
+            *clo = 0.0;
+            *chi = log(rate / g) / rate;
+            return 0;
+        }
+        case ORC_NOISE_BETA:
+            *clo = p->noise_p2[d];
+            *chi = p->noise_p3[d];
+            return 0;
+        default:
+            return -1;
+    }
+}
+
+static int noise_valid(const orc_problem *p) {
+    for (int d = 0; d < p->n; ++d) {
+        switch (p->noise) {
+            case ORC_NOISE_GAUSSIAN:
+                if (!(p->sigma[d] > 0.0)) return 0;
+                break;
+            case ORC_NOISE_UNIFORM:
+            case ORC_NOISE_EXPONENTIAL:
+            case ORC_NOISE_MULT_GAUSSIAN:
+                if (!p->noise_p0 || !(p->noise_p0[d] > 0.0)) return 0;
+                break;
+            case ORC_NOISE_BETA: {
+                if (!p->noise_p0 || !p->noise_p1 || !p->noise_p2 || !p->noise_p3) return 0;
+                double a = p->noise_p0[d], b = p->noise_p1[d];
+                if (!(a >= 1.0 && b >= 1.0 && a == floor(a) && b == floor(b) && a + b <= 64.0)) return 0;
+                if (!(p->noise_p3[d] > p->noise_p2[d])) return 0;
+                break;
+            }
+            default:
+                return 0;
+        }
+    }
+    return 1;
+}
+
+/* Cutting region size, Sec. 5.2 and its Remark: the cut interval per
+ * dimension, then the fixed number of slots per dimension. */
 int orc_window_shape(const orc_problem *p, int32_t *W, double *xstar) {
+    if (!noise_valid(p)) return -1;
     for (int d = 0; d < p->n; ++d) {
         if (p->window != NULL) {
             W[d] = p->window[d];
@@ -86,15 +158,13 @@ int orc_window_shape(const orc_problem *p, int32_t *W, double *xstar) {
             W[d] = p->x_count[d];
             xstar[d] = INFINITY;
         } else {
-            double s = p->sigma[d];
-            double arg = 1.0 / (p->gamma * s * sqrt(2.0 * M_PI));
-            if (!(arg > 1.0)) return -1; /* gamma at or above the peak density */
-            double xs = s * sqrt(2.0 * log(arg));
-            double w = floor(2.0 * xs / p->x_eta[d]) + 1.0;
+            double clo, chi;
+            if (cut_interval(p, d, &clo, &chi) != 0) return -1;
+            double w = floor((chi - clo) / p->x_eta[d]) + 1.0;
             if (!(w >= 1.0) || w > 1.0e6) return -1;
             W[d] = (int32_t)w;
             if (is_periodic(p, d) && W[d] > p->x_count[d]) return -1;
-            xstar[d] = xs;
+            xstar[d] = chi;
         }
     }
     return 0;
@@ -145,20 +215,75 @@ static double cell_mass(double elo, double ehi, double mu, double sigma) {
     return 1.0 - 0.5 * erfc((mu - elo) / k) - 0.5 * erfc((ehi - mu) / k);
 }
 
+/* Regularised incomplete beta I_z(a, b) for integer a, b >= 1: the
+ * probability that at least a of a + b - 1 independent trials with success
+ * probability z succeed, sum_{j=a}^{a+b-1} C(a+b-1, j) z^j (1-z)^{a+b-1-j}. */
+static double inc_beta_int(int a, int b, double z) {
+    if (z <= 0.0) return 0.0;
+    if (z >= 1.0) return 1.0;
+    const int n = a + b - 1;
+    double sum = 0.0;
+    for (int j = a; j <= n; ++j) {
+        double c = 1.0; /* C(n, j) */
+        for (int i = 1; i <= j; ++i) c = c * (double)(n - j + i) / (double)i;
+        sum += c * pow(z, (double)j) * pow(1.0 - z, (double)(n - j));
+    }
+    return sum;
+}
+
+/* Mass of the cell [elo, ehi) for the noise of dimension d around the mean
+ * mu (Algorithm 1's cell integral for the distributions of Sec. 6.2); xd is
+ * the state's centre in dimension d (multiplicative noise scales with it). */
+static double noise_mass(const orc_problem *p, int d, double elo, double ehi, double mu, double xd) {
+    const double tlo = elo - mu, thi = ehi - mu;
+    switch (p->noise) {
+        case ORC_NOISE_UNIFORM: {
+            const double a = p->noise_p0[d];
+            const double lo = tlo > -a ? tlo : -a, hi = thi < a ? thi : a;
+            return hi > lo ? (hi - lo) / (2.0 * a) : 0.0;
+        }
+        case ORC_NOISE_EXPONENTIAL: {
+            /* difference of the survival function exp(-rate t) at the two edges */
+            const double rate = p->noise_p0[d];
+            const double slo = tlo > 0.0 ? exp(-rate * tlo) : 1.0;
+            const double shi = thi > 0.0 ? exp(-rate * thi) : 1.0;
+            return slo - shi;
+        }
+        case ORC_NOISE_BETA: {
+            const int a = (int)p->noise_p0[d], b = (int)p->noise_p1[d];
+            const double lo = p->noise_p2[d], hi = p->noise_p3[d];
+            const double zlo = (tlo - lo) / (hi - lo), zhi = (thi - lo) / (hi - lo);
+            /* upper half: differences of the upper tail I_{1-z}(b, a) */
+            if (zlo >= 0.5) return inc_beta_int(b, a, 1.0 - zlo) - inc_beta_int(b, a, 1.0 - zhi);
+            return inc_beta_int(a, b, zhi) - inc_beta_int(a, b, zlo);
+        }
+        case ORC_NOISE_MULT_GAUSSIAN: {
+            const double s = p->noise_p0[d] * fabs(xd);
+            if (s == 0.0) return (elo <= mu && mu < ehi) ? 1.0 : 0.0; /* no noise at x_d = 0 */
+            return cell_mass(elo, ehi, mu, s);
+        }
+        default:
+            return cell_mass(elo, ehi, mu, p->sigma[d]);
+    }
+}
+
 /* Cutting window of one dimension, Remark on constructing the cutting region:
  * origin, per-slot mass and cell index (-1 for a dropped slot). */
-static int32_t dim_window(const orc_problem *p, int d, int32_t W, double xs, double mu,
+static int32_t dim_window(const orc_problem *p, int d, int32_t W, double mu, double xd,
                           double *fac, int64_t *cell) {
     const int32_t N = p->x_count[d];
     const double lb = p->x_lb[d], eta = p->x_eta[d];
     const int per = is_periodic(p, d);
+    const int gmode = (p->window == NULL && p->gamma != 0.0);
+    double clo = 0.0, chi = 0.0;
+    if (gmode) cut_interval(p, d, &clo, &chi);
     double od;
     if (p->window != NULL)
         od = floor((mu - lb) / eta + 0.5) - (double)((W - 1) / 2);
     else if (p->gamma == 0.0)
         od = 0.0;
     else
-        od = ceil(((mu - xs) - lb) / eta);
+        od = ceil(((mu + clo) - lb) / eta);
     /* Clamp far-away origins: outside [-(W+1), N+1] every slot is off the grid
      * anyway (non-periodic); periodic origins are kept within +-2^30. */
     if (!per) {
@@ -169,18 +294,17 @@ static int32_t dim_window(const orc_problem *p, int d, int32_t W, double xs, dou
         if (!(od <= 1073741824.0)) od = 1073741824.0;
     }
     const int32_t o = (int32_t)od;
-    const int gmode = (p->window == NULL && p->gamma != 0.0);
     for (int32_t k = 0; k < W; ++k) {
         int64_t s = (int64_t)o + k;
         double c = lb + (double)s * eta;
         int keep = per || (s >= 0 && s < N);
-        if (gmode && !(c <= mu + xs)) keep = 0;
+        if (gmode && !(c <= mu + chi)) keep = 0;
         if (!keep) {
             fac[k] = 0.0;
             cell[k] = -1;
             continue;
         }
-        fac[k] = cell_mass(c - 0.5 * eta, c + 0.5 * eta, mu, p->sigma[d]);
+        fac[k] = noise_mass(p, d, c - 0.5 * eta, c + 0.5 * eta, mu, xd);
         cell[k] = per ? (((s % N) + N) % N) : s;
     }
     return o;
@@ -215,6 +339,7 @@ static int shape_of(const orc_problem *p, orc_shape *sh) {
         p->n_params != sh->nu * sh->nw * (int64_t)(p->n * p->n + p->n))
         return -1;
     if (p->sys_kind == ORC_SYS_UNICYCLE && (p->n != 3 || p->m != 2 || p->n_params < 1 || p->p != 0)) return -1;
+    if (p->noise == ORC_NOISE_MULT_GAUSSIAN && p->window == NULL && p->gamma != 0.0) return -1;
     return 0;
 }
 
@@ -223,9 +348,12 @@ static int pair_factors(const orc_problem *p, const orc_shape *sh, int64_t x, in
                         int32_t *origin, double *fac, int64_t *cell) {
     double mu[ORC_MAXD];
     if (orc_mean(p, x, u, mu) != 0) return -1;
+    int32_t xi[ORC_MAXD];
+    decode(x, p->x_count, p->n, xi);
     int off = 0;
     for (int d = 0; d < p->n; ++d) {
-        int32_t o = dim_window(p, d, sh->W[d], sh->xs[d], mu[d], fac + off, cell + off);
+        const double xd = p->x_lb[d] + (double)xi[d] * p->x_eta[d];
+        int32_t o = dim_window(p, d, sh->W[d], mu[d], xd, fac + off, cell + off);
         if (origin) origin[d] = o;
         off += sh->W[d];
     }

@@ -65,7 +65,27 @@ typedef struct {
     const double *w_lb;        /* [p] */
     const double *w_eta;       /* [p] */
     const int32_t *w_count;    /* [p] */
+    /* Noise distribution per dimension (Sec. 6.2: the tool supports other
+     * distributions and multiplicative noise; Eq. (1a) for the latter).
+     * ORC_NOISE_GAUSSIAN uses sigma; the others their own parameters:
+     *   UNIFORM        noise ~ U[-a, a]                        p0 = a
+     *   EXPONENTIAL    noise ~ Exp(rate), density rate*e^{-rate t}, t >= 0
+     *                                                          p0 = rate
+     *   BETA           noise = lo + (hi - lo) * B, B ~ Beta(alpha, beta),
+     *                  integer alpha, beta >= 1                p0 = alpha, p1 = beta,
+     *                                                          p2 = lo, p3 = hi
+     *   MULT_GAUSSIAN  multiplicative: noise = s * x_d * Z, Z ~ N(0,1), x_d
+     *                  the state's centre (std s*|x_d|); dense or explicit
+     *                  windows only (the cut is disabled, Sec. 6.2)
+     *                                                          p0 = s
+     * Cutting region (gamma mode) of a bounded support: the support itself;
+     * of the exponential: [0, log(rate/gamma)/rate]. */
+    int32_t noise;
+    const double *noise_p0, *noise_p1, *noise_p2, *noise_p3; /* [n] each (unused ones may be NULL) */
 } orc_problem;
+
+enum { ORC_NOISE_GAUSSIAN = 0, ORC_NOISE_UNIFORM = 1, ORC_NOISE_EXPONENTIAL = 2, ORC_NOISE_BETA = 3,
+       ORC_NOISE_MULT_GAUSSIAN = 4 };
 
 typedef struct {
     int32_t kind;              /* ORC_SAFETY / ORC_REACH / ORC_REACH_AVOID */
@@ -82,8 +102,9 @@ typedef struct {
 /* N = floor((ub - lb)/eta + 1e-9) + 1 */
 int64_t orc_grid_count(double lb, double ub, double eta);
 
-/* Window widths W[n] and cut half-widths xstar[n] (INFINITY when not in gamma
- * mode).  Returns 0, or -1 when the cut is empty / invalid. */
+/* Window widths W[n] and cut offsets xstar[n]: the Gaussian cut half-width,
+ * the upper end of the cut interval for the other distributions (INFINITY
+ * when not in gamma mode).  Returns 0, or -1 when the cut is empty / invalid. */
 int orc_window_shape(const orc_problem *p, int32_t *W, double *xstar);
 
 /* Mean mu[n] = f(centre(x), centre(u), centre(w)) for linear state index x

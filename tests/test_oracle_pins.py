@@ -561,6 +561,141 @@ def test_disturbance_action_values_are_min_over_w():
 
 
 # --------------------------------------------------------------------------
+# Other noise distributions (Sec. 6.2): uniform, exponential, beta (integer
+# shapes) and multiplicative Gaussian, pinned to scipy's densities and CDFs.
+# --------------------------------------------------------------------------
+def _noise_dist(kind, prm, d, xd=0.0):
+    """scipy.stats distribution of the noise of dim d (independent of the oracle)."""
+    from scipy import stats
+    if kind == "uniform":
+        a = prm[0][d]
+        return stats.uniform(loc=-a, scale=2 * a)
+    if kind == "exponential":
+        return stats.expon(scale=1.0 / prm[0][d])
+    if kind == "beta":
+        return stats.beta(prm[0][d], prm[1][d], loc=prm[2][d], scale=prm[3][d] - prm[2][d])
+    if kind == "mult_gaussian":
+        return stats.norm(scale=prm[0][d] * abs(xd))
+    raise ValueError(kind)
+
+
+NOISES = [("uniform", [[0.37, 0.61]]), ("exponential", [[2.5, 1.3]]),
+          ("beta", [[2.0, 3.0], [3.0, 1.0], [-0.6, -0.2], [0.9, 1.1]]),
+          ("beta", [[1.0, 4.0], [1.0, 2.0], [-0.5, -1.0], [0.5, 0.3]]),
+          ("mult_gaussian", [[0.3, 0.45]])]
+
+
+def _noise_problem(kind, prm, gamma=0.0, window=None, n=2, npts=9):
+    lb, eta = -1.2, 0.3
+    rng = np.random.default_rng(3)
+    A = np.eye(n) * 0.8
+    cs = [rng.uniform(-0.3, 0.3, size=n) for _ in range(2)]
+    p = _affine_problem("noise", [lb] * n, [eta] * n, [npts] * n, [A, A], cs, [0.3] * n, gamma=gamma,
+                        window=window, u_lb=[0.0], u_eta=[1.0], u_count=[2])
+    p.noise, p.noise_params = kind, prm
+    return p
+
+
+@pytest.mark.parametrize("kind,prm", NOISES)
+def test_noise_cell_masses_match_quadrature(kind, prm):
+    """Dense rows: every cell mass equals the quadrature of scipy's density
+    over the cell (a product over the two dims)."""
+    from scipy import integrate
+    p = _noise_problem(kind, prm)
+    rng = np.random.default_rng(9)
+    for _ in range(4):
+        x, u = int(rng.integers(p.n_states)), int(rng.integers(2))
+        origin, probs = oracle.row(p, x, u)
+        mu = oracle.mean(p, x, u)
+        xi = np.unravel_index(x, p.x_count)
+        probs = probs.reshape(p.x_count)
+        m = []
+        for d in range(2):
+            xd = p.x_lb[d] + xi[d] * p.x_eta[d]
+            dist = _noise_dist(kind, prm, d, xd)
+            row = []
+            for j in range(p.x_count[d]):
+                c = p.x_lb[d] + j * p.x_eta[d]
+                lo, hi = c - p.x_eta[d] / 2 - mu[d], c + p.x_eta[d] / 2 - mu[d]
+                if kind == "mult_gaussian" and xd == 0.0:
+                    row.append(1.0 if lo <= 0.0 < hi else 0.0)
+                    continue
+                pts = [t for t in dist.support() if lo < t < hi]
+                v, _ = integrate.quad(dist.pdf, lo, hi, points=pts or None, epsabs=1e-14, epsrel=1e-12, limit=200)
+                row.append(v)
+            m.append(np.array(row))
+        np.testing.assert_allclose(probs, np.outer(m[0], m[1]), atol=2e-12, rtol=0)
+
+
+@pytest.mark.parametrize("kind,prm", [nz for nz in NOISES if nz[0] != "mult_gaussian"])
+def test_noise_cut_region_and_row_sums(kind, prm):
+    """Gamma mode: the kept slots are exactly the grid centres inside the
+    region where the density reaches gamma (the support for bounded
+    supports; for the exponential the density level set, found by root
+    finding), and each row sums to the distribution's mass over the kept
+    cells (scipy's CDF)."""
+    from scipy import optimize
+    gamma = 0.05
+    p = _noise_problem(kind, prm, gamma=gamma, n=2, npts=15)
+    Wd, _ = oracle.window_shape(p)
+    rng = np.random.default_rng(13)
+    for _ in range(10):
+        x, u = int(rng.integers(p.n_states)), int(rng.integers(2))
+        origin, probs = oracle.row(p, x, u)
+        mu = oracle.mean(p, x, u)
+        probs = probs.reshape(Wd)
+        total = 1.0
+        for d in range(2):
+            dist = _noise_dist(kind, prm, d)
+            lo_s, hi_s = dist.support()
+            if kind == "exponential":
+                hi_s = optimize.brentq(lambda t: dist.pdf(t) - gamma, 1e-12, 100.0, xtol=1e-14)
+            kept = [s for s in range(origin[d], origin[d] + Wd[d])
+                    if 0 <= s < p.x_count[d] and mu[d] + lo_s - 1e-9 <= p.x_lb[d] + s * p.x_eta[d] <= mu[d] + hi_s + 1e-9]
+            want = [s for s in range(p.x_count[d])
+                    if mu[d] + lo_s + 1e-9 < p.x_lb[d] + s * p.x_eta[d] < mu[d] + hi_s - 1e-9]
+            assert set(want) <= set(kept)
+            if kept:
+                e_lo = p.x_lb[d] + kept[0] * p.x_eta[d] - p.x_eta[d] / 2 - mu[d]
+                e_hi = p.x_lb[d] + kept[-1] * p.x_eta[d] + p.x_eta[d] / 2 - mu[d]
+                total *= dist.cdf(e_hi) - dist.cdf(e_lo)
+            else:
+                total = 0.0
+        assert abs(float(probs.sum()) - total) <= 1e-12
+
+
+def test_noise_uniform_chain_brute_force():
+    """5-cell chain with uniform noise (half-width 0.8): the oracle's V_0
+    equals brute force over all Markov policies and paths with T from
+    scipy's uniform CDF."""
+    from scipy import stats
+    a, drifts, N = 0.8, (-1, 0, 1), 2
+    T = np.zeros((5, 3, 5))
+    dist = stats.uniform(loc=-a, scale=2 * a)
+    for x in range(5):
+        for u, dr in enumerate(drifts):
+            for y in range(5):
+                T[x, u, y] = dist.cdf(y + 0.5 - x - dr) - dist.cdf(y - 0.5 - x - dr)
+    bf = _brute_force(T, "reach_avoid", N, {4}, {0}, set())
+    p = _affine_problem("uchain", [0.0], [1.0], [5], [np.eye(1)] * 3, [np.array([float(d)]) for d in drifts],
+                        [1.0], gamma=0.0, u_lb=[0.0], u_eta=[1.0], u_count=[3])
+    p.noise, p.noise_params = "uniform", [[a]]
+    spec = Spec(W.REACH_AVOID, targets=[([4.0], [4.0])], avoids=[([0.0], [0.0])])
+    np.testing.assert_allclose(oracle.synthesize(p, spec, N)["V"], bf, atol=1e-14, rtol=0)
+
+
+def test_noise_invalid_rejected():
+    for kind, prm, gamma in [("beta", [[2.5], [2.0], [-1.0], [1.0]], 0.0),   # non-integer shape
+                             ("uniform", [[0.2]], 10.0),                     # gamma above the flat density
+                             ("exponential", [[1.0]], 2.0),                  # gamma above the peak
+                             ("mult_gaussian", [[0.3]], 1e-3)]:              # multiplicative noise is uncut
+        p = _affine_problem("bad", [0.0], [0.3], [9], [np.eye(1)], [np.zeros(1)], [0.3], gamma=gamma)
+        p.noise, p.noise_params = kind, prm
+        with pytest.raises(ValueError):
+            oracle.window_shape(p) if kind != "mult_gaussian" else oracle.synthesize(p, Spec(W.SAFETY), 1)
+
+
+# --------------------------------------------------------------------------
 # P8: deterministic limit equals graph reachability (BFS)
 # --------------------------------------------------------------------------
 def _bfs_reach(n_states, succ, target, avoid, N):

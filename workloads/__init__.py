@@ -56,6 +56,12 @@ class Problem:
     w_lb: List[float] = field(default_factory=list)
     w_eta: List[float] = field(default_factory=list)
     w_count: List[int] = field(default_factory=list)
+    # noise distribution per dim: "gaussian" (sigma), "uniform" ([a]),
+    # "exponential" ([rate]), "beta" ([alpha], [beta], [lo], [hi]; integer
+    # shapes), "mult_gaussian" ([s]: std s * |x_d|); noise_params holds one
+    # list of n values per parameter
+    noise: str = "gaussian"
+    noise_params: Optional[List[List[float]]] = None
 
     @property
     def n(self) -> int:
