@@ -77,6 +77,33 @@ typedef struct amy_grid_s {
  *   disturbance fastest (record u * n_w + w), n_params = n_u * n_w * (n*n + n);
  *   disturb->periodic is ignored. */
 typedef enum { AMY_SYS_AFFINE_PER_INPUT = 0, AMY_SYS_UNICYCLE = 1 } amy_sys_kind;
+
+/* Noise distribution per dimension (Sec. 6.2: uniform, exponential and beta
+ * besides the normal, and multiplicative noise as in Eq. (1a)); NULL in
+ * amy_system = Gaussian with amy_build's sigma.  Parameters, [n] arrays:
+ *   AMY_NOISE_GAUSSIAN       none (sigma is amy_build's argument)
+ *   AMY_NOISE_UNIFORM        p0 = a: noise ~ U[-a, a]
+ *   AMY_NOISE_EXPONENTIAL    p0 = rate: noise ~ Exp(rate), density
+ *                            rate * exp(-rate t) for t >= 0
+ *   AMY_NOISE_BETA           p0 = alpha, p1 = beta (integers >= 1, sum <= 64),
+ *                            p2 = lo < p3 = hi: noise = lo + (hi - lo) B,
+ *                            B ~ Beta(alpha, beta)
+ *   AMY_NOISE_MULT_GAUSSIAN  p0 = s: multiplicative noise, std s * |x_d| at a
+ *                            state whose centre in dim d is x_d (no noise where
+ *                            x_d = 0); dense or explicit windows only (the paper
+ *                            disables the cut for multiplicative noise)
+ * Cells are still kept by their centres inside the cut interval around the
+ * mean (gamma mode): the support for the uniform and beta (gamma must not
+ * exceed the uniform's density 1/(2a)), [0, log(rate/gamma)/rate] for the
+ * exponential (gamma < rate).  amy_info's cut_half_width then reports the
+ * upper end of that interval. */
+typedef enum { AMY_NOISE_GAUSSIAN = 0, AMY_NOISE_UNIFORM = 1, AMY_NOISE_EXPONENTIAL = 2, AMY_NOISE_BETA = 3,
+               AMY_NOISE_MULT_GAUSSIAN = 4 } amy_noise_kind;
+typedef struct {
+    int32_t kind;
+    const double *p0, *p1, *p2, *p3;
+} amy_noise;
+
 typedef struct {
     int32_t kind;
     int32_t n;
@@ -84,6 +111,7 @@ typedef struct {
     const double *params;
     int64_t n_params;
     const struct amy_grid_s *disturb;  /* NULL: no disturbance */
+    const amy_noise *noise;            /* NULL: Gaussian (amy_build's sigma) */
 } amy_system;
 
 /* Cutting region (Sec. 5.2 and its Remark on constructing the region).

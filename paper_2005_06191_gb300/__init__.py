@@ -25,6 +25,7 @@ PRECS = {"fp64": 0, "fp32": 1, "fp32_kahan": 2}
 SYS_KINDS = {"affine": 0, "unicycle": 1}
 SPEC_KINDS = {"safety": 0, "reach": 1, "reach_avoid": 2}
 VSTORES = {"native": 0, "bf16": 1, "u16": 2}
+NOISE_KINDS = {"gaussian": 0, "uniform": 1, "exponential": 2, "beta": 3, "mult_gaussian": 4}
 POLICY_NONE = 0xFFFF
 
 
@@ -87,6 +88,13 @@ def _problem_structs(k: _Keep, p):
     wc = list(getattr(p, "w_count", None) or [])
     if wc:
         sysd.disturb = C.pointer(k.obj(_grid(k, p.w_lb, p.w_eta, wc)))
+    kind = getattr(p, "noise", "gaussian")
+    if kind != "gaussian":
+        nz = _abi.amy_noise()
+        nz.kind = NOISE_KINDS[kind]
+        for i, arr in enumerate(list(getattr(p, "noise_params", None) or [])[:4]):
+            setattr(nz, f"p{i}", k.f64(arr))
+        sysd.noise = C.pointer(k.obj(nz))
     states = _grid(k, p.x_lb, p.x_eta, p.x_count, p.x_periodic)
     inputs = _grid(k, p.u_lb, p.u_eta, p.u_count)
     cut = _abi.amy_cut()

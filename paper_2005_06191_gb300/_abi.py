@@ -24,9 +24,13 @@ class amy_grid(C.Structure):
     _fields_ = [("n", C.c_int32), ("lb", DP), ("eta", DP), ("count", IP), ("periodic", U8P)]
 
 
+class amy_noise(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("p0", DP), ("p1", DP), ("p2", DP), ("p3", DP)]
+
+
 class amy_system(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n", C.c_int32), ("m", C.c_int32), ("params", DP),
-                ("n_params", C.c_int64), ("disturb", C.POINTER(amy_grid))]
+                ("n_params", C.c_int64), ("disturb", C.POINTER(amy_grid)), ("noise", C.POINTER(amy_noise))]
 
 
 class amy_cut(C.Structure):

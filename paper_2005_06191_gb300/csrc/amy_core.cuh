@@ -23,6 +23,9 @@ enum WindowMode : int32_t { WM_DENSE = 0, WM_GAMMA = 1, WM_EXPLICIT = 2 };
 enum SysKind : int32_t { SYS_AFFINE = 0, SYS_UNICYCLE = 1 };
 enum SpecKind : int32_t { SPEC_SAFETY = 0, SPEC_REACH = 1, SPEC_REACH_AVOID = 2 };
 enum TMode : int32_t { TM_OTF = 0, TM_FULL = 1, TM_FACTORED = 2, TM_SEPARABLE = 3 };
+// Noise distribution per dimension (Sec. 6.2; multiplicative noise as in Eq. (1a)).
+enum NoiseKind : int32_t { NOISE_GAUSSIAN = 0, NOISE_UNIFORM = 1, NOISE_EXPONENTIAL = 2, NOISE_BETA = 3,
+                           NOISE_MULT_GAUSSIAN = 4 };
 
 // 16-bit fixed-point storage of a probability: value = bits / 65535.
 struct unorm16 {
@@ -44,9 +47,13 @@ struct Geom {
     int32_t W[MAXD];             // window width per dim
     int32_t wsum, wtot;          // sum and product of W
     int32_t wmode;               // WindowMode
-    double xs[MAXD];             // gamma-mode cut half width
-    double k2[MAXD];             // sigma*sqrt(2)
-    float rk2f[MAXD];            // 1/(sigma*sqrt(2)) in FP32
+    double xs[MAXD];             // gamma-mode cut half width (Gaussian noise)
+    double clo[MAXD], chi[MAXD]; // gamma-mode cut interval of the noise: [mu + clo, mu + chi]
+    double k2[MAXD];             // sigma*sqrt(2) (Gaussian noise)
+    float rk2f[MAXD];            // 1/(sigma*sqrt(2)) in FP32 (Gaussian noise)
+    int32_t noise;               // NoiseKind
+    double np[4][MAXD];          // its parameters: uniform a; exponential rate; beta alpha, beta,
+                                 // lo, hi (integer shapes); multiplicative Gaussian s (std s*|x_d|)
     int32_t sys;                 // SysKind
     int32_t ucount[MAXD];
     double ulb[MAXD], ueta[MAXD];
@@ -114,6 +121,14 @@ __device__ __forceinline__ double state_centre(const Geom &g, int d, int32_t j) 
     return dadd(g.lb[d], dmul((double)j, g.eta[d]));
 }
 
+// The centre in dim d of state x where the noise depends on it
+// (multiplicative noise), else 0 (unused).
+__device__ __forceinline__ double noise_centre(const Geom &g, int32_t x, int d) {
+    if (g.noise != NOISE_MULT_GAUSSIAN) return 0.0;
+    const int32_t j = (int32_t)(((uint32_t)x / (uint32_t)g.stride[d]) % (uint32_t)g.N[d]);
+    return state_centre(g, d, j);
+}
+
 // Mean of the post state, Algorithm 2 "Set mu = f(x, nu, w)" for the
 // disturbance-free system of Eq. 4.
 __device__ __forceinline__ void mean_of(const Geom &g, int32_t x, int32_t u, double *mu) {
@@ -178,8 +193,9 @@ __device__ __forceinline__ double mean_component(const Geom &g, int32_t x, int32
 }
 
 // Window origin of one dimension (first slot index, unwrapped), in the FP64
-// expression order fixed by the ABI.  Far-away origins are clamped where every
-// slot is off the grid anyway.
+// expression order fixed by the ABI: ceil(((mu + clo) - lb) / eta) in gamma
+// mode (for the Gaussian clo = -xs, and mu + (-xs) is mu - xs exactly).
+// Far-away origins are clamped where every slot is off the grid anyway.
 __device__ __forceinline__ int32_t origin_of(const Geom &g, int d, double mu) {
     double od;
     if (g.wmode == WM_EXPLICIT)
@@ -187,7 +203,7 @@ __device__ __forceinline__ int32_t origin_of(const Geom &g, int d, double mu) {
     else if (g.wmode == WM_DENSE)
         od = 0.0;
     else
-        od = ceil(ddiv(dsub(dsub(mu, g.xs[d]), g.lb[d]), g.eta[d]));
+        od = ceil(ddiv(dsub(dadd(mu, g.clo[d]), g.lb[d]), g.eta[d]));
     if (!((g.periodic >> d) & 1u)) {
         const double lo = -(double)(g.W[d] + 1), hi = (double)(g.N[d] + 1);
         if (!(od >= lo)) od = lo;
@@ -200,11 +216,11 @@ __device__ __forceinline__ int32_t origin_of(const Geom &g, int d, double mu) {
 }
 
 // Number of leading slots of the window that pass the gamma-mode upper test
-// centre <= mu + xs (centres grow with the slot, so test from the top).
+// centre <= mu + chi (centres grow with the slot, so test from the top).
 __device__ __forceinline__ int kept_upper(const Geom &g, int d, double mu, int32_t o) {
     int kmax = g.W[d];
     if (g.wmode == WM_GAMMA) {
-        const double hi = dadd(mu, g.xs[d]);
+        const double hi = dadd(mu, g.chi[d]);
         while (kmax > 0) {
             const double c = state_centre(g, d, o + kmax - 1);
             if (c <= hi) break;
@@ -225,30 +241,92 @@ __device__ __forceinline__ int32_t cell_of(const Geom &g, int d, int32_t s, bool
     return s < 0 ? 0 : (s >= N ? N - 1 : s);
 }
 
-// Per-dimension cell masses of one window (FP32 path).  Each edge's tail
-// beyond it (away from mu) is evaluated once with erfcf; a cell's mass is the
-// difference of its edge tails on the same side of mu, or one minus both tails
-// when it contains mu -- no probability close to one is subtracted.
-__device__ __forceinline__ void dim_masses_f32(const Geom &g, int d, double mu, int32_t o,
+// Regularised incomplete beta I_z(a, b) for integer a, b >= 1 (a + b <= 64):
+// the probability that at least a of a + b - 1 trials with success
+// probability z succeed, a binomial tail summed term by term.
+template <class R>
+__device__ __noinline__ R inc_beta_int(int a, int b, R z) {
+    if (z <= R(0)) return R(0);
+    if (z >= R(1)) return R(1);
+    const int n = a + b - 1;
+    R sum = R(0);
+    for (int j = a; j <= n; ++j) {
+        R c = R(1);  // C(n, j)
+        for (int i = 1; i <= j; ++i) c = c * (R)(n - j + i) / (R)i;
+        sum += c * pow(z, (R)j) * pow(R(1) - z, (R)(n - j));
+    }
+    return sum;
+}
+
+// Cell mass for the noise kinds other than the (additive or multiplicative)
+// Gaussian, Algorithm 1's cell integral for the distributions of Sec. 6.2;
+// tlo < thi are the cell's edges minus the mean.  Uniform on [-a, a]: the
+// overlap; exponential: the difference of the survival function at the two
+// edges; beta (noise = lo + (hi - lo) B, integer shapes): incomplete-beta
+// differences, from the upper tail in the upper half.  Kept out of line:
+// the Gaussian is the common case, and the unrolled kernels would otherwise
+// inline this code into every slot.
+template <class R>
+__device__ __noinline__ R noise_mass(const Geom &g, int d, R tlo, R thi) {
+    if (g.noise == NOISE_UNIFORM) {
+        const R a = (R)g.np[0][d];
+        const R lo = tlo > -a ? tlo : -a, hi = thi < a ? thi : a;
+        return hi > lo ? (hi - lo) / (R(2) * a) : R(0);
+    }
+    if (g.noise == NOISE_EXPONENTIAL) {
+        const R rate = (R)g.np[0][d];
+        const R slo = tlo > R(0) ? exp(-rate * tlo) : R(1);
+        const R shi = thi > R(0) ? exp(-rate * thi) : R(1);
+        return slo - shi;
+    }
+    // NOISE_BETA
+    const int a = (int)g.np[0][d], b = (int)g.np[1][d];
+    const R lo = (R)g.np[2][d], span = (R)(g.np[3][d] - g.np[2][d]);
+    const R zlo = (tlo - lo) / span, zhi = (thi - lo) / span;
+    if (zlo >= R(0.5)) return inc_beta_int<R>(b, a, R(1) - zlo) - inc_beta_int<R>(b, a, R(1) - zhi);
+    return inc_beta_int<R>(a, b, zhi) - inc_beta_int<R>(a, b, zlo);
+}
+
+// 1/(sigma*sqrt(2)) of dim d's Gaussian noise at a state whose centre in dim
+// d is xd: the fixed sigma, or s*|xd| for multiplicative noise (0 when that
+// std is 0: no noise, the whole mass in the cell holding the mean).
+__device__ __forceinline__ float gauss_r_f32(const Geom &g, int d, double xd) {
+    if (g.noise != NOISE_MULT_GAUSSIAN) return g.rk2f[d];
+    const double s = g.np[0][d] * fabs(xd);
+    return s > 0.0 ? (float)(1.0 / (s * 1.4142135623730951)) : 0.0f;
+}
+
+// FP32 mass of one cell with edges dlo < dhi (minus the mean) from the
+// Gaussian tails tlo = Q(|dlo|), thi = Q(|dhi|) taken on the far side of the
+// mean; r = 0 is the noiseless case of multiplicative noise.
+__device__ __forceinline__ float gauss_cell_f32(float dlo, float dhi, float tlo, float thi, float r) {
+    if (r == 0.0f) return (dlo <= 0.0f && 0.0f < dhi) ? 1.0f : 0.0f;
+    if (dlo >= 0.0f) return tlo - thi;
+    if (dhi <= 0.0f) return thi - tlo;
+    return 1.0f - tlo - thi;
+}
+
+// Per-dimension cell masses of one window (FP32 path).  Gaussian noise: each
+// edge's tail beyond it (away from mu) is evaluated once with erfcf; a cell's
+// mass is the difference of its edge tails on the same side of mu, or one
+// minus both tails when it contains mu -- no probability close to one is
+// subtracted.  The other kinds take each cell from its two edges.  xd: the
+// state's centre in dim d (multiplicative noise scales with it).
+__device__ __forceinline__ void dim_masses_f32(const Geom &g, int d, double mu, int32_t o, double xd,
                                                float *fac, int32_t *off) {
     const int W = g.W[d];
     const int kmax = kept_upper(g, d, mu, o);
     const double c0 = state_centre(g, d, o);
     const float e0 = (float)dsub(dsub(c0, dmul(0.5, g.eta[d])), mu);  // first edge - mu
     const float etaf = (float)g.eta[d];
-    const float r = g.rk2f[d];
+    const bool gauss = g.noise == NOISE_GAUSSIAN || g.noise == NOISE_MULT_GAUSSIAN;
+    const float r = gauss_r_f32(g, d, xd);
     float dlo = e0;
-    float tlo = 0.5f * erfcf(fabsf(dlo) * r);
+    float tlo = gauss ? 0.5f * erfcf(fabsf(dlo) * r) : 0.0f;
     for (int k = 0; k < W; ++k) {
         const float dhi = fmaf((float)(k + 1), etaf, e0);
-        const float thi = 0.5f * erfcf(fabsf(dhi) * r);
-        float mass;
-        if (dlo >= 0.0f)
-            mass = tlo - thi;
-        else if (dhi <= 0.0f)
-            mass = thi - tlo;
-        else
-            mass = 1.0f - tlo - thi;
+        const float thi = gauss ? 0.5f * erfcf(fabsf(dhi) * r) : 0.0f;
+        const float mass = gauss ? gauss_cell_f32(dlo, dhi, tlo, thi, r) : noise_mass<float>(g, d, dlo, dhi);
         bool on;
         const int32_t cell = cell_of(g, d, o + k, on);
         fac[k] = (on && k < kmax) ? fmaxf(mass, 0.0f) : 0.0f;
@@ -260,79 +338,84 @@ __device__ __forceinline__ void dim_masses_f32(const Geom &g, int d, double mu, 
 
 // FP64 path: each cell's mass from its own two edges, as in Algorithm 1.
 // Slot k of dim d's window (origin o, kmax slots kept): its mass and V offset.
-__device__ __forceinline__ void slot_mass_f64(const Geom &g, int d, double mu, int32_t o, int kmax, int k,
+__device__ __forceinline__ void slot_mass_f64(const Geom &g, int d, double mu, int32_t o, int kmax, int k, double xd,
                                               double &fac, int32_t &off) {
-    const double k2 = g.k2[d];
     const double h = dmul(0.5, g.eta[d]);
     const double c = state_centre(g, d, o + k);
     const double elo = dsub(c, h), ehi = dadd(c, h);
     double mass;
-    if (elo >= mu)
-        mass = 0.5 * erfc(ddiv(dsub(elo, mu), k2)) - 0.5 * erfc(ddiv(dsub(ehi, mu), k2));
-    else if (ehi <= mu)
-        mass = 0.5 * erfc(ddiv(dsub(mu, ehi), k2)) - 0.5 * erfc(ddiv(dsub(mu, elo), k2));
-    else
-        mass = 1.0 - 0.5 * erfc(ddiv(dsub(mu, elo), k2)) - 0.5 * erfc(ddiv(dsub(ehi, mu), k2));
+    if (g.noise == NOISE_GAUSSIAN || g.noise == NOISE_MULT_GAUSSIAN) {
+        const double k2 = g.noise == NOISE_GAUSSIAN ? g.k2[d] : dmul(dmul(g.np[0][d], fabs(xd)), 1.4142135623730951);
+        if (k2 == 0.0)
+            mass = (elo <= mu && mu < ehi) ? 1.0 : 0.0;
+        else if (elo >= mu)
+            mass = 0.5 * erfc(ddiv(dsub(elo, mu), k2)) - 0.5 * erfc(ddiv(dsub(ehi, mu), k2));
+        else if (ehi <= mu)
+            mass = 0.5 * erfc(ddiv(dsub(mu, ehi), k2)) - 0.5 * erfc(ddiv(dsub(mu, elo), k2));
+        else
+            mass = 1.0 - 0.5 * erfc(ddiv(dsub(mu, elo), k2)) - 0.5 * erfc(ddiv(dsub(ehi, mu), k2));
+    } else {
+        mass = noise_mass<double>(g, d, dsub(elo, mu), dsub(ehi, mu));
+    }
     bool on;
     const int32_t cell = cell_of(g, d, o + k, on);
     fac = (on && k < kmax) ? mass : 0.0;
     off = cell * g.stride[d];
 }
 
-__device__ __forceinline__ void dim_masses_f64(const Geom &g, int d, double mu, int32_t o,
+__device__ __forceinline__ void dim_masses_f64(const Geom &g, int d, double mu, int32_t o, double xd,
                                                double *fac, int32_t *off) {
     const int W = g.W[d];
     const int kmax = kept_upper(g, d, mu, o);
-    for (int k = 0; k < W; ++k) slot_mass_f64(g, d, mu, o, kmax, k, fac[k], off[k]);
+    for (int k = 0; k < W; ++k) slot_mass_f64(g, d, mu, o, kmax, k, xd, fac[k], off[k]);
 }
 
 // One slot of dim_masses_f32 on its own: the same edge values (edge k is
 // fmaf(k, eta, e0), edge 0 is e0) and the same arithmetic, so the mass is
 // bit for bit the one the incremental loop gives.
-__device__ __forceinline__ void slot_mass_f32(const Geom &g, int d, double mu, int32_t o, int kmax, int k,
+__device__ __forceinline__ void slot_mass_f32(const Geom &g, int d, double mu, int32_t o, int kmax, int k, double xd,
                                               float &fac, int32_t &off) {
     const double c0 = state_centre(g, d, o);
     const float e0 = (float)dsub(dsub(c0, dmul(0.5, g.eta[d])), mu);
     const float etaf = (float)g.eta[d];
-    const float r = g.rk2f[d];
     const float dlo = k == 0 ? e0 : fmaf((float)k, etaf, e0);
     const float dhi = fmaf((float)(k + 1), etaf, e0);
-    const float tlo = 0.5f * erfcf(fabsf(dlo) * r);
-    const float thi = 0.5f * erfcf(fabsf(dhi) * r);
     float mass;
-    if (dlo >= 0.0f)
-        mass = tlo - thi;
-    else if (dhi <= 0.0f)
-        mass = thi - tlo;
-    else
-        mass = 1.0f - tlo - thi;
+    if (g.noise == NOISE_GAUSSIAN || g.noise == NOISE_MULT_GAUSSIAN) {
+        const float r = gauss_r_f32(g, d, xd);
+        const float tlo = 0.5f * erfcf(fabsf(dlo) * r);
+        const float thi = 0.5f * erfcf(fabsf(dhi) * r);
+        mass = gauss_cell_f32(dlo, dhi, tlo, thi, r);
+    } else {
+        mass = noise_mass<float>(g, d, dlo, dhi);
+    }
     bool on;
     const int32_t cell = cell_of(g, d, o + k, on);
     fac = (on && k < kmax) ? fmaxf(mass, 0.0f) : 0.0f;
     off = cell * g.stride[d];
 }
 
-__device__ __forceinline__ void slot_mass(const Geom &g, int d, double mu, int32_t o, int kmax, int k, double &fac,
-                                          int32_t &off) {
-    slot_mass_f64(g, d, mu, o, kmax, k, fac, off);
+__device__ __forceinline__ void slot_mass(const Geom &g, int d, double mu, int32_t o, int kmax, int k, double xd,
+                                          double &fac, int32_t &off) {
+    slot_mass_f64(g, d, mu, o, kmax, k, xd, fac, off);
 }
-__device__ __forceinline__ void slot_mass(const Geom &g, int d, double mu, int32_t o, int kmax, int k, float &fac,
-                                          int32_t &off) {
-    slot_mass_f32(g, d, mu, o, kmax, k, fac, off);
+__device__ __forceinline__ void slot_mass(const Geom &g, int d, double mu, int32_t o, int kmax, int k, double xd,
+                                          float &fac, int32_t &off) {
+    slot_mass_f32(g, d, mu, o, kmax, k, xd, fac, off);
 }
 
 template <class R>
-__device__ __forceinline__ void dim_masses(const Geom &g, int d, double mu, int32_t o, R *fac,
+__device__ __forceinline__ void dim_masses(const Geom &g, int d, double mu, int32_t o, double xd, R *fac,
                                            int32_t *off);
 template <>
-__device__ __forceinline__ void dim_masses<float>(const Geom &g, int d, double mu, int32_t o,
+__device__ __forceinline__ void dim_masses<float>(const Geom &g, int d, double mu, int32_t o, double xd,
                                                   float *fac, int32_t *off) {
-    dim_masses_f32(g, d, mu, o, fac, off);
+    dim_masses_f32(g, d, mu, o, xd, fac, off);
 }
 template <>
-__device__ __forceinline__ void dim_masses<double>(const Geom &g, int d, double mu, int32_t o,
+__device__ __forceinline__ void dim_masses<double>(const Geom &g, int d, double mu, int32_t o, double xd,
                                                    double *fac, int32_t *off) {
-    dim_masses_f64(g, d, mu, o, fac, off);
+    dim_masses_f64(g, d, mu, o, xd, fac, off);
 }
 
 // Offsets of a stored row's slots from its stored origin (dropped slots keep a

@@ -75,10 +75,33 @@ amy_status fill_geom(const amy_system *sys, const amy_grid *st, const amy_grid *
     g.n = n;
     g.m = m;
     int64_t nx = 1, nu = 1;
+    // noise distribution (Gaussian unless sys->noise says otherwise)
+    const amy_noise *nz = sys->noise;
+    g.noise = nz ? nz->kind : NOISE_GAUSSIAN;
+    if (g.noise < NOISE_GAUSSIAN || g.noise > NOISE_MULT_GAUSSIAN)
+        return set_error(AMY_E_INVALID_ARG, "unknown noise kind %d", g.noise);
+    for (int d = 0; d < n; ++d) {
+        const double *pp[4] = {nz ? nz->p0 : nullptr, nz ? nz->p1 : nullptr, nz ? nz->p2 : nullptr,
+                               nz ? nz->p3 : nullptr};
+        const int need = g.noise == NOISE_GAUSSIAN ? 0 : g.noise == NOISE_BETA ? 4 : 1;
+        for (int i = 0; i < 4; ++i) {
+            if (i < need && !pp[i]) return set_error(AMY_E_INVALID_ARG, "noise kind %d needs %d parameter arrays", g.noise, need);
+            g.np[i][d] = i < need ? pp[i][d] : 0.0;
+            if (!std::isfinite(g.np[i][d])) return set_error(AMY_E_INVALID_ARG, "non-finite noise parameter");
+        }
+        if (g.noise == NOISE_UNIFORM || g.noise == NOISE_EXPONENTIAL || g.noise == NOISE_MULT_GAUSSIAN) {
+            if (!(g.np[0][d] > 0.0)) return set_error(AMY_E_INVALID_ARG, "noise parameter p0[%d] must be positive", d);
+        } else if (g.noise == NOISE_BETA) {
+            const double a = g.np[0][d], b = g.np[1][d];
+            if (!(a >= 1.0 && b >= 1.0 && a == std::floor(a) && b == std::floor(b) && a + b <= 64.0))
+                return set_error(AMY_E_INVALID_ARG, "beta noise needs integer shapes >= 1 summing to at most 64 (dim %d)", d);
+            if (!(g.np[3][d] > g.np[2][d])) return set_error(AMY_E_INVALID_ARG, "beta noise needs lo < hi (dim %d)", d);
+        }
+    }
     for (int d = 0; d < n; ++d) {
         if (st->count[d] < 1 || !(st->eta[d] > 0.0) || !std::isfinite(st->lb[d]) || !std::isfinite(st->eta[d]))
             return set_error(AMY_E_INVALID_ARG, "bad state grid in dim %d", d);
-        if (!(sigma[d] > 0.0) || !std::isfinite(sigma[d]))
+        if (g.noise == NOISE_GAUSSIAN && (!(sigma[d] > 0.0) || !std::isfinite(sigma[d])))
             return set_error(AMY_E_INVALID_ARG, "sigma[%d] must be positive", d);
         g.N[d] = st->count[d];
         g.lb[d] = st->lb[d];
@@ -143,8 +166,10 @@ amy_status fill_geom(const amy_system *sys, const amy_grid *st, const amy_grid *
     int32_t wsum = 0;
     for (int d = 0; d < n; ++d) {
         const bool per = (g.periodic >> d) & 1u;
-        g.k2[d] = sigma[d] * std::sqrt(2.0);
-        g.rk2f[d] = (float)(1.0 / (sigma[d] * std::sqrt(2.0)));
+        if (g.noise == NOISE_GAUSSIAN) {
+            g.k2[d] = sigma[d] * std::sqrt(2.0);
+            g.rk2f[d] = (float)(1.0 / (sigma[d] * std::sqrt(2.0)));
+        }
         if (cut->window) {
             g.wmode = WM_EXPLICIT;
             const int32_t W = cut->window[d];
@@ -160,14 +185,38 @@ amy_status fill_geom(const amy_system *sys, const amy_grid *st, const amy_grid *
         } else {
             g.wmode = WM_GAMMA;
             if (!(cut->gamma > 0.0) || !std::isfinite(cut->gamma)) return set_error(AMY_E_INVALID_ARG, "bad gamma");
-            const double arg = 1.0 / (cut->gamma * sigma[d] * std::sqrt(2.0 * M_PI));
-            if (!(arg > 1.0)) return set_error(AMY_E_INVALID_ARG, "gamma at or above the peak density (dim %d)", d);
-            const double xs = sigma[d] * std::sqrt(2.0 * std::log(arg));
-            const double w = std::floor(2.0 * xs / g.eta[d]) + 1.0;
+            // the cut interval [clo, chi] of the noise around the mean
+            double clo = 0.0, chi = 0.0;
+            if (g.noise == NOISE_GAUSSIAN) {
+                const double arg = 1.0 / (cut->gamma * sigma[d] * std::sqrt(2.0 * M_PI));
+                if (!(arg > 1.0)) return set_error(AMY_E_INVALID_ARG, "gamma at or above the peak density (dim %d)", d);
+                const double xs = sigma[d] * std::sqrt(2.0 * std::log(arg));
+                clo = -xs;
+                chi = xs;
+            } else if (g.noise == NOISE_UNIFORM) {
+                const double a = g.np[0][d];
+                if (!(cut->gamma <= 1.0 / (2.0 * a)))
+                    return set_error(AMY_E_INVALID_ARG, "gamma above the uniform density (dim %d)", d);
+                clo = -a;
+                chi = a;
+            } else if (g.noise == NOISE_EXPONENTIAL) {
+                const double rate = g.np[0][d];
+                if (!(cut->gamma < rate)) return set_error(AMY_E_INVALID_ARG, "gamma at or above the peak density (dim %d)", d);
+                clo = 0.0;
+                chi = std::log(rate / cut->gamma) / rate;
+            } else if (g.noise == NOISE_BETA) {
+                clo = g.np[2][d];
+                chi = g.np[3][d];
+            } else {
+                return set_error(AMY_E_INVALID_ARG, "multiplicative noise has no cut: use gamma 0 or explicit windows");
+            }
+            const double w = std::floor((chi - clo) / g.eta[d]) + 1.0;
             if (!(w >= 1.0) || w > 1.0e6) return set_error(AMY_E_INVALID_ARG, "bad window width (dim %d)", d);
             g.W[d] = (int32_t)w;
             if (per && g.W[d] > g.N[d]) return set_error(AMY_E_INVALID_ARG, "window wider than periodic dim %d", d);
-            g.xs[d] = xs;
+            g.clo[d] = clo;
+            g.chi[d] = chi;
+            g.xs[d] = chi;
         }
         wtot *= g.W[d];
         wsum += g.W[d];
@@ -286,6 +335,9 @@ amy_status plan_sep_tables(Geom &g, const std::vector<double> &params, int64_t &
             }
         }
     }
+    // multiplicative noise: the masses of dim d also depend on x_d itself
+    if (g.noise == NOISE_MULT_GAUSSIAN)
+        for (int d = 0; d < n; ++d) Sx[d] |= 1u << d;
     int64_t off = 0;
     for (int d = 0; d < n; ++d) {
         // state coordinates fastest: lanes of a warp (consecutive states, one
@@ -422,7 +474,7 @@ __global__ void __launch_bounds__(256) k_build_slots(const __grid_constant__ Geo
         const int kmax = kept_upper(g, d, mu[d], o);
         R m;
         int32_t off;
-        slot_mass(g, d, mu[d], o, kmax, sl - b, m, off);
+        slot_mass(g, d, mu[d], o, kmax, sl - b, noise_centre(g, x, d), m, off);
         F[i] = m;
         if (sl == b) O[(int64_t)d * npairs + pair] = (int16_t)o;
     }

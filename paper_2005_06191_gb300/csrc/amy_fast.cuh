@@ -62,30 +62,26 @@ __host__ __device__ inline size_t fast_smem_bytes(int n, int WM) {
 }
 
 // Masses and offsets of one dim into fixed-size register arrays (FP32 path;
-// same arithmetic as dim_masses_f32).
+// same arithmetic as dim_masses_f32; xd: the state's centre in dim d, used by
+// multiplicative noise).
 template <int WM>
-__device__ __forceinline__ void dim_masses_reg(const Geom &g, int d, double mu, int32_t o, int W, float (&fac)[WM],
-                                               int32_t (&off)[WM]) {
+__device__ __forceinline__ void dim_masses_reg(const Geom &g, int d, double mu, int32_t o, int W, double xd,
+                                               float (&fac)[WM], int32_t (&off)[WM]) {
     // W: this dim's window width (a compile-time constant when all widths equal WM)
     const int kmax = kept_upper(g, d, mu, o);
     const double c0 = state_centre(g, d, o);
     const float e0 = (float)dsub(dsub(c0, dmul(0.5, g.eta[d])), mu);
     const float etaf = (float)g.eta[d];
-    const float r = g.rk2f[d];
+    const bool gauss = g.noise == NOISE_GAUSSIAN || g.noise == NOISE_MULT_GAUSSIAN;
+    const float r = gauss_r_f32(g, d, xd);
     float dlo = e0;
-    float tlo = 0.5f * erfcf(fabsf(dlo) * r);
+    float tlo = gauss ? 0.5f * erfcf(fabsf(dlo) * r) : 0.0f;
 #pragma unroll
     for (int k = 0; k < WM; ++k) {
         if (k < W) {
             const float dhi = fmaf((float)(k + 1), etaf, e0);
-            const float thi = 0.5f * erfcf(fabsf(dhi) * r);
-            float mass;
-            if (dlo >= 0.0f)
-                mass = tlo - thi;
-            else if (dhi <= 0.0f)
-                mass = thi - tlo;
-            else
-                mass = 1.0f - tlo - thi;
+            const float thi = gauss ? 0.5f * erfcf(fabsf(dhi) * r) : 0.0f;
+            const float mass = gauss ? gauss_cell_f32(dlo, dhi, tlo, thi, r) : noise_mass<float>(g, d, dlo, dhi);
             bool on;
             const int32_t cell = cell_of(g, d, o + k, on);
             fac[k] = (on && k < kmax) ? fmaxf(mass, 0.0f) : 0.0f;
@@ -302,7 +298,7 @@ __device__ __forceinline__ void backup_tile(const Geom &g, const FastArgs<VT> &a
                     int32_t od = 0;  // window origin of this dim
                     if (TM == TM_OTF) {
                         od = origin_of(g, d, mu[d]);
-                        dim_masses_reg<WM>(g, d, mu[d], od, Wd, fk, ok);
+                        dim_masses_reg<WM>(g, d, mu[d], od, Wd, xc[d], fk, ok);
                     } else if (TM == TM_SEPARABLE) {
                         const int32_t e = es[d] + ui[d];
                         const uint4 *rec = reinterpret_cast<const uint4 *>(a.tab + g.toff[d] + (int64_t)e * g.trw[d]);
@@ -524,7 +520,7 @@ static __global__ void k_build_sep(const __grid_constant__ Geom g, uint32_t *__r
         }
         const double mud = mean_component(g, x, u, d);
         const int32_t o = origin_of(g, d, mud);
-        dim_masses_f32(g, d, mud, o, fac, off);
+        dim_masses_f32(g, d, mud, o, noise_centre(g, x, d), fac, off);
         uint32_t *rec = tab + g.toff[d] + e * g.trw[d];
         const int Wd = g.W[d];
         rec[0] = (uint32_t)o;

@@ -120,7 +120,7 @@ __device__ __forceinline__ void row_setup_otf(const Geom &g, int32_t x, int32_t 
     for (int d = 0; d < g.n; ++d) {
         const int32_t o = origin_of(g, d, mu[d]);
         if (origin) origin[d] = o;
-        dim_masses<R>(g, d, mu[d], o, fac + b, off + b);
+        dim_masses<R>(g, d, mu[d], o, noise_centre(g, x, d), fac + b, off + b);
         b += g.W[d];
     }
 }
@@ -500,7 +500,8 @@ __global__ void __launch_bounds__(32 * ROWS_MAX_GROUPS) k_backup_rows_otf(const 
                 o = origin_of(g, d, mu[d]);
                 kmax = kept_upper(g, d, mu[d], o);
             }
-            slot_mass(g, d, mu[d], o, kmax, sl - b, sfac[sl * 32 + lane], soff[sl * 32 + lane]);
+            slot_mass(g, d, mu[d], o, kmax, sl - b, noise_centre(g, x, d), sfac[sl * 32 + lane],
+                      soff[sl * 32 + lane]);
         }
     }
     __syncthreads();

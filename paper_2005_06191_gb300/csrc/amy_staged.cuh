@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(STAGE_MAX_THREADS) k_backup_staged(const __gri
                 o[d] = origin_of(g, d, mu[d]);
                 if (want_masses) {
                     int32_t ok[WM];
-                    dim_masses_reg<WM>(g, d, mu[d], o[d], WM, t[d], ok);
+                    dim_masses_reg<WM>(g, d, mu[d], o[d], WM, xc[d], t[d], ok);
                 }
             }
         } else {  // TM_SEPARABLE
