@@ -89,6 +89,9 @@ def _load():
         lib.orc_action_values.argtypes = [P, C.c_void_p, C.c_int64, C.c_void_p]
         lib.orc_synthesize.argtypes = [P, S, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_int]
+        lib.orc_philox4x64.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.orc_simulate.argtypes = [P, S, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
+                                     C.c_uint64, C.c_void_p]
         _lib = lib
     return _lib
 
@@ -249,4 +252,32 @@ def synthesize(p, sp, horizon: int, want_all: bool = False, nthreads: int = 0) -
     out = {"V": V, "pi": pi, "gap": gap}
     if want_all:
         out["V_all"] = V_all
+    return out
+
+
+def philox4x64(counter, key) -> np.ndarray:
+    """Philox4x64-10 of one 256-bit counter (4 words) under a 128-bit key (2 words)."""
+    lib = _load()
+    c = np.ascontiguousarray(np.asarray(counter, dtype=np.uint64))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint64))
+    assert c.size == 4 and k.size == 2
+    out = np.zeros(4, np.uint64)
+    lib.orc_philox4x64(c.ctypes.data, k.ctypes.data, out.ctypes.data)
+    return out
+
+
+def simulate(p, sp, horizon: int, policy, x0: Sequence[int], runs: int, seed: int) -> np.ndarray:
+    """Closed-loop runs of the finite MDP under policy[horizon][n_x] from each
+    initial state: the number of successful runs per state (Philox4x64-10
+    draws at counter (run, step, draw // 4, 0), key (seed, 0))."""
+    lib, keep = _load(), _Keep()
+    pol = np.ascontiguousarray(np.asarray(policy, dtype=np.uint16))
+    assert pol.size == horizon * p.n_states
+    xs = np.ascontiguousarray(np.asarray(x0, dtype=np.int64))
+    out = np.zeros(xs.size, np.int64)
+    rc = lib.orc_simulate(C.byref(_problem(p, keep)), C.byref(_spec(p, sp, keep)), int(horizon),
+                          pol.ctypes.data if horizon else None, xs.ctypes.data, xs.size, int(runs),
+                          C.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF), out.ctypes.data)
+    if rc != 0:
+        raise ValueError("orc_simulate failed")
     return out

@@ -628,3 +628,128 @@ int orc_synthesize(const orc_problem *p, const orc_spec *s, int32_t horizon, dou
     free(Vb);
     return err ? -1 : 0;
 }
+
+/* ---------------------------------------------------------------------------
+ * Closed-loop simulation (Sec. 7: the controller is validated by simulating
+ * the closed loop from initial states; here on the finite MDP itself, so the
+ * success frequency estimates V_0 exactly in expectation).
+ * ------------------------------------------------------------------------- */
+
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo) {
+    const unsigned __int128 p = (unsigned __int128)a * b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+void orc_philox4x64(const uint64_t *ctr, const uint64_t *key, uint64_t *out) {
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t hi0, lo0, hi1, lo1;
+        mulhilo64(0xD2E7470EE14C6C93ull, c0, &hi0, &lo0);
+        mulhilo64(0xCA5A826395121157ull, c2, &hi1, &lo1);
+        const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B97F4A7C15ull;
+        k1 += 0xBB67AE8584CAA73Bull;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+/* Uniform double in [0, 1) of draw q at step t of run g. */
+static double sim_draw(uint64_t g, int32_t t, int q, uint64_t seed) {
+    const uint64_t ctr[4] = {g, (uint64_t)t, (uint64_t)(q / 4), 0};
+    const uint64_t key[2] = {seed, 0};
+    uint64_t w[4];
+    orc_philox4x64(ctr, key, w);
+    return (double)(w[q % 4] >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* Spec status of a state: 1 = the run has succeeded, 0 = failed, -1 = goes on
+ * (safety: success only at the horizon). */
+static int sim_status(const orc_spec *s, uint8_t f) {
+    if (s->kind == ORC_SAFETY) return (f & 4) ? -1 : 0;
+    if (f & 1) return 1;
+    if (f & 2) return 0;
+    return -1;
+}
+
+int orc_simulate(const orc_problem *p, const orc_spec *s, int32_t horizon, const uint16_t *policy,
+                 const int64_t *x0, int64_t n_x0, int64_t runs, uint64_t seed, int64_t *successes) {
+    orc_shape sh;
+    if (horizon < 0 || runs < 0 || shape_of(p, &sh) != 0) return -1;
+    uint8_t *mask = (uint8_t *)malloc((size_t)sh.nx);
+    if (!mask) return -1;
+    if (orc_spec_mask(p, s, mask) != 0) {
+        free(mask);
+        return -1;
+    }
+    for (int64_t i = 0; i < n_x0; ++i)
+        if (x0[i] < 0 || x0[i] >= sh.nx) {
+            free(mask);
+            return -1;
+        }
+    int rc = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n_x0; ++i) {
+        double *fac = (double *)malloc(sizeof(double) * sh.wsum);
+        int64_t *cell = (int64_t *)malloc(sizeof(int64_t) * sh.wsum);
+        int32_t origin[ORC_MAXD];
+        int64_t wins = 0;
+        if (!fac || !cell) {
+#pragma omp atomic write
+            rc = -1;
+        } else {
+            for (int64_t r = 0; r < runs; ++r) {
+                const uint64_t g = (uint64_t)(i * runs + r);
+                int64_t x = x0[i];
+                int st = sim_status(s, mask[x]);
+                for (int32_t t = 0; t < horizon && st < 0; ++t) {
+                    const int64_t u = policy[(int64_t)t * sh.nx + x];
+                    int64_t w = 0;
+                    if (sh.nw > 1) {
+                        w = (int64_t)(sim_draw(g, t, p->n, seed) * (double)sh.nw);
+                        if (w >= sh.nw) w = sh.nw - 1;
+                    }
+                    pair_factors(p, &sh, x, u * sh.nw + w, origin, fac, cell);
+                    int64_t nxt = 0;
+                    int lost = 0, off = 0;
+                    for (int d = 0; d < p->n && !lost; ++d) {
+                        const double q = sim_draw(g, t, d, seed);
+                        double cum = 0.0;
+                        int64_t pick = -1;
+                        for (int k = 0; k < sh.W[d]; ++k) {
+                            cum += fac[off + k];
+                            if (q < cum) {
+                                pick = cell[off + k];
+                                break;
+                            }
+                        }
+                        if (pick < 0) lost = 1;
+                        else nxt += pick * sh.stride[d];
+                        off += sh.W[d];
+                    }
+                    if (lost) {
+                        st = 0;
+                        break;
+                    }
+                    x = nxt;
+                    st = sim_status(s, mask[x]);
+                }
+                if (st < 0) st = (s->kind == ORC_SAFETY) ? 1 : 0;
+                wins += st;
+            }
+        }
+        successes[i] = wins;
+        free(fac);
+        free(cell);
+    }
+    free(mask);
+    return rc;
+}

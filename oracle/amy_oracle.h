@@ -132,6 +132,28 @@ int orc_backup_states(const orc_problem *p, const orc_spec *s, const double *V_n
  * the disturbances w (just s_u without a disturbance grid): out[n_u]. */
 int orc_action_values(const orc_problem *p, const double *V_next, int64_t x, double *out);
 
+/* Philox4x64-10 (the counter-based generator of Salmon et al., SC'11): ten
+ * rounds of two 64x64->128-bit multiplies and a key schedule by the Weyl
+ * constants; out = the four 64-bit words for counter ctr[4] and key key[2]. */
+void orc_philox4x64(const uint64_t *ctr, const uint64_t *key, uint64_t *out);
+
+/* Closed-loop simulation of the finite MDP (the validation of Sec. 7: runs of
+ * the controlled system from chosen initial states) under a synthesized
+ * policy: policy[horizon][n_x] holds pi_t for t = 0..horizon-1 (as
+ * orc_synthesize writes it).  For each initial state x0[i], `runs` runs of
+ * `horizon` steps: a run succeeds when it meets the spec (reaches a target
+ * before any avoid state and before the horizon; stays in the safe set
+ * through the horizon).  Each step draws, per state dim d, the next cell by
+ * inverse CDF from that dim's window masses (a uniform draw beyond their sum
+ * -- the truncated or off-grid mass -- loses the run), and with a
+ * disturbance grid first draws its point uniformly.  Draw q of step t of
+ * global run g = i*runs + r is word q%4 of Philox4x64-10 at counter
+ * (g, t, q/4, 0), key (seed, 0), as a double (w >> 11) * 2^-53; draws
+ * q = 0..n-1 pick the dims, q = n the disturbance.  successes[i] counts the
+ * successful runs of x0[i]. */
+int orc_simulate(const orc_problem *p, const orc_spec *s, int32_t horizon, const uint16_t *policy,
+                 const int64_t *x0, int64_t n_x0, int64_t runs, uint64_t seed, int64_t *successes);
+
 /* Full synthesis over `horizon` backups.  V_out[n_x] = V_0.
  * pi_out: [horizon][n_x] (pi_k for k = 0..horizon-1) or NULL.
  * gap_out: [horizon][n_x] or NULL.  V_all: [(horizon+1)][n_x] (V_k, k=0..horizon) or NULL. */
