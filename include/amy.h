@@ -300,6 +300,33 @@ amy_status amy_backup_step(amy_handle h, const amy_spec *spec, const void *V_nex
 amy_status amy_query_rows(amy_handle h, const int64_t *x, const int64_t *u, int64_t count,
                           int32_t *origin_out, double *probs_out);
 
+/* Closed-loop Monte-Carlo validation of a synthesized controller (Sec. 7:
+ * the closed loop is simulated from initial states and the success
+ * frequency set against V_0).  Runs the finite MDP itself: from each initial
+ * state x0[i], runs_per_x0 runs of `horizon` steps, step t applying
+ * policy[t * n_states + x] (pi_t as amy_synthesize writes it with
+ * policy_all_steps; may be NULL when horizon == 0).  A run succeeds when it
+ * meets `spec`: reach / reach-avoid -- it enters a target box before any
+ * avoid box and within the horizon; safety -- it stays in the safe box for
+ * all `horizon` steps.  Each step draws, per state dim d, the next grid cell
+ * by inverse CDF over that dim's FP64 cell masses in window order (Algorithm
+ * 1's row, for every noise kind); a draw beyond their sum (the mass the cut
+ * or the grid's edge removes) fails the run.  With a disturbance grid the
+ * disturbance point is drawn uniformly, before the dims.  Draw q of step t of
+ * run r of x0[i] is word q % 4 of Philox4x64-10 (Salmon et al., SC'11) at
+ * counter (i * runs_per_x0 + r, t, q / 4, 0) under key (seed, 0), as
+ * (w >> 11) * 2^-53; q = 0..n-1 are the dims, q = n the disturbance.  The
+ * counts are thus fixed by (seed, runs_per_x0) whatever the launch.
+ * successes_out[i] receives the number of successful runs of x0[i].
+ * on_device != 0: policy, x0 and successes_out are device pointers;
+ * otherwise host pointers.  Synchronous in both cases (the call reads back
+ * its error word).  Errors: INVALID_ARG (null pointers, negative counts, more
+ * than 2^62 runs, an initial state out of range, a policy entry >= n_inputs
+ * at a state a run visits before it ends, a bad spec), CUDA. */
+amy_status amy_simulate(amy_handle h, const amy_spec *spec, int32_t horizon, const uint16_t *policy,
+                        const int64_t *x0, int64_t n_x0, int64_t runs_per_x0, uint64_t seed,
+                        int64_t *successes_out, int32_t on_device);
+
 /* Rebuild the stored rows in place (Algorithm 2 again) after replacing the
  * system parameters (params may be NULL to keep them): same grid, cut and
  * storage, no allocation.  Asynchronous on the handle's stream.  For

@@ -329,6 +329,45 @@ def amy_query_rows(h: AmyHandle, xs, us):
     return org, probs
 
 
+def amy_simulate(h: AmyHandle, spec, horizon: int, policy, x0, runs_per_x0: int, seed: int, out=None):
+    """amy_simulate: closed-loop runs of the finite MDP under policy[horizon][n_states]
+    from each initial state; returns the successful runs per state.
+
+    With torch CUDA tensors for policy, x0 (int64) and out (int64) everything
+    stays on the device; otherwise host arrays (a new int64 array is returned
+    when out is None)."""
+    k = _Keep()
+    s = _spec_struct(k, spec)
+    nx = h.n_states
+    if _is_cuda_tensor(policy) or _is_cuda_tensor(x0) or _is_cuda_tensor(out):
+        import torch
+        if not _is_cuda_tensor(x0):
+            raise ValueError("x0 must be a torch CUDA tensor when policy or out is one")
+        if horizon > 0:
+            _check_device_out(policy, "policy", nx * horizon, _policy_dtypes())
+        _check_device_out(x0, "x0", x0.numel(), (torch.int64,))
+        _check_device_out(out, "out", x0.numel(), (torch.int64,))
+        pp = C.c_void_p(policy.data_ptr()) if horizon > 0 else C.c_void_p(0)
+        _check(_lib().amy_simulate(h.ptr, C.byref(s), int(horizon), pp, C.c_void_p(x0.data_ptr()), x0.numel(),
+                                   int(runs_per_x0), C.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF),
+                                   C.c_void_p(out.data_ptr()), 1))
+        return out
+    xs = np.ascontiguousarray(np.asarray(x0, dtype=np.int64)).reshape(-1)
+    pol = None
+    if horizon > 0:
+        pol = np.ascontiguousarray(np.asarray(policy))
+        if pol.dtype not in (np.uint16, np.int16) or pol.size != nx * horizon:
+            raise ValueError(f"policy must be a 16-bit array of shape ({horizon}, {nx})")
+    res = out if out is not None else np.zeros(xs.size, dtype=np.int64)
+    if not (isinstance(res, np.ndarray) and res.dtype == np.int64 and res.size == xs.size and res.flags.c_contiguous):
+        raise ValueError(f"out must be a contiguous int64 array of {xs.size} values")
+    _check(_lib().amy_simulate(h.ptr, C.byref(s), int(horizon),
+                               C.c_void_p(pol.ctypes.data) if pol is not None else C.c_void_p(0),
+                               C.c_void_p(xs.ctypes.data), xs.size, int(runs_per_x0),
+                               C.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF), C.c_void_p(res.ctypes.data), 0))
+    return res
+
+
 def amy_rebuild(h: AmyHandle, params=None) -> None:
     """amy_rebuild: rebuild the stored rows in place (optionally with new system parameters)."""
     if params is None:
@@ -438,7 +477,7 @@ from .serving import (AmyServer, amy_cancel, amy_poll, amy_result_free,  # noqa:
 
 __all__ = [
     "AmyError", "AmyHandle", "AmyServer", "amy_build", "amy_synthesize", "amy_backup_step",
-    "amy_query_rows", "amy_info", "amy_destroy", "amy_grid_count", "amy_last_error",
+    "amy_query_rows", "amy_simulate", "amy_info", "amy_destroy", "amy_grid_count", "amy_last_error",
     "amy_rebuild", "amy_set_profiling", "amy_set_wait_limit", "amy_set_step_wait", "amy_set_plane", "amy_backup_work", "amy_measure_l2", "amy_kernel_times", "amy_synthesize_noalloc", "amy_measure_lane_loads", "amy_measure_fma",
     "amy_server_create", "amy_submit", "amy_poll", "amy_wait", "amy_cancel", "amy_server_stats",
     "amy_server_graph_stats",

@@ -17,7 +17,8 @@ OUT = os.path.join(PKG, "libamy.so")
 BUILD_DIR = os.path.join(PKG, "_build")
 
 SOURCES = [f for f in ("amy_engine.cu", "amy_fast.cu", "amy_fast_f32.cu", "amy_fast_u16.cu", "amy_fast_bf16.cu",
-                       "amy_batch.cu", "amy_server.cu", "amy_noalloc.cu", "amy_calibrate.cu")
+                       "amy_batch.cu", "amy_server.cu", "amy_noalloc.cu", "amy_calibrate.cu",
+                       "amy_simulate.cu")
            if os.path.exists(os.path.join(CSRC, f))]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-fast-math",

@@ -1851,6 +1851,67 @@ amy_status amy_query_rows(amy_handle h, const int64_t *x, const int64_t *u, int6
     return AMY_OK;
 }
 
+amy_status amy_simulate(amy_handle h, const amy_spec *spec, int32_t horizon, const uint16_t *policy,
+                        const int64_t *x0, int64_t n_x0, int64_t runs_per_x0, uint64_t seed,
+                        int64_t *successes_out, int32_t on_device) {
+    if (!h || !successes_out || (n_x0 > 0 && !x0) || (horizon > 0 && !policy))
+        return set_error(AMY_E_INVALID_ARG, "null argument");
+    if (horizon < 0 || n_x0 < 0 || runs_per_x0 < 0) return set_error(AMY_E_INVALID_ARG, "negative count");
+    if (runs_per_x0 > 0 && n_x0 > ((int64_t)1 << 62) / runs_per_x0)
+        return set_error(AMY_E_INVALID_ARG, "more than 2^62 runs");
+    SpecDev s;
+    amy_status st = make_spec(h->g, spec, s);
+    if (st != AMY_OK) return st;
+    if (n_x0 == 0) return AMY_OK;
+    const Geom &g = h->g;
+    if (!on_device)
+        for (int64_t i = 0; i < n_x0; ++i)
+            if (x0[i] < 0 || x0[i] >= g.nx)
+                return set_error(AMY_E_INVALID_ARG, "initial state %lld out of range", (long long)i);
+    const size_t pbytes = (size_t)horizon * (size_t)g.nx * sizeof(uint16_t);
+    const uint16_t *d_pi = policy;
+    const int64_t *d_x0 = x0;
+    unsigned long long *d_succ = reinterpret_cast<unsigned long long *>(successes_out);
+    uint16_t *own_pi = nullptr;
+    int64_t *own_x0 = nullptr;
+    unsigned long long *own_succ = nullptr;
+    unsigned int *d_err = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&d_err, sizeof(unsigned int), h->stream);
+    if (e == cudaSuccess && !on_device) {
+        if (pbytes) e = cudaMallocAsync((void **)&own_pi, pbytes, h->stream);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&own_x0, (size_t)n_x0 * 8, h->stream);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&own_succ, (size_t)n_x0 * 8, h->stream);
+        if (e == cudaSuccess && pbytes) e = cudaMemcpyAsync(own_pi, policy, pbytes, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(own_x0, x0, (size_t)n_x0 * 8, cudaMemcpyHostToDevice, h->stream);
+        d_pi = own_pi;
+        d_x0 = own_x0;
+        d_succ = own_succ;
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(unsigned int), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_succ, 0, (size_t)n_x0 * 8, h->stream);
+    if (e == cudaSuccess) {
+        st = launch_mask_any(h, s, h->d_V[0]);
+        if (st == AMY_OK)
+            st = launch_simulate(g, s.kind, h->d_mask, d_pi, horizon, d_x0, n_x0, runs_per_x0, seed, d_succ, d_err,
+                                 h->sm_count, h->stream);
+    }
+    unsigned int err = 0;
+    if (e == cudaSuccess && st == AMY_OK) e = cudaMemcpyAsync(&err, d_err, sizeof err, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && st == AMY_OK && !on_device)
+        e = cudaMemcpyAsync(successes_out, own_succ, (size_t)n_x0 * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (d_err) cudaFreeAsync(d_err, h->stream);
+    if (own_pi) cudaFreeAsync(own_pi, h->stream);
+    if (own_x0) cudaFreeAsync(own_x0, h->stream);
+    if (own_succ) cudaFreeAsync(own_succ, h->stream);
+    const cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    if (st != AMY_OK) return st;
+    if (e != cudaSuccess) return cuda_error(e, "simulate");
+    if (e2 != cudaSuccess) return cuda_error(e2, "simulate");
+    if (err & 1u) return set_error(AMY_E_INVALID_ARG, "an initial state is out of range");
+    if (err & 2u) return set_error(AMY_E_INVALID_ARG, "the policy names an input >= %d at a live state", g.nu / g.nw);
+    return AMY_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

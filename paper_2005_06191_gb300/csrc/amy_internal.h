@@ -63,6 +63,14 @@ constexpr int kPlaneSmemDefault = 100 * 1024;
 // 0 takes kPlaneSmemDefault.  pl.ok = 0 when the kernel does not apply.
 void plan_plane(const Geom &g, int tmode, int prec, const int32_t *spread, int smem_budget, PlanePlan &pl);
 
+// Closed-loop Monte-Carlo runs (amy_simulate.cu): n_x0 * runs runs of
+// `horizon` steps under pi[horizon][nx], successes counted per initial state
+// into succ[n_x0] (zeroed by the caller); err bits: 1 an initial state out of
+// range, 2 the policy names an input out of range at a live state.
+amy_status launch_simulate(const Geom &g, int spec_kind, const uint8_t *mask, const uint16_t *pi, int32_t horizon,
+                           const int64_t *x0, int64_t n_x0, int64_t runs, uint64_t seed, unsigned long long *succ,
+                           unsigned int *err, int sm_count, cudaStream_t st);
+
 // Type-erased arguments of the register-resident backup kernel.
 struct FastCall {
     const void *Vn;
