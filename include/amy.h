@@ -327,6 +327,31 @@ amy_status amy_simulate(amy_handle h, const amy_spec *spec, int32_t horizon, con
                         const int64_t *x0, int64_t n_x0, int64_t runs_per_x0, uint64_t seed,
                         int64_t *successes_out, int32_t on_device);
 
+/* Export of the abstraction as an MDP in PRISM's explicit-model files (the
+ * PRISM export the tool offers, Sec. 2), for model checking the synthesized
+ * result with another tool.  Writes, next to path_prefix:
+ *   <prefix>.tra    "S C T" then one line "s c s' p" per transition: states
+ *                   0..n_states-1 are the grid (C-order index), state
+ *                   n_states an absorbing sink (one choice, a self-loop);
+ *                   choice c of a grid state is input c; p is the row's mass
+ *                   as the handle's mode computes it (amy_query_rows), slots
+ *                   landing on one cell merged, and the mass the cut or the
+ *                   grid's edge removes (1 - the row's sum, when positive)
+ *                   goes to the sink, so every distribution sums to one;
+ *   <prefix>.lab    labels 0 "init" (every grid state), 1 "deadlock" (none),
+ *                   2 "target", 3 "avoid", 4 "safe" (safety specs), 5 "sink";
+ *   <prefix>.sta    grid indices (x0, ..., x{n-1}) per state, -1 for the sink;
+ *   <prefix>.props  the property whose maximal probability is V_0 of
+ *                   amy_synthesize with this spec and horizon: Pmax=? [ G<=N
+ *                   "safe" ], [ !"avoid" U<=N "target" ] or [ F<=N "target" ].
+ * n_transitions_out (may be NULL) receives T.  The files grow with
+ * n_states * n_inputs * prod W lines: meant for small abstractions.
+ * Synchronous.  Errors: INVALID_ARG (null pointer, negative horizon, bad
+ * spec, a file that cannot be written), UNSUPPORTED (a disturbance grid: the
+ * model is then a stochastic game), CUDA. */
+amy_status amy_export_prism(amy_handle h, const amy_spec *spec, int32_t horizon, const char *path_prefix,
+                            int64_t *n_transitions_out);
+
 /* Rebuild the stored rows in place (Algorithm 2 again) after replacing the
  * system parameters (params may be NULL to keep them): same grid, cut and
  * storage, no allocation.  Asynchronous on the handle's stream.  For

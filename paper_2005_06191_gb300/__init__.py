@@ -13,6 +13,7 @@ gamma or window; spec kind and boxes) can be passed.
 from __future__ import annotations
 
 import ctypes as C
+import os
 from typing import Optional
 
 import numpy as np
@@ -368,6 +369,16 @@ def amy_simulate(h: AmyHandle, spec, horizon: int, policy, x0, runs_per_x0: int,
     return res
 
 
+def amy_export_prism(h: AmyHandle, spec, horizon: int, path_prefix: str) -> int:
+    """amy_export_prism: writes <prefix>.tra/.lab/.sta/.props (PRISM explicit
+    MDP files of the handle's abstraction); returns the number of transitions."""
+    k = _Keep()
+    s = _spec_struct(k, spec)
+    n = C.c_int64(0)
+    _check(_lib().amy_export_prism(h.ptr, C.byref(s), int(horizon), os.fsencode(path_prefix), C.byref(n)))
+    return int(n.value)
+
+
 def amy_rebuild(h: AmyHandle, params=None) -> None:
     """amy_rebuild: rebuild the stored rows in place (optionally with new system parameters)."""
     if params is None:
@@ -477,7 +488,7 @@ from .serving import (AmyServer, amy_cancel, amy_poll, amy_result_free,  # noqa:
 
 __all__ = [
     "AmyError", "AmyHandle", "AmyServer", "amy_build", "amy_synthesize", "amy_backup_step",
-    "amy_query_rows", "amy_simulate", "amy_info", "amy_destroy", "amy_grid_count", "amy_last_error",
+    "amy_query_rows", "amy_simulate", "amy_export_prism", "amy_info", "amy_destroy", "amy_grid_count", "amy_last_error",
     "amy_rebuild", "amy_set_profiling", "amy_set_wait_limit", "amy_set_step_wait", "amy_set_plane", "amy_backup_work", "amy_measure_l2", "amy_kernel_times", "amy_synthesize_noalloc", "amy_measure_lane_loads", "amy_measure_fma",
     "amy_server_create", "amy_submit", "amy_poll", "amy_wait", "amy_cancel", "amy_server_stats",
     "amy_server_graph_stats",

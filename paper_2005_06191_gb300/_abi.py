@@ -93,6 +93,8 @@ PROTOTYPES = {
     "amy_query_rows": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "amy_simulate": (C.c_int32, [C.c_void_p, C.POINTER(amy_spec), C.c_int32, C.c_void_p, C.c_void_p, C.c_int64,
                                  C.c_int64, C.c_uint64, C.c_void_p, C.c_int32]),
+    "amy_export_prism": (C.c_int32, [C.c_void_p, C.POINTER(amy_spec), C.c_int32, C.c_char_p,
+                                     C.POINTER(C.c_int64)]),
     "amy_info": (C.c_int32, [C.c_void_p, C.POINTER(amy_info_t)]),
     "amy_rebuild": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64]),
     "amy_set_profiling": (C.c_int32, [C.c_void_p, C.c_int32]),

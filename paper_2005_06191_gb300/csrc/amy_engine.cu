@@ -4,6 +4,7 @@
 // Host side: validation, window shape (Sec. 5.2 Remark, scalars per dim),
 // device allocation and kernel launches.  Every per-state and per-pair step
 // runs in the kernels of amy_kernels.cuh.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1676,6 +1677,21 @@ amy_status synthesize_graph(amy_handle_s *h, const SpecDev &s, int32_t horizon, 
     return AMY_OK;
 }
 
+// Rows of `count` device-given pairs (x[i], u[i]) as the handle's mode
+// computes them (k_query_rows): window origins and prod-W FP64 masses.
+cudaError_t enqueue_rows(amy_handle_s *h, const int64_t *dx, const int64_t *du, int64_t count, int32_t *dor,
+                         double *dpr) {
+    const Geom &g = h->g;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((count + 127) / 128, 4096));
+    if (h->prec == AMY_PREC_FP64)
+        k_query_rows<double><<<blocks, 128, 0, h->stream>>>(g, h->tmode, (const double *)h->d_T, h->d_O, h->npairs,
+                                                            h->d_tab, dx, du, count, dor, dpr);
+    else
+        k_query_rows<float><<<blocks, 128, 0, h->stream>>>(g, h->tmode, (const float *)h->d_T, h->d_O, h->npairs,
+                                                           h->d_tab, dx, du, count, dor, dpr);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 extern "C" {
@@ -1828,18 +1844,7 @@ amy_status amy_query_rows(amy_handle h, const int64_t *x, const int64_t *u, int6
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&dpr, prb, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x, count * 8, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(du, u, count * 8, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) {
-        const int blocks = (int)std::min<int64_t>((count + 127) / 128, 4096);
-        if (h->prec == AMY_PREC_FP64)
-            k_query_rows<double><<<blocks, 128, 0, h->stream>>>(g, h->tmode, (const double *)h->d_T, h->d_O, h->npairs,
-                                                                h->d_tab,
-                                                                dx, du, count, dor, dpr);
-        else
-            k_query_rows<float><<<blocks, 128, 0, h->stream>>>(g, h->tmode, (const float *)h->d_T, h->d_O, h->npairs,
-                                                               h->d_tab,
-                                                               dx, du, count, dor, dpr);
-        e = cudaGetLastError();
-    }
+    if (e == cudaSuccess) e = enqueue_rows(h, dx, du, count, dor, dpr);
     if (e == cudaSuccess) e = cudaMemcpyAsync(origin_out, dor, count * g.n * 4, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(probs_out, dpr, prb, cudaMemcpyDeviceToHost, h->stream);
     if (dx) cudaFreeAsync(dx, h->stream);
@@ -1909,6 +1914,227 @@ amy_status amy_simulate(amy_handle h, const amy_spec *spec, int32_t horizon, con
     if (e2 != cudaSuccess) return cuda_error(e2, "simulate");
     if (err & 1u) return set_error(AMY_E_INVALID_ARG, "an initial state is out of range");
     if (err & 2u) return set_error(AMY_E_INVALID_ARG, "the policy names an input >= %d at a live state", g.nu / g.nw);
+    return AMY_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Export of the finite MDP in PRISM's explicit-model files (the tool's PRISM
+// export of the abstraction, Sec. 2): .tra (transitions), .lab (labels),
+// .sta (state coordinates) and .props (the bounded-horizon property whose
+// maximal probability is V_0).
+// ---------------------------------------------------------------------------
+namespace {
+
+struct FileCloser {
+    std::FILE *f = nullptr;
+    ~FileCloser() {
+        if (f) std::fclose(f);
+    }
+};
+
+amy_status open_out(const std::string &path, FileCloser &fc) {
+    fc.f = std::fopen(path.c_str(), "wb");
+    if (!fc.f) return set_error(AMY_E_INVALID_ARG, "cannot open %s for writing", path.c_str());
+    return AMY_OK;
+}
+
+amy_status close_out(const std::string &path, FileCloser &fc) {
+    const bool bad = std::ferror(fc.f) != 0;
+    const int rc = std::fclose(fc.f);
+    fc.f = nullptr;
+    if (bad || rc != 0) return set_error(AMY_E_INVALID_ARG, "write to %s failed", path.c_str());
+    return AMY_OK;
+}
+
+// Writes the .tra body for every (state, input) pair, rows from the handle's
+// own abstraction computed on the device in batches; returns the number of
+// transitions written.  A row's slots that land on one cell (a periodic
+// window wider than its ring) are merged; the mass the cut or the grid's
+// edge removes goes to the sink state nx.
+amy_status write_transitions(amy_handle_s *h, std::FILE *f, int64_t &n_trans) {
+    const Geom &g = h->g;
+    const int64_t nx = g.nx, nu = g.nu, wt = g.wtot;
+    const int64_t npair = nx * nu;
+    const int64_t batch = std::max<int64_t>(1, std::min<int64_t>(npair, ((int64_t)32 << 20) / (wt * 8)));
+    std::vector<int64_t> hx((size_t)batch), hu((size_t)batch);
+    std::vector<int32_t> horg((size_t)(batch * g.n));
+    std::vector<double> hpr((size_t)(batch * wt));
+    int64_t *dx = nullptr, *du = nullptr;
+    int32_t *dor = nullptr;
+    double *dpr = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&dx, (size_t)batch * 8, h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&du, (size_t)batch * 8, h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dor, (size_t)(batch * g.n) * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dpr, (size_t)(batch * wt) * 8, h->stream);
+    std::vector<std::pair<int64_t, double>> row((size_t)wt);
+    n_trans = 0;
+    for (int64_t p0 = 0; p0 < npair && e == cudaSuccess; p0 += batch) {
+        const int64_t cnt = std::min(batch, npair - p0);
+        for (int64_t i = 0; i < cnt; ++i) {
+            hx[(size_t)i] = (p0 + i) / nu;
+            hu[(size_t)i] = (p0 + i) % nu;
+        }
+        e = cudaMemcpyAsync(dx, hx.data(), (size_t)cnt * 8, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(du, hu.data(), (size_t)cnt * 8, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = enqueue_rows(h, dx, du, cnt, dor, dpr);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(horg.data(), dor, (size_t)(cnt * g.n) * 4, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hpr.data(), dpr, (size_t)(cnt * wt) * 8, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) break;
+        for (int64_t i = 0; i < cnt; ++i) {
+            const int32_t *org = &horg[(size_t)(i * g.n)];
+            const double *pr = &hpr[(size_t)(i * wt)];
+            size_t nr = 0;
+            double sum = 0.0;
+            int32_t k[MAXD] = {0};
+            for (int64_t t = 0; t < wt; ++t) {
+                if (pr[t] > 0.0) {
+                    int64_t tgt = 0;
+                    bool on = true;
+                    for (int d = 0; d < g.n; ++d) {
+                        int32_t c = org[d] + k[d];
+                        if ((g.periodic >> d) & 1u) c = ((c % g.N[d]) + g.N[d]) % g.N[d];
+                        else if (c < 0 || c >= g.N[d]) on = false;
+                        tgt += (int64_t)c * g.stride[d];
+                    }
+                    if (on) {
+                        row[nr++] = {tgt, pr[t]};
+                        sum += pr[t];
+                    }
+                }
+                for (int d = g.n - 1; d >= 0; --d) {
+                    if (++k[d] < g.W[d]) break;
+                    k[d] = 0;
+                }
+            }
+            std::sort(row.begin(), row.begin() + (std::ptrdiff_t)nr);
+            const int64_t x = hx[(size_t)i], u = hu[(size_t)i];
+            for (size_t j = 0; j < nr;) {
+                const int64_t tgt = row[j].first;
+                double v = 0.0;
+                for (; j < nr && row[j].first == tgt; ++j) v += row[j].second;
+                std::fprintf(f, "%lld %lld %lld %.17g\n", (long long)x, (long long)u, (long long)tgt, v);
+                ++n_trans;
+            }
+            const double lost = 1.0 - sum;
+            if (lost > 0.0) {
+                std::fprintf(f, "%lld %lld %lld %.17g\n", (long long)x, (long long)u, (long long)nx, lost);
+                ++n_trans;
+            }
+        }
+    }
+    if (dx) cudaFreeAsync(dx, h->stream);
+    if (du) cudaFreeAsync(du, h->stream);
+    if (dor) cudaFreeAsync(dor, h->stream);
+    if (dpr) cudaFreeAsync(dpr, h->stream);
+    const cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_error(e, "export rows");
+    if (e2 != cudaSuccess) return cuda_error(e2, "export rows");
+    return AMY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+amy_status amy_export_prism(amy_handle h, const amy_spec *spec, int32_t horizon, const char *path_prefix,
+                            int64_t *n_transitions_out) {
+    if (!h || !spec || !path_prefix || !*path_prefix) return set_error(AMY_E_INVALID_ARG, "null argument");
+    if (horizon < 0) return set_error(AMY_E_INVALID_ARG, "negative horizon");
+    const Geom &g = h->g;
+    if (g.nw > 1)
+        return set_error(AMY_E_UNSUPPORTED, "a disturbance grid makes the model a stochastic game, not an MDP");
+    SpecDev s;
+    amy_status st = make_spec(g, spec, s);
+    if (st != AMY_OK) return st;
+    const int64_t nx = g.nx, nu = g.nu;
+    std::vector<uint8_t> mask((size_t)nx);
+    st = launch_mask_any(h, s, h->d_V[0]);
+    if (st != AMY_OK) return st;
+    AMY_CUDA(cudaMemcpyAsync(mask.data(), h->d_mask, (size_t)nx, cudaMemcpyDeviceToHost, h->stream), "export mask");
+    AMY_CUDA(cudaStreamSynchronize(h->stream), "export mask");
+    const std::string pre(path_prefix);
+    // transitions: body to a part file, then the header and the body
+    const std::string tra = pre + ".tra", part = pre + ".tra.part";
+    int64_t n_trans = 0;
+    {
+        FileCloser fc;
+        if ((st = open_out(part, fc)) != AMY_OK) return st;
+        st = write_transitions(h, fc.f, n_trans);
+        if (st != AMY_OK) {
+            std::fclose(fc.f);
+            fc.f = nullptr;
+            std::remove(part.c_str());
+            return st;
+        }
+        std::fprintf(fc.f, "%lld 0 %lld 1\n", (long long)nx, (long long)nx);  // the sink: absorbing
+        ++n_trans;
+        if ((st = close_out(part, fc)) != AMY_OK) return st;
+    }
+    {
+        FileCloser out, in;
+        if ((st = open_out(tra, out)) != AMY_OK) return st;
+        std::fprintf(out.f, "%lld %lld %lld\n", (long long)(nx + 1), (long long)(nx * nu + 1), (long long)n_trans);
+        in.f = std::fopen(part.c_str(), "rb");
+        if (!in.f) return set_error(AMY_E_INVALID_ARG, "cannot reopen %s", part.c_str());
+        std::vector<char> buf(1 << 20);
+        size_t got;
+        while ((got = std::fread(buf.data(), 1, buf.size(), in.f)) > 0) std::fwrite(buf.data(), 1, got, out.f);
+        std::fclose(in.f);
+        in.f = nullptr;
+        if ((st = close_out(tra, out)) != AMY_OK) return st;
+        std::remove(part.c_str());
+    }
+    // labels: every grid state is initial; the sink carries only "sink"
+    {
+        const std::string lab = pre + ".lab";
+        FileCloser fc;
+        if ((st = open_out(lab, fc)) != AMY_OK) return st;
+        std::fprintf(fc.f, "0=\"init\" 1=\"deadlock\" 2=\"target\" 3=\"avoid\" 4=\"safe\" 5=\"sink\"\n");
+        for (int64_t x = 0; x < nx; ++x) {
+            const uint8_t f = mask[(size_t)x];
+            std::fprintf(fc.f, "%lld: 0%s%s%s\n", (long long)x, (f & F_TARGET) ? " 2" : "", (f & F_AVOID) ? " 3" : "",
+                         (s.kind == SPEC_SAFETY && (f & F_SAFE)) ? " 4" : "");
+        }
+        std::fprintf(fc.f, "%lld: 5\n", (long long)nx);
+        if ((st = close_out(lab, fc)) != AMY_OK) return st;
+    }
+    // state coordinates: grid indices per dim, the sink at -1
+    {
+        const std::string sta = pre + ".sta";
+        FileCloser fc;
+        if ((st = open_out(sta, fc)) != AMY_OK) return st;
+        std::fprintf(fc.f, "(");
+        for (int d = 0; d < g.n; ++d) std::fprintf(fc.f, d ? ",x%d" : "x%d", d);
+        std::fprintf(fc.f, ")\n");
+        for (int64_t x = 0; x <= nx; ++x) {
+            std::fprintf(fc.f, "%lld:(", (long long)x);
+            for (int d = 0; d < g.n; ++d) {
+                const long long c = x < nx ? (long long)((x / g.stride[d]) % g.N[d]) : -1;
+                std::fprintf(fc.f, d ? ",%lld" : "%lld", c);
+            }
+            std::fprintf(fc.f, ")\n");
+        }
+        if ((st = close_out(sta, fc)) != AMY_OK) return st;
+    }
+    // the property: V_0 is its maximal probability from every state
+    {
+        const std::string props = pre + ".props";
+        FileCloser fc;
+        if ((st = open_out(props, fc)) != AMY_OK) return st;
+        if (s.kind == SPEC_SAFETY)
+            std::fprintf(fc.f, "Pmax=? [ G<=%d \"safe\" ]\n", (int)horizon);
+        else if (s.n_avoid > 0)
+            std::fprintf(fc.f, "Pmax=? [ !\"avoid\" U<=%d \"target\" ]\n", (int)horizon);
+        else
+            std::fprintf(fc.f, "Pmax=? [ F<=%d \"target\" ]\n", (int)horizon);
+        if ((st = close_out(props, fc)) != AMY_OK) return st;
+    }
+    if (n_transitions_out) *n_transitions_out = n_trans;
     return AMY_OK;
 }
 
