@@ -18,21 +18,22 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "amy_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "amy_oracle_expr.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-_SYS = {"affine": 0, "unicycle": 1}
+_SYS = {"affine": 0, "unicycle": 1, "expr": 2}
 _SPEC = {"safety": 0, "reach": 1, "reach_avoid": 2}
 
 
 def build_oracle(force: bool = False) -> str:
     """Compile liboracle.so next to its source (gcc, FP64, no FMA contraction)."""
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
-                                               os.path.getmtime(os.path.join(_HERE, "amy_oracle.h")))):
+            and os.path.getmtime(_LIB) >= max([os.path.getmtime(f) for f in _SRCS]
+                                              + [os.path.getmtime(os.path.join(_HERE, "amy_oracle.h"))])):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+           "-fPIC", "-shared", "-o", tmp, *_SRCS, "-lm"]
     subprocess.check_call(cmd, cwd=_HERE)
     os.replace(tmp, _LIB)
     return _LIB
@@ -52,6 +53,7 @@ class _Problem(C.Structure):
         ("w_count", C.POINTER(C.c_int32)),
         ("noise", C.c_int32), ("noise_p0", C.POINTER(C.c_double)), ("noise_p1", C.POINTER(C.c_double)),
         ("noise_p2", C.POINTER(C.c_double)), ("noise_p3", C.POINTER(C.c_double)),
+        ("expr", C.c_void_p),
     ]
 
 
@@ -89,6 +91,11 @@ def _load():
         lib.orc_action_values.argtypes = [P, C.c_void_p, C.c_int64, C.c_void_p]
         lib.orc_synthesize.argtypes = [P, S, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_int]
+        lib.orc_expr_compile.restype = C.c_void_p
+        lib.orc_expr_compile.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_char_p, C.c_int]
+        lib.orc_expr_free.argtypes = [C.c_void_p]
+        lib.orc_expr_eval.restype = C.c_double
+        lib.orc_expr_eval.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.orc_philox4x64.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         lib.orc_simulate.argtypes = [P, S, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
                                      C.c_uint64, C.c_void_p]
@@ -98,6 +105,14 @@ def _load():
 
 def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class _ExprOwner:
+    def __init__(self, lib, h):
+        self.lib, self.h = lib, h
+
+    def __del__(self):
+        self.lib.orc_expr_free(self.h)
 
 
 class _Keep:
@@ -115,6 +130,18 @@ class _Keep:
         a = np.ascontiguousarray(np.asarray(v, dtype=np.int32))
         self.bufs.append(a)
         return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+    def expr(self, lib, p):
+        """Compiles a problem's mean expressions; freed with this object."""
+        texts = [str(t).encode() for t in p.exprs]
+        arr = (C.c_char_p * len(texts))(*texts)
+        err = C.create_string_buffer(256)
+        wc = list(getattr(p, "w_count", None) or [])
+        h = lib.orc_expr_compile(arr, p.n, p.m, len(wc), int(np.asarray(p.params).size), err, 256)
+        if not h:
+            raise ValueError(f"expression: {err.value.decode()}")
+        self.bufs.append(_ExprOwner(lib, h))
+        return h
 
     def u8(self, v):
         a = np.ascontiguousarray(np.asarray(v, dtype=np.uint8))
@@ -141,6 +168,8 @@ def _problem(p, keep: _Keep) -> _Problem:
     s.noise = _NOISE[getattr(p, "noise", "gaussian")]
     for i, arr in enumerate(list(getattr(p, "noise_params", None) or [])[:4]):
         setattr(s, f"noise_p{i}", keep.f64(arr))
+    if p.sys_kind == "expr":
+        s.expr = keep.expr(_load(), p)
     return s
 
 
@@ -281,3 +310,24 @@ def simulate(p, sp, horizon: int, policy, x0: Sequence[int], runs: int, seed: in
     if rc != 0:
         raise ValueError("orc_simulate failed")
     return out
+
+
+def expr_eval(exprs, n: int, m: int, p: int, params, x, u, w) -> np.ndarray:
+    """Every mean component of a text system at one point (x, u, w)."""
+    lib = _load()
+    texts = [str(t).encode() for t in exprs]
+    arr = (C.c_char_p * len(texts))(*texts)
+    err = C.create_string_buffer(256)
+    prm = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(-1))
+    h = lib.orc_expr_compile(arr, n, m, p, prm.size, err, 256)
+    if not h:
+        raise ValueError(f"expression: {err.value.decode()}")
+    try:
+        xs = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1))
+        us = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1)) if m else np.zeros(1)
+        ws = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(-1)) if p else np.zeros(1)
+        pp = prm if prm.size else np.zeros(1)
+        return np.array([lib.orc_expr_eval(h, d, xs.ctypes.data, us.ctypes.data, ws.ctypes.data, pp.ctypes.data)
+                         for d in range(n)])
+    finally:
+        lib.orc_expr_free(h)

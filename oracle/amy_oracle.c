@@ -180,6 +180,21 @@ int orc_mean(const orc_problem *p, int64_t x, int64_t u, double *mu) {
     int32_t xi[ORC_MAXD], ui[ORC_MAXD];
     double xc[ORC_MAXD], uc[ORC_MAXD];
     decode(x, p->x_count, n, xi);
+    if (p->sys_kind == ORC_SYS_EXPR) {
+        /* pair index u = input * n_w + disturbance, each in C order */
+        int64_t nw = 1;
+        for (int d = 0; d < p->p; ++d) nw *= p->w_count[d];
+        int32_t wi[ORC_MAXD];
+        double wc[ORC_MAXD];
+        decode(u / nw, p->u_count, m, ui);
+        decode(u % nw, p->w_count, p->p, wi);
+        for (int d = 0; d < n; ++d) xc[d] = p->x_lb[d] + (double)xi[d] * p->x_eta[d];
+        for (int d = 0; d < m; ++d) uc[d] = p->u_lb[d] + (double)ui[d] * p->u_eta[d];
+        for (int d = 0; d < p->p; ++d) wc[d] = p->w_lb[d] + (double)wi[d] * p->w_eta[d];
+        if (!p->expr) return -1;
+        for (int d = 0; d < n; ++d) mu[d] = orc_expr_eval(p->expr, d, xc, uc, wc, p->params);
+        return 0;
+    }
     if (p->sys_kind == ORC_SYS_UNICYCLE) decode(u, p->u_count, m, ui);
     else for (int d = 0; d < m; ++d) ui[d] = 0;
     for (int d = 0; d < n; ++d) xc[d] = p->x_lb[d] + (double)xi[d] * p->x_eta[d];
@@ -339,6 +354,7 @@ static int shape_of(const orc_problem *p, orc_shape *sh) {
         p->n_params != sh->nu * sh->nw * (int64_t)(p->n * p->n + p->n))
         return -1;
     if (p->sys_kind == ORC_SYS_UNICYCLE && (p->n != 3 || p->m != 2 || p->n_params < 1 || p->p != 0)) return -1;
+    if (p->sys_kind == ORC_SYS_EXPR && !p->expr) return -1;
     if (p->noise == ORC_NOISE_MULT_GAUSSIAN && p->window == NULL && p->gamma != 0.0) return -1;
     return 0;
 }

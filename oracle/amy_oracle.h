@@ -35,7 +35,20 @@ extern "C" {
 
 #define ORC_MAXD 8
 
-enum { ORC_SYS_AFFINE_PER_INPUT = 0, ORC_SYS_UNICYCLE = 1 };
+enum { ORC_SYS_AFFINE_PER_INPUT = 0, ORC_SYS_UNICYCLE = 1, ORC_SYS_EXPR = 2 };
+
+/* A system given as text (Sec. 3: the right-hand side of the difference
+ * equation written in a configuration file): one C-syntax arithmetic
+ * expression per mean component over x0.., u0.., w0.. (the representative
+ * points of the state, input and disturbance) and p0.. (the parameters);
+ * grammar and functions in amy_oracle_expr.c.  Compiled once, evaluated in
+ * FP64 with the C library's functions. */
+typedef struct orc_expr orc_expr;
+/* NULL on a syntax error or an unknown name, with a message in err. */
+orc_expr *orc_expr_compile(const char *const *text, int n, int m, int p, int64_t n_params, char *err, int errlen);
+void orc_expr_free(orc_expr *e);
+double orc_expr_eval(const orc_expr *e, int d, const double *x, const double *u, const double *w,
+                     const double *params);
 enum { ORC_SAFETY = 0, ORC_REACH = 1, ORC_REACH_AVOID = 2 };
 
 typedef struct {
@@ -50,7 +63,7 @@ typedef struct {
     const int32_t *u_count;    /* [m] */
     int32_t sys_kind;          /* ORC_SYS_* */
     const double *params;      /* affine: per input u (C-order) A_u[n*n] row-major then c_u[n];
-                                  unicycle: {tau} */
+                                  unicycle: {tau}; expressions: their parameters p0.. */
     int64_t n_params;
     const double *sigma;       /* [n] per-dim noise standard deviation */
     double gamma;              /* cutting threshold; 0 = dense */
@@ -82,6 +95,9 @@ typedef struct {
      * of the exponential: [0, log(rate/gamma)/rate]. */
     int32_t noise;
     const double *noise_p0, *noise_p1, *noise_p2, *noise_p3; /* [n] each (unused ones may be NULL) */
+    /* ORC_SYS_EXPR: the compiled mean expressions (params are their p0..);
+     * a disturbance grid is allowed, its point bound to w0.. */
+    const orc_expr *expr;
 } orc_problem;
 
 enum { ORC_NOISE_GAUSSIAN = 0, ORC_NOISE_UNIFORM = 1, ORC_NOISE_EXPONENTIAL = 2, ORC_NOISE_BETA = 3,

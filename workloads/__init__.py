@@ -27,6 +27,7 @@ SEED = 20050619
 
 AFFINE = "affine"        # mu = A_u x + c_u, A_u and c_u given per discrete input
 UNICYCLE = "unicycle"    # mu = (x + tau v cos th, y + tau v sin th, th + tau w)
+EXPR = "expr"            # mu_d = a C-syntax expression over x0.., u0.., w0.. and the params p0..
 
 SAFETY = "safety"
 REACH = "reach"
@@ -62,6 +63,9 @@ class Problem:
     # list of n values per parameter
     noise: str = "gaussian"
     noise_params: Optional[List[List[float]]] = None
+    # sys_kind "expr": one expression per state dim (the text right-hand side
+    # of Sec. 3); params are its p0, p1, ...
+    exprs: Optional[List[str]] = None
 
     @property
     def n(self) -> int:
@@ -196,6 +200,18 @@ def robot_dist(n_per_dim: int = 41, u_step: float = 0.2, w_step: float = 0.2, ho
     else:
         spec = Spec(REACH_AVOID, targets=[([5.0, 5.0], [10.0, 10.0])], avoids=[([-2.0, -2.0], [2.0, 2.0])])
     return Workload(p, spec, horizon, precision="fp32", tmode="otf")
+
+
+def robot_dist_expr(n_per_dim: int = 41, u_step: float = 0.2, w_step: float = 0.2, horizon: int = 8,
+                    kind: str = SAFETY) -> Workload:
+    """The robot of Sec. 7 given as text, as the tool's configuration file
+    gives it: x1+ = x1 + tau nu1 cos(nu2) + w, x2+ = x2 + tau nu1 sin(nu2) + w
+    (the same system as robot_dist, whose affine records restate it per
+    input and disturbance point)."""
+    w = robot_dist(n_per_dim, u_step, w_step, horizon, kind)
+    p = replace(w.problem, name=f"robot_dist_expr_{n_per_dim}", sys_kind=EXPR, params=np.array([10.0]),
+                exprs=["x0 + (p0*u0*cos(u1) + w0)", "x1 + (p0*u0*sin(u1) + w0)"])
+    return replace(w, problem=p)
 
 
 # ---------------------------------------------------------------------------
