@@ -75,8 +75,26 @@ typedef struct amy_grid_s {
  *   lowest input maximising that value.  Only the affine kind takes a grid:
  *   params then holds one (A, c) record per (input, disturbance) pair,
  *   disturbance fastest (record u * n_w + w), n_params = n_u * n_w * (n*n + n);
- *   disturb->periodic is ignored. */
-typedef enum { AMY_SYS_AFFINE_PER_INPUT = 0, AMY_SYS_UNICYCLE = 1 } amy_sys_kind;
+ *   disturb->periodic is ignored.
+ * AMY_SYS_EXPR: the system as text, as the tool's configuration files give
+ *   the right-hand side of the difference equation (Sec. 3): expr[d] (n
+ *   NUL-terminated strings) is mean component d, a C-syntax arithmetic
+ *   expression over the FP64 variables x0..x{n-1} (the state's centre),
+ *   u0..u{m-1} (the input's point), w0..w{p-1} (the disturbance's point, with
+ *   a disturbance grid) and p0..p{n_params-1} (params, which may be NULL when
+ *   n_params = 0): numeric literals (always doubles), unary + and -, binary +
+ *   - * / (left associative, * and / binding tighter), parentheses, and the
+ *   calls sin cos tan asin acos atan sinh cosh tanh exp log log10 sqrt fabs
+ *   floor ceil, atan2 pow fmin fmax.  Every operation is one FP64 operation
+ *   rounded as written (no fused multiply-add); the calls are CUDA's.  The
+ *   expressions are compiled at amy_build with NVRTC (UNSUPPORTED when
+ *   libnvrtc cannot be loaded) into a kernel that tabulates each component
+ *   over the coordinates it reads (8 bytes per record: the product of the
+ *   grid sizes of the variables it names); the kernels read the means from
+ *   those tables, and amy_rebuild with new params refills them.  A syntax
+ *   error or an unknown name is INVALID_ARG.  Only amy_build takes this kind
+ *   (the server and amy_synthesize_noalloc answer UNSUPPORTED). */
+typedef enum { AMY_SYS_AFFINE_PER_INPUT = 0, AMY_SYS_UNICYCLE = 1, AMY_SYS_EXPR = 2 } amy_sys_kind;
 
 /* Noise distribution per dimension (Sec. 6.2: uniform, exponential and beta
  * besides the normal, and multiplicative noise as in Eq. (1a)); NULL in
@@ -112,6 +130,7 @@ typedef struct {
     int64_t n_params;
     const struct amy_grid_s *disturb;  /* NULL: no disturbance */
     const amy_noise *noise;            /* NULL: Gaussian (amy_build's sigma) */
+    const char *const *expr;           /* AMY_SYS_EXPR: n expressions, else ignored */
 } amy_system;
 
 /* Cutting region (Sec. 5.2 and its Remark on constructing the region).

@@ -23,7 +23,7 @@ from ._abi import STATUS_NAMES
 
 TMODES = {"otf": 0, "stored_full": 1, "stored_factored": 2, "stored_separable": 3, "auto": 4}
 PRECS = {"fp64": 0, "fp32": 1, "fp32_kahan": 2}
-SYS_KINDS = {"affine": 0, "unicycle": 1}
+SYS_KINDS = {"affine": 0, "unicycle": 1, "expr": 2}
 SPEC_KINDS = {"safety": 0, "reach": 1, "reach_avoid": 2}
 VSTORES = {"native": 0, "bf16": 1, "u16": 2}
 NOISE_KINDS = {"gaussian": 0, "uniform": 1, "exponential": 2, "beta": 3, "mult_gaussian": 4}
@@ -96,6 +96,12 @@ def _problem_structs(k: _Keep, p):
         for i, arr in enumerate(list(getattr(p, "noise_params", None) or [])[:4]):
             setattr(nz, f"p{i}", k.f64(arr))
         sysd.noise = C.pointer(k.obj(nz))
+    if p.sys_kind == "expr":
+        texts = k.obj([str(t).encode() for t in (p.exprs or [])])
+        if len(texts) != p.n:
+            raise ValueError(f"a text system needs {p.n} expressions, got {len(texts)}")
+        arr = k.obj((C.c_char_p * len(texts))(*texts))
+        sysd.expr = C.cast(arr, C.POINTER(C.c_char_p))
     states = _grid(k, p.x_lb, p.x_eta, p.x_count, p.x_periodic)
     inputs = _grid(k, p.u_lb, p.u_eta, p.u_count)
     cut = _abi.amy_cut()

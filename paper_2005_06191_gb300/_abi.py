@@ -30,7 +30,8 @@ class amy_noise(C.Structure):
 
 class amy_system(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n", C.c_int32), ("m", C.c_int32), ("params", DP),
-                ("n_params", C.c_int64), ("disturb", C.POINTER(amy_grid)), ("noise", C.POINTER(amy_noise))]
+                ("n_params", C.c_int64), ("disturb", C.POINTER(amy_grid)), ("noise", C.POINTER(amy_noise)),
+                ("expr", C.POINTER(C.c_char_p))]
 
 
 class amy_cut(C.Structure):

@@ -18,7 +18,7 @@ BUILD_DIR = os.path.join(PKG, "_build")
 
 SOURCES = [f for f in ("amy_engine.cu", "amy_fast.cu", "amy_fast_f32.cu", "amy_fast_u16.cu", "amy_fast_bf16.cu",
                        "amy_batch.cu", "amy_server.cu", "amy_noalloc.cu", "amy_calibrate.cu",
-                       "amy_simulate.cu")
+                       "amy_simulate.cu", "amy_expr.cu")
            if os.path.exists(os.path.join(CSRC, f))]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-fast-math",
@@ -66,7 +66,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = OUT + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lpthread"]
+    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

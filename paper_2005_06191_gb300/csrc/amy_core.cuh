@@ -20,7 +20,7 @@ constexpr int MAX_BOXES = 16;
 constexpr int MAXWS = 160;  // largest sum of window widths a kernel keeps per row
 
 enum WindowMode : int32_t { WM_DENSE = 0, WM_GAMMA = 1, WM_EXPLICIT = 2 };
-enum SysKind : int32_t { SYS_AFFINE = 0, SYS_UNICYCLE = 1 };
+enum SysKind : int32_t { SYS_AFFINE = 0, SYS_UNICYCLE = 1, SYS_EXPR = 2 };
 enum SpecKind : int32_t { SPEC_SAFETY = 0, SPEC_REACH = 1, SPEC_REACH_AVOID = 2 };
 enum TMode : int32_t { TM_OTF = 0, TM_FULL = 1, TM_FACTORED = 2, TM_SEPARABLE = 3 };
 // Noise distribution per dimension (Sec. 6.2; multiplicative noise as in Eq. (1a)).
@@ -58,6 +58,12 @@ struct Geom {
     int32_t ucount[MAXD];
     double ulb[MAXD], ueta[MAXD];
     const double *params;        // device copy of the system parameters
+    // Text systems (SYS_EXPR): component d of the mean, tabulated over the
+    // coordinates it reads -- record e = sum_j xi_j * tsx[d][j] + sum_i ui_i *
+    // tsu[d][i], the index of the per-dimension tables -- at mtab[moff[d] + e].
+    const double *mtab;
+    int64_t moff[MAXD];
+    uint32_t xdep[MAXD], udep[MAXD];  // the coordinates each component's text reads (host planning)
     // Dependency-compressed per-dimension tables (separable stored mode):
     // mean component d depends only on the state dims j with tsx[d][j] != 0
     // and the input dims i with tsu[d][i] != 0, so its window origin and
@@ -129,6 +135,25 @@ __device__ __forceinline__ double noise_centre(const Geom &g, int32_t x, int d) 
     return state_centre(g, d, j);
 }
 
+// Component d of a text system's mean at state coordinates xi and (input,
+// disturbance) pair u: its tabulated value.
+__device__ __forceinline__ double expr_mean(const Geom &g, const int32_t *xi, int32_t u, int d) {
+    int64_t e = 0;
+    uint32_t r = (uint32_t)u;
+#pragma unroll
+    for (int i = MAXD - 1; i >= 0; --i) {
+        if (i < g.m) {
+            const uint32_t U = (uint32_t)g.ucount[i];
+            e += (int64_t)(r % U) * g.tsu[d][i];
+            r /= U;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < MAXD; ++j)
+        if (j < g.n) e += (int64_t)xi[j] * g.tsx[d][j];
+    return __ldg(g.mtab + g.moff[d] + e);
+}
+
 // Mean of the post state, Algorithm 2 "Set mu = f(x, nu, w)" for the
 // disturbance-free system of Eq. 4.
 __device__ __forceinline__ void mean_of(const Geom &g, int32_t x, int32_t u, double *mu) {
@@ -138,6 +163,12 @@ __device__ __forceinline__ void mean_of(const Geom &g, int32_t x, int32_t u, dou
 #pragma unroll
     for (int d = 0; d < MAXD; ++d)
         if (d < g.n) xc[d] = state_centre(g, d, xi[d]);
+    if (g.sys == SYS_EXPR) {
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d)
+            if (d < g.n) mu[d] = expr_mean(g, xi, u, d);
+        return;
+    }
     if (g.sys == SYS_AFFINE) {
         const int n = g.n;
         const double *A = g.params + (int64_t)u * (n * n + n);
@@ -171,6 +202,7 @@ __device__ __forceinline__ void mean_of(const Geom &g, int32_t x, int32_t u, dou
 __device__ __forceinline__ double mean_component(const Geom &g, int32_t x, int32_t u, int d) {
     int32_t xi[MAXD];
     decode_state(g, x, xi);
+    if (g.sys == SYS_EXPR) return expr_mean(g, xi, u, d);
     if (g.sys == SYS_AFFINE) {
         const int n = g.n;
         const double *A = g.params + (int64_t)u * (n * n + n);

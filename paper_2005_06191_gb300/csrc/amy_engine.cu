@@ -125,8 +125,8 @@ amy_status fill_geom(const amy_system *sys, const amy_grid *st, const amy_grid *
     int64_t nw = 1;
     const amy_grid *dg = sys->disturb;
     if (dg && dg->n > 0) {
-        if (sys->kind != AMY_SYS_AFFINE_PER_INPUT)
-            return set_error(AMY_E_UNSUPPORTED, "a disturbance grid needs the affine system kind");
+        if (sys->kind != AMY_SYS_AFFINE_PER_INPUT && sys->kind != AMY_SYS_EXPR)
+            return set_error(AMY_E_UNSUPPORTED, "a disturbance grid needs the affine or the text system kind");
         if (m + dg->n > MAXD) return set_error(AMY_E_INVALID_ARG, "input and disturbance dims must total at most 8");
         if (!dg->lb || !dg->eta || !dg->count) return set_error(AMY_E_INVALID_ARG, "null disturbance grid array");
         for (int d = 0; d < dg->n; ++d) {
@@ -157,6 +157,11 @@ amy_status fill_geom(const amy_system *sys, const amy_grid *st, const amy_grid *
         if (n != 3 || m != 2 || !sys->params || sys->n_params < 1)
             return set_error(AMY_E_INVALID_ARG, "unicycle needs n=3, m=2, params={tau}");
         g.sys = SYS_UNICYCLE;
+    } else if (sys->kind == AMY_SYS_EXPR) {
+        if (!sys->expr) return set_error(AMY_E_INVALID_ARG, "text system needs one expression per state dim");
+        if (sys->n_params < 0 || (sys->n_params > 0 && !sys->params))
+            return set_error(AMY_E_INVALID_ARG, "text system: bad parameter array");
+        g.sys = SYS_EXPR;
     } else {
         return set_error(AMY_E_INVALID_ARG, "unknown system kind %d", sys->kind);
     }
@@ -297,10 +302,12 @@ amy_status make_spec(const Geom &g, const amy_spec *spec, SpecDev &s) {
 // FP64); input dim i matters iff two inputs differing only in that coordinate
 // have bitwise different rows (A_u[d][:], c_u[d]).  Unicycle: x on (x, th, v),
 // y on (y, th, v), th on (th, w).
-amy_status plan_sep_tables(Geom &g, const std::vector<double> &params, int64_t &words,
-                           std::vector<int32_t> *upart) {
+// Which state and input coordinates each mean component reads (bit j of
+// Sx[d], bit i of Su[d]); the masses of dim d under multiplicative noise read
+// x_d as well.
+void system_deps(const Geom &g, const std::vector<double> &params, uint32_t *Sx, uint32_t *Su) {
     const int n = g.n, m = g.m;
-    uint32_t Sx[MAXD] = {0}, Su[MAXD] = {0};
+    for (int d = 0; d < MAXD; ++d) Sx[d] = Su[d] = 0;
     if (g.sys == SYS_UNICYCLE) {
         Sx[0] = (1u << 0) | (1u << 2);
         Su[0] = 1u << 0;
@@ -308,6 +315,11 @@ amy_status plan_sep_tables(Geom &g, const std::vector<double> &params, int64_t &
         Su[1] = 1u << 0;
         Sx[2] = 1u << 2;
         Su[2] = 1u << 1;
+    } else if (g.sys == SYS_EXPR) {
+        for (int d = 0; d < n; ++d) {
+            Sx[d] = g.xdep[d];
+            Su[d] = g.udep[d];
+        }
     } else {
         const int rec = n * n + n;
         int32_t ustr[MAXD];
@@ -336,15 +348,17 @@ amy_status plan_sep_tables(Geom &g, const std::vector<double> &params, int64_t &
             }
         }
     }
-    // multiplicative noise: the masses of dim d also depend on x_d itself
     if (g.noise == NOISE_MULT_GAUSSIAN)
         for (int d = 0; d < n; ++d) Sx[d] |= 1u << d;
-    int64_t off = 0;
-    for (int d = 0; d < n; ++d) {
-        // state coordinates fastest: lanes of a warp (consecutive states, one
-        // input) then read consecutive records
+}
+
+// Strides of the dependency-compressed index of each dim's table: state
+// coordinates fastest (lanes of a warp -- consecutive states, one input --
+// then read consecutive records), then the input coordinates.
+amy_status table_strides(Geom &g, const uint32_t *Sx, const uint32_t *Su) {
+    for (int d = 0; d < g.n; ++d) {
         int64_t st = 1;
-        for (int j = n - 1; j >= 0; --j) {
+        for (int j = g.n - 1; j >= 0; --j) {
             g.tsx[d][j] = 0;
             if (Sx[d] & (1u << j)) {
                 g.tsx[d][j] = (int32_t)st;
@@ -352,7 +366,7 @@ amy_status plan_sep_tables(Geom &g, const std::vector<double> &params, int64_t &
                 if (st > 2147483647LL) return set_error(AMY_E_UNSUPPORTED, "table of dim %d too large", d);
             }
         }
-        for (int i = m - 1; i >= 0; --i) {
+        for (int i = g.m - 1; i >= 0; --i) {
             g.tsu[d][i] = 0;
             if (Su[d] & (1u << i)) {
                 if (st > 2147483647LL) return set_error(AMY_E_UNSUPPORTED, "table of dim %d too large", d);
@@ -362,9 +376,22 @@ amy_status plan_sep_tables(Geom &g, const std::vector<double> &params, int64_t &
         }
         if (st > 2147483647LL) return set_error(AMY_E_UNSUPPORTED, "table of dim %d too large", d);
         g.tent[d] = (int32_t)st;
+    }
+    return AMY_OK;
+}
+
+amy_status plan_sep_tables(Geom &g, const std::vector<double> &params, int64_t &words,
+                           std::vector<int32_t> *upart) {
+    const int n = g.n, m = g.m;
+    uint32_t Sx[MAXD], Su[MAXD];
+    system_deps(g, params, Sx, Su);
+    amy_status st0 = table_strides(g, Sx, Su);
+    if (st0 != AMY_OK) return st0;
+    int64_t off = 0;
+    for (int d = 0; d < n; ++d) {
         g.trw[d] = ((1 + g.W[d]) + 3) / 4 * 4;
         g.toff[d] = off;
-        off += st * g.trw[d];
+        off += (int64_t)g.tent[d] * g.trw[d];
     }
     // input part of each table index, one record of urw words per input
     g.uoff = off;
@@ -519,6 +546,8 @@ struct amy_handle_s {
     int64_t budget;
     int64_t bytes;
     double *d_params;
+    ExprProgram expr;     // text system: its parsed expressions and table kernel source
+    double *d_mtab;       // and its mean tables (null for the built-in systems)
     void *d_T;
     int16_t *d_O;
     // stored rows (full or factored) with wide windows: the backup is split
@@ -647,6 +676,7 @@ void free_handle(amy_handle_s *h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     cudaFree(h->d_params);
+    cudaFree(h->d_mtab);
     cudaFree(h->d_T);
     cudaFree(h->d_O);
     cudaFree(h->d_split);
@@ -1190,6 +1220,16 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     std::vector<double> params;
     amy_status st = make_geom(sys, states, inputs, sigma, cut, g, params);
     if (st != AMY_OK) return st;
+    ExprProgram prog;
+    if (g.sys == SYS_EXPR) {
+        const int p_dist = (sys->disturb && sys->disturb->n > 0) ? sys->disturb->n : 0;
+        st = expr_compile(sys->expr, g.n, g.m - p_dist, p_dist, sys->n_params, prog);
+        if (st != AMY_OK) return st;
+        for (int d = 0; d < MAXD; ++d) {
+            g.xdep[d] = prog.dep_x[d];
+            g.udep[d] = prog.dep_u[d];
+        }
+    }
     if (opts->tmode < AMY_T_ON_THE_FLY || opts->tmode > AMY_T_AUTO)
         return set_error(AMY_E_INVALID_ARG, "unknown tmode");
     if (opts->prec < AMY_PREC_FP64 || opts->prec > AMY_PREC_FP32_KAHAN)
@@ -1234,6 +1274,11 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     h->tileX = choose_tile(g.nx, g.nu, h->sm_count);
     h->npairs = (int64_t)g.nx * g.nu;
     h->fast_wm = fast_wm(g, h->prec);
+    // the register-resident kernels compute on-the-fly means inline for the
+    // built-in systems only; a text system's on-the-fly rows take the generic
+    // kernels, which read its mean tables
+    if (g.sys == SYS_EXPR && tmode == AMY_T_ON_THE_FLY) h->fast_wm = 0;
+    h->expr = prog;
     h->ulanes = 0;
     h->rows = 1;
     h->grouped = 0;
@@ -1342,6 +1387,22 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     if (e != cudaSuccess) {
         free_handle(h);
         return cuda_error(e, "params upload");
+    }
+    if (h->g.sys == SYS_EXPR) {
+        // mean tables of the text system, indexed like the per-dimension tables
+        if (h->tmode != AMY_T_STORED_SEPARABLE) {
+            uint32_t Sx[MAXD], Su[MAXD];
+            system_deps(h->g, params, Sx, Su);
+            TRY(table_strides(h->g, Sx, Su));
+        }
+        int64_t tot = 0;
+        for (int d = 0; d < h->g.n; ++d) {
+            h->g.moff[d] = tot;
+            tot += h->g.tent[d];
+        }
+        TRY(dev_alloc(h, (void **)&h->d_mtab, (size_t)tot * sizeof(double), "mean tables"));
+        h->g.mtab = h->d_mtab;
+        TRY(expr_fill_means(h->expr, h->g, h->d_mtab, h->stream));
     }
     if (h->tmode != AMY_T_ON_THE_FLY) {
         if (h->prec == AMY_PREC_FP64)
@@ -1489,6 +1550,11 @@ amy_status amy_rebuild(amy_handle h, const double *params, int64_t n_params) {
         h->host_params.assign(params, params + n_params);
         AMY_CUDA(cudaMemcpyAsync(h->d_params, h->host_params.data(), n_params * sizeof(double),
                                  cudaMemcpyHostToDevice, h->stream), "params upload");
+        if (h->g.sys == SYS_EXPR) {
+            const amy_status st = expr_fill_means(h->expr, h->g, h->d_mtab, h->stream);
+            if (st != AMY_OK) return st;
+            h->graph_valid = false;
+        }
     }
     if (h->tmode == AMY_T_ON_THE_FLY) return AMY_OK;
     amy_status st = h->prec == AMY_PREC_FP64 ? launch_build<double>(h) : launch_build<float>(h);

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <climits>
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -62,6 +63,19 @@ constexpr int kPlaneSmemDefault = 100 * 1024;
 // states, read back after the table build (negative: unknown).  smem_budget
 // 0 takes kPlaneSmemDefault.  pl.ok = 0 when the kernel does not apply.
 void plan_plane(const Geom &g, int tmode, int prec, const int32_t *spread, int smem_budget, PlanePlan &pl);
+
+// Text systems (amy_expr.cu): the parsed mean expressions as the CUDA source
+// of their table kernel, and the variables each component reads (input bit i
+// < m for u_i, bit m + k for the disturbance w_k).
+struct ExprProgram {
+    std::string source;
+    uint32_t dep_x[MAXD];
+    uint32_t dep_u[MAXD];
+};
+amy_status expr_compile(const char *const *text, int n, int m_ctrl, int p_dist, int64_t n_params, ExprProgram &out);
+// Fills g.mtab (device, sum_d tent[d] doubles at moff[d]) on `st`: compiles
+// the kernel with NVRTC on first use per source, then launches it.
+amy_status expr_fill_means(const ExprProgram &prog, const Geom &g, double *d_mtab, cudaStream_t st);
 
 // Closed-loop Monte-Carlo runs (amy_simulate.cu): n_x0 * runs runs of
 // `horizon` steps under pi[horizon][nx], successes counted per initial state

@@ -89,17 +89,19 @@ def bf16_folded(v):
 
 
 def compare_rows(amy, w, tmode: str, prec: str, n_pairs: int = 512, seed: int = 1):
-    """Window origins bit-exact and row probabilities close, on sampled pairs."""
+    """Window origins bit-exact and row probabilities close, on sampled pairs
+    (with a disturbance grid, sampled (input, disturbance) pairs)."""
     p = w.problem
+    nw = oracle.n_disturbances(p)
     rng = np.random.default_rng(seed)
     xs = rng.integers(0, p.n_states, size=n_pairs)
-    us = rng.integers(0, p.n_inputs, size=n_pairs)
+    us = rng.integers(0, p.n_inputs * nw, size=n_pairs)
     with amy.amy_build(p, tmode=tmode, prec=prec) as h:
         org, probs = amy.amy_query_rows(h, xs, us)
     mism = 0
     worst = 0.0
     for i in range(n_pairs):
-        o_ref, pr_ref = oracle.row(p, int(xs[i]), int(us[i]))
+        o_ref, pr_ref = oracle.row(p, int(xs[i]), int(us[i]) // nw, int(us[i]) % nw)
         if not np.array_equal(o_ref, org[i]):
             mism += 1
             continue

@@ -288,6 +288,27 @@ def traffic6(n_per_dim: int = 21, horizon: int = 8, n_cells: int = 6, window: in
     return Workload(p, spec, horizon, precision="fp32_kahan", tmode="otf", v_store=v_store)
 
 
+def traffic_text(n_per_dim: int = 21, horizon: int = 8, n_cells: int = 6, window: int = 5,
+                 capacity: float = 12.0) -> Workload:
+    """A nonlinear traffic ring given as text: each cell keeps 0.6 of its
+    vehicles, takes 0.25 of its upstream neighbour's -- at most the capacity
+    p0 (a saturating flow) -- and 0.05 of its downstream one's; two inputs
+    feed cells 0 and 2.  Component i reads x_{i-1}, x_i, x_{i+1} only."""
+    base = traffic6(n_per_dim, horizon, n_cells, window)
+    exprs = []
+    for i in range(n_cells):
+        up, dn = (i - 1) % n_cells, (i + 1) % n_cells
+        e = f"0.6*x{i} + 0.25*fmin(x{up}, p0) + 0.05*x{dn}"
+        if i == 0:
+            e += " + 6*u0"
+        if i == 2 % n_cells:
+            e += " + 8*u1"
+        exprs.append(e)
+    p = replace(base.problem, name=f"traffic_text{n_cells}_{n_per_dim}", sys_kind=EXPR,
+                params=np.array([capacity]), exprs=exprs)
+    return replace(base, problem=p)
+
+
 # ---------------------------------------------------------------------------
 # served: stream of random linear problems (2-4 dims)
 # ---------------------------------------------------------------------------
