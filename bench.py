@@ -246,12 +246,13 @@ def run_amy(args, rank, world):
         step()
     torch.cuda.synchronize()
     lane_peaks = amy.amy_measure_lane_loads()  # roofline denominators (outside the timed region)
-    if args.prec == "fp64" or info["backup_kernel"] == 7:
+    plane_family = info["backup_kernel"] in (7, 8)
+    if args.prec == "fp64" or plane_family:
         lane_peaks.update({"fma_" + k: v for k, v in amy.amy_measure_fma().items()})
-    if info["backup_kernel"] == 7:
+    if plane_family:
         lane_peaks["l2_bytes"] = amy.amy_measure_l2()
     # the plane kernel's own work in one backup (counted in an untimed run)
-    work = amy.amy_backup_work(h, spec) if info["backup_kernel"] == 7 else None
+    work = amy.amy_backup_work(h, spec) if plane_family else None
     barrier(world)
     amy.amy_kernel_times(h)  # reset
     amy.amy_set_profiling(h, True)
@@ -274,7 +275,7 @@ def run_amy(args, rank, world):
     # (for the per-dimension tables: bounds reset + tables [+ shifted inner table])
     launches = (info["backup_launch_kernels"] * kt["backup_launches"] + info["build_kernels"] * kt["build_launches"]
                 + args.steps)
-    if info["backup_kernel"] == 7:
+    if plane_family:
         launches += args.steps  # the padded copy of V_N the plane kernel reads, once per synthesis
     # per backup: the persistent kernel performs the whole horizon in one launch
     bk_ms = kt["backup_ms"] / max(kt["backup_steps"], 1)
@@ -338,7 +339,7 @@ def run_amy(args, rank, world):
 
 
 def roofline_plane(args, w, info, backup_ms, work, lane_peaks):
-    """Roofline of the plane kernel (backup kernel 7) from the work it counts
+    """Roofline of the plane kernel (backup kernel 7, or its tiled form 8) from the work it counts
     in one backup (amy_backup_work): stage 1 streams V_{k+1} through L2 (each
     staged row reads K values, coalesced across a plane), stage 2 reads the
     partial box from shared memory, and both issue FP32 fused multiply-adds
@@ -367,10 +368,14 @@ def roofline_plane(args, w, info, backup_ms, work, lane_peaks):
     first = dict(cs[0])
     first["other_ceilings"] = [{k: c[k] for k in ("bound", "achieved", "peak", "unit", "frac")} for c in cs[1:]]
     traffic, src = measured_traffic(args, w.problem.n_states)
-    first.update({"traffic": traffic, "traffic_source": src, "backup_kernel": 7,
+    nominal = int(w.problem.n_states * w.problem.n_inputs * info["window_slots"])
+    first.update({"traffic": traffic, "traffic_source": src, "backup_kernel": info["backup_kernel"],
                   "work_per_backup": work,
-                  "nominal_window_slots_per_backup": int(w.problem.n_states * w.problem.n_inputs *
-                                                         info["window_slots"])})
+                  "nominal_window_slots_per_backup": nominal,
+                  # one FMA per window slot is the per-transition work of a
+                  # kernel that sums every slot; the plane kernels reassociate
+                  # the sum and perform fewer (work_per_backup)
+                  "nominal_slot_rate_vs_fma_peak": nominal / bk_s / lane_peaks["fma_fp32"]})
     return first
 
 
@@ -673,9 +678,9 @@ def main():
     ap.add_argument("--step-wait", dest="step_wait", type=int, default=None, choices=[0, 1],
                     help="persistent kernel between backups: 0 = neighbour tiles, 1 = grid barrier "
                          "(default: the handle's choice, autotuned)")
-    ap.add_argument("--plane", type=int, default=None, choices=[0, 1],
+    ap.add_argument("--plane", type=int, default=None, choices=[0, 1, 2],
                     help="banded problems with tables: 1 = the plane kernel (default where it applies), "
-                         "0 = the per-state kernel")
+                         "2 = its tiled form where that applies, 0 = the per-state kernel")
     ap.add_argument("--plane-smem", dest="plane_smem", type=int, default=0,
                     help="shared memory per block of the plane kernel in bytes (0 = default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -258,7 +258,8 @@ typedef struct {
                                    split over window-row groups (k_backup_rows or
                                    k_backup_rows_otf, then k_argmax_rows), 7 the
                                    plane kernel of banded problems with tables
-                                   (k_backup_plane, see amy_set_plane) */
+                                   (k_backup_plane, see amy_set_plane), 8 its tiled
+                                   form (k_backup_tile) */
     int32_t input_runs;         /* runs of consecutive inputs sharing outer records */
     int32_t inner_span;         /* inner slots K one outer contraction covers (kernels 3, 4) */
     int32_t build_kernels;      /* kernels one table build (amy_build / amy_rebuild) launches */
@@ -424,6 +425,16 @@ amy_status amy_set_step_wait(amy_handle h, int32_t mode);
  * register-resident kernel.  smem_bytes caps one block's shared memory
  * (16 KiB .. 200 KiB; 0 = 100 KiB, two blocks per SM); the partial box is
  * staged in chunks when it does not fit, which does not change the result.
+ * The plane kernel has a tiled form (backup_kernel 8): a block serves up to
+ * 4 groups of planes that differ only in the first staged dim a, and the
+ * dims whose windows none of them moves (no mean component of theirs reads
+ * x_a) are contracted once for the tile; the one remaining shared dim is
+ * applied per group afterwards.  Another FP32 order of the same terms again;
+ * it needs every other staged dim's component free of x_a and at most one
+ * shared dim reading x_a.  on = 1 takes it for planes of at least 256
+ * states, on = 2 wherever it applies, on = 3 never (in each case the plane
+ * kernel runs where the tiled form does not).  smem_bytes also caps the
+ * tiled form's block (0: two blocks per SM where they fit).
  * Errors: INVALID_ARG (null handle, bad mode or size). */
 amy_status amy_set_plane(amy_handle h, int32_t on, int32_t smem_bytes);
 

@@ -413,8 +413,10 @@ def amy_set_step_wait(h: AmyHandle, mode: int = 0) -> None:
 
 def amy_set_plane(h: AmyHandle, on: int = 1, smem_bytes: int = 0) -> None:
     """amy_set_plane: 1 = the plane kernel (banded problems with tables,
-    backup kernel 7) where it applies, 0 = the per-state kernel; smem_bytes
-    caps its shared memory per block (0 = default)."""
+    backup kernel 7) where it applies, in its tiled form (backup kernel 8)
+    for planes of at least 256 states; 2 = the tiled form wherever it
+    applies; 3 = never tiled; 0 = the per-state kernel.  smem_bytes caps the
+    shared memory per block (0 = default)."""
     _check(_lib().amy_set_plane(h.ptr, int(on), int(smem_bytes)))
 
 

@@ -863,6 +863,17 @@ int tm_kind_of(const amy_handle_s *h) {
 
 bool fast_path(const amy_handle_s *h) { return h->fast_wm > 0 && h->tmode != AMY_T_STORED_FULL; }
 
+// Whether the plane kernel runs in its tiled form (backup kernel 8): always
+// where it applies in mode 2, never in mode 3, and in the default mode 1 for
+// planes of at least kTileMinPlane states (on GB300 the tile kernel was faster
+// on the 21^6 traffic ring's planes of 441 states and slower on the rooms'
+// planes of 81, where the plane kernel packs five groups per block).
+constexpr int kTileMinPlane = 256;
+bool tile_on(const amy_handle_s *h) {
+    if (!h->plane.tile) return false;
+    return h->use_plane == 2 || (h->use_plane == 1 && h->plane.P >= kTileMinPlane);
+}
+
 // The tables' bounds on (window origin - own coordinate) as the launch sees them.
 void set_bounds(const amy_handle_s *h, FastCall &c) {
     c.run_starts = h->run_starts.empty() ? nullptr : h->run_starts.data();
@@ -922,6 +933,7 @@ FastCall fast_call(const amy_handle_s *h, int spec_kind, const void *Vn, void *V
     c.box_floats = h->box_floats;
     c.outer = h->outer;
     c.plane = (h->use_plane && h->plane.ok && h->d_Vp[0]) ? &h->plane : nullptr;
+    c.tile = tile_on(h);
     return c;
 }
 
@@ -1494,10 +1506,11 @@ amy_status amy_info(amy_handle h, amy_info_t *out) {
     out->backup_launch_kernels = h->d_split ? 2 : 1;
     out->inner_span = 0;
     if (fast_path(h) && h->use_plane && h->plane.ok && h->tmode == AMY_T_STORED_SEPARABLE) {
-        out->backup_kernel = 7;
+        const bool tile = tile_on(h);
+        out->backup_kernel = tile ? 8 : 7;
         out->input_lanes = 1;
         out->row_tiles = 0;
-        out->block_states = h->plane.G * h->plane.P;
+        out->block_states = tile ? h->plane.tT * h->plane.P : h->plane.G * h->plane.P;
         out->grouped_inputs = 0;
     } else if (fast_path(h)) {
         const FastCall c = fast_call(h, SPEC_SAFETY, nullptr, nullptr, nullptr, nullptr);
@@ -1584,7 +1597,7 @@ amy_status amy_set_step_wait(amy_handle h, int32_t mode) {
 
 amy_status amy_set_plane(amy_handle h, int32_t on, int32_t smem_bytes) {
     if (!h) return set_error(AMY_E_INVALID_ARG, "null handle");
-    if (on != 0 && on != 1) return set_error(AMY_E_INVALID_ARG, "plane mode %d (0 or 1)", (int)on);
+    if (on < 0 || on > 3) return set_error(AMY_E_INVALID_ARG, "plane mode %d (0 .. 3)", (int)on);
     if (smem_bytes != 0 && (smem_bytes < 16 * 1024 || smem_bytes > 200 * 1024))
         return set_error(AMY_E_INVALID_ARG, "plane kernel shared memory %d bytes (0, or 16 KiB..200 KiB)",
                          (int)smem_bytes);

@@ -4,6 +4,7 @@
 
 #include "amy_fast.cuh"
 #include "amy_plane.cuh"
+#include "amy_tile.cuh"
 #include "amy_internal.h"
 
 namespace amy {
@@ -64,6 +65,66 @@ amy_status launch_plane_repack(int v_store, const void *V, void *Vp, int64_t row
     return e == cudaSuccess ? AMY_OK : cuda_error(e, "plane repack launch");
 }
 
+// The tile kernel's part of a plane plan (pl.ok already set): tile dim a =
+// the first B dim, which no other B dim's component may read; the S dims
+// whose components do not read x_a are shared by the tile, at most one other
+// S dim's window moves with it.  smem_budget > 0 caps one block's shared
+// memory; 0 prefers two blocks per SM holding two values of dim a each.
+static void plan_tile(const Geom &g, PlanePlan &pl, int smem_budget) {
+    pl.tile = 0;
+    if (pl.nB < 1) return;
+    const int a = pl.bdim[0];
+    for (int b = 1; b < pl.nB; ++b)
+        if (g.tsx[pl.bdim[b]][a] != 0) return;
+    int nSh = 0, ow = -1;
+    int64_t Ksh = 1;
+    for (int s = 0; s < pl.nS; ++s) {
+        const int d = pl.sdim[s];
+        if (g.tsx[d][a] == 0) {
+            pl.tshdim[nSh++] = d;
+            Ksh *= g.W[d];
+        } else {
+            if (ow >= 0) return;  // two S dims move with x_a
+            ow = d;
+        }
+    }
+    if (nSh == 0 || Ksh > 4096) return;
+    if (ow >= 0 && g.W[ow] > 16) return;
+    const int threads = std::max(128, (pl.P + 31) / 32 * 32);
+    if (threads > TILE_MAX_THREADS) return;
+    // groups per tile and chunk (values of the first B dim staged at once):
+    // the largest tile whose block, holding two of those values, leaves room
+    // for two blocks per SM, else the largest tile holding one value at one
+    // block per SM
+    const int Na = g.N[a];
+    int T = 0;
+    int64_t chunk = 0;
+    for (int pass = smem_budget > 0 ? 1 : 0; pass < 2 && T == 0; ++pass) {
+        const int64_t budget = pass == 0 ? 112 * 1024 : (smem_budget > 0 ? smem_budget : 200 * 1024);
+        const int64_t want = pass == 0 ? 2 : 1;
+        for (int t = std::min(TILE_MAXT, Na); t >= 2 && T == 0; --t) {
+            int64_t ch = 0;
+            while ((int64_t)tile_smem_bytes((int)Ksh, threads, t, (int)((ch + 1) * pl.rs0), pl.Ppad) <= budget &&
+                   ch < 64)
+                ++ch;
+            if (ch >= want) {
+                T = t;
+                chunk = ch;
+            }
+        }
+    }
+    if (T < 2) return;
+    pl.tT = T;
+    pl.tnSh = nSh;
+    pl.tKsh = (int32_t)Ksh;
+    pl.tow = ow;
+    pl.tchunk = (int32_t)chunk;
+    pl.trent = (int32_t)(chunk * pl.rs0);
+    pl.tthreads = threads;
+    pl.tsmem = (int64_t)tile_smem_bytes((int)Ksh, threads, T, pl.trent, pl.Ppad);
+    pl.tile = 1;
+}
+
 void plan_plane(const Geom &g, int tmode, int prec, const int32_t *spread, int smem_budget, PlanePlan &pl) {
     pl = PlanePlan();
     const int n = g.n;
@@ -119,6 +180,7 @@ void plan_plane(const Geom &g, int tmode, int prec, const int32_t *spread, int s
     pl.smem = (int64_t)plane_smem_bytes(pl.G, pl.K, pl.rent, Ppad);
     if (pl.smem > 200 * 1024) return;
     pl.ok = 1;
+    plan_tile(g, pl, smem_budget);
 }
 
 int fast_variant(const Geom &g, int wm, int tmode) {

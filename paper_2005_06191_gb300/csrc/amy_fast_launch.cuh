@@ -10,6 +10,7 @@
 #include "amy_fast.cuh"
 #include "amy_internal.h"
 #include "amy_plane.cuh"
+#include "amy_tile.cuh"
 #include "amy_runs.cuh"
 #include "amy_staged.cuh"
 
@@ -361,8 +362,63 @@ amy_status launch_plane_t(const Geom &g, const FastCall &c, cudaStream_t st) {
     return e == cudaSuccess ? AMY_OK : cuda_error(e, "plane backup launch");
 }
 
+// The tile kernel (amy_tile.cuh) with the plan's tile part.
+template <class VT, int WM>
+amy_status launch_tile_t(const Geom &g, const FastCall &c, cudaStream_t st) {
+    const PlanePlan &pl = *c.plane;
+    TileArgs<VT> a;
+    a.Vo = (VT *)c.Vo;
+    a.Vpn = (const VT *)c.Vpn;
+    a.Vpo = (VT *)c.Vpo;
+    a.Vfinal = c.Vfinal;
+    a.pi = c.pi;
+    a.mask = c.mask;
+    a.tab = c.tab;
+    a.spec_kind = c.spec_kind;
+    a.kahan = c.kahan;
+    a.P = pl.P;
+    a.N1 = g.N[g.n - 1];
+    a.Ppad = pl.Ppad;
+    a.Q = pl.Ppad / 4;
+    a.adim = pl.bdim[0];
+    a.T = pl.tT;
+    a.Na = g.N[a.adim];
+    a.ntiles_a = (a.Na + a.T - 1) / a.T;
+    int64_t ngroups = 1;
+    for (int d = 0; d < g.n - 2; ++d) ngroups *= g.N[d];
+    a.nrest = ngroups / a.Na;
+    a.nB = pl.nB;
+    for (int i = 0; i < PLANE_MAXB; ++i) {
+        a.bdim[i] = pl.bdim[i];
+        a.brange[i] = pl.brange[i];
+        a.bstrideF[i] = pl.bstrideF[i];
+    }
+    a.rs0 = pl.rs0;
+    a.chunk = pl.tchunk;
+    a.rent = pl.trent;
+    a.nSh = pl.tnSh;
+    for (int i = 0; i < PLANE_MAXS; ++i) a.shdim[i] = pl.tshdim[i];
+    a.Ksh = pl.tKsh;
+    a.ow = pl.tow;
+    a.owstrideF = pl.tow >= 0 ? (int32_t)(g.stride[pl.tow] / pl.P) : 0;
+    a.work = c.work;
+    if (!a.Vpn || !a.Vpo) return set_error(AMY_E_INVALID_ARG, "tile backup without its padded V copies");
+    auto kern = k_backup_tile<VT, WM>;
+    static std::atomic<uint64_t> raised{0};
+    {
+        const amy_status r = smem_optin((const void *)kern, 200 * 1024 + 4096, raised, "tile backup smem attribute");
+        if (r != AMY_OK) return r;
+    }
+    const int64_t blocks = a.nrest * a.ntiles_a;
+    kern<<<(unsigned)blocks, (unsigned)pl.tthreads, (size_t)pl.tsmem, st>>>(g, a);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AMY_OK : cuda_error(e, "tile backup launch");
+}
+
 template <class VT, int WM>
 amy_status launch_tm(const Geom &g, int var, int tmode, const FastCall &c, int sm, cudaStream_t st) {
+    if (tmode == TM_SEPARABLE && c.plane && c.plane->ok && c.tile && c.plane->tile)
+        return launch_tile_t<VT, WM>(g, c, st);
     if (tmode == TM_SEPARABLE && c.plane && c.plane->ok) return launch_plane_t<VT, WM>(g, c, st);
     switch (tmode) {
         case TM_OTF: return launch_var<VT, WM, TM_OTF>(g, var, c, sm, st);

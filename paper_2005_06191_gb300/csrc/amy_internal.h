@@ -47,6 +47,13 @@ struct PlanePlan {
     int32_t Ppad = 0, Q = 0, teams = 0;  // padded plane, stage-1 team size, teams per group
     int32_t bstrideF[3] = {0, 0, 0};     // plane-index strides of the B dims
     int64_t smem = 0;
+    // The tile kernel (amy_tile.cuh, backup kernel 8): tiles of tT groups
+    // along the first B dim a, whose first stage is shared by the tile; the
+    // S dims split into tnSh shared ones (windows free of x_a) and at most one
+    // (tow) whose window moves with x_a.  tile = 0 when it does not apply.
+    int32_t tile = 0, tT = 0, tnSh = 0, tKsh = 0, tow = -1, tchunk = 0, trent = 0, tthreads = 0;
+    int32_t tshdim[6] = {0, 0, 0, 0, 0, 0};
+    int64_t tsmem = 0;
 };
 // Whether a problem has the plane kernel's structure (independent of the
 // tables' origin spreads): tables, FP32, four or more dims, no periodic dim,
@@ -116,6 +123,7 @@ struct FastCall {
     int32_t box_floats = 0;  // staged variant: box budget in floats (0 = 6144)
     int32_t outer = 0;       // per-run kernels, 3-D: values of dim 0 per row tile (0 = 1)
     const PlanePlan *plane = nullptr;  // tables mode: the plane kernel's plan when it runs
+    int32_t tile = 0;                  // 1: the tile kernel (8) where the plan has it, else the plane kernel
     unsigned long long *work = nullptr;  // plane kernel: work counters (3 words), or null
     const void *Vpn = nullptr;  // plane kernel: padded copy of V_{k+1}
     void *Vpo = nullptr;        // plane kernel: padded copy of V_k (written)

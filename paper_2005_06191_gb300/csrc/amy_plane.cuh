@@ -144,6 +144,143 @@ __device__ __forceinline__ int32_t plane_record(const Geom &g, const uint32_t *t
     return (int32_t)w[0];
 }
 
+// A Z window moved onto the grid: with W == WM slots and N >= W cells, the
+// window [o, o + W) is shifted to start s = clamp(o, 0, N - W) and its masses
+// re-indexed (slots that leave the grid carried zero mass, the cells that
+// enter it get zero mass), so that every slot addresses an on-grid cell and
+// the slot addresses are affine.  The nonzero terms keep their order, so the
+// sum is the same bit for bit.
+template <int WM>
+__device__ __forceinline__ int32_t plane_rebase(int32_t o, int32_t N, float (&t)[WM]) {
+    const int32_t s = min(max(o, 0), N - WM);
+    const int shift = s - o;
+    if (shift != 0) {
+        float u[WM];
+#pragma unroll
+        for (int k = 0; k < WM; ++k) {
+            const int m = k + shift;
+            u[k] = (m >= 0 && m < WM) ? sel_reg<WM>(t, m) : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < WM; ++k) t[k] = u[k];
+    }
+    return s;
+}
+
+// Stage 2 of the plane kernels for one state and one staged chunk: the sum
+// over the state's B rows in the chunk (rows whose first-B-dim value falls
+// in [c * chunk, (c + 1) * chunk)) of the product of its B masses and the
+// row's sum over the Z window, accumulated row by row into (acc, comp).
+// eB[b], eZ0, eZ1: the state part of the tables' indices; lo[b]: the low
+// end of the staged range of B dim b; Rg: the group's staged rows.  The
+// windows' masses are read from the tables (L1) here, so that nothing per
+// state stays live across stage 1.
+template <int WM>
+__device__ __forceinline__ void plane_stage2(const Geom &g, const uint32_t *__restrict__ tab, const int32_t *up,
+                                             int nB, const int32_t *bdim, const int32_t *eB, int32_t eZ0,
+                                             int32_t eZ1, const int32_t *lo, const float *Rg, int rs0, int rs1,
+                                             int chunk, int c, int Ppad, int kahan, float &acc, float &comp,
+                                             uint32_t &n_rld, uint32_t &n_rows, bool count) {
+    const int n = g.n;
+    const int32_t Nz0 = g.N[n - 2], Nz1 = g.N[n - 1];
+    // B windows: origin rows in the staged ranges, masses read where used
+    const uint32_t *rb[PLANE_MAXB];
+    int32_t ys[PLANE_MAXB];
+    int Wb[PLANE_MAXB];
+#pragma unroll
+    for (int b = 0; b < PLANE_MAXB; ++b) {
+        rb[b] = nullptr;
+        ys[b] = 0;
+        Wb[b] = 1;
+        if (b < nB) {
+            const int d = bdim[b];
+            rb[b] = tab + g.toff[d] + (int64_t)(eB[b] + __ldg(up + d)) * g.trw[d];
+            ys[b] = (int32_t)__ldg(rb[b]) - lo[b];
+            Wb[b] = g.W[d];
+        }
+    }
+    const int32_t y0s = ys[0] - c * chunk;
+    const int j0lo = max(0, -y0s), j0hi = min(Wb[0], chunk - y0s);
+    if (j0lo >= j0hi) return;  // no row of this chunk
+    float tz0[WM], tz1[WM];
+    const int32_t oz0 = plane_record<WM>(g, tab, n - 2, eZ0 + __ldg(up + n - 2), tz0);
+    const int32_t oz1 = plane_record<WM>(g, tab, n - 1, eZ1 + __ldg(up + n - 1), tz1);
+    const bool affine = g.W[n - 2] == WM && g.W[n - 1] == WM && Nz0 >= WM && Nz1 >= WM;
+    int32_t zb = 0;  // affine: offset of the window's first cell in a row
+    if (affine) zb = plane_rebase<WM>(oz0, Nz0, tz0) * Nz1 + plane_rebase<WM>(oz1, Nz1, tz1);
+    // Z-window sum of one staged row
+    auto zsum = [&](const float *row) {
+        float in = 0.0f;
+        if (affine) {
+            const float *rz = row + zb;
+#pragma unroll
+            for (int k0 = 0; k0 < WM; ++k0) {
+                const float *rr = rz + k0 * Nz1;
+                float q = 0.0f;
+#pragma unroll
+                for (int k1 = 0; k1 < WM; ++k1) q = fmaf(tz1[k1], rr[k1], q);
+                in = fmaf(tz0[k0], q, in);
+            }
+        } else {
+            // clamped cells: off-grid slots carry zero mass and read a valid R entry
+#pragma unroll
+            for (int k0 = 0; k0 < WM; ++k0) {
+                const float *rr = row + min(max(oz0 + k0, 0), Nz0 - 1) * Nz1;
+                float q = 0.0f;
+#pragma unroll
+                for (int k1 = 0; k1 < WM; ++k1) q = fmaf(tz1[k1], rr[min(max(oz1 + k1, 0), Nz1 - 1)], q);
+                in = fmaf(tz0[k0], q, in);
+            }
+        }
+        return in;
+    };
+    auto add_row = [&](float w, float in) {
+        accum_row(acc, comp, __fmul_rn(w, in), kahan);
+        if (count) {
+            n_rld += (uint32_t)(g.W[n - 2] * g.W[n - 1]);
+            ++n_rows;
+        }
+    };
+    // the row loops stay rolled (one copy of the Z contraction per row pair
+    // in the code); rows of the second B dim go two at a time, each pair's
+    // sums formed together and added in row order
+#pragma unroll 1
+    for (int j0 = j0lo; j0 < j0hi; ++j0) {
+        const int32_t y0 = y0s + j0;
+        const float w0 = nB > 0 ? __uint_as_float(__ldg(rb[0] + 1 + j0)) : 1.0f;
+        if (w0 == 0.0f) continue;
+        if (nB == 2) {
+            const float *r0 = Rg + (int64_t)(y0 * rs0 + ys[1]) * Ppad;
+            int j1 = 0;
+#pragma unroll 1
+            for (; j1 + 2 <= Wb[1]; j1 += 2) {
+                const float wa = __fmul_rn(w0, __uint_as_float(__ldg(rb[1] + 1 + j1)));
+                const float wb = __fmul_rn(w0, __uint_as_float(__ldg(rb[1] + 2 + j1)));
+                if (wa == 0.0f && wb == 0.0f) continue;
+                const float ina = zsum(r0 + (int64_t)j1 * rs1 * Ppad);
+                const float inb = zsum(r0 + (int64_t)(j1 + 1) * rs1 * Ppad);
+                if (wa != 0.0f) add_row(wa, ina);
+                if (wb != 0.0f) add_row(wb, inb);
+            }
+            if (j1 < Wb[1]) {
+                const float wa = __fmul_rn(w0, __uint_as_float(__ldg(rb[1] + 1 + j1)));
+                if (wa != 0.0f) add_row(wa, zsum(r0 + (int64_t)j1 * rs1 * Ppad));
+            }
+            continue;
+        }
+#pragma unroll 1
+        for (int j1 = 0; j1 < Wb[1]; ++j1) {
+            const float w1 = nB > 1 ? __fmul_rn(w0, __uint_as_float(__ldg(rb[1] + 1 + j1))) : w0;
+            if (w1 == 0.0f) continue;
+            for (int j2 = 0; j2 < Wb[2]; ++j2) {
+                const float w = nB > 2 ? __fmul_rn(w1, __uint_as_float(__ldg(rb[2] + 1 + j2))) : w1;
+                if (w == 0.0f) continue;
+                add_row(w, zsum(Rg + (int64_t)(y0 * rs0 + (ys[1] + j1) * rs1 + (ys[2] + j2)) * Ppad));
+            }
+        }
+    }
+}
+
 template <class VT, int WM>
 __global__ void __launch_bounds__(PLANE_MAX_THREADS, 2) k_backup_plane(const __grid_constant__ Geom g,
                                                                    const __grid_constant__ PlaneArgs<VT> a) {
@@ -377,68 +514,10 @@ __global__ void __launch_bounds__(PLANE_MAX_THREADS, 2) k_backup_plane(const __g
                 }
             }
             __syncthreads();
-            // stage 2: this state's B rows that fall in the chunk; its windows
-            // are read again from the tables (L1) so that nothing per state
-            // stays live across stage 1
-            if (fr) {
-                float tz0[WM], tz1[WM];
-                int32_t cz0[WM], cz1[WM];
-                {
-                    const int32_t oz0 = plane_record<WM>(g, a.tab, n - 2, eZ0 + __ldg(up + n - 2), tz0);
-                    const int32_t oz1 = plane_record<WM>(g, a.tab, n - 1, eZ1 + __ldg(up + n - 1), tz1);
-                    // clamped cells: off-grid slots carry zero mass and read a valid R entry
-#pragma unroll
-                    for (int k = 0; k < WM; ++k) {
-                        cz0[k] = min(max(oz0 + k, 0), Nz0 - 1) * Nz1;
-                        cz1[k] = min(max(oz1 + k, 0), Nz1 - 1);
-                    }
-                }
-                const uint32_t *rb[PLANE_MAXB];
-                int32_t yo[PLANE_MAXB];
-#pragma unroll
-                for (int b = 0; b < PLANE_MAXB; ++b) {
-                    rb[b] = nullptr;
-                    yo[b] = 0;
-                    if (b < nB) {
-                        const int d = a.bdim[b];
-                        rb[b] = a.tab + g.toff[d] + (int64_t)(eB[b] + __ldg(up + d)) * g.trw[d];
-                        // row of slot 0 in the group's staged range
-                        yo[b] = (int32_t)__ldg(rb[b]) - s_lo[gl * PLANE_MAXB + b];
-                    }
-                }
-                const int W0 = nB > 0 ? g.W[bd0] : 1;
-                const int W1 = nB > 1 ? g.W[a.bdim[1]] : 1;
-                const int W2 = nB > 2 ? g.W[a.bdim[2]] : 1;
-                for (int j0 = 0; j0 < W0; ++j0) {
-                    const int32_t y0 = yo[0] + j0 - c * a.chunk;
-                    if (y0 < 0 || y0 >= a.chunk) continue;
-                    const float w0 = nB > 0 ? __uint_as_float(__ldg(rb[0] + 1 + j0)) : 1.0f;
-                    if (w0 == 0.0f) continue;
-                    for (int j1 = 0; j1 < W1; ++j1) {
-                        const float w1 = nB > 1 ? __fmul_rn(w0, __uint_as_float(__ldg(rb[1] + 1 + j1))) : w0;
-                        if (w1 == 0.0f) continue;
-                        for (int j2 = 0; j2 < W2; ++j2) {
-                            const float w = nB > 2 ? __fmul_rn(w1, __uint_as_float(__ldg(rb[2] + 1 + j2))) : w1;
-                            if (w == 0.0f) continue;
-                            const float *row = Rg + (int64_t)(y0 * a.rs0 + (yo[1] + j1) * rs1 + (yo[2] + j2)) * Ppad;
-                            float in = 0.0f;
-#pragma unroll
-                            for (int k0 = 0; k0 < WM; ++k0) {
-                                const float *rr = row + cz0[k0];
-                                float q = 0.0f;
-#pragma unroll
-                                for (int k1 = 0; k1 < WM; ++k1) q = fmaf(tz1[k1], rr[cz1[k1]], q);
-                                in = fmaf(tz0[k0], q, in);
-                            }
-                            accum_row(acc, comp, __fmul_rn(w, in), a.kahan);
-                            if (a.work) {
-                                n_rld += (uint32_t)(g.W[n - 2] * g.W[n - 1]);
-                                ++n_rows;
-                            }
-                        }
-                    }
-                }
-            }
+            // stage 2: this state's B rows that fall in the chunk
+            if (fr)
+                plane_stage2<WM>(g, a.tab, up, nB, a.bdim, eB, eZ0, eZ1, s_lo + gl * PLANE_MAXB, Rg, a.rs0, rs1,
+                                 a.chunk, c, Ppad, a.kahan, acc, comp, n_rld, n_rows, a.work != nullptr);
             __syncthreads();
         }
         if (fr && acc > best) {
