@@ -61,6 +61,10 @@ MEASURED_TRAFFIC = {
     # 46,848 B written per launch of 32 backups
     ("unicycle", "stored_separable", "fp32", "native"):
         ("18ab757c2f94dba7", 23496, 78030, "profiles/k_synth_runs_unicycle_51x51x30.md"),
+    # k_backup_tile<float,5> at 18^6 (34,012,224 states): 548,219,904 B read + 469,441,536 B
+    # written per backup, scaled to the workload's states (V in and out and their re-fetches)
+    ("traffic6", "stored_separable", "fp32_kahan", "native"):
+        ("67e759b39b5c9992", 1017661440, 34012224, "profiles/k_backup_tile_traffic6.md"),
 }
 
 

@@ -30,6 +30,12 @@ namespace amy {
 constexpr int TILE_MAXT = 4;  // groups per tile
 constexpr int TILE_KU = 4;    // Sh combinations per step (two Ow cells at a time: 2 * TILE_KU loads in flight)
 constexpr int TILE_MAX_THREADS = 448;
+// Extra floats between consecutive staged rows of R (a multiple of 4): the row
+// pitch Ppad + AMY_TILE_RPAD moves rows onto other shared-memory banks.
+#ifndef AMY_TILE_RPAD
+#define AMY_TILE_RPAD 0
+#endif
+constexpr int TILE_RPAD = AMY_TILE_RPAD;
 
 template <class VT> struct TileArgs {
     VT *Vo;                // V_k
@@ -71,7 +77,7 @@ __host__ __device__ inline size_t tile_smem_head(int Ksh, int threads, int T) {
             (size_t)TILE_MAXT * 16 * 4 + (size_t)4 * T * threads * 4 + 15) / 16 * 16;
 }
 __host__ __device__ inline size_t tile_smem_bytes(int Ksh, int threads, int T, int rent, int Ppad) {
-    return tile_smem_head(Ksh, threads, T) + (size_t)T * rent * Ppad * 4;
+    return tile_smem_head(Ksh, threads, T) + (size_t)T * rent * (Ppad + TILE_RPAD) * 4;
 }
 
 template <class VT, int WM>
@@ -91,11 +97,12 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, 2) k_backup_tile(const __gri
     float *s_cmp = s_acc + a.T * blockDim.x;                              // [T][threads] compensations
     float *s_best = s_cmp + a.T * blockDim.x;                             // [T][threads] best value
     int32_t *s_arg = reinterpret_cast<int32_t *>(s_best + a.T * blockDim.x);  // its input
-    float *s_R = reinterpret_cast<float *>(smem_raw + tile_smem_head(a.Ksh, blockDim.x, a.T));  // [T][rent][Ppad]
+    float *s_R = reinterpret_cast<float *>(smem_raw + tile_smem_head(a.Ksh, blockDim.x, a.T));  // [T][rent][Rp]
 
     const int n = g.n;
     const int tid = threadIdx.x, NT = blockDim.x;
     const int P = a.P, Ppad = a.Ppad, Q = a.Q;
+    const int Rp = Ppad + TILE_RPAD;  // row pitch of R
     const int ad = a.adim;
     const int64_t rest = (int64_t)blockIdx.x % a.nrest;
     const int32_t a0 = (int32_t)((int64_t)blockIdx.x / a.nrest) * a.T;
@@ -374,7 +381,7 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, 2) k_backup_tile(const __gri
 #pragma unroll
                     for (int gg = 0; gg < TILE_MAXT; ++gg)
                         if (gg < Tt)
-                            *reinterpret_cast<float4 *>(s_R + ((int64_t)gg * a.rent + er) * Ppad + 4 * s1q) = r[gg];
+                            *reinterpret_cast<float4 *>(s_R + ((int64_t)gg * a.rent + er) * Rp + 4 * s1q) = r[gg];
                 }
                 __syncthreads();
                 // ---- stage 2: every free state's B rows that fall in the chunk
@@ -388,7 +395,7 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, 2) k_backup_tile(const __gri
                     for (int b = 0; b < PLANE_MAXB; ++b) eB[b] = b < nB ? tab_index(a.bdim[b], gg, p) : 0;
                     float acc = s_acc[i * NT + tid], comp = s_cmp[i * NT + tid];
                     plane_stage2<WM>(g, a.tab, up, nB, a.bdim, eB, tab_index(n - 2, gg, p), tab_index(n - 1, gg, p),
-                                     s_lo, s_R + (int64_t)gg * a.rent * Ppad, a.rs0, rs1, a.chunk, c, Ppad, a.kahan,
+                                     s_lo, s_R + (int64_t)gg * a.rent * Rp, a.rs0, rs1, a.chunk, c, Rp, a.kahan,
                                      acc, comp, n_rld, n_rows, a.work != nullptr);
                     s_acc[i * NT + tid] = acc;
                     s_cmp[i * NT + tid] = comp;
