@@ -187,7 +187,7 @@ WORKLOADS = {
     "rooms7": (lambda s: W.rooms7(n_per_dim=s or 9), "stored_separable", "fp32_kahan",
                "7-room temperature ring 9^7 states, 5 inputs, sigma 0.02, window 3^7, safety, horizon 10"),
     "traffic6": (lambda s: W.traffic6(n_per_dim=s or 21), "stored_separable", "fp32_kahan", TRAFFIC_NAME),
-    "robot_dist": (lambda s: W.robot_dist(n_per_dim=s or 41), "otf", "fp32",
+    "robot_dist": (lambda s: W.robot_dist(n_per_dim=s or 41), "stored_separable", "fp32",
                    "2-D robot of Sec. 7 with its disturbance: 41^2 states, 121 inputs, 11 disturbance points, "
                    "Sigma = 0.75 I, gamma 1e-3 (13x13 window), safety in X, horizon 8 (203401 state-input pairs)"),
 }
@@ -403,7 +403,8 @@ def roofline(args, w, info, backup_ms, free, lane_peaks, work=None):
         return roofline_plane(args, w, info, backup_ms, work, lane_peaks)
     pk = peaks()
     p = w.problem
-    nx, nu = p.n_states, p.n_inputs
+    # the kernels' pairs: (input, disturbance point) pairs with a disturbance grid
+    nx, nu = p.n_states, p.n_inputs * p.n_disturbances
     slots = info["window_slots"]
     esz = 8 if args.prec == "fp64" else 4  # stored masses and V in the arithmetic's width
     vbytes = 2 if args.v_store != "native" else esz
@@ -440,6 +441,9 @@ def roofline(args, w, info, backup_ms, free, lane_peaks, work=None):
                       "masses per (free state, input), read from shared memory")
     elif kern == 2:
         loads, path, what = gather, "shared", "one shared-memory load per (free state, input, slot)"
+    elif kern == 9:
+        loads, path, what = gather, "shared", ("one shared-memory load per (free state, input-disturbance "
+                                               "pair, slot) from the block's bordered copy of V")
     else:
         loads, path, what = gather, "global_l1", "one global (L1) load per (free state, input, slot)"
     peak = lane_peaks[path] / 1e9

@@ -259,7 +259,8 @@ typedef struct {
                                    k_backup_rows_otf, then k_argmax_rows), 7 the
                                    plane kernel of banded problems with tables
                                    (k_backup_plane, see amy_set_plane), 8 its tiled
-                                   form (k_backup_tile) */
+                                   form (k_backup_tile), 9 2-D tables with windows
+                                   wider than 8 (k_sums_sep2, then k_collect_keys) */
     int32_t input_runs;         /* runs of consecutive inputs sharing outer records */
     int32_t inner_span;         /* inner slots K one outer contraction covers (kernels 3, 4) */
     int32_t build_kernels;      /* kernels one table build (amy_build / amy_rebuild) launches */

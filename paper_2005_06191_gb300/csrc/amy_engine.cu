@@ -554,6 +554,10 @@ struct amy_handle_s {
     // over window rows (k_backup_rows), its pair sums S[u][x] kept here, or null
     void *d_split;
     int32_t split_groups;
+    // 2-D tables with windows wider than the register-resident kernels take
+    // (k_sums_sep2 + k_collect_keys, backup kernel 9): d_split holds the
+    // per-state max keys
+    int32_t sep_wide;
     // wide stored rows: the build runs one thread per (slot, pair)
     // (k_build_slots); stored full rows take their per-slot masses from
     // d_bfac (wsum x pairs) and expand them (k_build_expand)
@@ -764,6 +768,28 @@ amy_status launch_backup_t(amy_handle_s *h, int spec_kind, const VT *Vn, VT *Vo,
     a.O = h->d_O;
     a.npairs = h->npairs;
     a.tab = h->d_tab;
+    if constexpr (TM == TM_SEPARABLE && sizeof(R) == 4) {
+        if (h->sep_wide && h->d_split) {
+            // 2-D tables with wide windows: each input's value into a per-state
+            // max key, then V_k and pi_k from the keys (which are cleared)
+            const int64_t items = (int64_t)h->g.nx * (h->g.nu / h->g.nw);
+            const int blocks = (int)std::min<int64_t>((items + 255) / 256, (int64_t)h->sm_count * 64);
+            unsigned long long *keys = (unsigned long long *)h->d_split;
+            const Geom &g = h->g;
+            const size_t vsm = sep2_smem_bytes(g.N[0], g.W[0], g.N[1], g.W[1]);
+            if (g.periodic == 0 && vsm <= 48 * 1024)  // V staged in shared memory with a zero border
+                k_sums_sep2<VT, KAHAN, true><<<blocks, 256, vsm, h->stream>>>(g, h->d_tab, Vn, h->d_mask, spec_kind,
+                                                                              keys);
+            else
+                k_sums_sep2<VT, KAHAN, false><<<blocks, 256, 0, h->stream>>>(g, h->d_tab, Vn, h->d_mask, spec_kind,
+                                                                             keys);
+            AMY_CUDA(cudaGetLastError(), "input values launch");
+            const int cb = (int)std::min<int64_t>((h->g.nx + 255) / 256, 65535);
+            k_collect_keys<VT><<<cb, 256, 0, h->stream>>>(h->g, h->d_mask, spec_kind, keys, Vo, (float *)Vfinal, pi);
+            AMY_CUDA(cudaGetLastError(), "collect launch");
+            return AMY_OK;
+        }
+    }
     if constexpr (TM == TM_FULL || TM == TM_FACTORED || TM == TM_OTF) {
         if (h->d_split) {
             // split over window rows: pair sums, then max / argmax per state
@@ -1350,6 +1376,19 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
         h->runs = input_outer_runs(h->g, upart);
         input_run_layout(h->g, upart, h->run_starts, h->in_stride_b);
         TRY(dev_alloc(h, (void **)&h->d_tab, (size_t)h->tab_words * 4, "separable tables"));
+        if (h->fast_wm == 0 && g.n == 2 && std::max(g.W[0], g.W[1]) <= SEP2_WMAX) {
+            // the per-state max keys of the wide 2-D kernel (zero between backups)
+            const size_t kbytes = (size_t)g.nx * sizeof(unsigned long long);
+            if (h->budget <= 0 || h->bytes + (int64_t)kbytes <= h->budget) {
+                TRY(dev_alloc(h, &h->d_split, kbytes, "max keys"));
+                e = cudaMemset(h->d_split, 0, kbytes);
+                if (e != cudaSuccess) {
+                    free_handle(h);
+                    return cuda_error(e, "max keys init");
+                }
+                h->sep_wide = 1;
+            }
+        }
         e = cudaMemcpy(h->d_tab + h->g.uoff, upart.data(), upart.size() * 4, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             free_handle(h);
@@ -1502,7 +1541,7 @@ amy_status amy_info(amy_handle h, amy_info_t *out) {
     *out = h->info;
     out->device_bytes = h->bytes + (int64_t)h->stage_cap;
     out->step_wait = h->grid_barrier;
-    out->backup_kernel = h->d_split ? 6 : 0;
+    out->backup_kernel = h->d_split ? (h->sep_wide ? 9 : 6) : 0;
     out->backup_launch_kernels = h->d_split ? 2 : 1;
     out->inner_span = 0;
     if (fast_path(h) && h->use_plane && h->plane.ok && h->tmode == AMY_T_STORED_SEPARABLE) {

@@ -520,6 +520,170 @@ __global__ void __launch_bounds__(32 * ROWS_MAX_GROUPS) k_backup_rows_otf(const 
     }
 }
 
+// Backup of 2-D problems with per-dimension tables whose windows are too wide
+// for the register-resident kernels (the disturbed robot of Sec. 7: 13 x 13
+// windows, 121 inputs x 11 disturbance points), in two kernels.
+// k_sums_sep2: one thread per (control input, state), states fastest, so that
+// a warp's lanes read neighbouring cells of V (L1).  For each disturbance
+// point of the input the two dims' table records give the window origins and
+// masses; the window sum runs over the rows of dim 0, each row's inner sum in
+// slot order, the rows added in order (Kahan-compensated when asked);
+// off-grid slots have zero mass and read a clamped cell.  The input's value
+// is the min over its disturbance points (Algorithm 4's inner min), and
+// max_key[x] keeps the largest (value, -input) key by atomic max: the max
+// over inputs with the lowest maximiser, whatever the order of the atomics.
+// k_collect_keys then writes V_k and pi_k (spec values on masked states) and
+// clears the keys for the next backup.
+constexpr int SEP2_WMAX = 16;
+__device__ __forceinline__ unsigned long long sep2_key(float v, int u) {
+    // order-preserving map of the float onto 32 bits (negative values below
+    // positive ones), then the input complemented: ties favour the lowest input
+    uint32_t b = __float_as_uint(v);
+    b = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+    return ((unsigned long long)b << 32) | (unsigned long long)(0xFFFFu - (uint32_t)u);
+}
+__device__ __forceinline__ float sep2_key_value(unsigned long long k) {
+    uint32_t b = (uint32_t)(k >> 32);
+    b = (b & 0x80000000u) ? (b & 0x7fffffffu) : ~b;
+    return __uint_as_float(b);
+}
+
+// Shared-memory form (both dims non-periodic): V_{k+1} staged once per block
+// with a zero border of W + 1 cells on each side, so that every window slot
+// -- window origins are clamped to [-W - 1, N + 1] -- reads a staged cell and
+// the slots of a row are consecutive: one shared load per transition.
+__host__ __device__ inline size_t sep2_smem_bytes(int N0, int W0, int N1, int W1) {
+    // plus SEP2_WMAX floats of slack after the last row
+    return ((size_t)(N0 + 2 * (W0 + 1)) * (size_t)(N1 + 2 * (W1 + 1)) + SEP2_WMAX) * sizeof(float);
+}
+
+template <class VT, bool KAHAN, bool SMEM>
+__global__ void __launch_bounds__(256) k_sums_sep2(const __grid_constant__ Geom g, const uint32_t *__restrict__ tab,
+                                                   const VT *__restrict__ Vn, const uint8_t *__restrict__ mask,
+                                                   int32_t spec_kind, unsigned long long *__restrict__ max_key) {
+    extern __shared__ float vs[];
+    const int nuc = g.nu / g.nw;
+    const int64_t total = (int64_t)g.nx * nuc;
+    const int32_t N0 = g.N[0], N1 = g.N[1];
+    const int W0 = g.W[0], W1 = g.W[1];
+    const bool per0 = (g.periodic & 1u) != 0, per1 = (g.periodic & 2u) != 0;
+    const int32_t B0 = W0 + 1, B1 = W1 + 1, P1 = N1 + 2 * B1;  // border, padded row
+    if (SMEM) {
+        const int32_t P0 = N0 + 2 * B0;
+        for (int32_t k = threadIdx.x; k < P0 * P1; k += blockDim.x) {
+            const int32_t r = k / P1 - B0, c = k - (k / P1) * P1 - B1;
+            vs[k] = (r >= 0 && r < N0 && c >= 0 && c < N1) ? vload<float, VT>(Vn + (int64_t)r * N1 + c) : 0.0f;
+        }
+        __syncthreads();
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t uc = (int32_t)(i / g.nx), x = (int32_t)(i - (int64_t)uc * g.nx);
+        if (state_masked(spec_kind, mask[x])) continue;
+        const int32_t x0 = x / N1, x1 = x - (x / N1) * N1;
+        const int32_t e0 = x0 * g.tsx[0][0] + x1 * g.tsx[0][1], e1 = x0 * g.tsx[1][0] + x1 * g.tsx[1][1];
+        float vmin = 0.0f;
+        for (int w = 0; w < g.nw; ++w) {
+            const int32_t u = uc * g.nw + w;
+            const int32_t *up = reinterpret_cast<const int32_t *>(tab + g.uoff + (int64_t)u * g.urw);
+            const uint32_t *r0 = tab + g.toff[0] + (int64_t)(e0 + __ldg(up + 0)) * g.trw[0];
+            const uint32_t *r1 = tab + g.toff[1] + (int64_t)(e1 + __ldg(up + 1)) * g.trw[1];
+            const int32_t o0 = (int32_t)__ldg(r0);
+            // dim 1's record (origin, then W1 masses; 16-byte aligned, padded to
+            // 4 words) in 16-byte loads: the lanes of a warp read neighbouring records
+            uint32_t rw[SEP2_WMAX + 4];
+#pragma unroll
+            for (int q = 0; q < (SEP2_WMAX + 4) / 4; ++q) {
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (q * 4 < W1 + 1) v = __ldg(reinterpret_cast<const uint4 *>(r1) + q);
+                rw[q * 4 + 0] = v.x;
+                rw[q * 4 + 1] = v.y;
+                rw[q * 4 + 2] = v.z;
+                rw[q * 4 + 3] = v.w;
+            }
+            const int32_t o1 = (int32_t)rw[0];
+            float t1[SEP2_WMAX];
+#pragma unroll
+            for (int b = 0; b < SEP2_WMAX; ++b) t1[b] = b < W1 ? __uint_as_float(rw[1 + b]) : 0.0f;
+            float acc = 0.0f, comp = 0.0f;
+            if (SMEM) {
+                const float *base = vs + (o0 + B0) * P1 + (o1 + B1);
+                for (int a = 0; a < W0; ++a) {
+                    const float w0 = __uint_as_float(__ldg(r0 + 1 + a));
+                    if (w0 == 0.0f) continue;
+                    const float *row = base + a * P1;
+                    float r = 0.0f;
+#pragma unroll
+                    for (int b = 0; b < SEP2_WMAX; ++b)
+                        if (b < W1) r = fmaf(t1[b], row[b], r);
+                    accum<float, KAHAN>(acc, comp, __fmul_rn(w0, r));
+                }
+            } else {
+                // cells of the window's slots: wrapped (periodic dim) or clamped
+                // (off-grid slots have zero mass); the two loops stay apart so
+                // that the division is taken only for a periodic dim
+                int32_t c1[SEP2_WMAX];
+                if (per1) {
+                    int32_t c = o1 % N1;
+                    if (c < 0) c += N1;
+#pragma unroll
+                    for (int b = 0; b < SEP2_WMAX; ++b) {
+                        c1[b] = c;
+                        c = c + 1 == N1 ? 0 : c + 1;
+                    }
+                } else {
+#pragma unroll
+                    for (int b = 0; b < SEP2_WMAX; ++b) c1[b] = min(max(o1 + b, 0), N1 - 1);
+                }
+                int32_t c0w = 0;  // dim 0's first cell, wrapped (periodic dim only)
+                if (per0) {
+                    c0w = o0 % N0;
+                    if (c0w < 0) c0w += N0;
+                }
+                for (int a = 0; a < W0; ++a) {
+                    const float w0 = __uint_as_float(__ldg(r0 + 1 + a));
+                    const int32_t c0 = per0 ? c0w : min(max(o0 + a, 0), N0 - 1);
+                    c0w = c0w + 1 == N0 ? 0 : c0w + 1;
+                    if (w0 == 0.0f) continue;
+                    const VT *row = Vn + (int64_t)c0 * N1;
+                    float r = 0.0f;
+#pragma unroll
+                    for (int b = 0; b < SEP2_WMAX; ++b)
+                        if (b < W1) r = fmaf(t1[b], vload<float, VT>(row + c1[b]), r);
+                    accum<float, KAHAN>(acc, comp, __fmul_rn(w0, r));
+                }
+            }
+            vmin = (w == 0 || acc < vmin) ? acc : vmin;
+        }
+        atomicMax(max_key + x, sep2_key(vmin, uc));
+    }
+}
+
+template <class VT>
+__global__ void __launch_bounds__(256) k_collect_keys(const __grid_constant__ Geom g, const uint8_t *__restrict__ mask,
+                                                      int32_t spec_kind, unsigned long long *__restrict__ max_key,
+                                                      VT *__restrict__ Vo, float *__restrict__ Vfinal,
+                                                      uint16_t *__restrict__ pi) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.nx; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = (int32_t)i;
+        const uint8_t f = mask[x];
+        float best;
+        uint16_t arg;
+        if (state_masked(spec_kind, f)) {
+            best = (spec_kind != SPEC_SAFETY && (f & F_TARGET)) ? 1.0f : 0.0f;
+            arg = 0xFFFF;
+        } else {
+            const unsigned long long k = max_key[x];
+            best = sep2_key_value(k);
+            arg = (uint16_t)(0xFFFFu - (uint32_t)(k & 0xFFFFu));
+        }
+        max_key[x] = 0ull;
+        Vo[x] = vstore_cast<VT, float>(best);
+        if (Vfinal) Vfinal[x] = best;
+        if (pi) pi[x] = arg;
+    }
+}
+
 // Max over inputs of S[u][x] per state, lowest maximiser, spec values on
 // masked states (the collect step of k_backup).
 template <class R, class VT>

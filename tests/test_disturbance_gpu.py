@@ -40,6 +40,25 @@ def test_robot_dist_matches_oracle(amy, robot_ref, tmode, prec):
     assert st["policy_checked"] > 0
 
 
+def test_robot_dist_tables_take_the_wide_2d_kernel(amy, robot_ref):
+    """The robot's 13 x 13 windows with per-dimension tables: each input's
+    value (min over its disturbance points) by k_sums_sep2 into per-state max
+    keys, then k_collect_keys (backup kernel 9, two launches per backup), in
+    FP32 and with Kahan over rows, against the oracle; repeated syntheses on
+    one handle agree bit for bit (the keys are cleared between backups)."""
+    w, ref = robot_ref
+    for prec in ("fp32", "fp32_kahan"):
+        with amy.amy_build(w.problem, tmode="stored_separable", prec=prec) as h:
+            info = amy.amy_info(h)
+            assert info["backup_kernel"] == 9 and info["backup_launch_kernels"] == 2
+        compare_synthesis(amy, w, "stored_separable", prec, ref=ref)
+    compare_synthesis(amy, w, "stored_separable", "fp32", v_store="u16", ref=ref)
+    with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32") as h:
+        a = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
+        b = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
 def test_robot_dist_reach_avoid_16bit(amy):
     w = W.robot_dist(kind=W.REACH_AVOID, horizon=6)
     ref = oracle.synthesize(w.problem, w.spec, w.horizon, want_all=True)
