@@ -59,6 +59,11 @@ constexpr int PLANE_MAX_THREADS = 448;  // two blocks per SM at up to 72 registe
 #endif
 constexpr int PLANE_EB = AMY_PLANE_EB;  // R rows per stage-1 batch
 constexpr int PLANE_KU = AMY_PLANE_KU;  // S combinations per step of a batch
+// Stage-2 rows of the second staged dim whose window sums are formed together
+#ifndef AMY_PLANE_S2ROWS
+#define AMY_PLANE_S2ROWS 2
+#endif
+constexpr int PLANE_S2ROWS = AMY_PLANE_S2ROWS;
 
 template <class VT> struct PlaneArgs {
     const VT *Vn;          // V_{k+1} (unused: stage 1 reads the padded copy)
@@ -241,9 +246,9 @@ __device__ __forceinline__ void plane_stage2(const Geom &g, const uint32_t *__re
             ++n_rows;
         }
     };
-    // the row loops stay rolled (one copy of the Z contraction per row pair
-    // in the code); rows of the second B dim go two at a time, each pair's
-    // sums formed together and added in row order
+    // the row loops stay rolled (one copy of the Z contraction per batch in
+    // the code); rows of the second B dim go PLANE_S2ROWS at a time, each
+    // batch's sums formed together and added in row order
 #pragma unroll 1
     for (int j0 = j0lo; j0 < j0hi; ++j0) {
         const int32_t y0 = y0s + j0;
@@ -253,16 +258,23 @@ __device__ __forceinline__ void plane_stage2(const Geom &g, const uint32_t *__re
             const float *r0 = Rg + (int64_t)(y0 * rs0 + ys[1]) * Ppad;
             int j1 = 0;
 #pragma unroll 1
-            for (; j1 + 2 <= Wb[1]; j1 += 2) {
-                const float wa = __fmul_rn(w0, __uint_as_float(__ldg(rb[1] + 1 + j1)));
-                const float wb = __fmul_rn(w0, __uint_as_float(__ldg(rb[1] + 2 + j1)));
-                if (wa == 0.0f && wb == 0.0f) continue;
-                const float ina = zsum(r0 + (int64_t)j1 * rs1 * Ppad);
-                const float inb = zsum(r0 + (int64_t)(j1 + 1) * rs1 * Ppad);
-                if (wa != 0.0f) add_row(wa, ina);
-                if (wb != 0.0f) add_row(wb, inb);
+            for (; j1 + PLANE_S2ROWS <= Wb[1]; j1 += PLANE_S2ROWS) {
+                float wr[PLANE_S2ROWS], in[PLANE_S2ROWS];
+                bool any = false;
+#pragma unroll
+                for (int q = 0; q < PLANE_S2ROWS; ++q) {
+                    wr[q] = __fmul_rn(w0, __uint_as_float(__ldg(rb[1] + 1 + j1 + q)));
+                    any = any || wr[q] != 0.0f;
+                }
+                if (!any) continue;
+#pragma unroll
+                for (int q = 0; q < PLANE_S2ROWS; ++q) in[q] = zsum(r0 + (int64_t)(j1 + q) * rs1 * Ppad);
+#pragma unroll
+                for (int q = 0; q < PLANE_S2ROWS; ++q)
+                    if (wr[q] != 0.0f) add_row(wr[q], in[q]);
             }
-            if (j1 < Wb[1]) {
+#pragma unroll 1
+            for (; j1 < Wb[1]; ++j1) {
                 const float wa = __fmul_rn(w0, __uint_as_float(__ldg(rb[1] + 1 + j1)));
                 if (wa != 0.0f) add_row(wa, zsum(r0 + (int64_t)j1 * rs1 * Ppad));
             }
