@@ -56,33 +56,48 @@ UNIT = "transitions/s"
 # the captured launch, profile summary).  A capture on a reduced grid is scaled
 # to the full launch by the number of states (the traffic is V in/out, pi and
 # the mask per state; the tables are a few hundred KB at most).
+# (workload, tmode, prec, v_store) -> (digest of the kernel's header and its
+# includes when measured, DRAM bytes per backup, states of the measured case,
+# profile summary, kernel header); reported as null once the kernel changed
 MEASURED_TRAFFIC = {
     # k_synth_runs<float,3,3,0>, launch shape 1,288,1,0,3, grid barrier: 705,024 B read +
     # 46,848 B written per launch of 32 backups
     ("unicycle", "stored_separable", "fp32", "native"):
-        ("18ab757c2f94dba7", 23496, 78030, "profiles/k_synth_runs_unicycle_51x51x30.md"),
+        ("18ab757c2f94dba7", 23496, 78030, "profiles/k_synth_runs_unicycle_51x51x30.md", "amy_runs.cuh"),
     # k_backup_tile<float,5> at 18^6 (34,012,224 states): 548,219,904 B read + 469,441,536 B
     # written per backup, scaled to the workload's states (V in and out and their re-fetches)
     ("traffic6", "stored_separable", "fp32_kahan", "native"):
-        ("67e759b39b5c9992", 1017661440, 34012224, "profiles/k_backup_tile_traffic6.md"),
+        ("67e759b39b5c9992", 1017661440, 34012224, "profiles/k_backup_tile_traffic6.md", "amy_tile.cuh"),
 }
 
 
-def csrc_digest() -> str:
-    """Digest of the device code (the .cuh kernel and launch headers)."""
+def csrc_digest(root: str = None) -> str:
+    """Digest of device code: the header `root` (in csrc/) and every header it
+    includes from there, recursively; without `root`, every .cuh header."""
     import hashlib
+    import re
     d = os.path.join(ROOT, "paper_2005_06191_gb300", "csrc")
+    if root is None:
+        files = sorted(f for f in os.listdir(d) if f.endswith(".cuh"))
+    else:
+        files, todo = set(), [root]
+        while todo:
+            f = todo.pop()
+            if f in files or not os.path.exists(os.path.join(d, f)):
+                continue
+            files.add(f)
+            todo += re.findall(r'#include "([^"/]+)"', open(os.path.join(d, f)).read())
+        files = sorted(files)
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith(".cuh"):
-            h.update(f.encode())
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in files:
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def measured_traffic(args, n_states: int):
     e = MEASURED_TRAFFIC.get((args.workload, args.tmode, args.prec, args.v_store))
-    if e is None or e[0] != csrc_digest():
+    if e is None or e[0] != csrc_digest(e[4]):
         return None, None
     return int(round(e[1] * n_states / e[2])), e[3]
 
