@@ -170,3 +170,19 @@ def test_disturbance_rejected_for_the_unicycle(amy):
     with pytest.raises(amy.AmyError) as e:
         amy.amy_build(q, tmode="otf", prec="fp32")
     assert "UNSUPPORTED" in str(e.value)
+
+
+@pytest.mark.parametrize("periodic,window,n_w", [(None, [11, 9], 1), ([0, 1], [13, 15], 3), ([1, 1], [9, 11], 2),
+                                                 (None, [15, 15], 2)])
+def test_wide_2d_kernel_shapes(amy, periodic, window, n_w):
+    """Kernel 9 on seeded 2-D systems with windows of 9 to 16 slots: the
+    shared-memory form (no periodic dim) and the global-memory form (a
+    periodic dim), with and without a disturbance grid, against the oracle."""
+    rng = np.random.default_rng(700 + sum(window) + n_w)
+    w = _disturbed(rng, 2, [23, 19], 3, n_w, gamma=0.0, window=window, kind=W.REACH_AVOID, horizon=4,
+                   periodic=periodic)
+    ref = oracle.synthesize(w.problem, w.spec, w.horizon, want_all=True)
+    for prec in ("fp32", "fp32_kahan"):
+        with amy.amy_build(w.problem, tmode="stored_separable", prec=prec) as h:
+            assert amy.amy_info(h)["backup_kernel"] == 9
+        compare_synthesis(amy, w, "stored_separable", prec, ref=ref)
