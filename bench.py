@@ -60,14 +60,14 @@ UNIT = "transitions/s"
 # includes when measured, DRAM bytes per backup, states of the measured case,
 # profile summary, kernel header); reported as null once the kernel changed
 MEASURED_TRAFFIC = {
-    # k_synth_runs<float,3,3,0>, launch shape 1,288,1,0,3, grid barrier: 705,024 B read +
-    # 46,848 B written per launch of 32 backups
+    # k_synth_runs<float,3,3,0>, launch shape 1,288,1,0,3, grid barrier: 715,008 B read +
+    # 87,808 B written per launch of 32 backups
     ("unicycle", "stored_separable", "fp32", "native"):
-        ("18ab757c2f94dba7", 23496, 78030, "profiles/k_synth_runs_unicycle_51x51x30.md", "amy_runs.cuh"),
-    # k_backup_tile<float,5> at 18^6 (34,012,224 states): 548,219,904 B read + 469,441,536 B
+        ("0958ce257213d40a", 25088, 78030, "profiles/k_synth_runs_unicycle_51x51x30.md", "amy_runs.cuh"),
+    # k_backup_tile<float,5> at 18^6 (34,012,224 states): 555,728,384 B read + 474,146,560 B
     # written per backup, scaled to the workload's states (V in and out and their re-fetches)
     ("traffic6", "stored_separable", "fp32_kahan", "native"):
-        ("67e759b39b5c9992", 1017661440, 34012224, "profiles/k_backup_tile_traffic6.md", "amy_tile.cuh"),
+        ("74b66b3dbc3fe96f", 1029874944, 34012224, "profiles/k_backup_tile_traffic6.md", "amy_tile.cuh"),
 }
 
 
