@@ -535,6 +535,11 @@ __global__ void __launch_bounds__(32 * ROWS_MAX_GROUPS) k_backup_rows_otf(const 
 // k_collect_keys then writes V_k and pi_k (spec values on masked states) and
 // clears the keys for the next backup.
 constexpr int SEP2_WMAX = 16;
+// disturbance points of one input whose window sums are unrolled together
+#ifndef AMY_SEP2_WUNROLL
+#define AMY_SEP2_WUNROLL 1
+#endif
+constexpr int SEP2_WUNROLL = AMY_SEP2_WUNROLL;
 __device__ __forceinline__ unsigned long long sep2_key(float v, int u) {
     // order-preserving map of the float onto 32 bits (negative values below
     // positive ones), then the input complemented: ties favour the lowest input
@@ -583,6 +588,7 @@ __global__ void __launch_bounds__(256) k_sums_sep2(const __grid_constant__ Geom 
         const int32_t x0 = x / N1, x1 = x - (x / N1) * N1;
         const int32_t e0 = x0 * g.tsx[0][0] + x1 * g.tsx[0][1], e1 = x0 * g.tsx[1][0] + x1 * g.tsx[1][1];
         float vmin = 0.0f;
+#pragma unroll SEP2_WUNROLL
         for (int w = 0; w < g.nw; ++w) {
             const int32_t u = uc * g.nw + w;
             const int32_t *up = reinterpret_cast<const int32_t *>(tab + g.uoff + (int64_t)u * g.urw);
