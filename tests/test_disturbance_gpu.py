@@ -186,3 +186,20 @@ def test_wide_2d_kernel_shapes(amy, periodic, window, n_w):
         with amy.amy_build(w.problem, tmode="stored_separable", prec=prec) as h:
             assert amy.amy_info(h)["backup_kernel"] == 9
         compare_synthesis(amy, w, "stored_separable", prec, ref=ref)
+
+
+def test_wide_2d_kernel_in_captured_graphs(amy, robot_ref):
+    """Device outputs run the horizon as a captured CUDA graph: replays of
+    kernel 9 (its keys cleared by the collect kernel) give the host-output
+    synthesis bit for bit."""
+    import torch
+    w, _ = robot_ref
+    with amy.amy_build(w.problem, tmode="stored_separable", prec="fp32") as h:
+        Vh, Ph = amy.amy_synthesize(h, w.spec, w.horizon, policy_all_steps=True)
+        V = torch.empty(w.problem.n_states, dtype=torch.float32, device="cuda")
+        P = torch.empty((w.horizon, w.problem.n_states), dtype=torch.int16, device="cuda")
+        for _ in range(3):
+            amy.amy_synthesize(h, w.spec, w.horizon, V_out=V, policy_out=P, policy_all_steps=True)
+            torch.cuda.synchronize()
+            assert np.array_equal(V.cpu().numpy(), Vh)
+            assert np.array_equal(P.cpu().numpy().view(np.uint16), Ph)
