@@ -27,7 +27,10 @@
 
 namespace amy {
 
-constexpr int TILE_MAXT = 4;  // groups per tile
+#ifndef AMY_TILE_MAXT
+#define AMY_TILE_MAXT 4
+#endif
+constexpr int TILE_MAXT = AMY_TILE_MAXT;  // groups per tile (at most)
 constexpr int TILE_KU = 4;    // Sh combinations per step (two Ow cells at a time: 2 * TILE_KU loads in flight)
 constexpr int TILE_MAX_THREADS = 448;
 // Extra floats between consecutive staged rows of R (a multiple of 4): the row
