@@ -266,8 +266,7 @@ def run_amy(args, rank, world):
     torch.cuda.synchronize()
     lane_peaks = amy.amy_measure_lane_loads()  # roofline denominators (outside the timed region)
     plane_family = info["backup_kernel"] in (7, 8)
-    if args.prec == "fp64" or plane_family:
-        lane_peaks.update({"fma_" + k: v for k, v in amy.amy_measure_fma().items()})
+    lane_peaks.update({"fma_" + k: v for k, v in amy.amy_measure_fma().items()})
     if plane_family:
         lane_peaks["l2_bytes"] = amy.amy_measure_l2()
     # the plane kernel's own work in one backup (counted in an untimed run)
@@ -432,7 +431,7 @@ def roofline(args, w, info, backup_ms, free, lane_peaks, work=None):
                "frac": achieved / pk["hbm_gbs"], "traffic": measured_traffic(args, nx)[0],
                "peak_source": pk["source"], "algorithmic_bytes_per_launch": int(algo),
                "backup_kernel": info["backup_kernel"]}
-        if "fma_fp64" not in lane_peaks:
+        if args.prec != "fp64" or "fma_fp64" not in lane_peaks:
             return hbm
         # FP64: one fused multiply-add per (free state, input, slot) against the
         # measured FP64 FMA rate; the closer of the two ceilings is the bound
@@ -469,7 +468,15 @@ def roofline(args, w, info, backup_ms, free, lane_peaks, work=None):
              "algorithmic_lane_loads_per_backup": int(loads), "algorithmic_unit": what,
              "backup_kernel": kern,
              "window_slot_rate_vs_gather_ceiling": (gather / (backup_ms / 1e3) / 1e9) / peak}
-    if "fma_fp64" not in lane_peaks:
+    if args.prec != "fp64":
+        # FP32: one fused multiply-add per (free state, input, slot) -- the
+        # per-transition work of a kernel that sums every slot -- against the
+        # measured FP32 FMA rate, reported beside the lane-load ceiling
+        if "fma_fp32" in lane_peaks:
+            ach = gather / (backup_ms / 1e3) / 1e12
+            fpk = lane_peaks["fma_fp32"] / 1e12
+            lanes["other_ceiling"] = {"bound": "alu", "achieved": ach, "peak": fpk, "unit": "T FMA/s (FP32)",
+                                      "frac": ach / fpk}
         return lanes
     # FP64 on the fly: one FP64 fused multiply-add per (free state, input,
     # slot) against the measured FP64 FMA rate; the closer ceiling is the bound
