@@ -90,26 +90,33 @@ static void plan_tile(const Geom &g, PlanePlan &pl, int smem_budget) {
     }
     if (nSh == 0 || Ksh > 4096) return;
     if (ow >= 0 && g.W[ow] > 16) return;
-    const int threads = std::max(128, (pl.P + 31) / 32 * 32);
-    if (threads > TILE_MAX_THREADS) return;
+    if ((pl.P + 31) / 32 * 32 > TILE_MAX_THREADS) return;
+    // threads of a block holding t groups: one per state where they fit
+    // (small planes), else one per plane position (each thread then holds
+    // up to t states in stage 2)
+    auto threads_for = [&](int t) {
+        return std::min(TILE_MAX_THREADS, std::max(128, (t * pl.P + 31) / 32 * 32));
+    };
     // groups per tile and chunk (values of the first B dim staged at once):
     // the largest tile whose block, holding two of those values, leaves room
     // for two blocks per SM, else the largest tile holding one value at one
     // block per SM
     const int Na = g.N[a];
-    int T = 0;
+    int T = 0, threads = 0;
     int64_t chunk = 0;
     for (int pass = smem_budget > 0 ? 1 : 0; pass < 2 && T == 0; ++pass) {
         const int64_t budget = pass == 0 ? 112 * 1024 : (smem_budget > 0 ? smem_budget : 200 * 1024);
         const int64_t want = pass == 0 ? 2 : 1;
         for (int t = std::min(TILE_MAXT, Na); t >= 2 && T == 0; --t) {
+            const int th = threads_for(t);
             int64_t ch = 0;
-            while ((int64_t)tile_smem_bytes((int)Ksh, threads, t, (int)((ch + 1) * pl.rs0), pl.Ppad) <= budget &&
+            while ((int64_t)tile_smem_bytes((int)Ksh, th, t, (int)((ch + 1) * pl.rs0), pl.Ppad) <= budget &&
                    ch < 64)
                 ++ch;
             if (ch >= want) {
                 T = t;
                 chunk = ch;
+                threads = th;
             }
         }
     }
