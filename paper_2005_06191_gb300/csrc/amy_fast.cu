@@ -98,15 +98,15 @@ static void plan_tile(const Geom &g, PlanePlan &pl, int smem_budget) {
         return std::min(TILE_MAX_THREADS, std::max(128, (t * pl.P + 31) / 32 * 32));
     };
     // groups per tile and chunk (values of the first B dim staged at once):
-    // the largest tile whose block, holding two of those values, leaves room
-    // for two blocks per SM, else the largest tile holding one value at one
-    // block per SM
+    // the largest tile whose block, holding TILE_WANT0 of those values, fits
+    // TILE_BUDGET0 (two blocks per SM by default), else the largest tile
+    // holding one value at one block per SM
     const int Na = g.N[a];
     int T = 0, threads = 0;
     int64_t chunk = 0;
     for (int pass = smem_budget > 0 ? 1 : 0; pass < 2 && T == 0; ++pass) {
-        const int64_t budget = pass == 0 ? 112 * 1024 : (smem_budget > 0 ? smem_budget : 200 * 1024);
-        const int64_t want = pass == 0 ? 2 : 1;
+        const int64_t budget = pass == 0 ? TILE_BUDGET0 : (smem_budget > 0 ? smem_budget : 200 * 1024);
+        const int64_t want = pass == 0 ? TILE_WANT0 : 1;
         for (int t = std::min(TILE_MAXT, Na); t >= 2 && T == 0; --t) {
             const int th = threads_for(t);
             int64_t ch = 0;

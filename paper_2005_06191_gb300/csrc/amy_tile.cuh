@@ -31,7 +31,26 @@ namespace amy {
 #define AMY_TILE_MAXT 4
 #endif
 constexpr int TILE_MAXT = AMY_TILE_MAXT;  // groups per tile (at most)
-constexpr int TILE_KU = 4;    // Sh combinations per step (two Ow cells at a time: 2 * TILE_KU loads in flight)
+#ifndef AMY_TILE_KU
+#define AMY_TILE_KU 2
+#endif
+// Sh combinations per step (two Ow cells at a time: 2 * TILE_KU loads in flight)
+constexpr int TILE_KU = AMY_TILE_KU;
+// Blocks per SM the kernel is compiled for (its register cap), and the
+// planner's first choice: the shared memory of one block and the values of
+// the first staged dim it must hold at once for that many blocks per SM
+#ifndef AMY_TILE_MINB
+#define AMY_TILE_MINB 2
+#endif
+constexpr int TILE_MINB = AMY_TILE_MINB;
+#ifndef AMY_TILE_BUDGET0
+#define AMY_TILE_BUDGET0 (112 * 1024)
+#endif
+#ifndef AMY_TILE_WANT0
+#define AMY_TILE_WANT0 2
+#endif
+constexpr int TILE_BUDGET0 = AMY_TILE_BUDGET0;
+constexpr int TILE_WANT0 = AMY_TILE_WANT0;
 constexpr int TILE_MAX_THREADS = 448;
 // Extra floats between consecutive staged rows of R (a multiple of 4): the row
 // pitch Ppad + AMY_TILE_RPAD moves rows onto other shared-memory banks.
@@ -84,7 +103,7 @@ __host__ __device__ inline size_t tile_smem_bytes(int Ksh, int threads, int T, i
 }
 
 template <class VT, int WM>
-__global__ void __launch_bounds__(TILE_MAX_THREADS, 2) k_backup_tile(const __grid_constant__ Geom g,
+__global__ void __launch_bounds__(TILE_MAX_THREADS, TILE_MINB) k_backup_tile(const __grid_constant__ Geom g,
                                                                  const __grid_constant__ TileArgs<VT> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int32_t *s_lo = reinterpret_cast<int32_t *>(smem_raw);                // [PLANE_MAXB] tile bounds
