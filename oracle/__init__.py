@@ -54,10 +54,12 @@ class _Problem(C.Structure):
         ("noise", C.c_int32), ("noise_p0", C.POINTER(C.c_double)), ("noise_p1", C.POINTER(C.c_double)),
         ("noise_p2", C.POINTER(C.c_double)), ("noise_p3", C.POINTER(C.c_double)),
         ("expr", C.c_void_p),
+        ("noise_cdf", C.POINTER(C.c_double)),
     ]
 
 
-_NOISE = {"gaussian": 0, "uniform": 1, "exponential": 2, "beta": 3, "mult_gaussian": 4}
+_NOISE = {"gaussian": 0, "uniform": 1, "exponential": 2, "beta": 3, "mult_gaussian": 4, "user": 5}
+USER_KNOTS = 1024
 
 
 class _Spec(C.Structure):
@@ -96,6 +98,13 @@ def _load():
         lib.orc_expr_free.argtypes = [C.c_void_p]
         lib.orc_expr_eval.restype = C.c_double
         lib.orc_expr_eval.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.orc_expr_compile_pdf.restype = C.c_void_p
+        lib.orc_expr_compile_pdf.argtypes = [C.c_void_p, C.c_int, C.c_char_p, C.c_int]
+        lib.orc_gauss_legendre8.restype = C.c_double
+        lib.orc_gauss_legendre8.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
+        lib.orc_user_table.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_void_p]
+        lib.orc_user_cdf.restype = C.c_double
+        lib.orc_user_cdf.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double]
         lib.orc_philox4x64.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         lib.orc_simulate.argtypes = [P, S, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
                                      C.c_uint64, C.c_void_p]
@@ -170,6 +179,8 @@ def _problem(p, keep: _Keep) -> _Problem:
         setattr(s, f"noise_p{i}", keep.f64(arr))
     if p.sys_kind == "expr":
         s.expr = keep.expr(_load(), p)
+    if getattr(p, "noise", "gaussian") == "user":
+        s.noise_cdf = keep.f64(user_tables(p))
     return s
 
 
@@ -329,5 +340,56 @@ def expr_eval(exprs, n: int, m: int, p: int, params, x, u, w) -> np.ndarray:
         pp = prm if prm.size else np.zeros(1)
         return np.array([lib.orc_expr_eval(h, d, xs.ctypes.data, us.ctypes.data, ws.ctypes.data, pp.ctypes.data)
                          for d in range(n)])
+    finally:
+        lib.orc_expr_free(h)
+
+
+def _compile_pdf(lib, texts):
+    enc = [str(t).encode() for t in texts]
+    arr = (C.c_char_p * len(enc))(*enc)
+    err = C.create_string_buffer(256)
+    h = lib.orc_expr_compile_pdf(arr, len(enc), err, 256)
+    if not h:
+        raise ValueError(f"density: {err.value.decode()}")
+    return h
+
+
+def user_tables(p) -> np.ndarray:
+    """The CDF tables of a problem's user densities (one block per dim)."""
+    lib = _load()
+    texts = list(p.noise_pdf or [])
+    if len(texts) != p.n:
+        raise ValueError(f"user noise needs {p.n} densities")
+    lo, hi = p.noise_params[0], p.noise_params[1]
+    h = _compile_pdf(lib, texts)
+    try:
+        out = np.zeros((p.n, 2 * (USER_KNOTS + 1)), np.float64)
+        for d in range(p.n):
+            if lib.orc_user_table(h, d, float(lo[d]), float(hi[d]), out[d].ctypes.data) != 0:
+                raise ValueError(f"density {d}: not a density on [{lo[d]}, {hi[d]}]")
+        return out.reshape(-1)
+    finally:
+        lib.orc_expr_free(h)
+
+
+def gauss_legendre8(text: str, a: float, b: float) -> float:
+    """The oracle's 8-point Gauss-Legendre integral of a density text over [a, b]."""
+    lib = _load()
+    h = _compile_pdf(lib, [text])
+    try:
+        return lib.orc_gauss_legendre8(h, 0, float(a), float(b))
+    finally:
+        lib.orc_expr_free(h)
+
+
+def user_cdf(text: str, lo: float, hi: float, ts) -> np.ndarray:
+    """The oracle's interpolated CDF of one user density at the points ts."""
+    lib = _load()
+    h = _compile_pdf(lib, [text])
+    try:
+        table = np.zeros(2 * (USER_KNOTS + 1), np.float64)
+        if lib.orc_user_table(h, 0, float(lo), float(hi), table.ctypes.data) != 0:
+            raise ValueError("not a density")
+        return np.array([lib.orc_user_cdf(table.ctypes.data, float(lo), float(hi), float(t)) for t in ts])
     finally:
         lib.orc_expr_free(h)

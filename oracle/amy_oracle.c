@@ -113,6 +113,10 @@ static int cut_interval(const orc_problem *p, int d, double *clo, double *chi) {
             *clo = p->noise_p2[d];
             *chi = p->noise_p3[d];
             return 0;
+        case ORC_NOISE_USER: /* the user's box enclosing the support */
+            *clo = p->noise_p0[d];
+            *chi = p->noise_p1[d];
+            return 0;
         default:
             return -1;
     }
@@ -136,6 +140,10 @@ static int noise_valid(const orc_problem *p) {
                 if (!(p->noise_p3[d] > p->noise_p2[d])) return 0;
                 break;
             }
+            case ORC_NOISE_USER:
+                if (!p->noise_p0 || !p->noise_p1 || !p->noise_cdf) return 0;
+                if (!(p->noise_p1[d] > p->noise_p0[d])) return 0;
+                break;
             default:
                 return 0;
         }
@@ -271,6 +279,13 @@ static double noise_mass(const orc_problem *p, int d, double elo, double ehi, do
             /* upper half: differences of the upper tail I_{1-z}(b, a) */
             if (zlo >= 0.5) return inc_beta_int(b, a, 1.0 - zlo) - inc_beta_int(b, a, 1.0 - zhi);
             return inc_beta_int(a, b, zhi) - inc_beta_int(a, b, zlo);
+        }
+        case ORC_NOISE_USER: {
+            /* the normalised CDF of the user's density at the two edges */
+            const double *table = p->noise_cdf + (size_t)d * 2 * (ORC_USER_KNOTS + 1);
+            const double lo = p->noise_p0[d], hi = p->noise_p1[d];
+            const double m = orc_user_cdf(table, lo, hi, thi) - orc_user_cdf(table, lo, hi, tlo);
+            return m > 0.0 ? m : 0.0;
         }
         case ORC_NOISE_MULT_GAUSSIAN: {
             const double s = p->noise_p0[d] * fabs(xd);

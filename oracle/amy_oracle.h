@@ -49,6 +49,16 @@ orc_expr *orc_expr_compile(const char *const *text, int n, int m, int p, int64_t
 void orc_expr_free(orc_expr *e);
 double orc_expr_eval(const orc_expr *e, int d, const double *x, const double *u, const double *w,
                      const double *params);
+
+/* User densities (Sec. 6.2): one expression per dim in the variable t (the
+ * noise value), with a box [lo, hi] enclosing its support.  The table of a
+ * dim holds 2 (ORC_USER_KNOTS + 1) doubles: the normalised CDF at the knots,
+ * then the normalised density there (amy_oracle_expr.c). */
+#define ORC_USER_KNOTS 1024
+orc_expr *orc_expr_compile_pdf(const char *const *text, int n, char *err, int errlen);
+double orc_gauss_legendre8(const orc_expr *pdf, int d, double a, double b);
+int orc_user_table(const orc_expr *pdf, int d, double lo, double hi, double *table);
+double orc_user_cdf(const double *table, double lo, double hi, double t);
 enum { ORC_SAFETY = 0, ORC_REACH = 1, ORC_REACH_AVOID = 2 };
 
 typedef struct {
@@ -98,10 +108,13 @@ typedef struct {
     /* ORC_SYS_EXPR: the compiled mean expressions (params are their p0..);
      * a disturbance grid is allowed, its point bound to w0.. */
     const orc_expr *expr;
+    /* ORC_NOISE_USER: per dim the table of orc_user_table (n blocks of
+     * 2 (ORC_USER_KNOTS + 1) doubles); noise_p0 / noise_p1 the support box */
+    const double *noise_cdf;
 } orc_problem;
 
 enum { ORC_NOISE_GAUSSIAN = 0, ORC_NOISE_UNIFORM = 1, ORC_NOISE_EXPONENTIAL = 2, ORC_NOISE_BETA = 3,
-       ORC_NOISE_MULT_GAUSSIAN = 4 };
+       ORC_NOISE_MULT_GAUSSIAN = 4, ORC_NOISE_USER = 5 };
 
 typedef struct {
     int32_t kind;              /* ORC_SAFETY / ORC_REACH / ORC_REACH_AVOID */

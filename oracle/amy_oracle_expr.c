@@ -88,6 +88,7 @@ static double call2(int f, double a, double b) {
 typedef struct {
     const char *s;
     size_t pos;
+    int pdf; /* a density: the one variable t (read as x0) */
     int m, p, depth;
     int64_t n_params;
     int n;
@@ -226,6 +227,14 @@ static void parse_primary(parser *ps) {
             else emit(ps, OP_CALL1, f1, 0.0);
             return;
         }
+        if (ps->pdf) {
+            if (strcmp(name, "t") != 0) {
+                fail(ps, "unknown identifier (a density reads t only)");
+                return;
+            }
+            emit(ps, OP_X, 0, 0.0);
+            return;
+        }
         /* a variable: one letter then a decimal index without leading zeros */
         const char kind = name[0];
         const char *digits = name + 1;
@@ -305,7 +314,8 @@ void orc_expr_free(orc_expr *e) {
     free(e);
 }
 
-orc_expr *orc_expr_compile(const char *const *text, int n, int m, int p, int64_t n_params, char *err, int errlen) {
+static orc_expr *compile_any(const char *const *text, int n, int m, int p, int64_t n_params, int pdf, char *err,
+                             int errlen) {
     if (err && errlen > 0) err[0] = '\0';
     if (!text || n < 1 || n > ORC_MAXD || m < 0 || p < 0) {
         if (err && errlen > 0) snprintf(err, (size_t)errlen, "bad arguments");
@@ -322,6 +332,7 @@ orc_expr *orc_expr_compile(const char *const *text, int n, int m, int p, int64_t
         ps.m = m;
         ps.p = p;
         ps.n_params = n_params;
+        ps.pdf = pdf;
         ps.out = &e->prog[d];
         ps.err = err;
         ps.errlen = errlen;
@@ -339,6 +350,14 @@ orc_expr *orc_expr_compile(const char *const *text, int n, int m, int p, int64_t
         }
     }
     return e;
+}
+
+orc_expr *orc_expr_compile(const char *const *text, int n, int m, int p, int64_t n_params, char *err, int errlen) {
+    return compile_any(text, n, m, p, n_params, 0, err, errlen);
+}
+
+orc_expr *orc_expr_compile_pdf(const char *const *text, int n, char *err, int errlen) {
+    return compile_any(text, n, 0, 0, 0, 1, err, errlen);
 }
 
 double orc_expr_eval(const orc_expr *e, int d, const double *x, const double *u, const double *w,
@@ -368,4 +387,66 @@ double orc_expr_eval(const orc_expr *e, int d, const double *x, const double *u,
     const double r = top == 1 ? st[0] : NAN;
     if (st != stackbuf) free(st);
     return r;
+}
+
+/* ---- user densities (Sec. 6.2: the user gives the density and a box
+ * enclosing its support) ----------------------------------------------------
+ * The density of dim d is integrated over [lo, hi] once: at the M + 1 knots
+ * t_i = lo + i h (h = (hi - lo) / M; t_M = hi) its values f_i, and per interval the
+ * 8-point Gauss-Legendre rule, the interval sums added in order into the
+ * cumulative C_i; F_i = C_i / C_M and f_i / C_M normalise the density to
+ * one.  The CDF between knots is the cubic Hermite interpolant of (F_i, f_i),
+ * exact for CDFs of degree 3 and of error O(h^4) otherwise. */
+static const double kGLx[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+static const double kGLw[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+
+double orc_gauss_legendre8(const orc_expr *pdf, int d, double a, double b) {
+    const double c = 0.5 * (a + b), r = 0.5 * (b - a);
+    double sum = 0.0;
+    for (int q = 3; q >= 0; --q) {
+        const double t = c - r * kGLx[q];
+        sum = sum + kGLw[q] * orc_expr_eval(pdf, d, &t, NULL, NULL, NULL);
+    }
+    for (int q = 0; q < 4; ++q) {
+        const double t = c + r * kGLx[q];
+        sum = sum + kGLw[q] * orc_expr_eval(pdf, d, &t, NULL, NULL, NULL);
+    }
+    return r * sum;
+}
+
+int orc_user_table(const orc_expr *pdf, int d, double lo, double hi, double *table) {
+    const int M = ORC_USER_KNOTS;
+    if (!(hi > lo)) return -1;
+    const double h = (hi - lo) / (double)M;
+    double *F = table, *f = table + (M + 1);
+    F[0] = 0.0;
+    /* knot i at lo + i h, the last one at hi exactly */
+    for (int i = 0; i < M; ++i) {
+        const double a = lo + (double)i * h, b = i + 1 == M ? hi : lo + (double)(i + 1) * h;
+        F[i + 1] = F[i] + orc_gauss_legendre8(pdf, d, a, b);
+    }
+    const double Z = F[M];
+    if (!(Z > 0.0) || !isfinite(Z)) return -1;
+    for (int i = 0; i <= M; ++i) {
+        const double t = i == M ? hi : lo + (double)i * h;
+        F[i] = F[i] / Z;
+        f[i] = orc_expr_eval(pdf, d, &t, NULL, NULL, NULL) / Z;
+        if (!(f[i] >= 0.0) || !isfinite(f[i])) return -1;
+    }
+    return 0;
+}
+
+double orc_user_cdf(const double *table, double lo, double hi, double t) {
+    const int M = ORC_USER_KNOTS;
+    if (t <= lo) return 0.0;
+    if (t >= hi) return 1.0;
+    const double h = (hi - lo) / (double)M;
+    const double s = (t - lo) / h;
+    int i = (int)floor(s);
+    if (i > M - 1) i = M - 1;
+    const double tau = s - (double)i, tau2 = tau * tau, tau3 = tau2 * tau;
+    const double h00 = 2.0 * tau3 - 3.0 * tau2 + 1.0, h10 = tau3 - 2.0 * tau2 + tau;
+    const double h01 = -2.0 * tau3 + 3.0 * tau2, h11 = tau3 - tau2;
+    const double *F = table, *f = table + (M + 1);
+    return h00 * F[i] + h10 * h * f[i] + h01 * F[i + 1] + h11 * h * f[i + 1];
 }

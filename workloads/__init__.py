@@ -66,6 +66,10 @@ class Problem:
     # sys_kind "expr": one expression per state dim (the text right-hand side
     # of Sec. 3); params are its p0, p1, ...
     exprs: Optional[List[str]] = None
+    # noise "user": one density per dim in the variable t (Sec. 6.2: the user
+    # gives the density and a box enclosing its support, noise_params
+    # [[lo...], [hi...]]); it is normalised over the box
+    noise_pdf: Optional[List[str]] = None
 
     @property
     def n(self) -> int:
