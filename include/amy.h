@@ -110,16 +110,31 @@ typedef enum { AMY_SYS_AFFINE_PER_INPUT = 0, AMY_SYS_UNICYCLE = 1, AMY_SYS_EXPR 
  *                            state whose centre in dim d is x_d (no noise where
  *                            x_d = 0); dense or explicit windows only (the paper
  *                            disables the cut for multiplicative noise)
+ *   AMY_NOISE_USER           the user's density (Sec. 6.2: a density and a box
+ *                            enclosing its support): pdf[d] is a C-syntax
+ *                            expression in the variable t (the noise value; the
+ *                            grammar of AMY_SYS_EXPR), p0 = lo < p1 = hi the box.
+ *                            At amy_build it is compiled with NVRTC and tabulated
+ *                            over [lo, hi]: at 1025 knots its value, per knot
+ *                            interval its 8-point Gauss-Legendre integral summed
+ *                            into the CDF, both normalised by the total (the
+ *                            density need not integrate to one); a cell's mass
+ *                            is the difference of the CDF's cubic Hermite
+ *                            interpolant at its edges.  INVALID_ARG when the text
+ *                            is bad or a value is negative or not finite.
  * Cells are still kept by their centres inside the cut interval around the
- * mean (gamma mode): the support for the uniform and beta (gamma must not
- * exceed the uniform's density 1/(2a)), [0, log(rate/gamma)/rate] for the
- * exponential (gamma < rate).  amy_info's cut_half_width then reports the
+ * mean (gamma mode): the support for the uniform, beta and user densities
+ * (gamma must not exceed the uniform's density 1/(2a)),
+ * [0, log(rate/gamma)/rate] for the exponential (gamma < rate).  Only
+ * amy_build takes user densities (the server and amy_synthesize_noalloc
+ * answer UNSUPPORTED).  amy_info's cut_half_width then reports the
  * upper end of that interval. */
 typedef enum { AMY_NOISE_GAUSSIAN = 0, AMY_NOISE_UNIFORM = 1, AMY_NOISE_EXPONENTIAL = 2, AMY_NOISE_BETA = 3,
-               AMY_NOISE_MULT_GAUSSIAN = 4 } amy_noise_kind;
+               AMY_NOISE_MULT_GAUSSIAN = 4, AMY_NOISE_USER = 5 } amy_noise_kind;
 typedef struct {
     int32_t kind;
     const double *p0, *p1, *p2, *p3;
+    const char *const *pdf;  /* AMY_NOISE_USER: n densities in t, else ignored */
 } amy_noise;
 
 typedef struct {

@@ -26,7 +26,7 @@ PRECS = {"fp64": 0, "fp32": 1, "fp32_kahan": 2}
 SYS_KINDS = {"affine": 0, "unicycle": 1, "expr": 2}
 SPEC_KINDS = {"safety": 0, "reach": 1, "reach_avoid": 2}
 VSTORES = {"native": 0, "bf16": 1, "u16": 2}
-NOISE_KINDS = {"gaussian": 0, "uniform": 1, "exponential": 2, "beta": 3, "mult_gaussian": 4}
+NOISE_KINDS = {"gaussian": 0, "uniform": 1, "exponential": 2, "beta": 3, "mult_gaussian": 4, "user": 5}
 POLICY_NONE = 0xFFFF
 
 
@@ -95,6 +95,12 @@ def _problem_structs(k: _Keep, p):
         nz.kind = NOISE_KINDS[kind]
         for i, arr in enumerate(list(getattr(p, "noise_params", None) or [])[:4]):
             setattr(nz, f"p{i}", k.f64(arr))
+        if kind == "user":
+            texts = k.obj([str(t).encode() for t in (getattr(p, "noise_pdf", None) or [])])
+            if len(texts) != p.n:
+                raise ValueError(f"user noise needs {p.n} densities, got {len(texts)}")
+            arr = k.obj((C.c_char_p * len(texts))(*texts))
+            nz.pdf = C.cast(arr, C.POINTER(C.c_char_p))
         sysd.noise = C.pointer(k.obj(nz))
     if p.sys_kind == "expr":
         texts = k.obj([str(t).encode() for t in (p.exprs or [])])

@@ -25,7 +25,8 @@ class amy_grid(C.Structure):
 
 
 class amy_noise(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("p0", DP), ("p1", DP), ("p2", DP), ("p3", DP)]
+    _fields_ = [("kind", C.c_int32), ("p0", DP), ("p1", DP), ("p2", DP), ("p3", DP),
+                ("pdf", C.POINTER(C.c_char_p))]
 
 
 class amy_system(C.Structure):

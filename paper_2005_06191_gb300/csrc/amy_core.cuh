@@ -25,7 +25,9 @@ enum SpecKind : int32_t { SPEC_SAFETY = 0, SPEC_REACH = 1, SPEC_REACH_AVOID = 2 
 enum TMode : int32_t { TM_OTF = 0, TM_FULL = 1, TM_FACTORED = 2, TM_SEPARABLE = 3 };
 // Noise distribution per dimension (Sec. 6.2; multiplicative noise as in Eq. (1a)).
 enum NoiseKind : int32_t { NOISE_GAUSSIAN = 0, NOISE_UNIFORM = 1, NOISE_EXPONENTIAL = 2, NOISE_BETA = 3,
-                           NOISE_MULT_GAUSSIAN = 4 };
+                           NOISE_MULT_GAUSSIAN = 4, NOISE_USER = 5 };
+// Knot intervals of a user density's CDF table (the knots t_i = lo + i h).
+constexpr int USER_KNOTS = 1024;
 
 // 16-bit fixed-point storage of a probability: value = bits / 65535.
 struct unorm16 {
@@ -63,6 +65,10 @@ struct Geom {
     // tsu[d][i], the index of the per-dimension tables -- at mtab[moff[d] + e].
     const double *mtab;
     int64_t moff[MAXD];
+    // User densities (NOISE_USER): per dim the normalised CDF at the
+    // USER_KNOTS + 1 knots of the support box [np[0][d], np[1][d]], then the
+    // normalised density there (2 (USER_KNOTS + 1) doubles per dim)
+    const double *ucdf;
     uint32_t xdep[MAXD], udep[MAXD];  // the coordinates each component's text reads (host planning)
     // Dependency-compressed per-dimension tables (separable stored mode):
     // mean component d depends only on the state dims j with tsx[d][j] != 0
@@ -298,8 +304,33 @@ __device__ __noinline__ R inc_beta_int(int a, int b, R z) {
 // differences, from the upper tail in the upper half.  Kept out of line:
 // the Gaussian is the common case, and the unrolled kernels would otherwise
 // inline this code into every slot.
+// CDF of dim d's user density at t (t relative to the mean): 0 below the
+// box, 1 above, between knots the cubic Hermite interpolant of the tabulated
+// CDF values and densities, in FP64 with every operation rounded as written.
+__device__ __forceinline__ double user_cdf(const Geom &g, int d, double t) {
+    const double lo = g.np[0][d], hi = g.np[1][d];
+    if (t <= lo) return 0.0;
+    if (t >= hi) return 1.0;
+    const double h = ddiv(dsub(hi, lo), (double)USER_KNOTS);
+    const double s = ddiv(dsub(t, lo), h);
+    int i = (int)floor(s);
+    if (i > USER_KNOTS - 1) i = USER_KNOTS - 1;
+    const double tau = dsub(s, (double)i), tau2 = dmul(tau, tau), tau3 = dmul(tau2, tau);
+    const double h00 = dadd(dsub(dmul(2.0, tau3), dmul(3.0, tau2)), 1.0);
+    const double h10 = dadd(dsub(tau3, dmul(2.0, tau2)), tau);
+    const double h01 = dadd(dmul(-2.0, tau3), dmul(3.0, tau2));
+    const double h11 = dsub(tau3, tau2);
+    const double *F = g.ucdf + (int64_t)d * 2 * (USER_KNOTS + 1), *f = F + (USER_KNOTS + 1);
+    return dadd(dadd(dadd(dmul(h00, __ldg(F + i)), dmul(dmul(h10, h), __ldg(f + i))), dmul(h01, __ldg(F + i + 1))),
+                dmul(dmul(h11, h), __ldg(f + i + 1)));
+}
+
 template <class R>
 __device__ __noinline__ R noise_mass(const Geom &g, int d, R tlo, R thi) {
+    if (g.noise == NOISE_USER) {
+        const double m = dsub(user_cdf(g, d, (double)thi), user_cdf(g, d, (double)tlo));
+        return (R)(m > 0.0 ? m : 0.0);
+    }
     if (g.noise == NOISE_UNIFORM) {
         const R a = (R)g.np[0][d];
         const R lo = tlo > -a ? tlo : -a, hi = thi < a ? thi : a;

@@ -79,12 +79,13 @@ amy_status fill_geom(const amy_system *sys, const amy_grid *st, const amy_grid *
     // noise distribution (Gaussian unless sys->noise says otherwise)
     const amy_noise *nz = sys->noise;
     g.noise = nz ? nz->kind : NOISE_GAUSSIAN;
-    if (g.noise < NOISE_GAUSSIAN || g.noise > NOISE_MULT_GAUSSIAN)
+    if (g.noise < NOISE_GAUSSIAN || g.noise > NOISE_USER)
         return set_error(AMY_E_INVALID_ARG, "unknown noise kind %d", g.noise);
+    if (g.noise == NOISE_USER && !nz->pdf) return set_error(AMY_E_INVALID_ARG, "user noise needs its densities");
     for (int d = 0; d < n; ++d) {
         const double *pp[4] = {nz ? nz->p0 : nullptr, nz ? nz->p1 : nullptr, nz ? nz->p2 : nullptr,
                                nz ? nz->p3 : nullptr};
-        const int need = g.noise == NOISE_GAUSSIAN ? 0 : g.noise == NOISE_BETA ? 4 : 1;
+        const int need = g.noise == NOISE_GAUSSIAN ? 0 : g.noise == NOISE_BETA ? 4 : g.noise == NOISE_USER ? 2 : 1;
         for (int i = 0; i < 4; ++i) {
             if (i < need && !pp[i]) return set_error(AMY_E_INVALID_ARG, "noise kind %d needs %d parameter arrays", g.noise, need);
             g.np[i][d] = i < need ? pp[i][d] : 0.0;
@@ -97,6 +98,9 @@ amy_status fill_geom(const amy_system *sys, const amy_grid *st, const amy_grid *
             if (!(a >= 1.0 && b >= 1.0 && a == std::floor(a) && b == std::floor(b) && a + b <= 64.0))
                 return set_error(AMY_E_INVALID_ARG, "beta noise needs integer shapes >= 1 summing to at most 64 (dim %d)", d);
             if (!(g.np[3][d] > g.np[2][d])) return set_error(AMY_E_INVALID_ARG, "beta noise needs lo < hi (dim %d)", d);
+        } else if (g.noise == NOISE_USER) {
+            if (!(g.np[1][d] > g.np[0][d]))
+                return set_error(AMY_E_INVALID_ARG, "user noise needs a support box lo < hi (dim %d)", d);
         }
     }
     for (int d = 0; d < n; ++d) {
@@ -213,6 +217,9 @@ amy_status fill_geom(const amy_system *sys, const amy_grid *st, const amy_grid *
             } else if (g.noise == NOISE_BETA) {
                 clo = g.np[2][d];
                 chi = g.np[3][d];
+            } else if (g.noise == NOISE_USER) {  // the box enclosing the density's support
+                clo = g.np[0][d];
+                chi = g.np[1][d];
             } else {
                 return set_error(AMY_E_INVALID_ARG, "multiplicative noise has no cut: use gamma 0 or explicit windows");
             }
@@ -548,6 +555,7 @@ struct amy_handle_s {
     double *d_params;
     ExprProgram expr;     // text system: its parsed expressions and table kernel source
     double *d_mtab;       // and its mean tables (null for the built-in systems)
+    double *d_ucdf;       // user noise densities: their CDF tables (null otherwise)
     void *d_T;
     int16_t *d_O;
     // stored rows (full or factored) with wide windows: the backup is split
@@ -681,6 +689,7 @@ void free_handle(amy_handle_s *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     cudaFree(h->d_params);
     cudaFree(h->d_mtab);
+    cudaFree(h->d_ucdf);
     cudaFree(h->d_T);
     cudaFree(h->d_O);
     cudaFree(h->d_split);
@@ -1438,6 +1447,13 @@ amy_status amy_build(const amy_system *sys, const amy_grid *states, const amy_gr
     if (e != cudaSuccess) {
         free_handle(h);
         return cuda_error(e, "params upload");
+    }
+    if (h->g.noise == NOISE_USER) {
+        // the user densities' CDF tables, before anything computes a mass
+        TRY(dev_alloc(h, (void **)&h->d_ucdf, (size_t)h->g.n * 2 * (USER_KNOTS + 1) * sizeof(double),
+                      "user density tables"));
+        h->g.ucdf = h->d_ucdf;
+        TRY(user_tables(sys->noise->pdf, h->g, h->d_ucdf, h->stream));
     }
     if (h->g.sys == SYS_EXPR) {
         // mean tables of the text system, indexed like the per-dimension tables

@@ -51,8 +51,8 @@ constexpr Fn kFns[] = {{"sin", 1},  {"cos", 1},   {"tan", 1},  {"asin", 1},  {"a
 
 class Parser {
   public:
-    Parser(const char *text, int n, int m, int p, int64_t n_params)
-        : s_(text), n_(n), m_(m), p_(p), np_(n_params) {}
+    Parser(const char *text, int n, int m, int p, int64_t n_params, bool pdf = false)
+        : s_(text), n_(n), m_(m), p_(p), np_(n_params), pdf_(pdf) {}
 
     // Whole expression; false with a message on error.
     bool run(std::string &code, uint32_t &dep_x, uint32_t &dep_u, std::string &err) {
@@ -73,6 +73,7 @@ class Parser {
     size_t i_ = 0;
     int n_, m_, p_;
     int64_t np_;
+    bool pdf_;  // a density: the one variable is t
     int depth_ = 0;
     uint32_t dx_ = 0, du_ = 0;
     std::string msg_;
@@ -202,6 +203,11 @@ class Parser {
             out = std::string(fn->name) + "(" + a + (fn->arity == 2 ? ", " + bb : std::string()) + ")";
             return true;
         }
+        if (pdf_) {
+            if (id != "t") return fail("unknown identifier (a density reads t only)");
+            out = "t";
+            return true;
+        }
         // variable: a letter, then a decimal index without leading zeros
         const char k = id.empty() ? '\0' : id[0];
         const std::string num = id.size() > 1 ? id.substr(1) : std::string();
@@ -314,7 +320,7 @@ const Nvrtc &nvrtc() {
 std::mutex g_kernels_mu;
 std::map<std::string, cudaKernel_t> g_kernels;
 
-amy_status kernel_for(const std::string &src, cudaKernel_t &out) {
+amy_status compile_kernel(const std::string &src, const char *name, cudaKernel_t &out) {
     int dev = 0, major = 0, minor = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
@@ -322,7 +328,7 @@ amy_status kernel_for(const std::string &src, cudaKernel_t &out) {
     if (e != cudaSuccess) return cuda_error(e, "device query");
     char arch[48];
     snprintf(arch, sizeof arch, "--gpu-architecture=sm_%d%d", major, minor);
-    const std::string key = std::string(arch) + "\n" + src;
+    const std::string key = std::string(arch) + "\n" + name + "\n" + src;
     std::lock_guard<std::mutex> lk(g_kernels_mu);
     auto it = g_kernels.find(key);
     if (it != g_kernels.end()) {
@@ -354,12 +360,51 @@ amy_status kernel_for(const std::string &src, cudaKernel_t &out) {
     e = cudaLibraryLoadData(&lib, bin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (e != cudaSuccess) return cuda_error(e, "mean expressions: library load");
     cudaKernel_t k = nullptr;
-    e = cudaLibraryGetKernel(&k, lib, "amy_expr_means");
+    e = cudaLibraryGetKernel(&k, lib, name);
     if (e != cudaSuccess) return cuda_error(e, "mean expressions: kernel lookup");
     g_kernels.emplace(key, k);  // kept (and its library loaded) for the life of the process
     out = k;
     return AMY_OK;
 }
+
+// The user densities' table kernel: per dim (one thread each) the density at
+// the knots and its 8-point Gauss-Legendre integral over each knot interval
+// (nodes and weights: the Legendre polynomial P8's roots and their weights),
+// summed in order into the CDF, then both normalised by the total.
+const char *kUserHead =
+    "struct UserBox { double lo[8], hi[8]; int n; };\n"
+    "__device__ double amy_pdf(int d, double t) {\n"
+    "    switch (d) {\n";
+const char *kUserTail =
+    "    }\n"
+    "    return 0.0;\n"
+    "}\n"
+    "extern \"C\" __global__ void amy_user_tables(const UserBox b, double *__restrict__ out) {\n"
+    "    const int d = blockIdx.x * blockDim.x + threadIdx.x;\n"
+    "    if (d >= b.n) return;\n"
+    "    const int M = 1024;\n"
+    "    const double X[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};\n"
+    "    const double Wt[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};\n"
+    "    const double lo = b.lo[d], hi = b.hi[d], h = (hi - lo) / (double)M;\n"
+    "    double *F = out + (long long)d * 2 * (M + 1), *f = F + (M + 1);\n"
+    "    F[0] = 0.0;\n"
+    "    for (int i = 0; i < M; ++i) {\n"
+    "        const double a = lo + (double)i * h, e = i + 1 == M ? hi : lo + (double)(i + 1) * h;\n"
+    "        const double c = 0.5 * (a + e), r = 0.5 * (e - a);\n"
+    "        double sum = 0.0;\n"
+    "        for (int q = 3; q >= 0; --q) sum = sum + Wt[q] * amy_pdf(d, c - r * X[q]);\n"
+    "        for (int q = 0; q < 4; ++q) sum = sum + Wt[q] * amy_pdf(d, c + r * X[q]);\n"
+    "        F[i + 1] = F[i] + r * sum;\n"
+    "    }\n"
+    "    const double Z = F[M];\n"
+    "    for (int i = 0; i <= M; ++i) {\n"
+    "        const double t = i == M ? hi : lo + (double)i * h;\n"
+    "        F[i] = F[i] / Z;\n"
+    "        f[i] = amy_pdf(d, t) / Z;\n"
+    "    }\n"
+    "}\n";
+
+amy_status compile_kernel(const std::string &src, const char *name, cudaKernel_t &out);
 
 }  // namespace
 
@@ -385,7 +430,7 @@ amy_status expr_compile(const char *const *text, int n, int m_ctrl, int p_dist, 
 
 amy_status expr_fill_means(const ExprProgram &prog, const Geom &g, double *d_mtab, cudaStream_t st) {
     cudaKernel_t k = nullptr;
-    amy_status s = kernel_for(prog.source, k);
+    amy_status s = compile_kernel(prog.source, "amy_expr_means", k);
     if (s != AMY_OK) return s;
     ExprGrid eg;
     memset(&eg, 0, sizeof eg);
@@ -413,6 +458,57 @@ amy_status expr_fill_means(const ExprProgram &prog, const Geom &g, double *d_mta
     const dim3 grid((unsigned)std::min<int64_t>((most + 255) / 256, 4096), (unsigned)g.n);
     const cudaError_t e = cudaLaunchKernel((const void *)k, grid, dim3(256), args, 0, st);
     if (e != cudaSuccess) return cuda_error(e, "mean expressions launch");
+    return AMY_OK;
+}
+
+}  // namespace amy
+
+namespace amy {
+
+amy_status user_tables(const char *const *pdf, const Geom &g, double *d_tab, cudaStream_t st) {
+    if (!pdf) return set_error(AMY_E_INVALID_ARG, "user noise: null density list");
+    std::string src = kUserHead;
+    for (int d = 0; d < g.n; ++d) {
+        if (!pdf[d]) return set_error(AMY_E_INVALID_ARG, "user noise: null density for dim %d", d);
+        if (std::strlen(pdf[d]) > 65536) return set_error(AMY_E_INVALID_ARG, "user noise: density %d too long", d);
+        Parser ps(pdf[d], g.n, 0, 0, 0, true);
+        std::string code, err;
+        uint32_t dx = 0, du = 0;
+        if (!ps.run(code, dx, du, err))
+            return set_error(AMY_E_INVALID_ARG, "user noise, density %d: %s", d, err.c_str());
+        char head[48];
+        snprintf(head, sizeof head, "        case %d: return ", d);
+        src += head + code + ";\n";
+    }
+    src += kUserTail;
+    cudaKernel_t k = nullptr;
+    amy_status s = compile_kernel(src, "amy_user_tables", k);
+    if (s != AMY_OK) return s;
+    struct UserBox {
+        double lo[8], hi[8];
+        int n;
+    } b;
+    memset(&b, 0, sizeof b);
+    for (int d = 0; d < g.n; ++d) {
+        b.lo[d] = g.np[0][d];
+        b.hi[d] = g.np[1][d];
+    }
+    b.n = g.n;
+    void *args[] = {&b, &d_tab};
+    cudaError_t e = cudaLaunchKernel((const void *)k, dim3(1), dim3(32), args, 0, st);
+    if (e != cudaSuccess) return cuda_error(e, "user densities launch");
+    // the tables must describe densities: finite, non-negative, a positive total
+    const size_t per = (size_t)2 * (USER_KNOTS + 1);
+    std::vector<double> host((size_t)g.n * per);
+    e = cudaMemcpyAsync(host.data(), d_tab, host.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "user densities");
+    for (int d = 0; d < g.n; ++d) {
+        const double *F = host.data() + d * per, *f = F + (USER_KNOTS + 1);
+        bool ok = F[USER_KNOTS] == 1.0;
+        for (int i = 0; i <= USER_KNOTS && ok; ++i) ok = std::isfinite(F[i]) && std::isfinite(f[i]) && f[i] >= 0.0;
+        if (!ok) return set_error(AMY_E_INVALID_ARG, "user noise: density %d is not a density on its box", d);
+    }
     return AMY_OK;
 }
 

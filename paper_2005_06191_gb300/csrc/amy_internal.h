@@ -84,6 +84,12 @@ amy_status expr_compile(const char *const *text, int n, int m_ctrl, int p_dist, 
 // the kernel with NVRTC on first use per source, then launches it.
 amy_status expr_fill_means(const ExprProgram &prog, const Geom &g, double *d_mtab, cudaStream_t st);
 
+// User noise densities (amy_expr.cu): compiles the n density texts (the
+// variable t) and fills g.n tables of 2 (USER_KNOTS + 1) doubles at d_tab
+// (the normalised CDF at the knots of the box, then the density there);
+// INVALID_ARG for bad text or a table that is not a density.  Synchronous.
+amy_status user_tables(const char *const *pdf, const Geom &g, double *d_tab, cudaStream_t st);
+
 // Closed-loop Monte-Carlo runs (amy_simulate.cu): n_x0 * runs runs of
 // `horizon` steps under pi[horizon][nx], successes counted per initial state
 // into succ[n_x0] (zeroed by the caller); err bits: 1 an initial state out of

@@ -72,6 +72,8 @@ extern "C" amy_status amy_synthesize_noalloc(const amy_system *sys, const amy_gr
     if (st != AMY_OK) return st;
     if (g.sys == SYS_EXPR)
         return set_error(AMY_E_UNSUPPORTED, "text systems are built with amy_build (their mean tables need a handle)");
+    if (g.noise == NOISE_USER)
+        return set_error(AMY_E_UNSUPPORTED, "user noise densities are built with amy_build (their tables need a handle)");
     SpecDev sd;
     st = make_spec(g, spec, sd);
     if (st != AMY_OK) return st;

@@ -919,6 +919,8 @@ amy_status amy_submit(amy_server s, const amy_request *req, uint64_t *ticket) {
     amy_status st = make_geom(&req->sys, &req->states, &req->inputs, req->sigma, &req->cut, r->g, r->params);
     if (st == AMY_OK && r->g.sys == SYS_EXPR)
         st = set_error(AMY_E_UNSUPPORTED, "text systems are built with amy_build (their mean tables need a handle)");
+    if (st == AMY_OK && r->g.noise == NOISE_USER)
+        st = set_error(AMY_E_UNSUPPORTED, "user noise densities are built with amy_build (their tables need a handle)");
     if (st == AMY_OK) st = make_spec(r->g, &req->spec, r->spec);
     if (st == AMY_OK) st = plan_sep_tables(r->g, r->params, r->tab_words, &r->upart);
     if (st != AMY_OK) {

@@ -92,3 +92,56 @@ def test_noise_invalid_rejected(amy):
         with pytest.raises(amy.AmyError) as e:
             amy.amy_build(p, tmode="otf", prec="fp32")
         assert "INVALID_ARG" in str(e.value), p.noise
+
+
+USER_DENSITIES = [
+    ("bump", "exp(-t*t/(2*0.3*0.3))", -1.2, 1.2),
+    ("triangle", "fmax(0, 0.5 - fabs(t - 0.1))", -0.4, 0.6),
+    ("two humps", "exp(-(t - 0.35)*(t - 0.35)/0.02) + 0.5*exp(-(t + 0.3)*(t + 0.3)/0.05)", -1.0, 1.0),
+]
+
+
+@pytest.mark.parametrize("name,pdf,lo,hi", USER_DENSITIES)
+@pytest.mark.parametrize("n,per_dim", [(2, [31, 27]), (3, [8, 9, 7])])
+def test_user_densities_every_mode(amy, name, pdf, lo, hi, n, per_dim):
+    """The user's density and support box (Sec. 6.2), tabulated at build time
+    (NVRTC) on both sides with the same quadrature and interpolation, in every
+    row mode and precision, against the oracle."""
+    rng = np.random.default_rng(80 + n)
+    w = W.random_affine(rng, n, per_dim, 3, gamma=1e-2, kind=W.REACH_AVOID, horizon=4)
+    p = dataclasses.replace(w.problem, noise="user", noise_params=[[lo] * n, [hi] * n], noise_pdf=[pdf] * n,
+                            name=f"user_{name}_{n}")
+    w = W.with_sizes(w, problem=p)
+    ref = oracle.synthesize(w.problem, w.spec, w.horizon, want_all=True)
+    for tmode in ["otf", "stored_separable", "stored_factored", "stored_full"]:
+        compare_synthesis(amy, w, tmode, "fp32_kahan", ref=ref)
+    compare_synthesis(amy, w, "otf", "fp64", ref=ref)
+    compare_synthesis(amy, w, "stored_full", "fp64", ref=ref)
+    for tmode, prec, tol in [("otf", "fp64", 1e-13), ("stored_separable", "fp32", 2e-6)]:
+        mism, worst = compare_rows(amy, w, tmode, prec, n_pairs=128, seed=4)
+        assert mism == 0 and worst <= tol, (name, tmode, mism, worst)
+
+
+def test_user_density_rejected(amy):
+    base = W.random_affine(np.random.default_rng(2), 2, [9, 9], 3, gamma=1e-2).problem
+    for pdf, lo, hi in [("t", -1.0, 1.0), ("0", -1.0, 1.0), ("exp(t", -1.0, 1.0), ("x0", -1.0, 1.0),
+                        ("1", 1.0, 1.0)]:
+        p = dataclasses.replace(base, noise="user", noise_params=[[lo, lo], [hi, hi]], noise_pdf=[pdf, "1"])
+        with pytest.raises(amy.AmyError) as e:
+            amy.amy_build(p, tmode="otf", prec="fp32")
+        assert "INVALID_ARG" in str(e.value), pdf
+    p = dataclasses.replace(base, noise="user", noise_params=[[-1, -1], [1, 1]], noise_pdf=["1", "1"])
+    srv = amy.amy_server_create(batched=True, max_slots=4)
+    try:
+        with pytest.raises(amy.AmyError) as e:
+            amy.amy_submit(srv, W.with_sizes(W.random_affine(np.random.default_rng(2), 2, [9, 9], 3), problem=p))
+        assert "UNSUPPORTED" in str(e.value)
+    finally:
+        srv.close()
+    import torch
+    V = torch.empty(81, dtype=torch.float32, device="cuda")
+    P = torch.empty(81, dtype=torch.int16, device="cuda")
+    w = W.with_sizes(W.random_affine(np.random.default_rng(2), 2, [9, 9], 3), problem=p)
+    with pytest.raises(amy.AmyError) as e:
+        amy.amy_synthesize_noalloc(w.problem, w.spec, w.horizon, V, P)
+    assert "UNSUPPORTED" in str(e.value)
