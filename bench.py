@@ -50,24 +50,22 @@ UNIT = "transitions/s"
 # DRAM traffic of the dominant kernel per backup, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of the launch, divided by the
 # backups that launch performed).  A figure holds only for the kernel sources
-# it was captured on, so each entry carries the digest of the csrc/ tree at
-# capture time and is reported as null once the sources change.
-# key: (workload, tmode, prec, v_store) -> (digest, bytes per backup, states in
-# the captured launch, profile summary).  A capture on a reduced grid is scaled
-# to the full launch by the number of states (the traffic is V in/out, pi and
-# the mask per state; the tables are a few hundred KB at most).
-# (workload, tmode, prec, v_store) -> (digest of the kernel's header and its
-# includes when measured, DRAM bytes per backup, states of the measured case,
-# profile summary, kernel header); reported as null once the kernel changed
+# it was captured on: each entry carries the digest of the kernel's header and
+# the headers it includes, and is reported as null once they change.  A
+# capture on a reduced grid is scaled to the full launch by the number of
+# states (the traffic is V in/out, pi and the mask per state; the tables are a
+# few hundred KB at most).
+# (workload, tmode, prec, v_store) -> (digest, DRAM bytes per backup, states
+# of the measured case, profile summary, kernel header)
 MEASURED_TRAFFIC = {
-    # k_synth_runs<float,3,3,0>, launch shape 1,288,1,0,3, grid barrier: 715,008 B read +
-    # 87,808 B written per launch of 32 backups
+    # k_synth_runs<float,3,3,0>, launch shape 1,288,1,0,3, grid barrier: 710,656 B read +
+    # 65,024 B written per launch of 32 backups
     ("unicycle", "stored_separable", "fp32", "native"):
-        ("0958ce257213d40a", 25088, 78030, "profiles/k_synth_runs_unicycle_51x51x30.md", "amy_runs.cuh"),
-    # k_backup_tile<float,5> at 18^6 (34,012,224 states): 555,728,384 B read + 474,146,560 B
+        ("a0f7d4cc08dc1935", 24240, 78030, "profiles/k_synth_runs_unicycle_51x51x30.md", "amy_runs.cuh"),
+    # k_backup_tile<float,5> at 18^6 (34,012,224 states): 588,759,552 B read + 556,634,368 B
     # written per backup, scaled to the workload's states (V in and out and their re-fetches)
     ("traffic6", "stored_separable", "fp32_kahan", "native"):
-        ("74b66b3dbc3fe96f", 1029874944, 34012224, "profiles/k_backup_tile_traffic6.md", "amy_tile.cuh"),
+        ("79fb5754b27e9207", 1145393920, 34012224, "profiles/k_backup_tile_traffic6.md", "amy_tile.cuh"),
 }
 
 

@@ -64,6 +64,39 @@ constexpr int PLANE_KU = AMY_PLANE_KU;  // S combinations per step of a batch
 #define AMY_PLANE_S2ROWS 2
 #endif
 constexpr int PLANE_S2ROWS = AMY_PLANE_S2ROWS;
+// Paired FP32 FMAs (two lanes per instruction, each lane rounded as one
+// fmaf): the same values with half the FMA instructions.  Switched per site:
+// kernel 7's stage 1 (windows of at most 3 slots), kernel 8's stage 1, the
+// Z sums of stage 2 two rows at a time, stage 2's single rows (pairs of Z
+// rows).
+#ifndef AMY_FFMA2_P1
+#define AMY_FFMA2_P1 1
+#endif
+#ifndef AMY_FFMA2_T1
+#define AMY_FFMA2_T1 0
+#endif
+#ifndef AMY_FFMA2_S2
+#define AMY_FFMA2_S2 1
+#endif
+#ifndef AMY_FFMA2_S2T
+#define AMY_FFMA2_S2T 0
+#endif
+
+// acc += w * v, lane by lane
+template <bool PAIRED>
+__device__ __forceinline__ void fma4(float w, const float4 &v, float4 &acc) {
+    if constexpr (PAIRED) {
+        const float2 ww = make_float2(w, w);
+        const float2 lo = __ffma2_rn(ww, make_float2(v.x, v.y), make_float2(acc.x, acc.y));
+        const float2 hi = __ffma2_rn(ww, make_float2(v.z, v.w), make_float2(acc.z, acc.w));
+        acc = make_float4(lo.x, lo.y, hi.x, hi.y);
+    } else {
+        acc.x = fmaf(w, v.x, acc.x);
+        acc.y = fmaf(w, v.y, acc.y);
+        acc.z = fmaf(w, v.z, acc.z);
+        acc.w = fmaf(w, v.w, acc.w);
+    }
+}
 
 template <class VT> struct PlaneArgs {
     const VT *Vn;          // V_{k+1} (unused: stage 1 reads the padded copy)
@@ -239,6 +272,53 @@ __device__ __forceinline__ void plane_stage2(const Geom &g, const uint32_t *__re
         }
         return in;
     };
+#if AMY_FFMA2_S2
+    // affine windows: the Z sums of two staged rows at once, each row's terms
+    // in the order zsum takes them
+    auto zsum2 = [&](const float *ra, const float *rc) {
+        float2 in = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int k0 = 0; k0 < WM; ++k0) {
+            const float *pa = ra + zb + k0 * Nz1, *pc = rc + zb + k0 * Nz1;
+            float2 q = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int k1 = 0; k1 < WM; ++k1)
+                q = __ffma2_rn(make_float2(tz1[k1], tz1[k1]), make_float2(pa[k1], pc[k1]), q);
+            in = __ffma2_rn(make_float2(tz0[k0], tz0[k0]), q, in);
+        }
+        return in;
+    };
+#endif
+    // one row's Z sum with its Z rows taken in pairs (the same chains as zsum)
+    auto zsum_row = [&](const float *row) {
+#if AMY_FFMA2_S2T
+        if (affine) {
+            const float *rz = row + zb;
+            float q[WM];
+#pragma unroll
+            for (int k0 = 0; k0 + 1 < WM; k0 += 2) {
+                float2 qq = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int k1 = 0; k1 < WM; ++k1)
+                    qq = __ffma2_rn(make_float2(tz1[k1], tz1[k1]),
+                                    make_float2(rz[k0 * Nz1 + k1], rz[(k0 + 1) * Nz1 + k1]), qq);
+                q[k0] = qq.x;
+                q[k0 + 1] = qq.y;
+            }
+            if (WM % 2) {
+                float qq = 0.0f;
+#pragma unroll
+                for (int k1 = 0; k1 < WM; ++k1) qq = fmaf(tz1[k1], rz[(WM - 1) * Nz1 + k1], qq);
+                q[WM - 1] = qq;
+            }
+            float in = 0.0f;
+#pragma unroll
+            for (int k0 = 0; k0 < WM; ++k0) in = fmaf(tz0[k0], q[k0], in);
+            return in;
+        }
+#endif
+        return zsum(row);
+    };
     auto add_row = [&](float w, float in) {
         accum_row(acc, comp, __fmul_rn(w, in), kahan);
         if (count) {
@@ -267,8 +347,23 @@ __device__ __forceinline__ void plane_stage2(const Geom &g, const uint32_t *__re
                     any = any || wr[q] != 0.0f;
                 }
                 if (!any) continue;
+#if AMY_FFMA2_S2
+                if (affine) {
 #pragma unroll
-                for (int q = 0; q < PLANE_S2ROWS; ++q) in[q] = zsum(r0 + (int64_t)(j1 + q) * rs1 * Ppad);
+                    for (int q = 0; q + 1 < PLANE_S2ROWS; q += 2) {
+                        const float2 s2 = zsum2(r0 + (int64_t)(j1 + q) * rs1 * Ppad,
+                                                r0 + (int64_t)(j1 + q + 1) * rs1 * Ppad);
+                        in[q] = s2.x;
+                        in[q + 1] = s2.y;
+                    }
+                    if (PLANE_S2ROWS % 2)
+                        in[PLANE_S2ROWS - 1] = zsum_row(r0 + (int64_t)(j1 + PLANE_S2ROWS - 1) * rs1 * Ppad);
+                } else
+#endif
+                {
+#pragma unroll
+                    for (int q = 0; q < PLANE_S2ROWS; ++q) in[q] = zsum(r0 + (int64_t)(j1 + q) * rs1 * Ppad);
+                }
 #pragma unroll
                 for (int q = 0; q < PLANE_S2ROWS; ++q)
                     if (wr[q] != 0.0f) add_row(wr[q], in[q]);
@@ -276,7 +371,7 @@ __device__ __forceinline__ void plane_stage2(const Geom &g, const uint32_t *__re
 #pragma unroll 1
             for (; j1 < Wb[1]; ++j1) {
                 const float wa = __fmul_rn(w0, __uint_as_float(__ldg(rb[1] + 1 + j1)));
-                if (wa != 0.0f) add_row(wa, zsum(r0 + (int64_t)j1 * rs1 * Ppad));
+                if (wa != 0.0f) add_row(wa, zsum_row(r0 + (int64_t)j1 * rs1 * Ppad));
             }
             continue;
         }
@@ -287,7 +382,7 @@ __device__ __forceinline__ void plane_stage2(const Geom &g, const uint32_t *__re
             for (int j2 = 0; j2 < Wb[2]; ++j2) {
                 const float w = nB > 2 ? __fmul_rn(w1, __uint_as_float(__ldg(rb[2] + 1 + j2))) : w1;
                 if (w == 0.0f) continue;
-                add_row(w, zsum(Rg + (int64_t)(y0 * rs0 + (ys[1] + j1) * rs1 + (ys[2] + j2)) * Ppad));
+                add_row(w, zsum_row(Rg + (int64_t)(y0 * rs0 + (ys[1] + j1) * rs1 + (ys[2] + j2)) * Ppad));
             }
         }
     }
@@ -496,12 +591,7 @@ __global__ void __launch_bounds__(PLANE_MAX_THREADS, 2) k_backup_plane(const __g
                         for (int q = 0; q < PLANE_KU; ++q) {
                             const float w = ws[k + q];
 #pragma unroll
-                            for (int i = 0; i < PLANE_EB; ++i) {
-                                r[i].x = fmaf(w, v[q][i].x, r[i].x);
-                                r[i].y = fmaf(w, v[q][i].y, r[i].y);
-                                r[i].z = fmaf(w, v[q][i].z, r[i].z);
-                                r[i].w = fmaf(w, v[q][i].w, r[i].w);
-                            }
+                            for (int i = 0; i < PLANE_EB; ++i) fma4<AMY_FFMA2_P1 != 0 && WM <= 3>(w, v[q][i], r[i]);
                         }
                     }
                     for (; k < K; ++k) {
@@ -509,11 +599,7 @@ __global__ void __launch_bounds__(PLANE_MAX_THREADS, 2) k_backup_plane(const __g
                         const int32_t o = os[k];
 #pragma unroll
                         for (int i = 0; i < PLANE_EB; ++i) {
-                            const float4 v = vload4<VT>(pr[i] + o);
-                            r[i].x = fmaf(w, v.x, r[i].x);
-                            r[i].y = fmaf(w, v.y, r[i].y);
-                            r[i].z = fmaf(w, v.z, r[i].z);
-                            r[i].w = fmaf(w, v.w, r[i].w);
+                            fma4<AMY_FFMA2_P1 != 0 && WM <= 3>(w, vload4<VT>(pr[i] + o), r[i]);
                         }
                     }
 #pragma unroll

@@ -314,10 +314,7 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, TILE_MINB) k_backup_tile(con
                             const int j = ii - (s_owo[gg] - owlo);
                             if (gg < Tt && j >= 0 && j < Wow) {
                                 const float w = s_oww[gg * 16 + j];
-                                r[gg].x = fmaf(w, pa.x, r[gg].x);
-                                r[gg].y = fmaf(w, pa.y, r[gg].y);
-                                r[gg].z = fmaf(w, pa.z, r[gg].z);
-                                r[gg].w = fmaf(w, pa.w, r[gg].w);
+                                fma4<AMY_FFMA2_T1 != 0>(w, pa, r[gg]);
                             }
                         }
                     };
@@ -345,28 +342,16 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, TILE_MINB) k_backup_tile(con
 #pragma unroll
                                 for (int kk = 0; kk < TILE_KU; ++kk) {
                                     const float w = s_shw[k + kk];
-                                    p0.x = fmaf(w, va[kk].x, p0.x);
-                                    p0.y = fmaf(w, va[kk].y, p0.y);
-                                    p0.z = fmaf(w, va[kk].z, p0.z);
-                                    p0.w = fmaf(w, va[kk].w, p0.w);
-                                    p1.x = fmaf(w, vc[kk].x, p1.x);
-                                    p1.y = fmaf(w, vc[kk].y, p1.y);
-                                    p1.z = fmaf(w, vc[kk].z, p1.z);
-                                    p1.w = fmaf(w, vc[kk].w, p1.w);
+                                    fma4<AMY_FFMA2_T1 != 0>(w, va[kk], p0);
+                                    fma4<AMY_FFMA2_T1 != 0>(w, vc[kk], p1);
                                 }
                             }
                             for (; k < a.Ksh; ++k) {
                                 const int32_t o = s_sho[k];
                                 const float w = s_shw[k];
                                 const float4 va = vload4<VT>(v0 + o), vc = vload4<VT>(v1 + o);
-                                p0.x = fmaf(w, va.x, p0.x);
-                                p0.y = fmaf(w, va.y, p0.y);
-                                p0.z = fmaf(w, va.z, p0.z);
-                                p0.w = fmaf(w, va.w, p0.w);
-                                p1.x = fmaf(w, vc.x, p1.x);
-                                p1.y = fmaf(w, vc.y, p1.y);
-                                p1.z = fmaf(w, vc.z, p1.z);
-                                p1.w = fmaf(w, vc.w, p1.w);
+                                fma4<AMY_FFMA2_T1 != 0>(w, va, p0);
+                                fma4<AMY_FFMA2_T1 != 0>(w, vc, p1);
                             }
                             apply(ii, p0);
                             apply(ii + 1, p1);
@@ -382,19 +367,12 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, TILE_MINB) k_backup_tile(con
 #pragma unroll
                                 for (int kk = 0; kk < TILE_KU; ++kk) {
                                     const float w = s_shw[k + kk];
-                                    p0.x = fmaf(w, va[kk].x, p0.x);
-                                    p0.y = fmaf(w, va[kk].y, p0.y);
-                                    p0.z = fmaf(w, va[kk].z, p0.z);
-                                    p0.w = fmaf(w, va[kk].w, p0.w);
+                                    fma4<AMY_FFMA2_T1 != 0>(w, va[kk], p0);
                                 }
                             }
                             for (; k < a.Ksh; ++k) {
                                 const float w = s_shw[k];
-                                const float4 va = vload4<VT>(v0 + s_sho[k]);
-                                p0.x = fmaf(w, va.x, p0.x);
-                                p0.y = fmaf(w, va.y, p0.y);
-                                p0.z = fmaf(w, va.z, p0.z);
-                                p0.w = fmaf(w, va.w, p0.w);
+                                fma4<AMY_FFMA2_T1 != 0>(w, vload4<VT>(v0 + s_sho[k]), p0);
                             }
                             apply(ii, p0);
                         }
