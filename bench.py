@@ -62,10 +62,10 @@ MEASURED_TRAFFIC = {
     # 65,024 B written per launch of 32 backups
     ("unicycle", "stored_separable", "fp32", "native"):
         ("a0f7d4cc08dc1935", 24240, 78030, "profiles/k_synth_runs_unicycle_51x51x30.md", "amy_runs.cuh"),
-    # k_backup_tile<float,5> at 18^6 (34,012,224 states): 588,759,552 B read + 556,634,368 B
+    # k_backup_tile<float,5> at 18^6 (34,012,224 states): 597,405,440 B read + 563,790,848 B
     # written per backup, scaled to the workload's states (V in and out and their re-fetches)
     ("traffic6", "stored_separable", "fp32_kahan", "native"):
-        ("79fb5754b27e9207", 1145393920, 34012224, "profiles/k_backup_tile_traffic6.md", "amy_tile.cuh"),
+        ("1048333ee2290287", 1161196288, 34012224, "profiles/k_backup_tile_traffic6.md", "amy_tile.cuh"),
 }
 
 
