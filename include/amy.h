@@ -549,6 +549,15 @@ amy_status amy_measure_lane_loads(double *shared_per_s, double *global_per_s);
  * INVALID_ARG (null pointer), CUDA. */
 amy_status amy_measure_fma(double *fp32_per_s, double *fp64_per_s);
 
+/* Measured complementary error function rates of the current device, erfcf
+ * (FP32) and erfc (FP64), in evaluations per second summed over all threads
+ * (independent arguments spread over [0, 4.1], the tail-side arguments of the
+ * cell masses of Algorithm 1; neighbouring lanes at different arguments, every
+ * SM full): the ceiling of a backup that forms its masses on the fly, each
+ * (state, input) pair taking sum_i (W_i + 1) edge values.  Takes a few
+ * milliseconds.  Errors: INVALID_ARG (null pointer), CUDA. */
+amy_status amy_measure_erfc(double *fp32_per_s, double *fp64_per_s);
+
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of independent synthesis requests.
  * A scheduler thread admits queued requests while slots and device memory

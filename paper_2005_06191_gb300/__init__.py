@@ -474,6 +474,15 @@ def amy_measure_fma() -> dict:
     return {"fp32": f32.value, "fp64": f64.value}
 
 
+def amy_measure_erfc() -> dict:
+    """amy_measure_erfc: measured erfcf (FP32) and erfc (FP64) evaluation
+    rates (per second over the whole device; the ceiling of mass tables formed
+    on the fly)."""
+    f32, f64 = C.c_double(0.0), C.c_double(0.0)
+    _check(_lib().amy_measure_erfc(C.byref(f32), C.byref(f64)))
+    return {"fp32": f32.value, "fp64": f64.value}
+
+
 def amy_synthesize_noalloc(problem, spec, horizon: int, V_out, policy_out=None, prec: str = "fp32",
                            stream=None) -> None:
     """amy_synthesize_noalloc: on-the-fly synthesis whose intermediate device
@@ -503,7 +512,7 @@ from .serving import (AmyServer, amy_cancel, amy_poll, amy_result_free,  # noqa:
 __all__ = [
     "AmyError", "AmyHandle", "AmyServer", "amy_build", "amy_synthesize", "amy_backup_step",
     "amy_query_rows", "amy_simulate", "amy_export_prism", "amy_info", "amy_destroy", "amy_grid_count", "amy_last_error",
-    "amy_rebuild", "amy_set_profiling", "amy_set_wait_limit", "amy_set_step_wait", "amy_set_plane", "amy_backup_work", "amy_measure_l2", "amy_kernel_times", "amy_synthesize_noalloc", "amy_measure_lane_loads", "amy_measure_fma",
+    "amy_rebuild", "amy_set_profiling", "amy_set_wait_limit", "amy_set_step_wait", "amy_set_plane", "amy_backup_work", "amy_measure_l2", "amy_kernel_times", "amy_synthesize_noalloc", "amy_measure_lane_loads", "amy_measure_fma", "amy_measure_erfc",
     "amy_server_create", "amy_submit", "amy_poll", "amy_wait", "amy_cancel", "amy_server_stats",
     "amy_server_graph_stats",
     "amy_server_destroy", "amy_result_free", "TMODES", "PRECS", "VSTORES", "POLICY_NONE",

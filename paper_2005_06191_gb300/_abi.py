@@ -112,6 +112,7 @@ PROTOTYPES = {
     "amy_last_error": (C.c_char_p, []),
     "amy_measure_lane_loads": (C.c_int32, [DP, DP]),
     "amy_measure_fma": (C.c_int32, [DP, DP]),
+    "amy_measure_erfc": (C.c_int32, [DP, DP]),
     "amy_synthesize_noalloc": (C.c_int32, [C.POINTER(amy_system), C.POINTER(amy_grid), C.POINTER(amy_grid), DP,
                                            C.POINTER(amy_cut), C.c_int32, C.POINTER(amy_spec), C.c_int32,
                                            C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -1,5 +1,6 @@
 // amy_calibrate.cu -- measured ceilings used as roofline denominators: the
-// FP32 and FP64 fused multiply-add issue rates, and the two load paths the
+// FP32 and FP64 fused multiply-add issue rates, the FP32 and FP64 erfc
+// evaluation rates, the L2 read bandwidth, and the two load paths the
 // fused backup kernels gather V through:
 //   - shared memory: 32-bit loads, every warp reading 32 consecutive words
 //     (one wavefront per instruction, no bank conflict);
@@ -69,6 +70,35 @@ __global__ void __launch_bounds__(FMA_THREADS) k_cal_fma(R b, R c, int iters, R 
 #pragma unroll
     for (int i = 0; i < FMA_CHAINS; ++i) s += acc[i];
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// Complementary error function throughput: every thread evaluates erfc at
+// ERFC_CHAINS independent arguments per step, spread over [0, 4.1] (the
+// tail-side arguments (edge - mu) / (sigma sqrt 2) the cell masses take),
+// neighbouring lanes at different arguments as in the mass kernels; the
+// arguments depend on runtime values only, and the sums are written out.
+constexpr int ERFC_THREADS = 256;
+constexpr int ERFC_CHAINS = 4;
+
+template <class R>
+__global__ void __launch_bounds__(ERFC_THREADS) k_cal_erfc(R dx, int iters, R *__restrict__ out) {
+    R x[ERFC_CHAINS], s[ERFC_CHAINS];
+#pragma unroll
+    for (int i = 0; i < ERFC_CHAINS; ++i) {
+        x[i] = (R)((threadIdx.x & 31) + 32 * i) * (R)(4.0 / 128.0);
+        s[i] = (R)0;
+    }
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < ERFC_CHAINS; ++i) {
+            s[i] += erfc(x[i]);
+            x[i] += dx;
+        }
+    }
+    R t = 0;
+#pragma unroll
+    for (int i = 0; i < ERFC_CHAINS; ++i) t += s[i];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = t;
 }
 
 // L2 read bandwidth: 16-byte loads at L2 (not cached in L1) over a buffer
@@ -234,5 +264,50 @@ extern "C" amy_status amy_measure_lane_loads(double *shared_per_s, double *globa
     if (e != cudaSuccess) return cuda_error(e, "lane-load calibration");
     *shared_per_s = rate[0];
     *global_per_s = rate[1];
+    return AMY_OK;
+}
+
+extern "C" amy_status amy_measure_erfc(double *fp32_per_s, double *fp64_per_s) {
+    if (!fp32_per_s || !fp64_per_s) return set_error(AMY_E_INVALID_ARG, "null argument");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_error(e, "device query");
+    const int blocks = sms * 8;  // 2048 threads per SM
+    double *out = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&out, (size_t)blocks * ERFC_THREADS * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    double rate[2] = {0.0, 0.0};
+    for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
+        const int iters = which == 0 ? 256 : 32;  // x stays below 4 + iters * dx
+        float best = 3.4e38f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // first pass warms up
+            e = cudaEventRecord(a, st);
+            if (which == 0)
+                k_cal_erfc<float><<<blocks, ERFC_THREADS, 0, st>>>(1e-4f, iters, reinterpret_cast<float *>(out));
+            else
+                k_cal_erfc<double><<<blocks, ERFC_THREADS, 0, st>>>(1e-4, iters, out);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(b, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+            if (e == cudaSuccess && rep > 0 && ms < best) best = ms;
+        }
+        const double evals = (double)blocks * ERFC_THREADS * ERFC_CHAINS * iters;
+        rate[which] = evals / (best * 1e-3);
+    }
+    if (out) cudaFreeAsync(out, st);
+    if (st) cudaStreamSynchronize(st);
+    if (st) cudaStreamDestroy(st);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_error(e, "erfc calibration");
+    *fp32_per_s = rate[0];
+    *fp64_per_s = rate[1];
     return AMY_OK;
 }

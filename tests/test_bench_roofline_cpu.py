@@ -116,3 +116,26 @@ def test_plane_kernel_roofline_from_counted_work(monkeypatch):
     r16 = bench.roofline(_args("traffic6", "stored_separable", "fp32", "bf16"), w, info, 100.0, 0, lanes, work)
     l2c = [c for c in [r16] + r16["other_ceilings"] if c["bound"] == "l2"][0]
     assert l2c["achieved"] == pytest.approx(4e9 * 2 / 0.1 / 1e9)
+
+
+def test_on_the_fly_counts_erfc_edges(monkeypatch):
+    """Rows on the fly: sum_i (W_i + 1) erfc edge values per (free state,
+    input) pair against the measured erfc rate; the closest ceiling binds."""
+    monkeypatch.setattr(bench, "peaks", lambda: {"hbm_gbs": 6790.0, "source": "test"})
+    w = W.robot_lin()
+    nx, nu = w.problem.n_states, w.problem.n_inputs
+    info = _info(2, [41, 41], kernel=6)
+    evals = nx * nu * (41 + 1 + 41 + 1)
+    slow = dict(LANES, fma_fp64=0.62e12, erfc_fp64=1e9)
+    r = bench.roofline(_args("robot", "otf", "fp64"), w, info, 2.0, nx, slow)
+    assert r["unit"] == "G erfc/s (FP64)" and r["algorithmic_erfc_per_backup"] == evals
+    assert r["achieved"] == pytest.approx(evals / 2.0e-3 / 1e9)
+    assert len(r["other_ceilings"]) == 2 and r["frac"] >= max(c["frac"] for c in r["other_ceilings"])
+    fast = dict(LANES, fma_fp64=0.62e12, erfc_fp64=1e15)
+    r2 = bench.roofline(_args("robot", "otf", "fp64"), w, info, 2.0, nx, fast)
+    assert not r2["unit"].startswith("G erfc") and r2["other_ceilings"][-1]["unit"] == "G erfc/s (FP64)"
+    r32 = bench.roofline(_args("robot", "otf", "fp32"), w, info, 0.1, nx, dict(LANES, fma_fp32=38e12, erfc_fp32=1e9))
+    assert r32["unit"] == "G erfc/s (FP32)"
+    # stored rows and non-Gaussian noise take no erfc ceiling
+    r3 = bench.roofline(_args("robot", "stored_full", "fp64"), w, info, 2.0, nx, slow)
+    assert "other_ceilings" not in r3

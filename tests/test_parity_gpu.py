@@ -614,3 +614,6 @@ def test_backup_kernel_reported_and_lane_load_ceilings(amy):
     # FP32: 152 SMs x 128 lanes x ~2 GHz is about 4e13 FMA/s; FP64 far below it
     fma = amy.amy_measure_fma()
     assert 1e13 < fma["fp32"] < 1e14 and 1e10 < fma["fp64"] < fma["fp32"], fma
+    # erfc: tens of instructions per evaluation, so well below the FMA rates
+    erfc = amy.amy_measure_erfc()
+    assert 1e10 < erfc["fp32"] < fma["fp32"] and 1e8 < erfc["fp64"] < min(erfc["fp32"], fma["fp64"]), erfc
