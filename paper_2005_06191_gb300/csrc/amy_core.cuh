@@ -399,38 +399,72 @@ __device__ __forceinline__ void dim_masses_f32(const Geom &g, int d, double mu, 
     }
 }
 
-// FP64 path: each cell's mass from its own two edges, as in Algorithm 1.
-// Slot k of dim d's window (origin o, kmax slots kept): its mass and V offset.
+// FP64 path, Algorithm 1's cell integral.  Edge k of dim d's window (origin
+// o) lies at c(o + k) - eta/2, so that a cell's upper edge is the next cell's
+// lower edge (c(o + k) + eta/2 up to rounding) and a run of cells evaluates
+// each edge's tail once.  Edges are kept relative to the mean: t = edge - mu.
+__device__ __forceinline__ double edge_rel_f64(const Geom &g, int d, double mu, int32_t o, int k) {
+    return dsub(dsub(state_centre(g, d, o + k), dmul(0.5, g.eta[d])), mu);
+}
+
+// sigma * sqrt(2) of dim d's Gaussian noise at a state whose centre in dim d
+// is xd (0 for multiplicative noise at xd = 0: no noise)
+__device__ __forceinline__ double gauss_k2_f64(const Geom &g, int d, double xd) {
+    return g.noise == NOISE_GAUSSIAN ? g.k2[d] : dmul(dmul(g.np[0][d], fabs(xd)), 1.4142135623730951);
+}
+
+// Gaussian tail beyond edge t, away from the mean: erfc(|t| / k2) / 2
+__device__ __forceinline__ double gauss_tail_f64(double t, double k2) {
+    return k2 == 0.0 ? 0.0 : 0.5 * erfc(ddiv(fabs(t), k2));
+}
+
+// Mass of the cell with edges tlo < thi (minus the mean) from their tails:
+// the difference of the tails on the same side of the mean, or one minus
+// both tails when the cell holds the mean
+__device__ __forceinline__ double gauss_cell_f64(double tlo, double thi, double qlo, double qhi, double k2) {
+    if (k2 == 0.0) return (tlo <= 0.0 && 0.0 < thi) ? 1.0 : 0.0;
+    if (tlo >= 0.0) return qlo - qhi;
+    if (thi <= 0.0) return qhi - qlo;
+    return 1.0 - qlo - qhi;
+}
+
+// Slots [k0, k1) of dim d's window (origin o, kmax slots kept): put(k, mass,
+// V offset) for each, every edge evaluated once.  A slot's values do not
+// depend on the run it is evaluated in.
+template <class Put>
+__device__ __forceinline__ void slot_run_f64(const Geom &g, int d, double mu, int32_t o, int kmax, int k0, int k1,
+                                             double xd, Put &&put) {
+    const bool gauss = g.noise == NOISE_GAUSSIAN || g.noise == NOISE_MULT_GAUSSIAN;
+    const double k2 = gauss ? gauss_k2_f64(g, d, xd) : 0.0;
+    double tlo = edge_rel_f64(g, d, mu, o, k0);
+    double qlo = gauss ? gauss_tail_f64(tlo, k2) : 0.0;
+    for (int k = k0; k < k1; ++k) {
+        const double thi = edge_rel_f64(g, d, mu, o, k + 1);
+        const double qhi = gauss ? gauss_tail_f64(thi, k2) : 0.0;
+        const double mass = gauss ? gauss_cell_f64(tlo, thi, qlo, qhi, k2) : noise_mass<double>(g, d, tlo, thi);
+        bool on;
+        const int32_t cell = cell_of(g, d, o + k, on);
+        put(k, (on && k < kmax) ? mass : 0.0, cell * g.stride[d]);
+        tlo = thi;
+        qlo = qhi;
+    }
+}
+
+// Slot k of dim d's window on its own: its mass and V offset.
 __device__ __forceinline__ void slot_mass_f64(const Geom &g, int d, double mu, int32_t o, int kmax, int k, double xd,
                                               double &fac, int32_t &off) {
-    const double h = dmul(0.5, g.eta[d]);
-    const double c = state_centre(g, d, o + k);
-    const double elo = dsub(c, h), ehi = dadd(c, h);
-    double mass;
-    if (g.noise == NOISE_GAUSSIAN || g.noise == NOISE_MULT_GAUSSIAN) {
-        const double k2 = g.noise == NOISE_GAUSSIAN ? g.k2[d] : dmul(dmul(g.np[0][d], fabs(xd)), 1.4142135623730951);
-        if (k2 == 0.0)
-            mass = (elo <= mu && mu < ehi) ? 1.0 : 0.0;
-        else if (elo >= mu)
-            mass = 0.5 * erfc(ddiv(dsub(elo, mu), k2)) - 0.5 * erfc(ddiv(dsub(ehi, mu), k2));
-        else if (ehi <= mu)
-            mass = 0.5 * erfc(ddiv(dsub(mu, ehi), k2)) - 0.5 * erfc(ddiv(dsub(mu, elo), k2));
-        else
-            mass = 1.0 - 0.5 * erfc(ddiv(dsub(mu, elo), k2)) - 0.5 * erfc(ddiv(dsub(ehi, mu), k2));
-    } else {
-        mass = noise_mass<double>(g, d, dsub(elo, mu), dsub(ehi, mu));
-    }
-    bool on;
-    const int32_t cell = cell_of(g, d, o + k, on);
-    fac = (on && k < kmax) ? mass : 0.0;
-    off = cell * g.stride[d];
+    slot_run_f64(g, d, mu, o, kmax, k, k + 1, xd, [&](int, double m, int32_t f) {
+        fac = m;
+        off = f;
+    });
 }
 
 __device__ __forceinline__ void dim_masses_f64(const Geom &g, int d, double mu, int32_t o, double xd,
                                                double *fac, int32_t *off) {
-    const int W = g.W[d];
-    const int kmax = kept_upper(g, d, mu, o);
-    for (int k = 0; k < W; ++k) slot_mass_f64(g, d, mu, o, kmax, k, xd, fac[k], off[k]);
+    slot_run_f64(g, d, mu, o, kept_upper(g, d, mu, o), 0, g.W[d], xd, [&](int k, double m, int32_t f) {
+        fac[k] = m;
+        off[k] = f;
+    });
 }
 
 // One slot of dim_masses_f32 on its own: the same edge values (edge k is
@@ -456,6 +490,41 @@ __device__ __forceinline__ void slot_mass_f32(const Geom &g, int d, double mu, i
     const int32_t cell = cell_of(g, d, o + k, on);
     fac = (on && k < kmax) ? fmaxf(mass, 0.0f) : 0.0f;
     off = cell * g.stride[d];
+}
+
+// Slots [k0, k1) of dim d's window in FP32, each edge's tail evaluated once:
+// the values slot_mass_f32 gives one slot at a time.
+template <class Put>
+__device__ __forceinline__ void slot_run_f32(const Geom &g, int d, double mu, int32_t o, int kmax, int k0, int k1,
+                                             double xd, Put &&put) {
+    const double c0 = state_centre(g, d, o);
+    const float e0 = (float)dsub(dsub(c0, dmul(0.5, g.eta[d])), mu);
+    const float etaf = (float)g.eta[d];
+    const bool gauss = g.noise == NOISE_GAUSSIAN || g.noise == NOISE_MULT_GAUSSIAN;
+    const float r = gauss ? gauss_r_f32(g, d, xd) : 0.0f;
+    float dlo = k0 == 0 ? e0 : fmaf((float)k0, etaf, e0);
+    float tlo = gauss ? 0.5f * erfcf(fabsf(dlo) * r) : 0.0f;
+    for (int k = k0; k < k1; ++k) {
+        const float dhi = fmaf((float)(k + 1), etaf, e0);
+        const float thi = gauss ? 0.5f * erfcf(fabsf(dhi) * r) : 0.0f;
+        const float mass = gauss ? gauss_cell_f32(dlo, dhi, tlo, thi, r) : noise_mass<float>(g, d, dlo, dhi);
+        bool on;
+        const int32_t cell = cell_of(g, d, o + k, on);
+        put(k, (on && k < kmax) ? fmaxf(mass, 0.0f) : 0.0f, cell * g.stride[d]);
+        dlo = dhi;
+        tlo = thi;
+    }
+}
+
+template <class Put>
+__device__ __forceinline__ void slot_run(const Geom &g, int d, double mu, int32_t o, int kmax, int k0, int k1,
+                                         double xd, Put &&put, double) {
+    slot_run_f64(g, d, mu, o, kmax, k0, k1, xd, put);
+}
+template <class Put>
+__device__ __forceinline__ void slot_run(const Geom &g, int d, double mu, int32_t o, int kmax, int k0, int k1,
+                                         double xd, Put &&put, float) {
+    slot_run_f32(g, d, mu, o, kmax, k0, k1, xd, put);
 }
 
 __device__ __forceinline__ void slot_mass(const Geom &g, int d, double mu, int32_t o, int kmax, int k, double xd,

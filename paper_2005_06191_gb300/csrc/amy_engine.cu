@@ -482,36 +482,37 @@ int choose_tile(int32_t nx, int32_t nu, int sm_count) {
 
 // ---------------------------------------------------------------------------
 // Stored-row construction for wide windows with few pairs (where one thread
-// per pair leaves the GPU idle): one thread per (window slot, pair) computes
-// that slot's mass (the mean and origin in FP64, the mass as dim_masses does)
-// into F[slot][pair] -- the factored layout -- and the first slot of each dim
-// writes the pair's origin; k_build_expand then forms each full-row entry as
-// the product of its dims' masses in the order k_build multiplies them.
+// per pair leaves the GPU idle): one thread per (run of BUILD_RUN window
+// slots, pair) computes those slots' masses (the mean and origin in FP64, the
+// masses as dim_masses does, each edge evaluated once) into F[slot][pair] --
+// the factored layout -- and the run holding a dim's first slot writes the
+// pair's origin; k_build_expand then forms each full-row entry as the product
+// of its dims' masses in the order k_build multiplies them.
 // ---------------------------------------------------------------------------
+constexpr int BUILD_RUN = 8;
 template <class R>
 __global__ void __launch_bounds__(256) k_build_slots(const __grid_constant__ Geom g, R *__restrict__ F,
                                                      int16_t *__restrict__ O, int64_t npairs) {
-    const int64_t total = (int64_t)g.wsum * npairs;
+    const int nruns = (g.wsum + BUILD_RUN - 1) / BUILD_RUN;
+    const int64_t total = (int64_t)nruns * npairs;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t sl = (int32_t)(i / npairs);
-        const int64_t pair = i - (int64_t)sl * npairs;
+        const int32_t r = (int32_t)(i / npairs);
+        const int64_t pair = i - (int64_t)r * npairs;
         const int32_t u = (int32_t)(pair / g.nx);
         const int32_t x = (int32_t)(pair - (int64_t)u * g.nx);
-        int d = 0, b = 0;
-        while (sl >= b + g.W[d]) {
-            b += g.W[d];
-            ++d;
-        }
         double mu[MAXD];
         mean_of(g, x, u, mu);
-        const int32_t o = origin_of(g, d, mu[d]);
-        const int kmax = kept_upper(g, d, mu[d], o);
-        R m;
-        int32_t off;
-        slot_mass(g, d, mu[d], o, kmax, sl - b, noise_centre(g, x, d), m, off);
-        F[i] = m;
-        if (sl == b) O[(int64_t)d * npairs + pair] = (int16_t)o;
+        const int s0 = r * BUILD_RUN, s1 = min(g.wsum, s0 + BUILD_RUN);
+        int b = 0;
+        for (int d = 0; d < g.n && b < s1; b += g.W[d], ++d) {
+            const int k0 = max(s0 - b, 0), k1 = min(s1 - b, g.W[d]);
+            if (k0 >= k1) continue;
+            const int32_t o = origin_of(g, d, mu[d]);
+            slot_run(g, d, mu[d], o, kept_upper(g, d, mu[d], o), k0, k1, noise_centre(g, x, d),
+                     [&](int k, R m, int32_t) { F[(int64_t)(b + k) * npairs + pair] = m; }, R(0));
+            if (k0 == 0) O[(int64_t)d * npairs + pair] = (int16_t)o;
+        }
     }
 }
 
@@ -1072,7 +1073,7 @@ amy_status launch_build(amy_handle_s *h) {
         return st;
     }
     if (h->slot_build) {
-        const int64_t items = (int64_t)h->g.wsum * h->npairs;
+        const int64_t items = (int64_t)((h->g.wsum + BUILD_RUN - 1) / BUILD_RUN) * h->npairs;
         const int bs = (int)std::min<int64_t>((items + 255) / 256, (int64_t)h->sm_count * 64);
         R *F = h->tmode == AMY_T_STORED_FULL ? (R *)h->d_bfac : (R *)h->d_T;
         k_build_slots<R><<<bs, 256, 0, h->stream>>>(h->g, F, h->d_O, h->npairs);

@@ -470,8 +470,8 @@ __global__ void __launch_bounds__(32 * ROWS_MAX_GROUPS) k_backup_rows(const __gr
 }
 
 // The same split for rows on the fly.  The pair's masses are computed once
-// per block and shared: group q evaluates the slots q, q + G, ... of the
-// concatenated per-dim windows (the mean and origins in FP64, each slot's
+// per block and shared: group q evaluates a contiguous share of the slots of
+// the concatenated per-dim windows (the mean and origins in FP64, each slot's
 // mass as dim_masses computes it) into shared memory, laid out [slot][lane]
 // so that the row sums read them without bank conflicts; then every group
 // sums its window rows from there.
@@ -490,18 +490,20 @@ __global__ void __launch_bounds__(32 * ROWS_MAX_GROUPS) k_backup_rows_otf(const 
     if (live) {
         double mu[MAXD];
         mean_of(g, x, u, mu);
-        int d = 0, b = 0;
-        int32_t o = origin_of(g, 0, mu[0]);
-        int kmax = kept_upper(g, 0, mu[0], o);
-        for (int sl = q; sl < g.wsum; sl += G) {
-            while (sl >= b + g.W[d]) {
-                b += g.W[d];
-                ++d;
-                o = origin_of(g, d, mu[d]);
-                kmax = kept_upper(g, d, mu[d], o);
-            }
-            slot_mass(g, d, mu[d], o, kmax, sl - b, noise_centre(g, x, d), sfac[sl * 32 + lane],
-                      soff[sl * 32 + lane]);
+        // group q takes a contiguous share of the concatenated slots, so that
+        // neighbouring slots of a dim share their edge evaluations
+        const int s0 = (int)((int64_t)g.wsum * q / G), s1 = (int)((int64_t)g.wsum * (q + 1) / G);
+        int b = 0;
+        for (int d = 0; d < g.n && b < s1; b += g.W[d], ++d) {
+            const int k0 = max(s0 - b, 0), k1 = min(s1 - b, g.W[d]);
+            if (k0 >= k1) continue;
+            const int32_t o = origin_of(g, d, mu[d]);
+            slot_run(g, d, mu[d], o, kept_upper(g, d, mu[d], o), k0, k1, noise_centre(g, x, d),
+                     [&](int k, R m, int32_t f) {
+                         sfac[(b + k) * 32 + lane] = m;
+                         soff[(b + k) * 32 + lane] = f;
+                     },
+                     R(0));
         }
     }
     __syncthreads();
