@@ -470,9 +470,11 @@ __global__ void __launch_bounds__(32 * ROWS_MAX_GROUPS) k_backup_rows(const __gr
 }
 
 // The same split for rows on the fly.  The pair's masses are computed once
-// per block and shared: group q evaluates a contiguous share of the slots of
-// the concatenated per-dim windows (the mean and origins in FP64, each slot's
-// mass as dim_masses computes it) into shared memory, laid out [slot][lane]
+// per block and shared: the pair's mean, origins and kept widths are formed
+// once per dim (FP64, which this part issues at 1/64 of the FP32 rate), then
+// group q evaluates a contiguous share of the slots of the concatenated
+// per-dim windows (each slot's mass as dim_masses computes it) into shared
+// memory, laid out [slot][lane]
 // so that the row sums read them without bank conflicts; then every group
 // sums its window rows from there.
 template <class R, class VT, bool KAHAN>
@@ -483,13 +485,26 @@ __global__ void __launch_bounds__(32 * ROWS_MAX_GROUPS) k_backup_rows_otf(const 
     R *sfac = reinterpret_cast<R *>(smem_raw);                            // [wsum][32]
     int32_t *soff = reinterpret_cast<int32_t *>(sfac + (size_t)g.wsum * 32);  // [wsum][32]
     __shared__ R part[ROWS_MAX_GROUPS][32];
+    __shared__ double s_mu[MAXD][32];
+    __shared__ int32_t s_o[MAXD][32], s_kmax[MAXD][32];
     const int lane = threadIdx.x, q = threadIdx.y, G = blockDim.y;
     const int32_t x = (int32_t)blockIdx.x * 32 + lane;
     const int32_t u = (int32_t)blockIdx.y;
     const bool live = x < g.nx && !state_masked(a.spec_kind, a.mask[x]);
-    if (live) {
+    if (live && q < g.n) {
+        // the pair's mean, window origins and kept widths (FP64), once per
+        // dim: group q takes dims q, q + G, ...
         double mu[MAXD];
         mean_of(g, x, u, mu);
+        for (int d = q; d < g.n; d += G) {
+            const int32_t o = origin_of(g, d, mu[d]);
+            s_mu[d][lane] = mu[d];
+            s_o[d][lane] = o;
+            s_kmax[d][lane] = kept_upper(g, d, mu[d], o);
+        }
+    }
+    __syncthreads();
+    if (live) {
         // group q takes a contiguous share of the concatenated slots, so that
         // neighbouring slots of a dim share their edge evaluations
         const int s0 = (int)((int64_t)g.wsum * q / G), s1 = (int)((int64_t)g.wsum * (q + 1) / G);
@@ -497,8 +512,7 @@ __global__ void __launch_bounds__(32 * ROWS_MAX_GROUPS) k_backup_rows_otf(const 
         for (int d = 0; d < g.n && b < s1; b += g.W[d], ++d) {
             const int k0 = max(s0 - b, 0), k1 = min(s1 - b, g.W[d]);
             if (k0 >= k1) continue;
-            const int32_t o = origin_of(g, d, mu[d]);
-            slot_run(g, d, mu[d], o, kept_upper(g, d, mu[d], o), k0, k1, noise_centre(g, x, d),
+            slot_run(g, d, s_mu[d][lane], s_o[d][lane], s_kmax[d][lane], k0, k1, noise_centre(g, x, d),
                      [&](int k, R m, int32_t f) {
                          sfac[(b + k) * 32 + lane] = m;
                          soff[(b + k) * 32 + lane] = f;
