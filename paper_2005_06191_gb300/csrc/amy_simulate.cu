@@ -122,15 +122,27 @@ __global__ void __launch_bounds__(256) k_simulate(const __grid_constant__ Geom g
                         const double q = draw(d);
                         double cum = 0.0;
                         int32_t pick = -1;
+                        // the window's cells in order, each edge's tail evaluated
+                        // once (the masses slot_mass_f64 gives), until the draw
+                        // falls in the cumulative mass
+                        const bool gauss = g.noise == NOISE_GAUSSIAN || g.noise == NOISE_MULT_GAUSSIAN;
+                        const double k2 = gauss ? gauss_k2_f64(g, d, xd) : 0.0;
+                        double tlo = edge_rel_f64(g, d, mu[d], o, 0);
+                        double qlo = gauss ? gauss_tail_f64(tlo, k2) : 0.0;
                         for (int k = 0; k < g.W[d]; ++k) {
-                            double f;
-                            int32_t off;
-                            slot_mass_f64(g, d, mu[d], o, kmax, k, xd, f, off);
-                            cum += f;
+                            const double thi = edge_rel_f64(g, d, mu[d], o, k + 1);
+                            const double qhi = gauss ? gauss_tail_f64(thi, k2) : 0.0;
+                            const double mass =
+                                gauss ? gauss_cell_f64(tlo, thi, qlo, qhi, k2) : noise_mass<double>(g, d, tlo, thi);
+                            bool on;
+                            const int32_t cell = cell_of(g, d, o + k, on);
+                            cum += (on && k < kmax) ? mass : 0.0;
                             if (q < cum) {
-                                pick = off;
+                                pick = cell * g.stride[d];
                                 break;
                             }
+                            tlo = thi;
+                            qlo = qhi;
                         }
                         if (pick < 0) lost = true;
                         else nxt += pick;
