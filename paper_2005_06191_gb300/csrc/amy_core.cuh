@@ -450,15 +450,6 @@ __device__ __forceinline__ void slot_run_f64(const Geom &g, int d, double mu, in
     }
 }
 
-// Slot k of dim d's window on its own: its mass and V offset.
-__device__ __forceinline__ void slot_mass_f64(const Geom &g, int d, double mu, int32_t o, int kmax, int k, double xd,
-                                              double &fac, int32_t &off) {
-    slot_run_f64(g, d, mu, o, kmax, k, k + 1, xd, [&](int, double m, int32_t f) {
-        fac = m;
-        off = f;
-    });
-}
-
 __device__ __forceinline__ void dim_masses_f64(const Geom &g, int d, double mu, int32_t o, double xd,
                                                double *fac, int32_t *off) {
     slot_run_f64(g, d, mu, o, kept_upper(g, d, mu, o), 0, g.W[d], xd, [&](int k, double m, int32_t f) {
@@ -467,33 +458,9 @@ __device__ __forceinline__ void dim_masses_f64(const Geom &g, int d, double mu, 
     });
 }
 
-// One slot of dim_masses_f32 on its own: the same edge values (edge k is
-// fmaf(k, eta, e0), edge 0 is e0) and the same arithmetic, so the mass is
-// bit for bit the one the incremental loop gives.
-__device__ __forceinline__ void slot_mass_f32(const Geom &g, int d, double mu, int32_t o, int kmax, int k, double xd,
-                                              float &fac, int32_t &off) {
-    const double c0 = state_centre(g, d, o);
-    const float e0 = (float)dsub(dsub(c0, dmul(0.5, g.eta[d])), mu);
-    const float etaf = (float)g.eta[d];
-    const float dlo = k == 0 ? e0 : fmaf((float)k, etaf, e0);
-    const float dhi = fmaf((float)(k + 1), etaf, e0);
-    float mass;
-    if (g.noise == NOISE_GAUSSIAN || g.noise == NOISE_MULT_GAUSSIAN) {
-        const float r = gauss_r_f32(g, d, xd);
-        const float tlo = 0.5f * erfcf(fabsf(dlo) * r);
-        const float thi = 0.5f * erfcf(fabsf(dhi) * r);
-        mass = gauss_cell_f32(dlo, dhi, tlo, thi, r);
-    } else {
-        mass = noise_mass<float>(g, d, dlo, dhi);
-    }
-    bool on;
-    const int32_t cell = cell_of(g, d, o + k, on);
-    fac = (on && k < kmax) ? fmaxf(mass, 0.0f) : 0.0f;
-    off = cell * g.stride[d];
-}
-
 // Slots [k0, k1) of dim d's window in FP32, each edge's tail evaluated once:
-// the values slot_mass_f32 gives one slot at a time.
+// the values dim_masses_f32 gives (edge k is fmaf(k, eta, e0), edge 0 is e0),
+// whichever run a slot is evaluated in.
 template <class Put>
 __device__ __forceinline__ void slot_run_f32(const Geom &g, int d, double mu, int32_t o, int kmax, int k0, int k1,
                                              double xd, Put &&put) {
@@ -525,15 +492,6 @@ template <class Put>
 __device__ __forceinline__ void slot_run(const Geom &g, int d, double mu, int32_t o, int kmax, int k0, int k1,
                                          double xd, Put &&put, float) {
     slot_run_f32(g, d, mu, o, kmax, k0, k1, xd, put);
-}
-
-__device__ __forceinline__ void slot_mass(const Geom &g, int d, double mu, int32_t o, int kmax, int k, double xd,
-                                          double &fac, int32_t &off) {
-    slot_mass_f64(g, d, mu, o, kmax, k, xd, fac, off);
-}
-__device__ __forceinline__ void slot_mass(const Geom &g, int d, double mu, int32_t o, int kmax, int k, double xd,
-                                          float &fac, int32_t &off) {
-    slot_mass_f32(g, d, mu, o, kmax, k, xd, fac, off);
 }
 
 template <class R>

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256) k_simulate(const __grid_constant__ Geom g
                         double cum = 0.0;
                         int32_t pick = -1;
                         // the window's cells in order, each edge's tail evaluated
-                        // once (the masses slot_mass_f64 gives), until the draw
+                        // once (the masses slot_run_f64 gives), until the draw
                         // falls in the cumulative mass
                         const bool gauss = g.noise == NOISE_GAUSSIAN || g.noise == NOISE_MULT_GAUSSIAN;
                         const double k2 = gauss ? gauss_k2_f64(g, d, xd) : 0.0;
